@@ -1,0 +1,220 @@
+"""FP64 CPU oracle of the smoothed 2D image-method objective.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only users.  The product path never
+imports this package.  It shares no code with the CUDA library.
+
+The arithmetic lives in ``drt_oracle.cpp`` (plain C++, FP64, OpenMP over
+receivers); this module compiles it on demand with g++ and wraps it with
+ctypes.  Inputs are promoted from the FP32 scene arrays to float64 exactly.
+
+Functions and the passages they follow:
+
+* ``smooth``            Eq. 1 (step), Eq. 4 (sigmoid), Eqs. 5-6 (hard sigmoid), Eq. 3 (scaling)
+* ``power``             Sec. V (candidate list, image method, continuous validity), Eq. 7 (sum over paths)
+* ``loss``              Eq. 8 (min over receivers) and Sec. III (loss = -objective)
+* ``power_jvp``         exact forward-mode derivative of ``power`` (Sec. III: gradient of the loss)
+* ``power_cstep``       complex-step derivative of ``power`` (independent derivative mechanism)
+* ``gradient``          sum_r g_r dP_r/dtheta, assembled from ``power_jvp``
+* ``paths``             per-candidate vertices, validity, visibility, length and power for one receiver
+* ``candidates``        the candidate table of Sec. V (no wall twice in a row)
+
+Readings of the paper that the oracle fixes (the paper leaves them open):
+incoherent scalar power p = Gamma^k V / L^2 with Gamma = 0.5; smoothing
+arguments are Euclidean signed distances; a leg is not tested against the
+walls its own end points lie on; ties of the min go to the lowest index.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drt_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_KIND = {"sigmoid": 0, "hard_sigmoid": 1, "step": 2}
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (g++ -O2, no fast-math, OpenMP) if it is missing or stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        # DRT_ORACLE_LIB points the wrapper at another build of drt_oracle.cpp
+        # (the mutation tests load deliberately broken copies this way).
+        lib = ctypes.CDLL(os.environ.get("DRT_ORACLE_LIB") or build())
+        d, i, ll = ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+        p = ctypes.c_void_p
+        lib.drt_oracle_num_candidates.restype = ll
+        lib.drt_oracle_num_candidates.argtypes = [i, i]
+        lib.drt_oracle_candidates.argtypes = [i, i, p, p]
+        lib.drt_oracle_smooth.argtypes = [d, d, i, p, p]
+        lib.drt_oracle_power.argtypes = [p, i, p, p, i, i, d, i, d, i, p]
+        lib.drt_oracle_power_jvp.argtypes = [p, i, p, p, i, i, d, i, d, p, p, i, p, p]
+        lib.drt_oracle_power_cstep.argtypes = [p, i, p, p, i, i, d, i, d, p, p, d, i, p]
+        lib.drt_oracle_paths.argtypes = [p, i, p, p, i, d, i, d, p, p, p, p, p, p]
+        _lib = lib
+        return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _kind(smoothing) -> int:
+    return _KIND[smoothing] if isinstance(smoothing, str) else int(smoothing)
+
+
+def _threads(threads):
+    return int(threads) if threads else (os.cpu_count() or 1)
+
+
+def num_candidates(n_walls: int, max_order: int) -> int:
+    return int(_load().drt_oracle_num_candidates(n_walls, max_order))
+
+
+def candidates(n_walls: int, max_order: int):
+    """(seq [N, K] with -1 padding, order [N]) in table order."""
+    n = num_candidates(n_walls, max_order)
+    seq = np.zeros((n, max(max_order, 1)), dtype=np.int32)
+    order = np.zeros(n, dtype=np.int32)
+    _load().drt_oracle_candidates(n_walls, max_order, _ptr(seq), _ptr(order))
+    return seq[:, :max_order], order
+
+
+def smooth(x: float, alpha: float, smoothing) -> tuple[float, float]:
+    """(s(x; alpha), ds/dx)."""
+    s, ds = ctypes.c_double(), ctypes.c_double()
+    _load().drt_oracle_smooth(float(x), float(alpha), _kind(smoothing), ctypes.byref(s),
+                              ctypes.byref(ds))
+    return s.value, ds.value
+
+
+def _scene_args(walls, tx, rx):
+    walls, tx, rx = _f64(walls).reshape(-1, 4), _f64(tx).reshape(2), _f64(rx).reshape(-1, 2)
+    return walls, tx, rx
+
+
+def power(walls, tx, rx, max_order: int, alpha: float, smoothing, refl_coef: float = 0.5,
+          threads=None) -> np.ndarray:
+    """Received power P_r (float64 [R])."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    out = np.zeros(rx.shape[0], dtype=np.float64)
+    rc = _load().drt_oracle_power(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx), rx.shape[0],
+                                  int(max_order), float(alpha), _kind(smoothing),
+                                  float(refl_coef), _threads(threads), _ptr(out))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def power_jvp(walls, tx, rx, max_order, alpha, smoothing, dwalls, dtx, refl_coef=0.5,
+              threads=None):
+    """(P, dP) with dP the derivative of P along (dwalls, dtx)."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    dwalls, dtx = _f64(dwalls).reshape(walls.shape), _f64(dtx).reshape(2)
+    P = np.zeros(rx.shape[0]); dP = np.zeros(rx.shape[0])
+    rc = _load().drt_oracle_power_jvp(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx),
+                                      rx.shape[0], int(max_order), float(alpha),
+                                      _kind(smoothing), float(refl_coef), _ptr(dwalls),
+                                      _ptr(dtx), _threads(threads), _ptr(P), _ptr(dP))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return P, dP
+
+
+def power_cstep(walls, tx, rx, max_order, alpha, smoothing, dwalls, dtx, h=1e-30,
+                refl_coef=0.5, threads=None):
+    """Complex-step derivative of P along (dwalls, dtx)."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    dwalls, dtx = _f64(dwalls).reshape(walls.shape), _f64(dtx).reshape(2)
+    dP = np.zeros(rx.shape[0])
+    rc = _load().drt_oracle_power_cstep(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx),
+                                        rx.shape[0], int(max_order), float(alpha),
+                                        _kind(smoothing), float(refl_coef), _ptr(dwalls),
+                                        _ptr(dtx), float(h), _threads(threads), _ptr(dP))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return dP
+
+
+def gradient(walls, tx, rx, max_order, alpha, smoothing, g, params="all", refl_coef=0.5,
+             threads=None):
+    """sum_r g_r dP_r/dtheta for the requested parameters.
+
+    ``params``: "tx" (2 values), "all" (tx then the W x 4 wall coordinates), or
+    a list of flat indices into [tx (2), walls (4W)].  Each parameter costs one
+    forward-mode pass over the receivers with g_r != 0.
+    """
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    g = _f64(g).reshape(-1)
+    nz = np.nonzero(g)[0]
+    rx_nz, g_nz = rx[nz], g[nz]
+    W = walls.shape[0]
+    if isinstance(params, str):
+        idx = list(range(2)) if params == "tx" else list(range(2 + 4 * W))
+    else:
+        idx = list(params)
+    out = np.zeros(len(idx))
+    for n, p in enumerate(idx):
+        dtx = np.zeros(2); dw = np.zeros(4 * W)
+        if p < 2:
+            dtx[p] = 1.0
+        else:
+            dw[p - 2] = 1.0
+        if rx_nz.shape[0] == 0:
+            continue
+        _, dP = power_jvp(walls, tx, rx_nz, max_order, alpha, smoothing, dw, dtx, refl_coef,
+                          threads)
+        out[n] = float(np.dot(g_nz, dP))
+    return out
+
+
+def loss(P) -> tuple[float, int]:
+    """(L, argmin): L = -min_r P_r (Eq. 8, Sec. III); ties go to the lowest index."""
+    P = np.asarray(P, dtype=np.float64)
+    i = int(np.argmin(P))          # numpy returns the first minimum
+    return -float(P[i]), i
+
+
+def paths(walls, tx, rx1, max_order, alpha, smoothing, refl_coef=0.5) -> dict:
+    """Per-candidate detail for one receiver ``rx1`` ([2])."""
+    walls, tx, rx1 = _scene_args(walls, tx, rx1)
+    W, K = walls.shape[0], int(max_order)
+    n = num_candidates(W, K)
+    deg = np.zeros(n, np.int32)
+    verts = np.zeros((n, K + 2, 2)); val = np.zeros(n); vis = np.zeros((n, K + 1))
+    length = np.zeros(n); pw = np.zeros(n)
+    rc = _load().drt_oracle_paths(_ptr(walls), W, _ptr(tx), _ptr(rx1), K, float(alpha),
+                                  _kind(smoothing), float(refl_coef), _ptr(deg), _ptr(verts),
+                                  _ptr(val), _ptr(vis), _ptr(length), _ptr(pw))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    seq, order = candidates(W, K)
+    return dict(seq=seq, order=order, degenerate=deg, verts=verts, validity=val, vis=vis,
+                length=length, power=pw)
+

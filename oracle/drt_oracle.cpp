@@ -1,0 +1,451 @@
+// FP64 CPU oracle of the smoothed, differentiable 2D image-method objective
+// (Eertmans, Jacques, Oestges, "Fully Differentiable Ray Tracing via
+// Discontinuity Smoothing for Radio Network Optimization").
+//
+// TEST INFRASTRUCTURE ONLY.  Plain, slow and written to be read against the
+// paper: no blocking, no fusion, no reordering.  It shares no code, header or
+// constant with the CUDA library; only tests/, the smoke check and the CPU
+// baseline of the benchmark load it.
+//
+// What it computes, per receiver r and per path candidate (Sec. V):
+//   1. wall frame: e = B - A, l = |e|, u = e / l, n = (-u_y, u_x);
+//      d_w(p) = n . (p - A)   (signed distance to the wall's infinite line)
+//      t_w(p) = u . (p - A)   (coordinate along the wall)
+//   2. candidates: every wall sequence (w_1..w_k), k = 0..K, with no wall
+//      repeated twice in a row (the visibility matrix of Sec. V with all
+//      pairs visible except a wall with itself); ordered by k, then
+//      lexicographically.
+//   3. image method (Sec. V-B, item 1): I_0 = TX, I_j = I_{j-1} - 2 d_{w_j}(I_{j-1}) n_{w_j};
+//      backtrace on the relaxed (infinite) walls: Q_{k+1} = RX and, for
+//      j = k..1, Q_j = the intersection of the line (Q_{j+1}, I_j) with the
+//      line of w_j; Q_0 = TX.
+//   4. continuous validity (Sec. V-A), every comparison x0 > x1 replaced by
+//      s(x0 - x1; alpha):
+//        on-segment   s(t_j) s(l_j - t_j)
+//        same side    s(p) s(q) + s(-p) s(-q), p = d_{w_j}(Q_{j-1}), q = d_{w_j}(Q_{j+1})
+//      and obstruction of each leg Q_j -> Q_{j+1} by every wall w other than
+//      the walls its two end points lie on: with X(x, y) = s(x) s(-y) + s(-x) s(y)
+//      ("x and y on opposite sides"),
+//        blocked = X(d_w(Q_j), d_w(Q_{j+1})) * X(m . (A_w - Q_j), m . (B_w - Q_j)),
+//      m the unit normal of the leg; the leg's visibility is prod_w (1 - blocked).
+//   5. path power (reading of Eq. 7 as incoherent scalar power):
+//        p = Gamma^k * prod_j V_j * prod_j vis_j / L^2,  L = sum of leg lengths;
+//      received power P_r = sum of p over the candidates (Eq. 7's sum over S).
+//   6. smoothing s (Sec. IV): unit step (Eq. 1), sigmoid (Eq. 4) or hard
+//      sigmoid (Eqs. 5-6), each scaled as s(alpha x) (Eq. 3).
+//
+// Degenerate relaxed geometry (the line (Q_{j+1}, I_j) parallel to the wall,
+// or a leg of zero length) contributes 0.
+//
+// Derivatives come from the scalar type: the same templated code runs with
+// double (values), a forward-mode dual number, or std::complex<double>
+// (complex-step differentiation, comparisons taken on the real part).
+
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------- scalars
+struct Dual {
+  double v, d;
+  Dual(double v_ = 0.0, double d_ = 0.0) : v(v_), d(d_) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+inline Dual operator+(double a, Dual b) { return Dual(a) + b; }
+inline Dual operator+(Dual a, double b) { return a + Dual(b); }
+inline Dual operator-(double a, Dual b) { return Dual(a) - b; }
+inline Dual operator-(Dual a, double b) { return a - Dual(b); }
+inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+inline Dual operator/(double a, Dual b) { return Dual(a) / b; }
+inline Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
+inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, a.d * e); }
+inline Dual sqrt(Dual a) { double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
+
+typedef std::complex<double> Cplx;
+
+inline double re(double x) { return x; }
+inline double re(const Dual& x) { return x.v; }
+inline double re(const Cplx& x) { return x.real(); }
+
+using std::exp;
+using std::sqrt;
+
+// ---------------------------------------------------------------- smoothing
+enum Kind { SIGMOID = 0, HARD_SIGMOID = 1, STEP = 2 };
+
+// s(x; alpha) = s(alpha x) (Eq. 3).
+template <class T>
+T smooth(const T& x, double alpha, int kind) {
+  if (kind == STEP) {
+    // Eq. 1: theta(x) = 1 if x > 0 else 0.
+    return T(re(x) > 0.0 ? 1.0 : 0.0);
+  }
+  T z = alpha * x;
+  if (kind == SIGMOID) {
+    // Eq. 4: 1 / (1 + exp(-z)); the two algebraically equal forms keep the
+    // exponential's argument non-positive.
+    if (re(z) >= 0.0) return 1.0 / (1.0 + exp(-z));
+    T e = exp(z);
+    return e / (1.0 + e);
+  }
+  // Eqs. 5-6: relu6(z + 3) / 6 with relu6(y) = min(max(0, y), 6).
+  T y = z + 3.0;
+  if (re(y) <= 0.0) return T(0.0);
+  if (re(y) >= 6.0) return T(1.0);
+  return y / 6.0;
+}
+
+// ---------------------------------------------------------------- geometry
+template <class T>
+struct Vec {
+  T x, y;
+};
+template <class T>
+Vec<T> sub(const Vec<T>& a, const Vec<T>& b) { return Vec<T>{a.x - b.x, a.y - b.y}; }
+template <class T>
+T dot(const Vec<T>& a, const Vec<T>& b) { return a.x * b.x + a.y * b.y; }
+
+template <class T>
+struct Wall {
+  Vec<T> a, b;   // end points A, B
+  Vec<T> u, n;   // unit direction and unit normal of the line
+  T len;         // |B - A|
+};
+
+template <class T>
+Wall<T> make_wall(const T* xy) {
+  Wall<T> w;
+  w.a = Vec<T>{xy[0], xy[1]};
+  w.b = Vec<T>{xy[2], xy[3]};
+  Vec<T> e = sub(w.b, w.a);
+  w.len = sqrt(dot(e, e));
+  w.u = Vec<T>{e.x / w.len, e.y / w.len};
+  w.n = Vec<T>{-w.u.y, w.u.x};
+  return w;
+}
+
+// signed distance of p to the wall's line
+template <class T>
+T dist_line(const Wall<T>& w, const Vec<T>& p) { return dot(w.n, sub(p, w.a)); }
+
+// coordinate of p along the wall, from A towards B
+template <class T>
+T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }
+
+// mirror image of p across the wall's line
+template <class T>
+Vec<T> mirror(const Wall<T>& w, const Vec<T>& p) {
+  T d = dist_line(w, p);
+  return Vec<T>{p.x - 2.0 * d * w.n.x, p.y - 2.0 * d * w.n.y};
+}
+
+// ---------------------------------------------------------------- candidates
+// All sequences of 0..K walls with no immediate repeat; by length, then
+// lexicographic.
+std::vector<std::vector<int>> candidates(int W, int K) {
+  std::vector<std::vector<int>> out;
+  out.push_back(std::vector<int>());
+  std::vector<std::vector<int>> level(1);
+  for (int k = 1; k <= K; ++k) {
+    std::vector<std::vector<int>> next;
+    for (const auto& s : level)
+      for (int w = 0; w < W; ++w) {
+        if (!s.empty() && s.back() == w) continue;
+        std::vector<int> t = s;
+        t.push_back(w);
+        next.push_back(t);
+      }
+    for (const auto& s : next) out.push_back(s);
+    level.swap(next);
+  }
+  return out;
+}
+
+struct Params {
+  int K;
+  double alpha;
+  int kind;
+  double gamma;
+};
+
+// Per-path record for inspection by tests (filled only when requested).
+struct PathRecord {
+  int degenerate;
+  double verts[2 * 8];   // up to K = 6: Q_0..Q_{k+1}
+  double validity;       // prod_j V_j
+  double vis[7];         // per-leg visibility
+  double length;         // L
+  double power;          // p
+};
+
+// Power of one path candidate `seq` (k = seq.size()) from tx to rx.
+template <class T>
+T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& rx,
+             const std::vector<int>& seq, const Params& P, PathRecord* rec) {
+  const int k = (int)seq.size();
+  const int W = (int)walls.size();
+  // images I_0..I_k
+  std::vector<Vec<T>> img(k + 1);
+  img[0] = tx;
+  for (int j = 1; j <= k; ++j) img[j] = mirror(walls[seq[j - 1]], img[j - 1]);
+  // backtrace Q_0..Q_{k+1}
+  std::vector<Vec<T>> Q(k + 2);
+  Q[k + 1] = rx;
+  Q[0] = tx;
+  bool degenerate = false;
+  for (int j = k; j >= 1; --j) {
+    const Wall<T>& w = walls[seq[j - 1]];
+    T a = dist_line(w, img[j]);
+    T b = dist_line(w, Q[j + 1]);
+    if (re(b) - re(a) == 0.0) { degenerate = true; break; }
+    T t = b / (b - a);
+    Q[j] = Vec<T>{Q[j + 1].x + (img[j].x - Q[j + 1].x) * t,
+                  Q[j + 1].y + (img[j].y - Q[j + 1].y) * t};
+  }
+  std::vector<T> leg_len(k + 1);
+  std::vector<Vec<T>> leg_normal(k + 1);
+  if (!degenerate) {
+    for (int j = 0; j <= k; ++j) {
+      Vec<T> d = sub(Q[j + 1], Q[j]);
+      T l = sqrt(dot(d, d));
+      if (re(l) == 0.0) { degenerate = true; break; }
+      leg_len[j] = l;
+      leg_normal[j] = Vec<T>{-d.y / l, d.x / l};
+    }
+  }
+  if (rec) {
+    rec->degenerate = degenerate ? 1 : 0;
+    for (int i = 0; i < k + 2 && i < 8; ++i) {
+      rec->verts[2 * i] = degenerate ? NAN : re(Q[i].x);
+      rec->verts[2 * i + 1] = degenerate ? NAN : re(Q[i].y);
+    }
+  }
+  if (degenerate) {
+    if (rec) { rec->validity = 0; rec->length = 0; rec->power = 0; }
+    return T(0.0);
+  }
+  const double a = P.alpha;
+  const int kind = P.kind;
+  // continuous validity of each reflection
+  T validity = T(1.0);
+  for (int j = 1; j <= k; ++j) {
+    const Wall<T>& w = walls[seq[j - 1]];
+    T tj = along(w, Q[j]);
+    T on_seg = smooth(tj, a, kind) * smooth(w.len - tj, a, kind);
+    T p = dist_line(w, Q[j - 1]);
+    T q = dist_line(w, Q[j + 1]);
+    T same_side = smooth(p, a, kind) * smooth(q, a, kind) +
+                  smooth(T(-p), a, kind) * smooth(T(-q), a, kind);
+    validity = validity * on_seg * same_side;
+  }
+  // obstruction of each leg
+  T visibility = T(1.0);
+  for (int j = 0; j <= k; ++j) {
+    const int skip_a = (j >= 1) ? seq[j - 1] : -1;     // wall holding Q_j
+    const int skip_b = (j + 1 <= k) ? seq[j] : -1;     // wall holding Q_{j+1}
+    T vis = T(1.0);
+    for (int wi = 0; wi < W; ++wi) {
+      if (wi == skip_a || wi == skip_b) continue;
+      const Wall<T>& w = walls[wi];
+      // the leg's end points on opposite sides of the wall's line ...
+      T x1 = dist_line(w, Q[j]);
+      T y1 = dist_line(w, Q[j + 1]);
+      T cross1 = smooth(x1, a, kind) * smooth(T(-y1), a, kind) +
+                 smooth(T(-x1), a, kind) * smooth(y1, a, kind);
+      // ... and the wall's end points on opposite sides of the leg's line
+      T x2 = dot(leg_normal[j], sub(w.a, Q[j]));
+      T y2 = dot(leg_normal[j], sub(w.b, Q[j]));
+      T cross2 = smooth(x2, a, kind) * smooth(T(-y2), a, kind) +
+                 smooth(T(-x2), a, kind) * smooth(y2, a, kind);
+      vis = vis * (1.0 - cross1 * cross2);
+    }
+    if (rec && j < 7) rec->vis[j] = re(vis);
+    visibility = visibility * vis;
+  }
+  T L = T(0.0);
+  for (int j = 0; j <= k; ++j) L = L + leg_len[j];
+  double gk = 1.0;
+  for (int j = 0; j < k; ++j) gk *= P.gamma;
+  T power = gk * validity * visibility / (L * L);
+  if (rec) {
+    rec->validity = re(validity);
+    rec->length = re(L);
+    rec->power = re(power);
+  }
+  return power;
+}
+
+template <class T>
+std::vector<Wall<T>> make_walls(const std::vector<T>& xy, int W) {
+  std::vector<Wall<T>> walls;
+  walls.reserve(W);
+  for (int i = 0; i < W; ++i) walls.push_back(make_wall<T>(&xy[4 * i]));
+  return walls;
+}
+
+// P_r for one receiver, summed over the candidate table in order.
+template <class T>
+T received_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& rx,
+                 const std::vector<std::vector<int>>& cands, const Params& P) {
+  T sum = T(0.0);
+  for (const auto& seq : cands) sum = sum + path_power(walls, tx, rx, seq, P, nullptr);
+  return sum;
+}
+
+int check_args(const double* walls, int W, const double* tx, const double* rx, int R, int K,
+               double alpha, int kind) {
+  if (!walls || !tx || (R > 0 && !rx)) return 1;
+  if (W < 1 || R < 0 || K < 0 || K > 6 || !(alpha >= 0.0)) return 1;
+  if (kind < 0 || kind > 2) return 1;
+  return 0;
+}
+
+void set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+}
+
+}  // namespace
+
+extern "C" {
+
+// Number of path candidates for W walls and maximum order K.
+long long drt_oracle_num_candidates(int W, int K) {
+  long long n = 1, level = 1;
+  for (int k = 1; k <= K; ++k) {
+    level = (k == 1) ? W : level * (W - 1);
+    n += level;
+  }
+  return n;
+}
+
+// Candidate table: seq_out [N][K] (unused slots -1), order_out [N].
+int drt_oracle_candidates(int W, int K, int* seq_out, int* order_out) {
+  auto c = candidates(W, K);
+  for (size_t i = 0; i < c.size(); ++i) {
+    order_out[i] = (int)c[i].size();
+    for (int j = 0; j < K; ++j) seq_out[i * K + j] = j < (int)c[i].size() ? c[i][j] : -1;
+  }
+  return 0;
+}
+
+// Smoothing function and its derivative at x (dual number).
+int drt_oracle_smooth(double x, double alpha, int kind, double* s, double* ds) {
+  Dual r = smooth(Dual(x, 1.0), alpha, kind);
+  *s = r.v;
+  *ds = r.d;
+  return 0;
+}
+
+// Received power P[r] for every receiver.
+int drt_oracle_power(const double* walls_xy, int W, const double* tx, const double* rx, int R,
+                     int K, double alpha, int kind, double gamma, int nthreads, double* P) {
+  if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind)) return 1;
+  set_threads(nthreads);
+  std::vector<double> xy(walls_xy, walls_xy + 4 * W);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<double> t{tx[0], tx[1]};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    Vec<double> q{rx[2 * r], rx[2 * r + 1]};
+    P[r] = received_power(walls, t, q, cands, prm);
+  }
+  return 0;
+}
+
+// Forward-mode derivative of every P[r] along the direction (dwalls [W][4], dtx [2]).
+int drt_oracle_power_jvp(const double* walls_xy, int W, const double* tx, const double* rx,
+                         int R, int K, double alpha, int kind, double gamma,
+                         const double* dwalls, const double* dtx, int nthreads, double* P,
+                         double* dP) {
+  if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind) || !dwalls || !dtx) return 1;
+  set_threads(nthreads);
+  std::vector<Dual> xy(4 * W);
+  for (int i = 0; i < 4 * W; ++i) xy[i] = Dual(walls_xy[i], dwalls[i]);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<Dual> t{Dual(tx[0], dtx[0]), Dual(tx[1], dtx[1])};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    Vec<Dual> q{Dual(rx[2 * r]), Dual(rx[2 * r + 1])};
+    Dual v = received_power(walls, t, q, cands, prm);
+    if (P) P[r] = v.v;
+    dP[r] = v.d;
+  }
+  return 0;
+}
+
+// Complex-step derivative: Im P(x + i h dir) / h.
+int drt_oracle_power_cstep(const double* walls_xy, int W, const double* tx, const double* rx,
+                           int R, int K, double alpha, int kind, double gamma,
+                           const double* dwalls, const double* dtx, double h, int nthreads,
+                           double* dP) {
+  if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind) || !dwalls || !dtx) return 1;
+  set_threads(nthreads);
+  std::vector<Cplx> xy(4 * W);
+  for (int i = 0; i < 4 * W; ++i) xy[i] = Cplx(walls_xy[i], h * dwalls[i]);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<Cplx> t{Cplx(tx[0], h * dtx[0]), Cplx(tx[1], h * dtx[1])};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    Vec<Cplx> q{Cplx(rx[2 * r]), Cplx(rx[2 * r + 1])};
+    Cplx v = received_power(walls, t, q, cands, prm);
+    dP[r] = v.imag() / h;
+  }
+  return 0;
+}
+
+// Per-candidate detail for one receiver.  Arrays sized by the caller:
+// degenerate [N], verts [N][K+2][2], validity [N], vis [N][K+1], length [N], power [N].
+int drt_oracle_paths(const double* walls_xy, int W, const double* tx, const double* rx1, int K,
+                     double alpha, int kind, double gamma, int* degenerate, double* verts,
+                     double* validity, double* vis, double* length, double* power) {
+  if (check_args(walls_xy, W, tx, rx1, 1, K, alpha, kind)) return 1;
+  std::vector<double> xy(walls_xy, walls_xy + 4 * W);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<double> t{tx[0], tx[1]};
+  Vec<double> q{rx1[0], rx1[1]};
+  for (size_t i = 0; i < cands.size(); ++i) {
+    PathRecord rec;
+    for (int v = 0; v < 16; ++v) rec.verts[v] = NAN;
+    for (int v = 0; v < 7; ++v) rec.vis[v] = NAN;
+    path_power(walls, t, q, cands[i], prm, &rec);
+    const int k = (int)cands[i].size();
+    degenerate[i] = rec.degenerate;
+    for (int v = 0; v < K + 2; ++v) {
+      const bool used = v < k + 2;
+      verts[(i * (K + 2) + v) * 2 + 0] = used ? rec.verts[2 * v] : NAN;
+      verts[(i * (K + 2) + v) * 2 + 1] = used ? rec.verts[2 * v + 1] : NAN;
+    }
+    for (int j = 0; j < K + 1; ++j) vis[i * (K + 1) + j] = (j <= k && !rec.degenerate) ? rec.vis[j] : NAN;
+    validity[i] = rec.validity;
+    length[i] = rec.length;
+    power[i] = rec.power;
+  }
+  return 0;
+}
+
+}  // extern "C"
