@@ -1,0 +1,375 @@
+"""Benchmark of the smoothed image-method objective on GB300.
+
+One step = one pass of the whole hot path over the large scene (square + 60
+random segments = 64 walls, 256 x 256 receiver grid, K <= 2 i.e. 4097 wall
+sequences, alpha = 100, hard sigmoid): received power of every receiver
+(forward kernel), the min-power loss, its gradient w.r.t. power, and the
+hand-written adjoint (gradient w.r.t. the TX and all wall end points).
+
+Prints one JSON line (rank 0).  Multi-GPU (torchrun): every rank runs its own
+replica (independent problem: its own TX position), no collective on the data
+path; timing is the max over ranks ("weak" scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("path×RX evals/s fwd+adjoint, % FP32 roofline; time-to-optimum vs plain at 1e-3")
+UNIT = "path×RX evals/s"
+L2_FLUSH_BYTES = 256 << 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "forward_large_scene_traffic.txt")
+
+
+def workload_scene(rank: int = 0, rx_grid: int = 256):
+    from paper_2401_11882_gb300 import scenes
+    sc = scenes.clutter_scene(60, rx_grid, 0, 100.0, "hard_sigmoid", 2, True)
+    if rank:
+        # an independent problem per rank: the TX moves along the grid's middle row
+        sc = sc.replace(tx=np.array([0.5 + 0.011 * ((rank % 30) - 15), 0.2], np.float32))
+    return sc
+
+
+def workload_config(sc, n_cand):
+    return {
+        "workload": (f"square + 60 random segments ({sc.n_walls} walls, seed 0), "
+                     f"{int(round(sc.n_rx ** 0.5))}x{int(round(sc.n_rx ** 0.5))} RX grid, "
+                     f"K<={sc.max_order} ({n_cand} wall sequences), "
+                     f"alpha={sc.alpha:g}, {sc.smoothing}; forward + min-loss + adjoint "
+                     "(grad wrt TX and all wall end points)"),
+        "n_walls": sc.n_walls, "n_rx": sc.n_rx, "max_order": sc.max_order, "alpha": sc.alpha,
+        "smoothing": sc.smoothing, "evals_per_step": sc.n_rx * n_cand,
+        "l2": "flushed between timed steps (256 MiB write)",
+        "inputs": "resident in HBM",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(sc, n_cand, budget_s: float = 8.0, max_rx: int = 4096):
+    """Oracle forward over a growing prefix of the receivers until ~budget_s of wall time."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n = 16
+    while True:
+        t0 = time.perf_counter()
+        oracle.power(sc.walls, sc.tx, sc.rx[:n], sc.max_order, sc.alpha, sc.smoothing,
+                     sc.refl_coef, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or n >= max_rx:
+            break
+        n = min(max_rx, max(2 * n, int(n * budget_s / max(dt, 1e-3))))
+    return n * n_cand / dt, threads, n, dt
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2401_11882_gb300 import workload
+    sc = workload_scene(0, args.rx_grid)
+    n_cand = workload.num_candidates(sc.n_walls, sc.max_order)
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n_rx = 2 * threads
+    sub = sc.rx[:n_rx]
+    for _ in range(args.warmup):
+        oracle.power(sc.walls, sc.tx, sub[:threads], sc.max_order, sc.alpha, sc.smoothing)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.power(sc.walls, sc.tx, sub, sc.max_order, sc.alpha, sc.smoothing, threads=threads)
+    dt = time.perf_counter() - t0
+    value = args.steps * n_rx * n_cand / dt
+    sample = f"{n_rx} receivers x {n_cand} sequences per step (forward power only)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc, n_cand),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def file_hash(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per forward launch from the committed ncu summary, if it was taken on
+    the current forward kernel source (key: value lines)."""
+    src = os.path.join(ROOT, "paper_2401_11882_gb300", "csrc", "drt_forward.cu")
+    try:
+        d = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    d[k.strip()] = v.strip()
+        if d.get("kernel_sha256_16") == file_hash(src):
+            return float(d["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2401_11882_gb300 as drt
+    from paper_2401_11882_gb300 import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    sc = workload_scene(rank, args.rx_grid)
+    n_cand = drt.num_candidates(sc.n_walls, sc.max_order)
+    work = workload.forward_work(sc.n_walls, sc.max_order, sc.n_rx)
+    w = torch.tensor(sc.walls, device=dev)
+    t = torch.tensor(sc.tx, device=dev)
+    r = torch.tensor(sc.rx, device=dev)
+    K, alpha, sm = sc.max_order, sc.alpha, sc.smoothing
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def step(i=None):
+        e = ev[i] if i is not None else None
+        if e:
+            e[0].record()
+        P = drt.forward(w, t, r, K, alpha, sm)
+        if e:
+            e[1].record()
+        loss, am = drt.min_loss(P)
+        gp = drt.min_loss_backward(am, None, sc.n_rx)
+        gtx, gw = drt.vjp(w, t, r, K, alpha, sm, gp)
+        if e:
+            e[2].record()
+        return loss, gtx, gw
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    fwd_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    evals = sc.n_rx * n_cand
+    value = world * args.steps * evals / (total_ms / 1e3)
+
+    # end to end through the public API, from pinned host buffers (inputs H2D, loss,
+    # power and gradients D2H every step)
+    hw = torch.tensor(sc.walls).pin_memory()
+    ht = torch.tensor(sc.tx).pin_memory()
+    hr = torch.tensor(sc.rx).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        drt.objective_host(hw, ht, hr, K, alpha, sm, device=dev, grad_walls=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = drt.objective_host(hw, ht, hr, K, alpha, sm, device=dev, grad_walls=True)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = hw.numel() * 4 + ht.numel() * 4 + hr.numel() * 4
+    d2h = sum(o.numel() * o.element_size() for o in out)
+
+    # extras (not part of the timed step): sigmoid forward, dense adjoint on the
+    # 128-wall gradient scene, forward with invalid-path culling
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = measure_extras(drt, dev, sc, w, t, r)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(pk.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    peak = workload.fp32_peak_tflops(props.multi_processor_count, sm_max)
+    fwd_avg_s = (sum(fwd_ms) / len(fwd_ms)) / 1e3
+    achieved = work["flops"] / fwd_avg_s / 1e12
+    traffic = measured_traffic()
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, cores, n, dt = oracle_rate(sc, n_cand)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {n} receivers of the workload x {n_cand} sequences, "
+                         f"forward power only, {dt:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(sc, n_cand),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "forward_kernel<hard sigmoid> (+ its chunk-sum kernel)",
+                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
+                                    f"FLOP x {sm_max:.0f} MHz (max SM clock)",
+                     "flops_per_launch": work["flops"], "ms_per_launch": fwd_avg_s * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * args.steps * evals / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk,
+        "extra": extras,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_extras(drt, dev, sc, w, t, r):
+    import torch
+    from paper_2401_11882_gb300 import scenes, workload
+
+    def timed(fn, n=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n / 1e3
+
+    out = {}
+    n_cand = workload.num_candidates(sc.n_walls, sc.max_order)
+    ev = sc.n_rx * n_cand
+    s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "sigmoid"))
+    out["sigmoid_forward_evals_per_s"] = ev / s
+    s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
+                                  tile=drt.TileConfig(cull_invalid=True)))
+    out["hard_forward_culled_evals_per_s"] = ev / s
+    g = scenes.gradient_scene()
+    gw, gt, gr = (torch.tensor(g.walls, device=dev), torch.tensor(g.tx, device=dev),
+                  torch.tensor(g.rx, device=dev))
+    gp = torch.full((g.n_rx,), 1.0 / g.n_rx, device=dev)
+    gc = workload.num_candidates(g.n_walls, g.max_order)
+    sf = timed(lambda: drt.forward(gw, gt, gr, 2, 100.0, "hard_sigmoid"), 2)
+    sv = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", gp), 2)
+    out["gradient_scene_dense"] = {
+        "workload": "128 random segments, 128x128 RX grid, K<=2 (16385 sequences), alpha=100, "
+                    "hard sigmoid, dense g = 1/R, grad wrt TX and 512 wall coordinates",
+        "fwd_ms": sf * 1e3, "vjp_ms": sv * 1e3,
+        "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sf + sv)}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--rx-grid", type=int, default=256,
+                    help="receiver grid side (256 = the benchmark workload; smaller for profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

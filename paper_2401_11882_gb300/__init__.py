@@ -1,5 +1,17 @@
 """GB300-native smoothed, differentiable 2D image-method ray tracing.
 
+Public calls (PyTorch tensors on a CUDA device, float32):
+
+* ``power(walls, tx, rx, max_order, alpha, smoothing)``: received power per
+  receiver, differentiable in ``walls`` and ``tx`` (hand-written adjoint).
+* ``loss(power)``: -min over receivers; ``objective(...)`` = loss(power(...)).
+* ``forward``, ``vjp``, ``min_loss``: the raw C-ABI calls.
+
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
+from .ops import (TileConfig, forward, loss, min_loss, min_loss_backward, num_candidates,
+                  objective, objective_host, power, vjp)
+
+__all__ = ["TileConfig", "forward", "loss", "min_loss", "min_loss_backward", "num_candidates",
+           "objective", "objective_host", "power", "vjp"]

@@ -1,0 +1,577 @@
+// Hand-written adjoint (reverse mode) of the forward pass: the vector-Jacobian
+// product  sum_r g_r dP_r / d(tx, walls)  (Sec. III: gradient of the loss with
+// respect to the scene parameters).
+//
+// Nothing of the forward pass is stored: each (receiver, candidate) recomputes
+// its image chain, reflection points, legs and validity, then runs two sweeps
+// over the walls.  Sweep 1 rebuilds each leg's visibility as a product of
+// non-zero factors plus a count of exact zeros, so that the derivative of the
+// product w.r.t. one factor never divides by zero.  Sweep 2 recomputes each
+// factor and pushes its adjoint into the vertices, the leg normals and the
+// wall.  The vertex and leg adjoints then flow back through the leg lengths,
+// the validity, the backtrace and the image chain to the transmitter.
+//
+// The mapping is the forward's: 32 receivers per warp, one warp-uniform
+// candidate at a time.  Per-wall adjoints are summed over the warp with
+// shuffles (only when a lane has a non-zero one), added into a per-CTA
+// shared-memory table, and written per CTA; a last kernel adds the CTA tables
+// in a fixed order and chains the per-wall quantities (n, c, t0, len) back to
+// the end points.
+#include <cuda_runtime.h>
+
+#include "drt_common.cuh"
+#include "drt_internal.h"
+
+namespace drt {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Slots of the per-wall accumulator.
+enum : int { S_NX = 0, S_NY, S_C, S_AX, S_AY, S_BX, S_BY, S_T0, S_LEN };
+
+struct VSmem {
+  float4 *G, *E, *T;
+  float* acc;   // [W][VJP_SLOTS] (wall gradient only)
+};
+
+// One leg x wall factor f = 1 - X(x1, y1) X(x2, y2), written as
+// Xb1 + X1 Xb2 with Xb = 1 - X = s(x) s(y) + s(-x) s(-y), and its partials.
+struct LegWall {
+  float f, dx1, dy1, dx2, dy2;
+};
+
+template <int MODE, bool GRAD>
+__device__ __forceinline__ LegWall leg_wall(float x1, float y1, float x2, float y2, float alpha) {
+  const Smooth3 a = smooth3<MODE>(x1, alpha), b = smooth3<MODE>(y1, alpha);
+  const Smooth3 c = smooth3<MODE>(x2, alpha), d = smooth3<MODE>(y2, alpha);
+  const float X1 = fmaf(a.s, b.sb, a.sb * b.s), Xb1 = fmaf(a.s, b.s, a.sb * b.sb);
+  const float X2 = fmaf(c.s, d.sb, c.sb * d.s), Xb2 = fmaf(c.s, d.s, c.sb * d.sb);
+  LegWall r;
+  r.f = fmaf(X1, Xb2, Xb1);
+  if (GRAD) {
+    // df/dX1 = -X2, df/dX2 = -X1; dX/dx = s'(x) (s(-y) - s(y)), dX/dy = s'(y) (s(-x) - s(x))
+    r.dx1 = -X2 * a.ds * (b.sb - b.s);
+    r.dy1 = -X2 * b.ds * (a.sb - a.s);
+    r.dx2 = -X1 * c.ds * (d.sb - d.s);
+    r.dy2 = -X1 * d.ds * (c.sb - c.s);
+  } else {
+    r.dx1 = r.dy1 = r.dx2 = r.dy2 = 0.f;
+  }
+  return r;
+}
+
+template <int MODE, int K, bool WG>
+__device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float2 rx,
+                                         const Cand& cd, float alpha, float gk, float g,
+                                         float& txb_x, float& txb_y) {
+  // ------------------------------------------------ forward recompute (guarded)
+  float Ix[K + 1], Iy[K + 1], dimg[K + 1];
+  Ix[0] = tx.x;
+  Iy[0] = tx.y;
+  dimg[0] = 0.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    dimg[j] = line_dist(G, Ix[j - 1], Iy[j - 1]);
+    Ix[j] = fmaf(-2.f * dimg[j], G.x, Ix[j - 1]);
+    Iy[j] = fmaf(-2.f * dimg[j], G.y, Iy[j - 1]);
+  }
+  float Qx[K + 2], Qy[K + 2], ta[K + 1], tb[K + 1], tt[K + 1];
+  Qx[0] = tx.x;
+  Qy[0] = tx.y;
+  Qx[K + 1] = rx.x;
+  Qy[K + 1] = rx.y;
+  bool degenerate = false;
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    ta[j] = line_dist(G, Ix[j], Iy[j]);
+    tb[j] = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    float t = __fdiv_rn(tb[j], tb[j] - ta[j]);
+    if (!(fabsf(t) <= 1e8f)) {
+      degenerate = true;
+      t = 0.f;
+    }
+    tt[j] = t;
+    Qx[j] = fmaf(t, Ix[j] - Qx[j + 1], Qx[j + 1]);
+    Qy[j] = fmaf(t, Iy[j] - Qy[j + 1], Qy[j + 1]);
+  }
+  float mx[K + 1], my[K + 1], mq[K + 1], len[K + 1];
+  float L = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float len2 = fmaf(dx, dx, dy * dy);
+    float inv = 0.f;
+    if (len2 > 0.f) {
+      inv = rsqrtf(len2);
+    } else {
+      degenerate = true;
+    }
+    len[j] = len2 * inv;
+    L += len[j];
+    mx[j] = -dy * inv;
+    my[j] = dx * inv;
+    mq[j] = fmaf(mx[j], Qx[j], my[j] * Qy[j]);
+  }
+  if (degenerate) {
+    g = 0.f;
+    L = 1.f;
+  }
+  float V[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 G = s.G[w];
+    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -s.T[w].x));
+    const Smooth3 s1 = smooth3<MODE>(tau, alpha), s2 = smooth3<MODE>(G.w - tau, alpha);
+    const Smooth3 sp = smooth3<MODE>(line_dist(G, Qx[j - 1], Qy[j - 1]), alpha);
+    const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
+    V[j] = s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+  }
+  // sweep 1: visibility as (product of non-zero factors, number of zero factors)
+  float nz[K + 1];
+  int zc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    nz[j] = 1.f;
+    zc[j] = 0;
+  }
+  for (int w = 0; w < W; ++w) {
+    const float4 G = s.G[w];
+    const float4 E = s.E[w];
+    float dv[K + 2];
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) dv[i] = line_dist(G, Qx[i], Qy[i]);
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+      if (skip) continue;
+      const float x2 = fmaf(mx[j], E.x, fmaf(my[j], E.y, -mq[j]));
+      const float y2 = fmaf(mx[j], E.z, fmaf(my[j], E.w, -mq[j]));
+      const float f = leg_wall<MODE, false>(dv[j], dv[j + 1], x2, y2, alpha).f;
+      if (f == 0.f) {
+        zc[j] += 1;
+      } else {
+        nz[j] *= f;
+      }
+    }
+  }
+  // ------------------------------------------------ factor adjoints
+  // p = C * prod(F), C = Gamma^k / L^2, F = {V_1..V_K, vis_0..vis_K}
+  constexpr int NF = 2 * K + 1;
+  float F[NF];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) F[j - 1] = V[j];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) F[K + j] = zc[j] ? 0.f : nz[j];
+  float pre[NF + 1], suf[NF + 1];
+  pre[0] = 1.f;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) pre[i + 1] = pre[i] * F[i];
+  suf[NF] = 1.f;
+#pragma unroll
+  for (int i = NF - 1; i >= 0; --i) suf[i] = suf[i + 1] * F[i];
+  const float C = __fdiv_rn(gk, L * L);
+  const float p = C * pre[NF];
+  const float gC = g * C;
+  float Vb[K + 1], visb[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) Vb[j] = gC * pre[j - 1] * suf[j];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) visb[j] = gC * pre[K + j] * suf[K + j + 1];
+  const float Lb = -2.f * g * __fdiv_rn(p, L);
+
+  // ------------------------------------------------ sweep 2: obstruction adjoint
+  float Qbx[K + 2], Qby[K + 2], mAx[K + 1], mAy[K + 1], sm[K + 1];
+#pragma unroll
+  for (int i = 0; i <= K + 1; ++i) Qbx[i] = Qby[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) mAx[j] = mAy[j] = sm[j] = 0.f;
+
+  for (int w = 0; w < W; ++w) {
+    const float4 G = s.G[w];
+    const float4 E = s.E[w];
+    float dv[K + 2], vb[K + 2];
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) {
+      dv[i] = line_dist(G, Qx[i], Qy[i]);
+      vb[i] = 0.f;
+    }
+    float Abx = 0.f, Aby = 0.f, Bbx = 0.f, Bby = 0.f;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+      if (skip) continue;
+      const float x2 = fmaf(mx[j], E.x, fmaf(my[j], E.y, -mq[j]));
+      const float y2 = fmaf(mx[j], E.z, fmaf(my[j], E.w, -mq[j]));
+      const LegWall lw = leg_wall<MODE, true>(dv[j], dv[j + 1], x2, y2, alpha);
+      // d vis / d f = product of the other factors
+      float dvis;
+      if (zc[j] == 0) {
+        dvis = __fdividef(nz[j], lw.f);
+      } else {
+        dvis = (zc[j] == 1 && lw.f == 0.f) ? nz[j] : 0.f;
+      }
+      const float fb = visb[j] * dvis;
+      vb[j] = fmaf(fb, lw.dx1, vb[j]);
+      vb[j + 1] = fmaf(fb, lw.dy1, vb[j + 1]);
+      const float x2b = fb * lw.dx2, y2b = fb * lw.dy2;
+      // x2 = m . (A - Q_j), y2 = m . (B - Q_j)
+      mAx[j] = fmaf(x2b, E.x, fmaf(y2b, E.z, mAx[j]));
+      mAy[j] = fmaf(x2b, E.y, fmaf(y2b, E.w, mAy[j]));
+      sm[j] += x2b + y2b;
+      if (WG) {
+        Abx = fmaf(x2b, mx[j], Abx);
+        Aby = fmaf(x2b, my[j], Aby);
+        Bbx = fmaf(y2b, mx[j], Bbx);
+        Bby = fmaf(y2b, my[j], Bby);
+      }
+    }
+    // vertex distances d(Q_i) = n . Q_i - c
+    float nbx = 0.f, nby = 0.f, cb = 0.f;
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) {
+      Qbx[i] = fmaf(vb[i], G.x, Qbx[i]);
+      Qby[i] = fmaf(vb[i], G.y, Qby[i]);
+      if (WG) {
+        nbx = fmaf(vb[i], Qx[i], nbx);
+        nby = fmaf(vb[i], Qy[i], nby);
+        cb -= vb[i];
+      }
+    }
+    if (WG) {
+      const bool any = (nbx != 0.f) | (nby != 0.f) | (cb != 0.f) | (Abx != 0.f) |
+                       (Aby != 0.f) | (Bbx != 0.f) | (Bby != 0.f);
+      if (__any_sync(FULL, any)) {
+        nbx = warp_sum(nbx);
+        nby = warp_sum(nby);
+        cb = warp_sum(cb);
+        Abx = warp_sum(Abx);
+        Aby = warp_sum(Aby);
+        Bbx = warp_sum(Bbx);
+        Bby = warp_sum(Bby);
+        const int lane = threadIdx.x & 31;
+        float v = nbx;
+        v = lane == S_NY ? nby : v;
+        v = lane == S_C ? cb : v;
+        v = lane == S_AX ? Abx : v;
+        v = lane == S_AY ? Aby : v;
+        v = lane == S_BX ? Bbx : v;
+        v = lane == S_BY ? Bby : v;
+        if (lane <= S_BY) atomicAdd(&s.acc[w * VJP_SLOTS + lane], v);
+      }
+    }
+  }
+
+  // ------------------------------------------------ legs: normals and lengths
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    // m_bar = sum x2b (A - Q_j) + y2b (B - Q_j); the -Q_j part and dx2/dQ_j = -m
+    const float mbx = mAx[j] - sm[j] * Qx[j];
+    const float mby = mAy[j] - sm[j] * Qy[j];
+    Qbx[j] -= sm[j] * mx[j];
+    Qby[j] -= sm[j] * my[j];
+    // m = (-D_y, D_x)/len: D_bar = (mb_y, -mb_x)/len - (mb . m) D/len^2 ; len_bar = Lb
+    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float il = len[j] > 0.f ? 1.f / len[j] : 0.f;
+    const float mm = fmaf(mbx, mx[j], mby * my[j]);
+    const float Dbx = fmaf(mby, il, fmaf(-mm * il * il, dx, Lb * dx * il));
+    const float Dby = fmaf(-mbx, il, fmaf(-mm * il * il, dy, Lb * dy * il));
+    Qbx[j + 1] += Dbx;
+    Qby[j + 1] += Dby;
+    Qbx[j] -= Dbx;
+    Qby[j] -= Dby;
+  }
+
+  // ------------------------------------------------ validity, backtrace, images
+  float rn_x[K + 1], rn_y[K + 1], rc[K + 1], rt0[K + 1], rl[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 G = s.G[w];
+    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -s.T[w].x));
+    const float pv = line_dist(G, Qx[j - 1], Qy[j - 1]);
+    const float qv = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    const Smooth3 s1 = smooth3<MODE>(tau, alpha), s2 = smooth3<MODE>(G.w - tau, alpha);
+    const Smooth3 sp = smooth3<MODE>(pv, alpha), sq = smooth3<MODE>(qv, alpha);
+    const float S = fmaf(sp.s, sq.s, sp.sb * sq.sb);
+    const float a1 = Vb[j] * s2.s * S, a2 = Vb[j] * s1.s * S, aS = Vb[j] * s1.s * s2.s;
+    const float taub = a1 * s1.ds - a2 * s2.ds;
+    const float pb = aS * sp.ds * (sq.s - sq.sb);
+    const float qb = aS * sq.ds * (sp.s - sp.sb);
+    rl[j] = a2 * s2.ds;
+    rt0[j] = -taub;
+    // tau = n_y Qx - n_x Qy - t0
+    Qbx[j] = fmaf(taub, G.y, Qbx[j]);
+    Qby[j] = fmaf(-taub, G.x, Qby[j]);
+    rn_x[j] = -taub * Qy[j];
+    rn_y[j] = taub * Qx[j];
+    // p = n . Q_{j-1} - c ; q = n . Q_{j+1} - c
+    Qbx[j - 1] = fmaf(pb, G.x, Qbx[j - 1]);
+    Qby[j - 1] = fmaf(pb, G.y, Qby[j - 1]);
+    Qbx[j + 1] = fmaf(qb, G.x, Qbx[j + 1]);
+    Qby[j + 1] = fmaf(qb, G.y, Qby[j + 1]);
+    rn_x[j] = fmaf(pb, Qx[j - 1], fmaf(qb, Qx[j + 1], rn_x[j]));
+    rn_y[j] = fmaf(pb, Qy[j - 1], fmaf(qb, Qy[j + 1], rn_y[j]));
+    rc[j] = -(pb + qb);
+  }
+  float Ibx[K + 1], Iby[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) Ibx[j] = Iby[j] = 0.f;
+  // backtrace, reversed: Q_j = Q_{j+1} + t (I_j - Q_{j+1}), t = b / (b - a)
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float t = tt[j];
+    const float ex = Ix[j] - Qx[j + 1], ey = Iy[j] - Qy[j + 1];
+    Qbx[j + 1] = fmaf(1.f - t, Qbx[j], Qbx[j + 1]);
+    Qby[j + 1] = fmaf(1.f - t, Qby[j], Qby[j + 1]);
+    Ibx[j] = fmaf(t, Qbx[j], Ibx[j]);
+    Iby[j] = fmaf(t, Qby[j], Iby[j]);
+    const float tbar = fmaf(Qbx[j], ex, Qby[j] * ey);
+    const float den = tb[j] - ta[j];
+    const float id2 = (den != 0.f && !degenerate) ? 1.f / (den * den) : 0.f;
+    const float abar = tbar * tb[j] * id2;
+    const float bbar = -tbar * ta[j] * id2;
+    Ibx[j] = fmaf(abar, G.x, Ibx[j]);
+    Iby[j] = fmaf(abar, G.y, Iby[j]);
+    Qbx[j + 1] = fmaf(bbar, G.x, Qbx[j + 1]);
+    Qby[j + 1] = fmaf(bbar, G.y, Qby[j + 1]);
+    rn_x[j] = fmaf(abar, Ix[j], fmaf(bbar, Qx[j + 1], rn_x[j]));
+    rn_y[j] = fmaf(abar, Iy[j], fmaf(bbar, Qy[j + 1], rn_y[j]));
+    rc[j] -= abar + bbar;
+  }
+  // image chain, reversed: I_j = I_{j-1} - 2 d n, d = n . I_{j-1} - c
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float dbar = -2.f * fmaf(Ibx[j], G.x, Iby[j] * G.y);
+    Ibx[j - 1] += fmaf(dbar, G.x, Ibx[j]);
+    Iby[j - 1] += fmaf(dbar, G.y, Iby[j]);
+    rn_x[j] = fmaf(-2.f * dimg[j], Ibx[j], fmaf(dbar, Ix[j - 1], rn_x[j]));
+    rn_y[j] = fmaf(-2.f * dimg[j], Iby[j], fmaf(dbar, Iy[j - 1], rn_y[j]));
+    rc[j] -= dbar;
+  }
+  txb_x += Qbx[0] + Ibx[0];
+  txb_y += Qby[0] + Iby[0];
+  if (WG) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const bool any = (rn_x[j] != 0.f) | (rn_y[j] != 0.f) | (rc[j] != 0.f) |
+                       (rt0[j] != 0.f) | (rl[j] != 0.f);
+      if (__any_sync(FULL, any)) {
+        const float a0 = warp_sum(rn_x[j]), a1 = warp_sum(rn_y[j]), a2 = warp_sum(rc[j]);
+        const float a3 = warp_sum(rt0[j]), a4 = warp_sum(rl[j]);
+        float v = a0;
+        int slot = S_NX;
+        if (lane == 1) { v = a1; slot = S_NY; }
+        if (lane == 2) { v = a2; slot = S_C; }
+        if (lane == 3) { v = a3; slot = S_T0; }
+        if (lane == 4) { v = a4; slot = S_LEN; }
+        if (lane < 5) atomicAdd(&s.acc[cd.w[j - 1] * VJP_SLOTS + slot], v);
+      }
+    }
+  }
+}
+
+template <int MODE, bool WG>
+__global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
+  extern __shared__ float4 smem[];
+  VSmem s;
+  s.G = smem;
+  s.E = smem + a.W;
+  s.T = smem + 2 * a.W;
+  s.acc = reinterpret_cast<float*>(smem + 3 * a.W);
+  for (int w = threadIdx.x; w < a.W; w += blockDim.x) {
+    const WallGeom g = wall_geometry(a.walls[w]);
+    s.G[w] = g.G;
+    s.E[w] = g.E;
+    s.T[w] = g.T;
+  }
+  if (WG)
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) s.acc[i] = 0.f;
+  __syncthreads();
+
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  float txb_x = 0.f, txb_y = 0.f;
+  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    long long r = tile * 32 + lane;
+    const bool live = r < a.R;
+    if (!live) r = a.R - 1;
+    const float g = live ? __ldg(a.grad_power + r) : 0.f;
+    if (__all_sync(FULL, g == 0.f)) continue;
+    const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
+    const long long c0 = chunk * a.chunk;
+    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+    for (long long c = c0; c < c1; ++c) {
+      const Cand cd = decode_candidate(c, a.W, a.K);
+      switch (cd.k) {
+        case 0: path_vjp<MODE, 0, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb_x, txb_y); break;
+        case 1: path_vjp<MODE, 1, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y); break;
+        case 2: path_vjp<MODE, 2, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y); break;
+        default: path_vjp<MODE, 3, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y); break;
+      }
+    }
+  }
+  txb_x = warp_sum(txb_x);
+  txb_y = warp_sum(txb_y);
+  if (lane == 0) {
+    a.warp_tx[2 * gwarp] = txb_x;
+    a.warp_tx[2 * gwarp + 1] = txb_y;
+  }
+  if (WG) {
+    __syncthreads();
+    float* out = a.cta_walls + (size_t)blockIdx.x * a.W * VJP_SLOTS;
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) out[i] = s.acc[i];
+  }
+}
+
+// Sums the per-CTA wall tables and the per-warp TX partials in a fixed order
+// and chains (n, c, t0, len) back to the end points A, B of each wall:
+//   u = (B - A)/|B - A|, n = (-u_y, u_x), c = n . A, t0 = u . A.
+__global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpArgs a, int n_ctas,
+                                                           int n_warps, int wall_grad) {
+  if (wall_grad) {
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < a.W; w += gridDim.x * blockDim.x) {
+      float acc[VJP_SLOTS];
+#pragma unroll
+      for (int k = 0; k < VJP_SLOTS; ++k) acc[k] = 0.f;
+      for (int c = 0; c < n_ctas; ++c) {
+        const float* src = a.cta_walls + ((size_t)c * a.W + w) * VJP_SLOTS;
+#pragma unroll
+        for (int k = 0; k < VJP_SLOTS; ++k) acc[k] += src[k];
+      }
+      const float4 ab = a.walls[w];
+      const WallGeom g = wall_geometry(ab);
+      const float nx = g.G.x, ny = g.G.y, len = g.G.w;
+      const float ux = ny, uy = -nx;
+      float nbx = acc[S_NX], nby = acc[S_NY];
+      float Abx = acc[S_AX], Aby = acc[S_AY], Bbx = acc[S_BX], Bby = acc[S_BY];
+      // c = n . A
+      nbx = fmaf(acc[S_C], ab.x, nbx);
+      nby = fmaf(acc[S_C], ab.y, nby);
+      Abx = fmaf(acc[S_C], nx, Abx);
+      Aby = fmaf(acc[S_C], ny, Aby);
+      // t0 = u . A
+      float ubx = acc[S_T0] * ab.x, uby = acc[S_T0] * ab.y;
+      Abx = fmaf(acc[S_T0], ux, Abx);
+      Aby = fmaf(acc[S_T0], uy, Aby);
+      // n = (-u_y, u_x)
+      ubx += nby;
+      uby -= nbx;
+      // u = e / len, len = |e|, e = B - A
+      const float uu = fmaf(ubx, ux, uby * uy);
+      const float ebx = fmaf(acc[S_LEN], ux, (ubx - uu * ux) / len);
+      const float eby = fmaf(acc[S_LEN], uy, (uby - uu * uy) / len);
+      Abx -= ebx;
+      Aby -= eby;
+      Bbx += ebx;
+      Bby += eby;
+      reinterpret_cast<float4*>(a.grad_walls)[w] = make_float4(Abx, Aby, Bbx, Bby);
+    }
+  }
+  if (blockIdx.x == 0) {
+    __shared__ float sx[256], sy[256];
+    float x = 0.f, y = 0.f;
+    for (int i = threadIdx.x; i < n_warps; i += blockDim.x) {
+      x += a.warp_tx[2 * i];
+      y += a.warp_tx[2 * i + 1];
+    }
+    sx[threadIdx.x] = x;
+    sy[threadIdx.x] = y;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) {
+        sx[threadIdx.x] += sx[threadIdx.x + o];
+        sy[threadIdx.x] += sy[threadIdx.x + o];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      a.grad_tx[0] = sx[0];
+      a.grad_tx[1] = sy[0];
+    }
+  }
+}
+
+template <int MODE, bool WG>
+void launch_vjp_t(const VjpArgs& a, int ctas, int threads, size_t smem, cudaStream_t st) {
+  vjp_kernel<MODE, WG><<<ctas, threads, smem, st>>>(a);
+}
+
+}  // namespace
+
+size_t vjp_smem_bytes(int W, bool wall_grad) {
+  return (size_t)3 * W * sizeof(float4) + (wall_grad ? (size_t)W * VJP_SLOTS * sizeof(float) : 0);
+}
+
+cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
+  const bool wg = a.grad_walls != nullptr;
+  const size_t smem = vjp_smem_bytes(a.W, wg);
+  switch (mode * 2 + (wg ? 1 : 0)) {
+    case MODE_SIGMOID * 2: launch_vjp_t<MODE_SIGMOID, false>(a, ctas, threads, smem, st); break;
+    case MODE_SIGMOID * 2 + 1: launch_vjp_t<MODE_SIGMOID, true>(a, ctas, threads, smem, st); break;
+    case MODE_HARD * 2: launch_vjp_t<MODE_HARD, false>(a, ctas, threads, smem, st); break;
+    case MODE_HARD * 2 + 1: launch_vjp_t<MODE_HARD, true>(a, ctas, threads, smem, st); break;
+    case MODE_STEP * 2: launch_vjp_t<MODE_STEP, false>(a, ctas, threads, smem, st); break;
+    default: launch_vjp_t<MODE_STEP, true>(a, ctas, threads, smem, st); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_warps = ctas * (threads / 32);
+  const int fb = wg ? (a.W + 255) / 256 : 1;
+  vjp_finalize_kernel<<<fb, 256, 0, st>>>(a, ctas, n_warps, wg ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = vjp_smem_bytes(W, wg);
+  switch (mode * 2 + (wg ? 1 : 0)) {
+    case MODE_SIGMOID * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_SIGMOID, false>, threads, smem);
+    case MODE_SIGMOID * 2 + 1:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_SIGMOID, true>, threads, smem);
+    case MODE_HARD * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_HARD, false>, threads, smem);
+    case MODE_HARD * 2 + 1:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_HARD, true>, threads, smem);
+    case MODE_STEP * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_STEP, false>, threads, smem);
+    default:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_STEP, true>, threads, smem);
+  }
+}
+
+cudaError_t vjp_set_smem_limit(int W) {
+  const int s0 = (int)vjp_smem_bytes(W, false), s1 = (int)vjp_smem_bytes(W, true);
+  cudaError_t e = cudaSuccess;
+#define DRT_SET(M, B, S)                                                                    \
+  e = cudaFuncSetAttribute(vjp_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
+  if (e != cudaSuccess) return e;
+  DRT_SET(MODE_SIGMOID, false, s0)
+  DRT_SET(MODE_SIGMOID, true, s1)
+  DRT_SET(MODE_HARD, false, s0)
+  DRT_SET(MODE_HARD, true, s1)
+  DRT_SET(MODE_STEP, false, s0)
+  DRT_SET(MODE_STEP, true, s1)
+#undef DRT_SET
+  return e;
+}
+
+}  // namespace drt

@@ -1,0 +1,308 @@
+// C ABI of the library (include/drt.h): argument validation, work
+// decomposition, workspace sizing and kernel launches.  No entry point
+// allocates device memory or synchronises the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "drt.h"
+#include "drt_internal.h"
+
+namespace drt {
+namespace {
+
+thread_local std::string g_last_error;
+
+drt_status fail(drt_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+drt_status fail(drt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+drt_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(DRT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Per-device facts, cached: SM count, and whether the kernels' dynamic shared
+// memory limit has been raised on that device.
+struct DeviceInfo {
+  int sms = 0;
+  bool smem_set = false;
+};
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+
+drt_status device_info(int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(DRT_ERR_UNSUPPORTED, "device index %d", dev);
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DeviceInfo& d = g_dev[dev];
+  if (d.sms == 0) {
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  if (!d.smem_set) {
+    e = forward_set_smem_limit(DRT_MAX_WALLS);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(forward)");
+    e = vjp_set_smem_limit(DRT_MAX_WALLS);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(vjp)");
+    d.smem_set = true;
+  }
+  *sms = d.sms;
+  return DRT_OK;
+}
+
+long long num_candidates(int W, int K) {
+  long long n = 1, level = 1;
+  for (int k = 1; k <= K; ++k) {
+    level = (k == 1) ? W : level * (W - 1);
+    n += level;
+  }
+  return n;
+}
+
+drt_status check_scene(const drt_scene* sc) {
+  if (!sc) return fail(DRT_ERR_INVALID_ARG, "scene is NULL");
+  if (sc->n_walls < 1 || sc->n_walls > DRT_MAX_WALLS)
+    return fail(sc->n_walls > DRT_MAX_WALLS ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
+                "n_walls = %d outside 1..%d", sc->n_walls, DRT_MAX_WALLS);
+  if (sc->n_rx < 0) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 0", sc->n_rx);
+  if (sc->max_order < 0 || sc->max_order > DRT_MAX_ORDER)
+    return fail(sc->max_order > DRT_MAX_ORDER ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
+                "max_order = %d outside 0..%d", sc->max_order, DRT_MAX_ORDER);
+  if (!(sc->alpha >= 0.f) || !std::isfinite(sc->alpha))
+    return fail(DRT_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+  if (!std::isfinite(sc->refl_coef)) return fail(DRT_ERR_INVALID_ARG, "refl_coef must be finite");
+  if (sc->smoothing < 0 || sc->smoothing > 2)
+    return fail(DRT_ERR_INVALID_ARG, "unknown smoothing %d", sc->smoothing);
+  if (!sc->walls || !aligned(sc->walls, 16))
+    return fail(DRT_ERR_INVALID_ARG, "walls must be a 16-byte aligned device pointer");
+  if (!sc->tx || !aligned(sc->tx, 4)) return fail(DRT_ERR_INVALID_ARG, "tx pointer");
+  if (sc->n_rx > 0 && (!sc->rx || !aligned(sc->rx, 8)))
+    return fail(DRT_ERR_INVALID_ARG, "rx must be an 8-byte aligned device pointer");
+  return DRT_OK;
+}
+
+drt_status check_tile(const drt_tile* t) {
+  if (!t) return DRT_OK;
+  if (t->warps_per_cta < 0 || t->warps_per_cta > 8)
+    return fail(DRT_ERR_INVALID_ARG, "warps_per_cta = %d outside 0..8", t->warps_per_cta);
+  if (t->cands_per_unit < 0) return fail(DRT_ERR_INVALID_ARG, "cands_per_unit < 0");
+  if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32)
+    return fail(DRT_ERR_INVALID_ARG, "ctas_per_sm = %d outside 0..32", t->ctas_per_sm);
+  return DRT_OK;
+}
+
+// Largest number of (chunk, receiver) partial sums the forward keeps.
+constexpr long long MAX_PARTIALS = 1LL << 26;
+
+enum Kernel { FWD, VJP };
+
+drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
+  int sms = 0;
+  drt_status st = device_info(&sms);
+  if (st != DRT_OK) return st;
+  const int W = sc->n_walls, K = sc->max_order;
+  const long long R = sc->n_rx;
+  const int warps = (t && t->warps_per_cta) ? t->warps_per_cta : 8;
+  d->threads = warps * 32;
+  d->n_cand = num_candidates(W, K);
+  long long chunk = (t && t->cands_per_unit) ? t->cands_per_unit : 64;
+  if (kern == FWD && R > 0) {
+    const long long max_chunks = std::max(1LL, MAX_PARTIALS / R);
+    chunk = std::max(chunk, (d->n_cand + max_chunks - 1) / max_chunks);
+  }
+  if (chunk > (1LL << 30)) chunk = 1LL << 30;
+  d->chunk = (int)chunk;
+  d->n_chunks = (d->n_cand + chunk - 1) / chunk;
+  d->n_tiles = (R + 31) / 32;
+  d->n_units = d->n_tiles * d->n_chunks;
+  int per_sm = (t && t->ctas_per_sm) ? t->ctas_per_sm : 0;
+  if (per_sm == 0) {
+    const int mode = sc->smoothing;
+    cudaError_t e = (kern == FWD) ? forward_occupancy(mode, d->threads, W, &per_sm)
+                                  : vjp_occupancy(mode, true, d->threads, W, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
+  }
+  long long ctas = (long long)sms * per_sm;
+  const long long needed = (d->n_units + warps - 1) / warps;
+  if (kern == FWD) ctas = std::min(ctas, std::max(1LL, needed));
+  d->ctas = (int)std::max(1LL, ctas);
+  return DRT_OK;
+}
+
+void gamma_powers(float gamma, float* gk) {
+  gk[0] = 1.f;
+  for (int k = 1; k <= DRT_MAX_ORDER; ++k) gk[k] = gk[k - 1] * gamma;
+}
+
+size_t vjp_workspace(const drt_scene* sc, const Decomp& d) {
+  const size_t warps = (size_t)d.ctas * (d.threads / 32);
+  return (size_t)d.ctas * sc->n_walls * VJP_SLOTS * sizeof(float) + warps * 2 * sizeof(float);
+}
+
+}  // namespace
+}  // namespace drt
+
+using namespace drt;
+
+extern "C" {
+
+const char* drt_status_string(drt_status s) {
+  switch (s) {
+    case DRT_OK: return "ok";
+    case DRT_ERR_INVALID_ARG: return "invalid argument";
+    case DRT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DRT_ERR_CUDA: return "CUDA error";
+    case DRT_ERR_TIMEOUT: return "device wait timed out";
+    case DRT_ERR_WORKSPACE: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+const char* drt_last_error(void) { return g_last_error.c_str(); }
+
+drt_status drt_num_candidates(int32_t n_walls, int32_t max_order, int64_t* count) {
+  if (!count) return fail(DRT_ERR_INVALID_ARG, "count is NULL");
+  if (n_walls < 1 || max_order < 0) return fail(DRT_ERR_INVALID_ARG, "n_walls/max_order");
+  if (max_order > DRT_MAX_ORDER) return fail(DRT_ERR_UNSUPPORTED, "max_order > %d", DRT_MAX_ORDER);
+  *count = num_candidates(n_walls, max_order);
+  return DRT_OK;
+}
+
+drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(scene, tile, FWD, &d)) != DRT_OK) return st;
+  *bytes = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  return DRT_OK;
+}
+
+drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (scene->n_rx > 0 && !power) return fail(DRT_ERR_INVALID_ARG, "power is NULL");
+  if (scene->n_rx == 0) return DRT_OK;
+  Decomp d;
+  if ((st = decompose(scene, tile, FWD, &d)) != DRT_OK) return st;
+  const size_t need = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  if (!workspace || workspace_bytes < need)
+    return fail(DRT_ERR_WORKSPACE, "forward needs %zu workspace bytes, got %zu", need,
+                workspace_bytes);
+  FwdArgs a;
+  a.walls = reinterpret_cast<const float4*>(scene->walls);
+  a.W = scene->n_walls;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  a.partial = static_cast<float*>(workspace);
+  a.power = power;
+  cudaError_t e = launch_forward(a, scene->smoothing, d.ctas, d.threads,
+                                 static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return DRT_OK;
+}
+
+drt_status drt_loss(const float* power, int32_t n_rx, float* loss, int32_t* argmin,
+                    void* stream) {
+  if (!power || !loss || !argmin) return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  if (n_rx < 1) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 1", n_rx);
+  cudaError_t e = launch_loss(power, n_rx, loss, argmin, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "loss launch");
+  return DRT_OK;
+}
+
+drt_status drt_loss_backward(const int32_t* argmin, const float* grad_loss, int32_t n_rx,
+                             float* grad_power, void* stream) {
+  if (!argmin || !grad_power) return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  if (n_rx < 1) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 1", n_rx);
+  cudaError_t e = launch_loss_backward(argmin, grad_loss, n_rx, grad_power,
+                                       static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "loss backward launch");
+  return DRT_OK;
+}
+
+drt_status drt_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(scene, tile, VJP, &d)) != DRT_OK) return st;
+  *bytes = vjp_workspace(scene, d);
+  return DRT_OK;
+}
+
+drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
+                   float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
+                   void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!grad_tx || (scene->n_rx > 0 && !grad_power))
+    return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  if (grad_walls && !aligned(grad_walls, 16))
+    return fail(DRT_ERR_INVALID_ARG, "grad_walls must be 16-byte aligned");
+  Decomp d;
+  if ((st = decompose(scene, tile, VJP, &d)) != DRT_OK) return st;
+  const size_t need = vjp_workspace(scene, d);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
+    return fail(DRT_ERR_WORKSPACE, "vjp needs %zu aligned workspace bytes, got %zu", need,
+                workspace_bytes);
+  VjpArgs a;
+  a.walls = reinterpret_cast<const float4*>(scene->walls);
+  a.W = scene->n_walls;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.grad_power = grad_power;
+  float* ws = static_cast<float*>(workspace);
+  a.cta_walls = ws;
+  a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.grad_tx = grad_tx;
+  a.grad_walls = grad_walls;
+  cudaError_t e = launch_vjp(a, scene->smoothing, d.ctas, d.threads,
+                             static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
+  return DRT_OK;
+}
+
+}  // extern "C"

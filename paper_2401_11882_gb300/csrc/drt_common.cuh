@@ -1,0 +1,138 @@
+// Device-side building blocks shared by the forward and adjoint kernels:
+// per-wall records staged in shared memory, the smoothing functions, and the
+// path-candidate decoder.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "drt.h"
+
+namespace drt {
+
+constexpr int KMAX = DRT_MAX_ORDER;
+constexpr int WMAX = DRT_MAX_WALLS;
+constexpr float LOG2E = 1.4426950408889634f;
+
+enum : int { MODE_SIGMOID = 0, MODE_HARD = 1, MODE_STEP = 2 };
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------ smoothing
+// s(x; alpha) = s(alpha x) (Eq. 3) for the three functions of Sec. IV:
+// the value s(x), the complement s(-x) (by C4 equal to 1 - s(x), but
+// evaluated directly so that it keeps its relative accuracy when small), and
+// the derivative ds/dx.
+struct Smooth3 {
+  float s, sb, ds;
+};
+
+template <int MODE>
+__device__ __forceinline__ Smooth3 smooth3(float x, float alpha) {
+  Smooth3 r;
+  if (MODE == MODE_HARD) {
+    // Eqs. 5-6: relu6(alpha x + 3) / 6 = sat(alpha/6 x + 1/2); slope alpha/6 on the
+    // open interval (-3/alpha, 3/alpha), 0 elsewhere (the kinks get 0).
+    const float a6 = alpha * (1.0f / 6.0f);
+    const float t = fmaf(x, a6, 0.5f);
+    r.s = __saturatef(t);
+    r.sb = __saturatef(fmaf(-x, a6, 0.5f));
+    r.ds = (t > 0.0f && t < 1.0f) ? a6 : 0.0f;
+  } else if (MODE == MODE_STEP) {
+    // Eq. 1: theta(x) = [x > 0]; theta(0) = 0 on both sides.
+    r.s = x > 0.0f ? 1.0f : 0.0f;
+    r.sb = x < 0.0f ? 1.0f : 0.0f;
+    r.ds = 0.0f;
+  } else {
+    // Eq. 4 with e = exp(-alpha |x|) in (0, 1]: s(|x|) = 1/(1+e), s(-|x|) = e/(1+e).
+    const float z = x * (alpha * LOG2E);
+    const float e = ex2_approx(-fabsf(z));
+    const float q = 1.0f / (1.0f + e);
+    const float big = q, small = e * q;
+    r.s = z >= 0.0f ? big : small;
+    r.sb = z >= 0.0f ? small : big;
+    r.ds = alpha * small * q;
+  }
+  return r;
+}
+
+// ------------------------------------------------------------ candidates
+// Path candidate c of the list of every wall sequence of length 0..K with no
+// wall twice in a row (Sec. V), ordered by length, then lexicographically.
+struct Cand {
+  int k;
+  int w[KMAX > 0 ? KMAX : 1];
+};
+
+__device__ __forceinline__ Cand decode_candidate(long long c, int W, int K) {
+  Cand cd;
+  cd.k = 0;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) cd.w[j] = -1;
+  if (c == 0) return cd;
+  c -= 1;
+  long long block = W;      // number of candidates of order k: W (W-1)^(k-1)
+  int k = 1;
+  while (k < K && c >= block) {
+    c -= block;
+    block *= (W - 1);
+    ++k;
+  }
+  cd.k = k;
+  // first wall: c / (W-1)^(k-1); every later digit d in [0, W-2] skips the previous wall
+  long long stride = block / W;
+  int prev = (int)(c / stride);
+  cd.w[0] = prev;
+  long long rem = c - (long long)prev * stride;
+#pragma unroll
+  for (int j = 1; j < KMAX; ++j) {
+    if (j < k) {
+      stride /= (W - 1);
+      const int d = (int)(rem / stride);
+      rem -= (long long)d * stride;
+      prev = d < prev ? d : d + 1;
+      cd.w[j] = prev;
+    }
+  }
+  return cd;
+}
+
+// ------------------------------------------------------------ wall records
+// Per wall (Sec. V, relaxed geometry on the wall's infinite line):
+//   G = {nx, ny, c, len}: unit normal n = (-u_y, u_x) of the unit direction
+//       u = (B - A)/|B - A|, offset c = n . A (signed distance d(p) = n . p - c),
+//       segment length.
+//   E = {ax, ay, bx, by}: the end points.
+//   T = {t0, 0, 0, 0}: t0 = u . A (coordinate along the wall: u . p - t0).
+struct WallGeom {
+  float4 G, E, T;
+};
+
+__device__ __forceinline__ WallGeom wall_geometry(float4 ab) {
+  WallGeom g;
+  const float ex = ab.z - ab.x, ey = ab.w - ab.y;
+  const float len = __fsqrt_rn(fmaf(ex, ex, ey * ey));
+  const float ux = __fdiv_rn(ex, len), uy = __fdiv_rn(ey, len);
+  const float nx = -uy, ny = ux;
+  g.G = make_float4(nx, ny, fmaf(nx, ab.x, ny * ab.y), len);
+  g.E = ab;
+  g.T = make_float4(fmaf(ux, ab.x, uy * ab.y), 0.f, 0.f, 0.f);
+  return g;
+}
+
+// signed distance of p to the line of a wall record
+__device__ __forceinline__ float line_dist(const float4& G, float px, float py) {
+  return fmaf(G.x, px, fmaf(G.y, py, -G.z));
+}
+
+}  // namespace drt

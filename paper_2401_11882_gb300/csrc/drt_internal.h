@@ -1,0 +1,76 @@
+// Host <-> kernel argument blocks and launchers (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "drt.h"
+
+namespace drt {
+
+// Work decomposition shared by the forward and adjoint kernels: a unit is
+// (32 receivers) x (`chunk` consecutive candidates); unit u covers receiver
+// tile u % n_tiles and candidate chunk u / n_tiles.
+struct Decomp {
+  long long n_cand;
+  int chunk;
+  long long n_chunks, n_tiles, n_units;
+  int threads;   // threads per CTA
+  int ctas;      // persistent grid size
+};
+
+struct FwdArgs {
+  const float4* walls;
+  int W;
+  const float* rx;
+  long long R;
+  const float* tx;
+  int K;
+  float alpha;
+  float gk[DRT_MAX_ORDER + 1];   // Gamma^k
+  long long n_cand;
+  int chunk;
+  long long n_chunks, n_tiles, n_units;
+  int cull;
+  float* partial;   // [n_chunks][R]
+  float* power;     // [R]
+};
+
+struct VjpArgs {
+  const float4* walls;
+  int W;
+  const float* rx;
+  long long R;
+  const float* tx;
+  int K;
+  float alpha;
+  float gk[DRT_MAX_ORDER + 1];
+  long long n_cand;
+  int chunk;
+  long long n_chunks, n_tiles, n_units;
+  const float* grad_power;   // [R]
+  float* cta_walls;          // [ctas][W][9] per-CTA wall-gradient partials (wall gradient only)
+  float* warp_tx;            // [ctas * warps_per_cta][2]
+  float* grad_tx;            // [2]
+  float* grad_walls;         // [W][4] or null
+};
+
+// number of float slots per wall in the adjoint's accumulators:
+// d/d{nx, ny, c, ax, ay, bx, by, t0, len}
+constexpr int VJP_SLOTS = 9;
+
+size_t forward_smem_bytes(int W);
+cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t forward_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t forward_set_smem_limit(int W);
+cudaError_t launch_loss(const float* power, int R, float* loss, int32_t* argmin, cudaStream_t st);
+cudaError_t launch_loss_backward(const int32_t* argmin, const float* grad_loss, int R,
+                                 float* grad_power, cudaStream_t st);
+
+size_t vjp_smem_bytes(int W, bool wall_grad);
+cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t vjp_occupancy(int mode, bool wall_grad, int threads, int W, int* ctas_per_sm);
+cudaError_t vjp_set_smem_limit(int W);
+
+}  // namespace drt

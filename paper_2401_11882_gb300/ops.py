@@ -1,0 +1,211 @@
+"""PyTorch-facing calls of the library: argument marshalling over the C ABI.
+
+Every step of the computation runs in the CUDA kernels of libdrt.so; this
+module only checks tensors, provides workspace memory from PyTorch's
+allocator, passes raw device pointers and the current CUDA stream, and wraps
+the forward / adjoint pair as a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+
+@dataclass(frozen=True)
+class TileConfig:
+    """Work decomposition of the path kernels (0 = library default)."""
+
+    warps_per_cta: int = 0
+    cands_per_unit: int = 0
+    ctas_per_sm: int = 0
+    cull_invalid: bool = False
+
+    def as_c(self) -> _lib.Tile:
+        return _lib.Tile(self.warps_per_cta, self.cands_per_unit, self.ctas_per_sm,
+                         _lib.TILE_CULL_INVALID if self.cull_invalid else 0)
+
+
+def _stream_ptr(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _as_f32(t: torch.Tensor, shape_last: int | None, name: str, align: int) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    t = t.detach()
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"{name} must have shape [n, {shape_last}]")
+    if not t.is_contiguous() or t.data_ptr() % align:
+        t = t.contiguous().clone()
+    return t
+
+
+def _workspace(device: torch.device, nbytes: int) -> torch.Tensor:
+    """Scratch memory from PyTorch's stream-aware caching allocator."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def make_scene(walls: torch.Tensor, tx: torch.Tensor, rx: torch.Tensor, max_order: int,
+               alpha: float, smoothing: str, refl_coef: float = 0.5):
+    """Validate tensors and build the C scene descriptor (keeps tensors alive)."""
+    walls = _as_f32(walls, 4, "walls", 16)
+    rx = _as_f32(rx, 2, "rx", 8)
+    tx = _as_f32(tx.reshape(1, 2), 2, "tx", 4)
+    if walls.device != rx.device or walls.device != tx.device:
+        raise ValueError("walls, tx and rx must be on the same device")
+    if smoothing not in _lib.SMOOTHING:
+        raise ValueError(f"unknown smoothing {smoothing!r}")
+    sc = _lib.Scene(walls.data_ptr(), walls.shape[0], rx.data_ptr(), rx.shape[0], tx.data_ptr(),
+                    int(max_order), float(alpha), _lib.SMOOTHING[smoothing], float(refl_coef))
+    return sc, (walls, tx, rx)
+
+
+def num_candidates(n_walls: int, max_order: int) -> int:
+    out = ctypes.c_int64()
+    _lib.call("drt_num_candidates", n_walls, max_order, ctypes.byref(out))
+    return out.value
+
+
+def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+            refl_coef: float = 0.5, tile: TileConfig | None = None,
+            out: torch.Tensor | None = None) -> torch.Tensor:
+    """Received power per receiver (float32 [R]) on the current stream."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_forward_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    power = out if out is not None else torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    _lib.call("drt_forward", ctypes.byref(sc), tlp, _ptr(power), _ptr(ws),
+              ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return power
+
+
+def min_loss(power: torch.Tensor):
+    """(loss, argmin): loss = -min_r power[r] (float32 [1]), argmin int32 [1]."""
+    power = _as_f32(power.reshape(-1, 1), 1, "power", 4)
+    dev = power.device
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    arg = torch.empty(1, dtype=torch.int32, device=dev)
+    _lib.call("drt_loss", _ptr(power), power.shape[0], _ptr(loss), _ptr(arg), _stream_ptr(dev))
+    return loss, arg
+
+
+def min_loss_backward(argmin: torch.Tensor, grad_loss: torch.Tensor | None, n_rx: int) -> torch.Tensor:
+    dev = argmin.device
+    g = torch.empty(n_rx, dtype=torch.float32, device=dev)
+    gl = None if grad_loss is None else _as_f32(grad_loss.reshape(1, 1), 1, "grad_loss", 4)
+    _lib.call("drt_loss_backward", _ptr(argmin), None if gl is None else _ptr(gl), n_rx, _ptr(g),
+              _stream_ptr(dev))
+    return g
+
+
+def vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, grad_power: torch.Tensor,
+        refl_coef: float = 0.5, wall_grad: bool = True, tile: TileConfig | None = None):
+    """(grad_tx [2], grad_walls [W, 4] or None) = grad_power^T d power / d (tx, walls)."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    gp = _as_f32(grad_power.reshape(-1, 1), 1, "grad_power", 4)
+    if gp.shape[0] != sc.n_rx:
+        raise ValueError("grad_power must have one entry per receiver")
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_vjp_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    gtx = torch.empty(2, dtype=torch.float32, device=dev)
+    gw = torch.empty(sc.n_walls, 4, dtype=torch.float32, device=dev) if wall_grad else None
+    _lib.call("drt_vjp", ctypes.byref(sc), tlp, _ptr(gp), _ptr(gtx),
+              None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+              _stream_ptr(dev))
+    return gtx, gw
+
+
+class PowerFunction(torch.autograd.Function):
+    """power = P(walls, tx) with the hand-written adjoint as backward.
+
+    The backward recomputes the path geometry (nothing but the inputs is saved)."""
+
+    @staticmethod
+    def forward(ctx, walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile):
+        ctx.save_for_backward(walls, tx, rx)
+        ctx.args = (max_order, alpha, smoothing, refl_coef, tile)
+        return forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
+
+    @staticmethod
+    def backward(ctx, grad_power):
+        walls, tx, rx = ctx.saved_tensors
+        max_order, alpha, smoothing, refl_coef, tile = ctx.args
+        need_w, need_tx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_w or need_tx):
+            return (None,) * 8
+        gtx, gw = vjp(walls, tx, rx, max_order, alpha, smoothing, grad_power.contiguous(),
+                      refl_coef, wall_grad=need_w, tile=tile)
+        return (gw if need_w else None, gtx.reshape(tx.shape) if need_tx else None,
+                None, None, None, None, None, None)
+
+
+class MinLossFunction(torch.autograd.Function):
+    """loss = -min_r power[r] (Eq. 8 objective, Sec. III loss)."""
+
+    @staticmethod
+    def forward(ctx, power):
+        loss, arg = min_loss(power)
+        ctx.save_for_backward(arg)
+        ctx.n = power.shape[0]
+        return loss.reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (arg,) = ctx.saved_tensors
+        return min_loss_backward(arg, grad_loss.reshape(1).float().contiguous(), ctx.n)
+
+
+def power(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+          refl_coef: float = 0.5, tile: TileConfig | None = None) -> torch.Tensor:
+    """Differentiable (in walls and tx) received power per receiver."""
+    return PowerFunction.apply(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
+
+
+def loss(power_values: torch.Tensor) -> torch.Tensor:
+    """Differentiable loss -min_r power[r]."""
+    return MinLossFunction.apply(power_values)
+
+
+def objective(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", refl_coef=0.5,
+              tile=None):
+    """loss(power(...)) as one differentiable call."""
+    return loss(power(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile))
+
+
+def objective_host(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", refl_coef=0.5,
+                   device="cuda", grad_walls=False, tile=None):
+    """End-to-end call from host arrays: copy the inputs to the device, run power,
+    loss and its gradient, copy (loss, power, grad_tx[, grad_walls]) back to the host."""
+    dev = torch.device(device)
+    w = torch.as_tensor(walls).to(dev, non_blocking=True)
+    t = torch.as_tensor(tx).to(dev, non_blocking=True)
+    r = torch.as_tensor(rx).to(dev, non_blocking=True)
+    p = forward(w, t, r, max_order, alpha, smoothing, refl_coef, tile)
+    l, arg = min_loss(p)
+    g = min_loss_backward(arg, None, p.shape[0])
+    gtx, gw = vjp(w, t, r, max_order, alpha, smoothing, g, refl_coef, wall_grad=grad_walls,
+                  tile=tile)
+    out = [l.to("cpu", non_blocking=True), p.to("cpu", non_blocking=True),
+           gtx.to("cpu", non_blocking=True)]
+    if grad_walls:
+        out.append(gw.to("cpu", non_blocking=True))
+    torch.cuda.current_stream(dev).synchronize()
+    return tuple(out)

@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads, exports every entry point its header
+declares, and validates arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(drt_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_11882_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert {"drt_forward", "drt_vjp", "drt_loss", "drt_num_candidates"} <= names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2401_11882_gb300 import _lib
+    assert _declared() <= set(_lib.SIGNATURES), sorted(_declared() - set(_lib.SIGNATURES))
+
+
+def test_num_candidates_host_only(lib):
+    out = ctypes.c_int64()
+    assert lib.drt_num_candidates(64, 2, ctypes.byref(out)) == 0 and out.value == 4097
+    assert lib.drt_num_candidates(128, 2, ctypes.byref(out)) == 0 and out.value == 16385
+    assert lib.drt_num_candidates(0, 1, ctypes.byref(out)) == 1
+    assert lib.drt_num_candidates(5, 4, ctypes.byref(out)) == 2      # K above the maximum
+    assert lib.drt_num_candidates(5, 1, None) == 1
+
+
+def test_status_strings(lib):
+    assert lib.drt_status_string(0) == b"ok"
+    assert lib.drt_status_string(5) == b"workspace too small"
+
+
+def _scene(**kw):
+    from paper_2401_11882_gb300 import _lib
+    d = dict(walls=16, n_walls=4, rx=64, n_rx=3, tx=128, max_order=1, alpha=10.0, smoothing=1,
+             refl_coef=0.5)
+    d.update(kw)
+    return _lib.Scene(**d)
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("n_walls", 0, 1), ("n_walls", 5000, 2), ("max_order", 4, 2), ("max_order", -1, 1),
+    ("alpha", -1.0, 1), ("alpha", float("nan"), 1), ("smoothing", 7, 1), ("walls", 0, 1),
+    ("walls", 8, 1), ("rx", 4, 1), ("n_rx", -2, 1), ("refl_coef", float("inf"), 1)])
+def test_forward_rejects_bad_scene_before_any_launch(lib, field, value, status):
+    # Rejected on the host: no CUDA call is made, so this runs without a GPU.
+    sc = _scene(**{field: value})
+    out = ctypes.c_size_t()
+    assert lib.drt_forward_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == status
+    assert lib.drt_forward(ctypes.byref(sc), None, ctypes.c_void_p(256), None, 0, None) == status
+    assert lib.drt_vjp(ctypes.byref(sc), None, ctypes.c_void_p(256), ctypes.c_void_p(256), None,
+                       None, 0, None) == status
+    assert len(lib.drt_last_error()) > 0
+
+
+def test_loss_rejects_bad_args(lib):
+    p = ctypes.c_void_p(256)
+    assert lib.drt_loss(None, 4, p, p, None) == 1
+    assert lib.drt_loss(p, 0, p, p, None) == 1
+    assert lib.drt_loss_backward(None, None, 4, p, None) == 1

@@ -1,0 +1,164 @@
+"""Hand-written adjoint (drt_vjp) against the FP64 oracle's exact derivatives and
+against central finite differences."""
+import numpy as np
+import pytest
+
+from parity import assert_grad_close
+from paper_2401_11882_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def drt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_11882_gb300 as m
+    return m
+
+
+def _tensors(sc):
+    dev = torch.device("cuda:0")
+    return (torch.tensor(sc.walls, device=dev), torch.tensor(sc.tx, device=dev),
+            torch.tensor(sc.rx, device=dev))
+
+
+def _vjp(drt, sc, g, wall_grad=True, tile=None):
+    w, t, r = _tensors(sc)
+    gtx, gw = drt.vjp(w, t, r, sc.max_order, sc.alpha, sc.smoothing,
+                      torch.tensor(g, dtype=torch.float32, device=w.device), sc.refl_coef,
+                      wall_grad=wall_grad, tile=tile)
+    torch.cuda.synchronize()
+    return gtx.cpu().numpy(), (gw.cpu().numpy() if gw is not None else None)
+
+
+def _oracle_grad(oracle_mod, sc, g, params="all"):
+    return oracle_mod.gradient(sc.walls, sc.tx, sc.rx, sc.max_order, sc.alpha, sc.smoothing, g,
+                               params, sc.refl_coef)
+
+
+CASES = [
+    (0, 6, 45, 1, 20.0, "sigmoid"),
+    (1, 8, 40, 2, 10.0, "sigmoid"),
+    (2, 8, 33, 2, 40.0, "hard_sigmoid"),
+    (3, 5, 70, 0, 30.0, "hard_sigmoid"),
+    (4, 7, 40, 2, 1.0, "step"),
+    (5, 5, 36, 3, 15.0, "sigmoid"),
+    (6, 10, 64, 2, 100.0, "hard_sigmoid"),
+]
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha,smoothing", CASES)
+def test_dense_vjp_all_parameters(drt, oracle_mod, seed, W, R, K, alpha, smoothing):
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, smoothing, boundary=(seed % 2 == 1))
+    g = rng.normal(size=sc.n_rx)
+    gtx, gw = _vjp(drt, sc, g)
+    ref = _oracle_grad(oracle_mod, sc, g.astype(np.float32).astype(np.float64))
+    assert_grad_close(gtx, ref[:2], "grad_tx")
+    assert_grad_close(gw.ravel(), ref[2:], "grad_walls")
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid", "step"])
+def test_tiny_scene_loss_gradient(drt, oracle_mod, smoothing):
+    sc = scenes.tiny_scene(alpha=100.0, smoothing=smoothing)
+    w, t, r = _tensors(sc)
+    w.requires_grad_(True)
+    t.requires_grad_(True)
+    L = drt.objective(w, t, r, sc.max_order, sc.alpha, sc.smoothing)
+    L.backward()
+    P = oracle_mod.power(sc.walls, sc.tx, sc.rx, sc.max_order, sc.alpha, sc.smoothing)
+    _, am = oracle_mod.loss(P)
+    g = np.zeros(sc.n_rx)
+    g[am] = -1.0
+    ref = _oracle_grad(oracle_mod, sc, g)
+    assert_grad_close(t.grad.cpu().numpy(), ref[:2], "grad_tx")
+    assert_grad_close(w.grad.cpu().numpy().ravel(), ref[2:], "grad_walls")
+
+
+def test_against_central_differences(drt, oracle_mod):
+    # h = 1e-4 central differences of the FP64 forward, smooth case.
+    rng = np.random.default_rng(21)
+    sc = scenes.random_small_scene(rng, 6, 30, 2, 10.0, "sigmoid", boundary=True)
+    g = rng.normal(size=sc.n_rx)
+    gtx, gw = _vjp(drt, sc, g)
+    h = 1e-4
+    walls = sc.walls.astype(np.float64)
+    tx = sc.tx.astype(np.float64)
+    fd = []
+    for p in range(2 + walls.size):
+        dt, dw = np.zeros(2), np.zeros(walls.size)
+        if p < 2:
+            dt[p] = h
+        else:
+            dw[p - 2] = h
+        Pp = oracle_mod.power(walls + dw.reshape(walls.shape), tx + dt, sc.rx, 2, 10.0, "sigmoid")
+        Pm = oracle_mod.power(walls - dw.reshape(walls.shape), tx - dt, sc.rx, 2, 10.0, "sigmoid")
+        fd.append(g @ (Pp - Pm) / (2 * h))
+    fd = np.array(fd)
+    assert_grad_close(np.concatenate([gtx, gw.ravel()]), fd, "adjoint vs central FD")
+
+
+def test_gradient_scene_sampled(drt, oracle_mod):
+    # 128 random walls, 128 x 128 receivers, K <= 2 (16385 sequences): the VJP is linear in g,
+    # so g = indicator of 8 sampled receivers is checked against the oracle's derivative of
+    # their summed power, for the TX and 10 sampled wall coordinates.
+    sc = scenes.gradient_scene(alpha=100.0, smoothing="hard_sigmoid")
+    rng = np.random.default_rng(0)
+    idx = rng.choice(sc.n_rx, 8, replace=False)
+    g = np.zeros(sc.n_rx)
+    g[idx] = 1.0
+    gtx, gw = _vjp(drt, sc, g)
+    coords = rng.choice(4 * sc.n_walls, 10, replace=False)
+    sub = sc.replace(rx=sc.rx[idx])
+    ref = _oracle_grad(oracle_mod, sub, np.ones(8), [0, 1] + [2 + int(c) for c in coords])
+    assert_grad_close(gtx, ref[:2], "grad_tx")
+    got = gw.ravel()[coords]
+    # per-coordinate: each sampled wall coordinate against its exact derivative
+    np.testing.assert_allclose(got, ref[2:], rtol=1e-3,
+                               atol=1e-3 * 1e-3 * max(np.abs(ref[2:]).max(), np.abs(ref[:2]).max()))
+
+
+def test_tx_only_matches_full(drt):
+    rng = np.random.default_rng(5)
+    sc = scenes.random_small_scene(rng, 9, 50, 2, 50.0, "hard_sigmoid", boundary=True)
+    g = rng.normal(size=sc.n_rx)
+    a, _ = _vjp(drt, sc, g, wall_grad=False)
+    b, _ = _vjp(drt, sc, g, wall_grad=True)
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6 * np.abs(b).max())
+
+
+def test_sparse_g_skips_but_matches(drt, oracle_mod):
+    rng = np.random.default_rng(6)
+    sc = scenes.random_small_scene(rng, 8, 100, 2, 30.0, "sigmoid", boundary=True)
+    g = np.zeros(sc.n_rx)
+    g[57] = 2.0
+    gtx, gw = _vjp(drt, sc, g)
+    ref = _oracle_grad(oracle_mod, sc, g)
+    assert_grad_close(gtx, ref[:2], "grad_tx")
+    assert_grad_close(gw.ravel(), ref[2:], "grad_walls")
+
+
+def test_autograd_matches_direct_vjp(drt):
+    rng = np.random.default_rng(7)
+    sc = scenes.random_small_scene(rng, 7, 40, 2, 25.0, "sigmoid", boundary=True)
+    w, t, r = _tensors(sc)
+    w.requires_grad_(True)
+    t.requires_grad_(True)
+    P = drt.power(w, t, r, sc.max_order, sc.alpha, sc.smoothing)
+    gvec = torch.randn_like(P)
+    (P * gvec).sum().backward()
+    gtx, gw = _vjp(drt, sc, gvec.cpu().numpy())
+    # wall gradients are summed with shared-memory atomics, whose order varies
+    np.testing.assert_allclose(t.grad.cpu().numpy(), gtx, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(w.grad.cpu().numpy(), gw, rtol=2e-5, atol=1e-6 * np.abs(gw).max())
+
+
+def test_vjp_deterministic_tx(drt):
+    sc = scenes.clutter_scene(12, 8, seed=1, max_order=2, alpha=50.0)
+    g = np.random.default_rng(0).normal(size=sc.n_rx)
+    a, _ = _vjp(drt, sc, g, wall_grad=False)
+    b, _ = _vjp(drt, sc, g, wall_grad=False)
+    np.testing.assert_array_equal(a, b)
