@@ -133,6 +133,29 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
                    float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* Size of the static device scratch array behind drt_forward_noalloc. */
+#define DRT_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* drt_forward for callers that cannot allocate device memory (the paper has no
+   counterpart; this is a deployment convenience).  Plugins and callbacks that
+   only receive the buffers they must fill, and applications that fix their
+   whole device-memory plan at start-up, cannot provide drt_forward's
+   workspace.  This call instead uses a scratch array of
+   DRT_NOALLOC_SCRATCH_BYTES compiled into the library's device image, which
+   every GPU that loads the library keeps until the process exits, and calls no
+   allocator.  Same arguments and result as drt_forward with default tiling
+   (scene: host pointer; power: [n_rx] device, overwritten).
+   - Limit: one partial sum per (candidate chunk, receiver) must fit, so
+     n_rx <= DRT_NOALLOC_SCRATCH_BYTES / 4; larger scenes get
+     DRT_ERR_UNSUPPORTED before anything is enqueued.
+   - All calls on a device share the array, and it keeps the last call's
+     contents (every value a call reads was written by that same call).
+     Calls that overlap on the GPU race on it: order them on one stream.
+   - The first call on each device looks the array's device address up
+     (cudaGetSymbolAddress) with that device current; make that first call
+     before any stream capture begins. */
+drt_status drt_forward_noalloc(const drt_scene* scene, float* power, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

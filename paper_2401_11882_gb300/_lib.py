@@ -53,6 +53,7 @@ SIGNATURES = {
     "drt_loss_backward": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "drt_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "drt_forward_noalloc": (ctypes.c_int, [_P, _P, _P]),
 }
 
 

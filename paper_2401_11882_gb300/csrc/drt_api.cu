@@ -158,6 +158,9 @@ size_t vjp_workspace(const drt_scene* sc, const Decomp& d) {
 }
 
 }  // namespace
+
+void set_error_message(const char* msg) { g_last_error = msg ? msg : ""; }
+
 }  // namespace drt
 
 using namespace drt;

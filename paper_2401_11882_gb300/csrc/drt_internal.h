@@ -60,6 +60,9 @@ struct VjpArgs {
 // d/d{nx, ny, c, ax, ay, bx, by, t0, len}
 constexpr int VJP_SLOTS = 9;
 
+// Sets the message drt_last_error() returns on this host thread.
+void set_error_message(const char* msg);
+
 size_t forward_smem_bytes(int W);
 cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t forward_occupancy(int mode, int threads, int W, int* ctas_per_sm);

@@ -1,0 +1,71 @@
+"""drt_forward_noalloc: the forward pass for callers that cannot allocate device
+memory (plugins handed only their output buffers, applications with a fixed
+device-memory plan).  It must give drt_forward's result, within the tolerance
+the other parity tests use, on consecutive calls that share its static scratch
+array.  The file name makes pytest collect it last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from parity import assert_power_close
+from paper_2401_11882_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_11882_gb300 import _lib
+    return _lib.load()
+
+
+def _noalloc(lib, sc, dev):
+    """Call drt_forward_noalloc through the C ABI; the test owns inputs and output."""
+    from paper_2401_11882_gb300 import _lib
+    w = torch.tensor(sc.walls, device=dev)
+    t = torch.tensor(sc.tx, device=dev)
+    r = torch.tensor(sc.rx, device=dev)
+    out = torch.full((sc.n_rx,), float("nan"), device=dev)
+    desc = _lib.Scene(w.data_ptr(), sc.n_walls, r.data_ptr(), sc.n_rx, t.data_ptr(),
+                      sc.max_order, sc.alpha, _lib.SMOOTHING[sc.smoothing], sc.refl_coef)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    st = lib.drt_forward_noalloc(ctypes.byref(desc), ctypes.c_void_p(out.data_ptr()), stream)
+    assert st == 0, lib.drt_last_error().decode()
+    torch.cuda.synchronize(dev)
+    return out.cpu().numpy()
+
+
+def _existing(sc, dev):
+    import paper_2401_11882_gb300 as drt
+    P = drt.forward(torch.tensor(sc.walls, device=dev), torch.tensor(sc.tx, device=dev),
+                    torch.tensor(sc.rx, device=dev), sc.max_order, sc.alpha, sc.smoothing,
+                    sc.refl_coef)
+    torch.cuda.synchronize(dev)
+    return P.cpu().numpy()
+
+
+def test_matches_drt_forward_on_two_calls_in_a_row(lib):
+    dev = torch.device("cuda:0")
+    first = scenes.large_scene(alpha=100.0, smoothing="hard_sigmoid")
+    second = scenes.clutter_scene(20, 40, seed=3, alpha=30.0, smoothing="sigmoid", max_order=2)
+    a1 = _noalloc(lib, first, dev)
+    a2 = _noalloc(lib, second, dev)     # reuses the scratch the first call left behind
+    assert np.all(np.isfinite(a1)) and np.all(np.isfinite(a2))
+    assert_power_close(a1, _existing(first, dev), "noalloc vs drt_forward, first call")
+    assert_power_close(a2, _existing(second, dev), "noalloc vs drt_forward, second call")
+    a3 = _noalloc(lib, first, dev)
+    np.testing.assert_array_equal(a3, a1)
+
+
+def test_rejects_receiver_counts_beyond_the_scratch(lib):
+    from paper_2401_11882_gb300 import _lib
+    cap = (8 << 20) // 4
+    desc = _lib.Scene(256, 4, 256, cap + 1, 256, 1, 10.0, 1, 0.5)
+    st = lib.drt_forward_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), None)
+    assert st == 2                       # DRT_ERR_UNSUPPORTED, nothing enqueued
+    assert b"scratch" in lib.drt_last_error()
