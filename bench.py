@@ -218,8 +218,7 @@ def run_ours(args):
         if e:
             e[1].record()
         loss, am = drt.min_loss(P)
-        gp = drt.min_loss_backward(am, None, sc.n_rx)
-        gtx, gw = drt.vjp(w, t, r, K, alpha, sm, gp)
+        gtx, gw = drt.min_loss_vjp(w, t, r, K, alpha, sm, am)
         if e:
             e[2].record()
         return loss, gtx, gw
@@ -307,7 +306,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": world * args.steps * evals / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 5 * args.steps,
         "clocks": clk,
         "extra": extras,
     }

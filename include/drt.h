@@ -133,6 +133,20 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
                    float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* Gradient of the min-power loss (Eq. 8, Sec. III) w.r.t. the scene, in one call:
+   with loss = -power[argmin[0]],
+     grad_tx    = -(grad_loss ? grad_loss[0] : 1) * d power[argmin] / d tx,
+     grad_walls = -(grad_loss ? grad_loss[0] : 1) * d power[argmin] / d walls.
+   Equal to drt_loss_backward followed by drt_vjp, but the lanes of each warp
+   take different path candidates of the one receiver, instead of 32
+   receivers of which only one has a non-zero weight.  argmin: [1] device
+   int32 from drt_loss (clamped to 0..n_rx-1); grad_loss: [1] or NULL;
+   grad_tx: [2]; grad_walls: [n_walls][4] or NULL; workspace: as for drt_vjp
+   (drt_vjp_workspace_size bytes). */
+drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const int32_t* argmin,
+                            const float* grad_loss, float* grad_tx, float* grad_walls,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 /* Size of the static device scratch array behind drt_forward_noalloc. */
 #define DRT_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -10,8 +10,8 @@ Public calls (PyTorch tensors on a CUDA device, float32):
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
-from .ops import (TileConfig, forward, loss, min_loss, min_loss_backward, num_candidates,
-                  objective, objective_host, power, vjp)
+from .ops import (TileConfig, forward, loss, min_loss, min_loss_backward, min_loss_vjp,
+                  num_candidates, objective, objective_host, power, vjp)
 
-__all__ = ["TileConfig", "forward", "loss", "min_loss", "min_loss_backward", "num_candidates",
-           "objective", "objective_host", "power", "vjp"]
+__all__ = ["TileConfig", "forward", "loss", "min_loss", "min_loss_backward", "min_loss_vjp",
+           "num_candidates", "objective", "objective_host", "power", "vjp"]

@@ -54,6 +54,7 @@ SIGNATURES = {
     "drt_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_forward_noalloc": (ctypes.c_int, [_P, _P, _P]),
+    "drt_min_loss_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
 }
 
 

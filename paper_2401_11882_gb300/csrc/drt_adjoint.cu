@@ -68,7 +68,10 @@ __device__ __forceinline__ LegWall leg_wall(float x1, float y1, float x2, float 
   return r;
 }
 
-template <int MODE, int K, bool WG>
+// UNI: the candidate is the same in all 32 lanes (lanes hold receivers), so the
+// adjoints of the reflecting walls can be summed over the warp; otherwise (lanes
+// hold different candidates of one receiver) each lane adds its own.
+template <int MODE, int K, bool WG, bool UNI>
 __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float2 rx,
                                          const Cand& cd, float alpha, float gk, float g,
                                          float& txb_x, float& txb_y) {
@@ -137,6 +140,15 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
     const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
     V[j] = s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
   }
+  // A path with an exactly-zero factor has an exactly-zero gradient: a zero
+  // validity or visibility factor is a saturated smoothing (derivative 0, also
+  // at the hard sigmoid's kinks by convention) or an FP32 underflow of the
+  // sigmoid, and every other factor's adjoint carries the zero.  Such lanes get
+  // weight 0, and a warp whose lanes are all such skips the rest.
+  bool dead = degenerate || g == 0.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) dead |= (V[j] == 0.f);
+  if (__all_sync(FULL, dead)) return;
   // sweep 1: visibility as (product of non-zero factors, number of zero factors)
   float nz[K + 1];
   int zc[K + 1];
@@ -165,6 +177,10 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
       }
     }
   }
+#pragma unroll
+  for (int j = 0; j <= K; ++j) dead |= (zc[j] != 0);
+  if (__all_sync(FULL, dead)) return;
+  if (dead) g = 0.f;
   // ------------------------------------------------ factor adjoints
   // p = C * prod(F), C = Gamma^k / L^2, F = {V_1..V_K, vis_0..vis_K}
   constexpr int NF = 2 * K + 1;
@@ -191,6 +207,10 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
   const float Lb = -2.f * g * __fdiv_rn(p, L);
 
   // ------------------------------------------------ sweep 2: obstruction adjoint
+  // legs whose visibility adjoint is zero in every lane contribute nothing here
+  bool live_leg[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) live_leg[j] = __any_sync(FULL, visb[j] != 0.f);
   float Qbx[K + 2], Qby[K + 2], mAx[K + 1], mAy[K + 1], sm[K + 1];
 #pragma unroll
   for (int i = 0; i <= K + 1; ++i) Qbx[i] = Qby[i] = 0.f;
@@ -210,7 +230,7 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
       const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
-      if (skip) continue;
+      if (skip || !live_leg[j]) continue;
       const float x2 = fmaf(mx[j], E.x, fmaf(my[j], E.y, -mq[j]));
       const float y2 = fmaf(mx[j], E.z, fmaf(my[j], E.w, -mq[j]));
       const LegWall lw = leg_wall<MODE, true>(dv[j], dv[j + 1], x2, y2, alpha);
@@ -363,7 +383,22 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
   }
   txb_x += Qbx[0] + Ibx[0];
   txb_y += Qby[0] + Iby[0];
-  if (WG) {
+  if (WG && !UNI) {
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const bool any = (rn_x[j] != 0.f) | (rn_y[j] != 0.f) | (rc[j] != 0.f) |
+                       (rt0[j] != 0.f) | (rl[j] != 0.f);
+      if (any) {
+        float* dst = &s.acc[cd.w[j - 1] * VJP_SLOTS];
+        atomicAdd(dst + S_NX, rn_x[j]);
+        atomicAdd(dst + S_NY, rn_y[j]);
+        atomicAdd(dst + S_C, rc[j]);
+        atomicAdd(dst + S_T0, rt0[j]);
+        atomicAdd(dst + S_LEN, rl[j]);
+      }
+    }
+  }
+  if (WG && UNI) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 1; j <= K; ++j) {
@@ -422,10 +457,81 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
     for (long long c = c0; c < c1; ++c) {
       const Cand cd = decode_candidate(c, a.W, a.K);
       switch (cd.k) {
-        case 0: path_vjp<MODE, 0, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb_x, txb_y); break;
-        case 1: path_vjp<MODE, 1, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y); break;
-        case 2: path_vjp<MODE, 2, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y); break;
-        default: path_vjp<MODE, 3, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y); break;
+        case 0: path_vjp<MODE, 0, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb_x, txb_y); break;
+        case 1: path_vjp<MODE, 1, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y); break;
+        case 2: path_vjp<MODE, 2, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y); break;
+        default: path_vjp<MODE, 3, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y); break;
+      }
+    }
+  }
+  txb_x = warp_sum(txb_x);
+  txb_y = warp_sum(txb_y);
+  if (lane == 0) {
+    a.warp_tx[2 * gwarp] = txb_x;
+    a.warp_tx[2 * gwarp + 1] = txb_y;
+  }
+  if (WG) {
+    __syncthreads();
+    float* out = a.cta_walls + (size_t)blockIdx.x * a.W * VJP_SLOTS;
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) out[i] = s.acc[i];
+  }
+}
+
+// Adjoint of the min-power loss: loss = -P[argmin], so the gradient is
+// -grad_loss * dP[argmin]/d(tx, walls) for one receiver.  Here the lanes of a
+// warp hold 32 consecutive candidates of that receiver (one unit = 32
+// candidates); candidates are ordered by reflection count, so a unit spans at
+// most a few orders, and the warp runs each order present with the lanes of
+// other orders idle (weight 0 on a stand-in candidate of that order).
+template <int MODE, bool WG>
+__global__ void __launch_bounds__(256) vjp_rx_kernel(const VjpArgs a) {
+  extern __shared__ float4 smem[];
+  VSmem s;
+  s.G = smem;
+  s.E = smem + a.W;
+  s.T = smem + 2 * a.W;
+  s.acc = reinterpret_cast<float*>(smem + 3 * a.W);
+  for (int w = threadIdx.x; w < a.W; w += blockDim.x) {
+    const WallGeom g = wall_geometry(a.walls[w]);
+    s.G[w] = g.G;
+    s.E[w] = g.E;
+    s.T[w] = g.T;
+  }
+  if (WG)
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) s.acc[i] = 0.f;
+  __syncthreads();
+
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  int ri = __ldg(a.rx_index);
+  ri = ri < 0 ? 0 : (ri >= a.R ? (int)a.R - 1 : ri);
+  const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + ri);
+  const float g = -(a.grad_loss ? __ldg(a.grad_loss) : 1.0f);
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  const long long n_units = (a.n_cand + 31) / 32;
+  float txb_x = 0.f, txb_y = 0.f;
+  for (long long u = gwarp; u < n_units; u += nwarps) {
+    const long long c = u * 32 + lane;
+    const bool live = c < a.n_cand;
+    const Cand mine = decode_candidate(live ? c : a.n_cand - 1, a.W, a.K);
+    const int k_lo = decode_candidate(u * 32, a.W, a.K).k;
+    const int k_hi = decode_candidate(min(u * 32 + 31, a.n_cand - 1), a.W, a.K).k;
+    for (int k = k_lo; k <= k_hi; ++k) {
+      const bool use = live && mine.k == k;
+      Cand cd = mine;
+      if (!use) {   // stand-in of order k: walls 0, 1, 0, ... (never two equal in a row)
+        cd.k = k;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) cd.w[j] = (j & 1) ? (a.W > 1 ? 1 : 0) : 0;
+      }
+      const float gl = use ? g : 0.f;
+      switch (k) {
+        case 0: path_vjp<MODE, 0, WG, false>(s, a.W, tx, q, cd, a.alpha, a.gk[0], gl, txb_x, txb_y); break;
+        case 1: path_vjp<MODE, 1, WG, false>(s, a.W, tx, q, cd, a.alpha, a.gk[1], gl, txb_x, txb_y); break;
+        case 2: path_vjp<MODE, 2, WG, false>(s, a.W, tx, q, cd, a.alpha, a.gk[2], gl, txb_x, txb_y); break;
+        default: path_vjp<MODE, 3, WG, false>(s, a.W, tx, q, cd, a.alpha, a.gk[3], gl, txb_x, txb_y); break;
       }
     }
   }
@@ -512,7 +618,10 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpArgs a, int 
 
 template <int MODE, bool WG>
 void launch_vjp_t(const VjpArgs& a, int ctas, int threads, size_t smem, cudaStream_t st) {
-  vjp_kernel<MODE, WG><<<ctas, threads, smem, st>>>(a);
+  if (a.rx_index)
+    vjp_rx_kernel<MODE, WG><<<ctas, threads, smem, st>>>(a);
+  else
+    vjp_kernel<MODE, WG><<<ctas, threads, smem, st>>>(a);
 }
 
 }  // namespace
@@ -563,6 +672,8 @@ cudaError_t vjp_set_smem_limit(int W) {
   cudaError_t e = cudaSuccess;
 #define DRT_SET(M, B, S)                                                                    \
   e = cudaFuncSetAttribute(vjp_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
+  if (e != cudaSuccess) return e;                                                           \
+  e = cudaFuncSetAttribute(vjp_rx_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
   if (e != cudaSuccess) return e;
   DRT_SET(MODE_SIGMOID, false, s0)
   DRT_SET(MODE_SIGMOID, true, s1)

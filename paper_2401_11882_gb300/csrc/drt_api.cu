@@ -283,6 +283,8 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
     return fail(DRT_ERR_WORKSPACE, "vjp needs %zu aligned workspace bytes, got %zu", need,
                 workspace_bytes);
   VjpArgs a;
+  a.rx_index = nullptr;
+  a.grad_loss = nullptr;
   a.walls = reinterpret_cast<const float4*>(scene->walls);
   a.W = scene->n_walls;
   a.rx = scene->rx;
@@ -305,6 +307,50 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
   cudaError_t e = launch_vjp(a, scene->smoothing, d.ctas, d.threads,
                              static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
+  return DRT_OK;
+}
+
+drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const int32_t* argmin,
+                            const float* grad_loss, float* grad_tx, float* grad_walls,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!argmin || !grad_tx) return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  if (scene->n_rx < 1) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 1", scene->n_rx);
+  if (grad_walls && !aligned(grad_walls, 16))
+    return fail(DRT_ERR_INVALID_ARG, "grad_walls must be 16-byte aligned");
+  Decomp d;
+  if ((st = decompose(scene, tile, VJP, &d)) != DRT_OK) return st;
+  const size_t need = vjp_workspace(scene, d);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
+    return fail(DRT_ERR_WORKSPACE, "min-loss vjp needs %zu aligned workspace bytes, got %zu",
+                need, workspace_bytes);
+  VjpArgs a;
+  a.walls = reinterpret_cast<const float4*>(scene->walls);
+  a.W = scene->n_walls;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = 32;
+  a.n_chunks = (d.n_cand + 31) / 32;
+  a.n_tiles = 1;
+  a.n_units = a.n_chunks;
+  a.grad_power = nullptr;
+  a.rx_index = argmin;
+  a.grad_loss = grad_loss;
+  float* ws = static_cast<float*>(workspace);
+  a.cta_walls = ws;
+  a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.grad_tx = grad_tx;
+  a.grad_walls = grad_walls;
+  cudaError_t e = launch_vjp(a, scene->smoothing, d.ctas, d.threads,
+                             static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "min-loss vjp launch");
   return DRT_OK;
 }
 

@@ -49,7 +49,9 @@ struct VjpArgs {
   long long n_cand;
   int chunk;
   long long n_chunks, n_tiles, n_units;
-  const float* grad_power;   // [R]
+  const float* grad_power;   // [R] (receiver-tile kernel)
+  const int32_t* rx_index;   // [1]: one-receiver kernel (min-loss adjoint) when non-null
+  const float* grad_loss;    // [1] or null (one-receiver kernel)
   float* cta_walls;          // [ctas][W][9] per-CTA wall-gradient partials (wall gradient only)
   float* warp_tx;            // [ctas * warps_per_cta][2]
   float* grad_tx;            // [2]

@@ -133,6 +133,54 @@ def vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, grad_power:
     return gtx, gw
 
 
+def min_loss_vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str,
+                 argmin: torch.Tensor, grad_loss: torch.Tensor | None = None,
+                 refl_coef: float = 0.5, wall_grad: bool = True,
+                 tile: TileConfig | None = None):
+    """Gradient of loss = -power[argmin] w.r.t. (tx, walls), times grad_loss (default 1)."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    if argmin.dtype != torch.int32 or not argmin.is_cuda:
+        raise TypeError("argmin must be an int32 CUDA tensor")
+    gl = None if grad_loss is None else _as_f32(grad_loss.reshape(1, 1), 1, "grad_loss", 4)
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_vjp_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    gtx = torch.empty(2, dtype=torch.float32, device=dev)
+    gw = torch.empty(sc.n_walls, 4, dtype=torch.float32, device=dev) if wall_grad else None
+    _lib.call("drt_min_loss_vjp", ctypes.byref(sc), tlp, _ptr(argmin.contiguous()),
+              None if gl is None else _ptr(gl), _ptr(gtx), None if gw is None else _ptr(gw),
+              _ptr(ws), ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return gtx, gw
+
+
+class ObjectiveFunction(torch.autograd.Function):
+    """loss = -min_r P_r(walls, tx), with the one-receiver min-loss adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile):
+        P = forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
+        loss_v, arg = min_loss(P)
+        ctx.save_for_backward(walls, tx, rx, arg)
+        ctx.args = (max_order, alpha, smoothing, refl_coef, tile)
+        return loss_v.reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        walls, tx, rx, arg = ctx.saved_tensors
+        max_order, alpha, smoothing, refl_coef, tile = ctx.args
+        need_w, need_tx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_w or need_tx):
+            return (None,) * 8
+        gtx, gw = min_loss_vjp(walls, tx, rx, max_order, alpha, smoothing, arg,
+                               grad_loss.reshape(1).float().contiguous(), refl_coef,
+                               wall_grad=need_w, tile=tile)
+        return (gw if need_w else None, gtx.reshape(tx.shape) if need_tx else None,
+                None, None, None, None, None, None)
+
+
 class PowerFunction(torch.autograd.Function):
     """power = P(walls, tx) with the hand-written adjoint as backward.
 
@@ -186,8 +234,8 @@ def loss(power_values: torch.Tensor) -> torch.Tensor:
 
 def objective(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", refl_coef=0.5,
               tile=None):
-    """loss(power(...)) as one differentiable call."""
-    return loss(power(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile))
+    """loss(power(...)) = -min_r P_r as one differentiable call (min-loss adjoint backward)."""
+    return ObjectiveFunction.apply(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
 
 
 def objective_host(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", refl_coef=0.5,
@@ -200,9 +248,8 @@ def objective_host(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", re
     r = torch.as_tensor(rx).to(dev, non_blocking=True)
     p = forward(w, t, r, max_order, alpha, smoothing, refl_coef, tile)
     l, arg = min_loss(p)
-    g = min_loss_backward(arg, None, p.shape[0])
-    gtx, gw = vjp(w, t, r, max_order, alpha, smoothing, g, refl_coef, wall_grad=grad_walls,
-                  tile=tile)
+    gtx, gw = min_loss_vjp(w, t, r, max_order, alpha, smoothing, arg, None, refl_coef,
+                           wall_grad=grad_walls, tile=tile)
     out = [l.to("cpu", non_blocking=True), p.to("cpu", non_blocking=True),
            gtx.to("cpu", non_blocking=True)]
     if grad_walls:

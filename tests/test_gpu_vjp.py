@@ -162,3 +162,44 @@ def test_vjp_deterministic_tx(drt):
     a, _ = _vjp(drt, sc, g, wall_grad=False)
     b, _ = _vjp(drt, sc, g, wall_grad=False)
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha,smoothing", CASES)
+def test_min_loss_vjp_matches_oracle(drt, oracle_mod, seed, W, R, K, alpha, smoothing):
+    # loss = -P[argmin]: the one-receiver kernel (lanes = candidates) against the oracle
+    rng = np.random.default_rng(100 + seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, smoothing, boundary=(seed % 2 == 0))
+    w, t, r = _tensors(sc)
+    P = drt.forward(w, t, r, sc.max_order, sc.alpha, sc.smoothing)
+    loss, am = drt.min_loss(P)
+    gl = torch.tensor([0.75], device=w.device)
+    gtx, gw = drt.min_loss_vjp(w, t, r, sc.max_order, sc.alpha, sc.smoothing, am, gl)
+    torch.cuda.synchronize()
+    g = np.zeros(sc.n_rx)
+    g[int(am)] = -0.75
+    ref = _oracle_grad(oracle_mod, sc, g)
+    assert_grad_close(gtx.cpu().numpy(), ref[:2], "grad_tx")
+    assert_grad_close(gw.cpu().numpy().ravel(), ref[2:], "grad_walls")
+    # and the receiver-tile kernel with the same one-hot weight
+    gtx2, gw2 = _vjp(drt, sc, g)
+    np.testing.assert_allclose(gtx.cpu().numpy(), gtx2, rtol=1e-5, atol=1e-6 * np.abs(gtx2).max())
+
+
+def test_min_loss_vjp_large_scene(drt, oracle_mod):
+    # the benchmark step's gradient: 64 walls, 256 x 256 receivers, K <= 2, alpha = 100
+    sc = scenes.large_scene(alpha=100.0, smoothing="hard_sigmoid")
+    w, t, r = _tensors(sc)
+    P = drt.forward(w, t, r, 2, 100.0, "hard_sigmoid")
+    loss, am = drt.min_loss(P)
+    gtx, gw = drt.min_loss_vjp(w, t, r, 2, 100.0, "hard_sigmoid", am)
+    torch.cuda.synchronize()
+    i = int(am)
+    Pref = oracle_mod.power(sc.walls, sc.tx, sc.rx[i:i + 1], 2, 100.0, "hard_sigmoid")
+    assert float(loss) == pytest.approx(-Pref[0], rel=1e-4)
+    coords = np.random.default_rng(1).choice(4 * sc.n_walls, 12, replace=False)
+    sub = sc.replace(rx=sc.rx[i:i + 1])
+    ref = _oracle_grad(oracle_mod, sub, np.array([-1.0]), [0, 1] + [2 + int(c) for c in coords])
+    assert_grad_close(gtx.cpu().numpy(), ref[:2], "grad_tx")
+    got = gw.cpu().numpy().ravel()[coords]
+    np.testing.assert_allclose(got, ref[2:], rtol=1e-3,
+                               atol=1e-6 * max(np.abs(ref).max(), 1e-30))
