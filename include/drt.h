@@ -147,6 +147,76 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
                             const float* grad_loss, float* grad_tx, float* grad_walls,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+   Batched gradient descent on the TX position (Sec. VII, antenna placement),
+   for many scenes of uneven size, each with several starting positions.
+   A problem is (scene s, start t); each step evaluates the received power of
+   every receiver of every problem, the loss -min_r P_r (Eq. 8), its gradient
+   w.r.t. the TX by the adjoint of the argmin receiver, and one Adam update of
+   the TX, clamped to a box.  One step is captured once into a CUDA graph and
+   replayed.  Usage: drt_batch_plan_create -> drt_batch_workspace_size ->
+   drt_batch_bind -> drt_batch_run (any number of times) ->
+   drt_batch_plan_destroy.  Results are deterministic (fixed summation order).
+   ------------------------------------------------------------------------ */
+typedef struct {
+  const float* walls;            /* device [sum_s W_s][4], 16-byte aligned, scene after scene */
+  const int32_t* wall_off;       /* device [n_scenes + 1]: scene s owns walls wall_off[s] .. wall_off[s+1]-1 */
+  const float* rx;               /* device [sum_s R_s][2], 8-byte aligned */
+  const int32_t* rx_off;         /* device [n_scenes + 1] */
+  const int32_t* max_order;      /* device [n_scenes]: K of each scene, 0..DRT_MAX_ORDER */
+  const int32_t* wall_off_host;  /* host copies of the three arrays above, used to plan the work */
+  const int32_t* rx_off_host;
+  const int32_t* max_order_host;
+  int32_t n_scenes;              /* S >= 1; each scene needs 1 <= W <= DRT_MAX_WALLS, R >= 1 */
+  int32_t n_tx;                  /* T >= 1 starting positions per scene */
+  int32_t smoothing;             /* drt_smoothing */
+  float refl_coef;               /* Gamma */
+} drt_batch;
+
+typedef struct {
+  float* tx;                     /* device [S][T][2], in/out: TX positions */
+  float* adam_m;                 /* device [S][T][2], in/out: Adam first moments (start at 0) */
+  float* adam_v;                 /* device [S][T][2], in/out: Adam second moments (start at 0) */
+  int32_t* step;                 /* device [1], in/out: steps taken so far (Adam's t - 1) */
+  float* loss;                   /* device [S][T], out: loss of the latest step, before its update */
+  float* loss_history;           /* device [history_len][S][T] or NULL: row i = loss of step i */
+  int32_t history_len;
+  const float* alpha_schedule;   /* device [n_alpha]: alpha of step i = schedule[min(i, n_alpha - 1)] */
+  int32_t n_alpha;               /* >= 1 */
+  float lr, beta1, beta2, eps;   /* Adam */
+  float lo_x, lo_y, hi_x, hi_y;  /* the TX is clamped to this box after every update */
+} drt_descent_state;
+
+typedef struct drt_batch_plan drt_batch_plan;
+
+/* Plans the work of a batch (host memory only): validates the host copies of
+   the offsets, orders the forward work longest first, sizes the workspace.
+   tile: warps_per_cta (1..8) and ctas_per_sm are used; NULL for defaults.
+   *plan receives a handle owned by the caller (drt_batch_plan_destroy). */
+drt_status drt_batch_plan_create(const drt_batch* batch, const drt_tile* tile,
+                                 drt_batch_plan** plan);
+
+/* Device workspace the plan needs (bytes, 256-byte aligned). */
+drt_status drt_batch_workspace_size(const drt_batch_plan* plan, size_t* bytes);
+
+/* Binds the descent state and workspace to the plan: copies the work tables
+   into the workspace (on `stream`) and captures one step into a CUDA graph on
+   a stream the plan owns.  The batch's and the state's arrays and the
+   workspace must stay valid while the plan is used. */
+drt_status drt_batch_bind(drt_batch_plan* plan, const drt_descent_state* state, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Enqueues n_steps descent steps on `stream`: graph replays when use_graph is
+   non-zero, direct kernel launches otherwise (same results). */
+drt_status drt_batch_run(drt_batch_plan* plan, int32_t n_steps, int32_t use_graph, void* stream);
+
+/* Plan facts (host out, 8 values): problems, forward units, adjoint units,
+   forward CTAs, adjoint CTAs, largest W, receivers x starts, threads per CTA. */
+drt_status drt_batch_plan_info(const drt_batch_plan* plan, int64_t* info);
+
+/* Releases the plan (its graph and stream); NULL is accepted. */
+drt_status drt_batch_plan_destroy(drt_batch_plan* plan);
+
 /* Size of the static device scratch array behind drt_forward_noalloc. */
 #define DRT_NOALLOC_SCRATCH_BYTES (8u << 20)
 

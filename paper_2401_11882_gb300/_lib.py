@@ -35,6 +35,25 @@ class Tile(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+class Batch(ctypes.Structure):
+    _fields_ = [("walls", ctypes.c_void_p), ("wall_off", ctypes.c_void_p), ("rx", ctypes.c_void_p),
+                ("rx_off", ctypes.c_void_p), ("max_order", ctypes.c_void_p),
+                ("wall_off_host", ctypes.c_void_p), ("rx_off_host", ctypes.c_void_p),
+                ("max_order_host", ctypes.c_void_p), ("n_scenes", ctypes.c_int32),
+                ("n_tx", ctypes.c_int32), ("smoothing", ctypes.c_int32),
+                ("refl_coef", ctypes.c_float)]
+
+
+class DescentState(ctypes.Structure):
+    _fields_ = [("tx", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("step", ctypes.c_void_p), ("loss", ctypes.c_void_p),
+                ("loss_history", ctypes.c_void_p), ("history_len", ctypes.c_int32),
+                ("alpha_schedule", ctypes.c_void_p), ("n_alpha", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("lo_x", ctypes.c_float), ("lo_y", ctypes.c_float),
+                ("hi_x", ctypes.c_float), ("hi_y", ctypes.c_float)]
+
+
 class DrtError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
@@ -55,6 +74,12 @@ SIGNATURES = {
     "drt_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_forward_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "drt_min_loss_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "drt_batch_plan_create": (ctypes.c_int, [_P, _P, _P]),
+    "drt_batch_workspace_size": (ctypes.c_int, [_P, _P]),
+    "drt_batch_bind": (ctypes.c_int, [_P, _P, _P, _SZ, _P]),
+    "drt_batch_run": (ctypes.c_int, [_P, _I32, _I32, _P]),
+    "drt_batch_plan_info": (ctypes.c_int, [_P, _P]),
+    "drt_batch_plan_destroy": (ctypes.c_int, [_P]),
 }
 
 

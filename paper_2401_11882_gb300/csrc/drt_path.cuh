@@ -1,0 +1,225 @@
+// Per-path forward evaluation shared by the single-scene and batched kernels:
+// wall staging into shared memory and the power of one path candidate for one
+// receiver (Sec. V, Eq. 7 term).
+#pragma once
+
+#include "drt_common.cuh"
+
+namespace drt {
+
+// Shared-memory layout: 4 float4 per wall, as separate arrays.
+//   sG, sE, sT: wall_geometry() records.
+//   sH: smoothing-ready record for the obstruction loop:
+//     hard    {a6 nx, a6 ny, 1/2 - a6 c, s(d(TX))}            a6 = alpha/6
+//     step    {nx, ny, -c, theta(d(TX))}
+//     sigmoid {k nx, k ny, -k c, sign(z_TX) * 2^-|z_TX|}      k = alpha log2(e)
+struct SmemWalls {
+  float4 *G, *E, *T, *H;
+};
+
+template <int MODE>
+__device__ void stage_walls(const float4* __restrict__ walls, int W, float2 tx, float alpha,
+                            SmemWalls s) {
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    const WallGeom g = wall_geometry(walls[w]);
+    s.G[w] = g.G;
+    s.E[w] = g.E;
+    s.T[w] = g.T;
+    float4 h;
+    if (MODE == MODE_HARD) {
+      const float a6 = alpha * (1.0f / 6.0f);
+      h = make_float4(g.G.x * a6, g.G.y * a6, fmaf(-g.G.z, a6, 0.5f), 0.f);
+      h.w = __saturatef(fmaf(h.x, tx.x, fmaf(h.y, tx.y, h.z)));
+    } else if (MODE == MODE_STEP) {
+      h = make_float4(g.G.x, g.G.y, -g.G.z, 0.f);
+      h.w = fmaf(h.x, tx.x, fmaf(h.y, tx.y, h.z)) > 0.f ? 1.f : 0.f;
+    } else {
+      const float kap = alpha * LOG2E;
+      h = make_float4(g.G.x * kap, g.G.y * kap, -g.G.z * kap, 0.f);
+      const float z = fmaf(h.x, tx.x, fmaf(h.y, tx.y, h.z));
+      h.w = copysignf(ex2_approx(-fabsf(z)), z);
+    }
+    s.H[w] = h;
+  }
+}
+
+// s() of an argument already scaled and offset by the H record (hard: sat; step: theta).
+template <int MODE>
+__device__ __forceinline__ float side(float z) {
+  if (MODE == MODE_HARD) return __saturatef(z);
+  return z > 0.f ? 1.f : 0.f;
+}
+
+// Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
+template <int MODE, int K>
+__device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
+                                            const Cand& cd, float alpha, float gk, int cull) {
+  // --- image method (Sec. V-B): TX images in the walls of the sequence.
+  float Ix[K + 1], Iy[K + 1];
+  Ix[0] = tx.x;
+  Iy[0] = tx.y;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float d = line_dist(G, Ix[j - 1], Iy[j - 1]);
+    Ix[j] = fmaf(-2.f * d, G.x, Ix[j - 1]);
+    Iy[j] = fmaf(-2.f * d, G.y, Iy[j - 1]);
+  }
+  // --- backtrace on the infinite lines: Q_{K+1} = RX, Q_j = line(Q_{j+1}, I_j) x wall j.
+  float Qx[K + 2], Qy[K + 2];
+  Qx[0] = tx.x;
+  Qy[0] = tx.y;
+  Qx[K + 1] = rx.x;
+  Qy[K + 1] = rx.y;
+  bool degenerate = false;
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float a = line_dist(G, Ix[j], Iy[j]);
+    const float b = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    // parallel lines (or a reflection point absurdly far away): no path
+    float t = __fdiv_rn(b, b - a);
+    if (!(fabsf(t) <= 1e8f)) {
+      degenerate = true;
+      t = 0.f;
+    }
+    Qx[j] = fmaf(t, Ix[j] - Qx[j + 1], Qx[j + 1]);
+    Qy[j] = fmaf(t, Iy[j] - Qy[j + 1], Qy[j + 1]);
+  }
+  // --- legs: length and the smoothing-ready normal form of each leg's line.
+  float L = 0.f;
+  float mx[K + 1], my[K + 1], mc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float len2 = fmaf(dx, dx, dy * dy);
+    degenerate |= !(len2 > 0.f);
+    const float inv = rsqrtf(len2);
+    L = fmaf(len2, inv, L);
+    const float nx = -dy * inv, ny = dx * inv;
+    const float nq = fmaf(nx, Qx[j], ny * Qy[j]);
+    if (MODE == MODE_HARD) {
+      const float a6 = alpha * (1.0f / 6.0f);
+      mx[j] = nx * a6;
+      my[j] = ny * a6;
+      mc[j] = fmaf(-nq, a6, 0.5f);
+    } else if (MODE == MODE_STEP) {
+      mx[j] = nx;
+      my[j] = ny;
+      mc[j] = -nq;
+    } else {
+      const float kap = alpha * LOG2E;
+      mx[j] = nx * kap;
+      my[j] = ny * kap;
+      mc[j] = -nq * kap;
+    }
+  }
+  // --- continuous validity of each reflection (Sec. V-A): on the segment, and the
+  //     previous and next vertices on the same side of the wall's line.
+  float V = 1.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 G = s.G[w];
+    const float t0 = s.T[w].x;
+    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -t0));   // u = (ny, -nx)
+    const Smooth3 s1 = smooth3<MODE>(tau, alpha);
+    const Smooth3 s2 = smooth3<MODE>(G.w - tau, alpha);
+    const Smooth3 sp = smooth3<MODE>(line_dist(G, Qx[j - 1], Qy[j - 1]), alpha);
+    const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
+    V *= s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+  }
+  // optional: skip the obstruction loop when the whole warp's validity is exactly 0
+  if (cull && __all_sync(0xffffffffu, V == 0.f || degenerate)) return 0.f;
+  // --- obstruction of every leg by every wall except the ones its end points lie on.
+  float vis[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) vis[j] = 1.f;
+
+  if constexpr (MODE != MODE_SIGMOID) {
+    // blocked = X(x1, y1) X(x2, y2) with X(x, y) = s(x) s(-y) + s(-x) s(y) = s_x + s_y (1 - 2 s_x).
+#pragma unroll 2
+    for (int w = 0; w < W; ++w) {
+      const float4 h = s.H[w];
+      const float4 e = s.E[w];
+      float sv[K + 2], uv[K + 1];
+      sv[0] = h.w;
+      uv[0] = fmaf(-2.f, h.w, 1.f);
+#pragma unroll
+      for (int i = 1; i <= K + 1; ++i) sv[i] = side<MODE>(fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z)));
+#pragma unroll
+      for (int i = 1; i <= K; ++i) uv[i] = fmaf(-2.f, sv[i], 1.f);
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        const float sa = side<MODE>(fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j])));
+        const float sb = side<MODE>(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
+        const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
+        const float x1 = fmaf(sv[j + 1], uv[j], sv[j]);
+        float bl = x1 * x2;
+        const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+        bl = skip ? 0.f : bl;
+        vis[j] = fmaf(-vis[j], bl, vis[j]);
+      }
+    }
+  } else {
+    // Sigmoid: with e = 2^-|z| <= 1 per argument, for a pair (x, y)
+    //   Ns = e_x + e_y, No = 1 + e_x e_y, D = (1 + e_x)(1 + e_y) = Ns + No,
+    //   X = (same sign ? Ns : No) / D and 1 - X = (same sign ? No : Ns) / D,
+    // and 1 - X1 X2 = (Xb1 D2 + X1 Xb2) / (D1 D2) in numerators: every term is a
+    // sum of non-negative products, so a nearly blocked leg keeps its relative
+    // accuracy.  Numerator and denominator products are folded into vis every 8 walls.
+    float vn[K + 1], vd[K + 1];
+#pragma unroll
+    for (int j = 0; j <= K; ++j) vn[j] = vd[j] = 1.f;
+    for (int w0 = 0; w0 < W; w0 += 8) {
+      const int w1 = min(w0 + 8, W);
+      for (int w = w0; w < w1; ++w) {
+        const float4 h = s.H[w];
+        const float4 e = s.E[w];
+        float ze[K + 2], ee[K + 2];
+        ze[0] = h.w;
+        ee[0] = fabsf(h.w);
+#pragma unroll
+        for (int i = 1; i <= K + 1; ++i) {
+          ze[i] = fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
+          ee[i] = ex2_approx(-fabsf(ze[i]));
+        }
+#pragma unroll
+        for (int j = 0; j <= K; ++j) {
+          const float za = fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+          const float zb = fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
+          const float ea = ex2_approx(-fabsf(za));
+          const float eb = ex2_approx(-fabsf(zb));
+          // pair 1: the leg's end points w.r.t. the wall's line
+          const float ns1 = ee[j] + ee[j + 1];
+          const float no1 = fmaf(ee[j], ee[j + 1], 1.f);
+          const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+          const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
+          // pair 2: the wall's end points w.r.t. the leg's line
+          const float ns2 = ea + eb;
+          const float no2 = fmaf(ea, eb, 1.f);
+          const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+          const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+          const float den = (ns1 + no1) * (ns2 + no2);
+          float num = fmaf(xb1, ns2 + no2, x1 * xb2);
+          const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+          num = skip ? den : num;
+          vn[j] *= num;
+          vd[j] *= den;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        vis[j] *= __fdividef(vn[j], vd[j]);
+        vn[j] = vd[j] = 1.f;
+      }
+    }
+  }
+  float p = V * gk;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) p *= vis[j];
+  p = __fdiv_rn(p, L * L);
+  return degenerate ? 0.f : p;
+}
+
+}  // namespace drt

@@ -1,0 +1,405 @@
+// Per-path adjoint shared by the single-scene and batched adjoint kernels:
+// recompute one path candidate for one receiver and push the adjoint of its
+// power into the transmitter, the path vertices and the walls (Sec. III:
+// gradient of the loss with respect to the scene parameters).
+#pragma once
+
+#include "drt_common.cuh"
+#include "drt_internal.h"
+
+namespace drt {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Slots of the per-wall accumulator.
+enum : int { S_NX = 0, S_NY, S_C, S_AX, S_AY, S_BX, S_BY, S_T0, S_LEN };
+
+struct VSmem {
+  float4 *G, *E, *T;
+  float* acc;   // [W][VJP_SLOTS] (wall gradient only)
+};
+
+// One leg x wall factor f = 1 - X(x1, y1) X(x2, y2), written as
+// Xb1 + X1 Xb2 with Xb = 1 - X = s(x) s(y) + s(-x) s(-y), and its partials.
+struct LegWall {
+  float f, dx1, dy1, dx2, dy2;
+};
+
+template <int MODE, bool GRAD>
+__device__ __forceinline__ LegWall leg_wall(float x1, float y1, float x2, float y2, float alpha) {
+  const Smooth3 a = smooth3<MODE>(x1, alpha), b = smooth3<MODE>(y1, alpha);
+  const Smooth3 c = smooth3<MODE>(x2, alpha), d = smooth3<MODE>(y2, alpha);
+  const float X1 = fmaf(a.s, b.sb, a.sb * b.s), Xb1 = fmaf(a.s, b.s, a.sb * b.sb);
+  const float X2 = fmaf(c.s, d.sb, c.sb * d.s), Xb2 = fmaf(c.s, d.s, c.sb * d.sb);
+  LegWall r;
+  r.f = fmaf(X1, Xb2, Xb1);
+  if (GRAD) {
+    // df/dX1 = -X2, df/dX2 = -X1; dX/dx = s'(x) (s(-y) - s(y)), dX/dy = s'(y) (s(-x) - s(x))
+    r.dx1 = -X2 * a.ds * (b.sb - b.s);
+    r.dy1 = -X2 * b.ds * (a.sb - a.s);
+    r.dx2 = -X1 * c.ds * (d.sb - d.s);
+    r.dy2 = -X1 * d.ds * (c.sb - c.s);
+  } else {
+    r.dx1 = r.dy1 = r.dx2 = r.dy2 = 0.f;
+  }
+  return r;
+}
+
+// UNI: the candidate is the same in all 32 lanes (lanes hold receivers), so the
+// adjoints of the reflecting walls can be summed over the warp; otherwise (lanes
+// hold different candidates of one receiver) each lane adds its own.
+template <int MODE, int K, bool WG, bool UNI>
+__device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float2 rx,
+                                         const Cand& cd, float alpha, float gk, float g,
+                                         float& txb_x, float& txb_y) {
+  // ------------------------------------------------ forward recompute (guarded)
+  float Ix[K + 1], Iy[K + 1], dimg[K + 1];
+  Ix[0] = tx.x;
+  Iy[0] = tx.y;
+  dimg[0] = 0.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    dimg[j] = line_dist(G, Ix[j - 1], Iy[j - 1]);
+    Ix[j] = fmaf(-2.f * dimg[j], G.x, Ix[j - 1]);
+    Iy[j] = fmaf(-2.f * dimg[j], G.y, Iy[j - 1]);
+  }
+  float Qx[K + 2], Qy[K + 2], ta[K + 1], tb[K + 1], tt[K + 1];
+  Qx[0] = tx.x;
+  Qy[0] = tx.y;
+  Qx[K + 1] = rx.x;
+  Qy[K + 1] = rx.y;
+  bool degenerate = false;
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    ta[j] = line_dist(G, Ix[j], Iy[j]);
+    tb[j] = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    float t = __fdiv_rn(tb[j], tb[j] - ta[j]);
+    if (!(fabsf(t) <= 1e8f)) {
+      degenerate = true;
+      t = 0.f;
+    }
+    tt[j] = t;
+    Qx[j] = fmaf(t, Ix[j] - Qx[j + 1], Qx[j + 1]);
+    Qy[j] = fmaf(t, Iy[j] - Qy[j + 1], Qy[j + 1]);
+  }
+  float mx[K + 1], my[K + 1], mq[K + 1], len[K + 1];
+  float L = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float len2 = fmaf(dx, dx, dy * dy);
+    float inv = 0.f;
+    if (len2 > 0.f) {
+      inv = rsqrtf(len2);
+    } else {
+      degenerate = true;
+    }
+    len[j] = len2 * inv;
+    L += len[j];
+    mx[j] = -dy * inv;
+    my[j] = dx * inv;
+    mq[j] = fmaf(mx[j], Qx[j], my[j] * Qy[j]);
+  }
+  if (degenerate) {
+    g = 0.f;
+    L = 1.f;
+  }
+  float V[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 G = s.G[w];
+    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -s.T[w].x));
+    const Smooth3 s1 = smooth3<MODE>(tau, alpha), s2 = smooth3<MODE>(G.w - tau, alpha);
+    const Smooth3 sp = smooth3<MODE>(line_dist(G, Qx[j - 1], Qy[j - 1]), alpha);
+    const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
+    V[j] = s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+  }
+  // A path with an exactly-zero factor has an exactly-zero gradient: a zero
+  // validity or visibility factor is a saturated smoothing (derivative 0, also
+  // at the hard sigmoid's kinks by convention) or an FP32 underflow of the
+  // sigmoid, and every other factor's adjoint carries the zero.  Such lanes get
+  // weight 0, and a warp whose lanes are all such skips the rest.
+  bool dead = degenerate || g == 0.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) dead |= (V[j] == 0.f);
+  if (__all_sync(FULL, dead)) return;
+  // sweep 1: visibility as (product of non-zero factors, number of zero factors)
+  float nz[K + 1];
+  int zc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    nz[j] = 1.f;
+    zc[j] = 0;
+  }
+  for (int w = 0; w < W; ++w) {
+    const float4 G = s.G[w];
+    const float4 E = s.E[w];
+    float dv[K + 2];
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) dv[i] = line_dist(G, Qx[i], Qy[i]);
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+      if (skip) continue;
+      const float x2 = fmaf(mx[j], E.x, fmaf(my[j], E.y, -mq[j]));
+      const float y2 = fmaf(mx[j], E.z, fmaf(my[j], E.w, -mq[j]));
+      const float f = leg_wall<MODE, false>(dv[j], dv[j + 1], x2, y2, alpha).f;
+      if (f == 0.f) {
+        zc[j] += 1;
+      } else {
+        nz[j] *= f;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j <= K; ++j) dead |= (zc[j] != 0);
+  if (__all_sync(FULL, dead)) return;
+  if (dead) g = 0.f;
+  // ------------------------------------------------ factor adjoints
+  // p = C * prod(F), C = Gamma^k / L^2, F = {V_1..V_K, vis_0..vis_K}
+  constexpr int NF = 2 * K + 1;
+  float F[NF];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) F[j - 1] = V[j];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) F[K + j] = zc[j] ? 0.f : nz[j];
+  float pre[NF + 1], suf[NF + 1];
+  pre[0] = 1.f;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) pre[i + 1] = pre[i] * F[i];
+  suf[NF] = 1.f;
+#pragma unroll
+  for (int i = NF - 1; i >= 0; --i) suf[i] = suf[i + 1] * F[i];
+  const float C = __fdiv_rn(gk, L * L);
+  const float p = C * pre[NF];
+  const float gC = g * C;
+  float Vb[K + 1], visb[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) Vb[j] = gC * pre[j - 1] * suf[j];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) visb[j] = gC * pre[K + j] * suf[K + j + 1];
+  const float Lb = -2.f * g * __fdiv_rn(p, L);
+
+  // ------------------------------------------------ sweep 2: obstruction adjoint
+  // legs whose visibility adjoint is zero in every lane contribute nothing here
+  bool live_leg[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) live_leg[j] = __any_sync(FULL, visb[j] != 0.f);
+  float Qbx[K + 2], Qby[K + 2], mAx[K + 1], mAy[K + 1], sm[K + 1];
+#pragma unroll
+  for (int i = 0; i <= K + 1; ++i) Qbx[i] = Qby[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) mAx[j] = mAy[j] = sm[j] = 0.f;
+
+  for (int w = 0; w < W; ++w) {
+    const float4 G = s.G[w];
+    const float4 E = s.E[w];
+    float dv[K + 2], vb[K + 2];
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) {
+      dv[i] = line_dist(G, Qx[i], Qy[i]);
+      vb[i] = 0.f;
+    }
+    float Abx = 0.f, Aby = 0.f, Bbx = 0.f, Bby = 0.f;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+      if (skip || !live_leg[j]) continue;
+      const float x2 = fmaf(mx[j], E.x, fmaf(my[j], E.y, -mq[j]));
+      const float y2 = fmaf(mx[j], E.z, fmaf(my[j], E.w, -mq[j]));
+      const LegWall lw = leg_wall<MODE, true>(dv[j], dv[j + 1], x2, y2, alpha);
+      // d vis / d f = product of the other factors
+      float dvis;
+      if (zc[j] == 0) {
+        dvis = __fdividef(nz[j], lw.f);
+      } else {
+        dvis = (zc[j] == 1 && lw.f == 0.f) ? nz[j] : 0.f;
+      }
+      const float fb = visb[j] * dvis;
+      vb[j] = fmaf(fb, lw.dx1, vb[j]);
+      vb[j + 1] = fmaf(fb, lw.dy1, vb[j + 1]);
+      const float x2b = fb * lw.dx2, y2b = fb * lw.dy2;
+      // x2 = m . (A - Q_j), y2 = m . (B - Q_j)
+      mAx[j] = fmaf(x2b, E.x, fmaf(y2b, E.z, mAx[j]));
+      mAy[j] = fmaf(x2b, E.y, fmaf(y2b, E.w, mAy[j]));
+      sm[j] += x2b + y2b;
+      if (WG) {
+        Abx = fmaf(x2b, mx[j], Abx);
+        Aby = fmaf(x2b, my[j], Aby);
+        Bbx = fmaf(y2b, mx[j], Bbx);
+        Bby = fmaf(y2b, my[j], Bby);
+      }
+    }
+    // vertex distances d(Q_i) = n . Q_i - c
+    float nbx = 0.f, nby = 0.f, cb = 0.f;
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) {
+      Qbx[i] = fmaf(vb[i], G.x, Qbx[i]);
+      Qby[i] = fmaf(vb[i], G.y, Qby[i]);
+      if (WG) {
+        nbx = fmaf(vb[i], Qx[i], nbx);
+        nby = fmaf(vb[i], Qy[i], nby);
+        cb -= vb[i];
+      }
+    }
+    if (WG) {
+      const bool any = (nbx != 0.f) | (nby != 0.f) | (cb != 0.f) | (Abx != 0.f) |
+                       (Aby != 0.f) | (Bbx != 0.f) | (Bby != 0.f);
+      if (__any_sync(FULL, any)) {
+        nbx = warp_sum(nbx);
+        nby = warp_sum(nby);
+        cb = warp_sum(cb);
+        Abx = warp_sum(Abx);
+        Aby = warp_sum(Aby);
+        Bbx = warp_sum(Bbx);
+        Bby = warp_sum(Bby);
+        const int lane = threadIdx.x & 31;
+        float v = nbx;
+        v = lane == S_NY ? nby : v;
+        v = lane == S_C ? cb : v;
+        v = lane == S_AX ? Abx : v;
+        v = lane == S_AY ? Aby : v;
+        v = lane == S_BX ? Bbx : v;
+        v = lane == S_BY ? Bby : v;
+        if (lane <= S_BY) atomicAdd(&s.acc[w * VJP_SLOTS + lane], v);
+      }
+    }
+  }
+
+  // ------------------------------------------------ legs: normals and lengths
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    // m_bar = sum x2b (A - Q_j) + y2b (B - Q_j); the -Q_j part and dx2/dQ_j = -m
+    const float mbx = mAx[j] - sm[j] * Qx[j];
+    const float mby = mAy[j] - sm[j] * Qy[j];
+    Qbx[j] -= sm[j] * mx[j];
+    Qby[j] -= sm[j] * my[j];
+    // m = (-D_y, D_x)/len: D_bar = (mb_y, -mb_x)/len - (mb . m) D/len^2 ; len_bar = Lb
+    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float il = len[j] > 0.f ? 1.f / len[j] : 0.f;
+    const float mm = fmaf(mbx, mx[j], mby * my[j]);
+    const float Dbx = fmaf(mby, il, fmaf(-mm * il * il, dx, Lb * dx * il));
+    const float Dby = fmaf(-mbx, il, fmaf(-mm * il * il, dy, Lb * dy * il));
+    Qbx[j + 1] += Dbx;
+    Qby[j + 1] += Dby;
+    Qbx[j] -= Dbx;
+    Qby[j] -= Dby;
+  }
+
+  // ------------------------------------------------ validity, backtrace, images
+  float rn_x[K + 1], rn_y[K + 1], rc[K + 1], rt0[K + 1], rl[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 G = s.G[w];
+    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -s.T[w].x));
+    const float pv = line_dist(G, Qx[j - 1], Qy[j - 1]);
+    const float qv = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    const Smooth3 s1 = smooth3<MODE>(tau, alpha), s2 = smooth3<MODE>(G.w - tau, alpha);
+    const Smooth3 sp = smooth3<MODE>(pv, alpha), sq = smooth3<MODE>(qv, alpha);
+    const float S = fmaf(sp.s, sq.s, sp.sb * sq.sb);
+    const float a1 = Vb[j] * s2.s * S, a2 = Vb[j] * s1.s * S, aS = Vb[j] * s1.s * s2.s;
+    const float taub = a1 * s1.ds - a2 * s2.ds;
+    const float pb = aS * sp.ds * (sq.s - sq.sb);
+    const float qb = aS * sq.ds * (sp.s - sp.sb);
+    rl[j] = a2 * s2.ds;
+    rt0[j] = -taub;
+    // tau = n_y Qx - n_x Qy - t0
+    Qbx[j] = fmaf(taub, G.y, Qbx[j]);
+    Qby[j] = fmaf(-taub, G.x, Qby[j]);
+    rn_x[j] = -taub * Qy[j];
+    rn_y[j] = taub * Qx[j];
+    // p = n . Q_{j-1} - c ; q = n . Q_{j+1} - c
+    Qbx[j - 1] = fmaf(pb, G.x, Qbx[j - 1]);
+    Qby[j - 1] = fmaf(pb, G.y, Qby[j - 1]);
+    Qbx[j + 1] = fmaf(qb, G.x, Qbx[j + 1]);
+    Qby[j + 1] = fmaf(qb, G.y, Qby[j + 1]);
+    rn_x[j] = fmaf(pb, Qx[j - 1], fmaf(qb, Qx[j + 1], rn_x[j]));
+    rn_y[j] = fmaf(pb, Qy[j - 1], fmaf(qb, Qy[j + 1], rn_y[j]));
+    rc[j] = -(pb + qb);
+  }
+  float Ibx[K + 1], Iby[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) Ibx[j] = Iby[j] = 0.f;
+  // backtrace, reversed: Q_j = Q_{j+1} + t (I_j - Q_{j+1}), t = b / (b - a)
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float t = tt[j];
+    const float ex = Ix[j] - Qx[j + 1], ey = Iy[j] - Qy[j + 1];
+    Qbx[j + 1] = fmaf(1.f - t, Qbx[j], Qbx[j + 1]);
+    Qby[j + 1] = fmaf(1.f - t, Qby[j], Qby[j + 1]);
+    Ibx[j] = fmaf(t, Qbx[j], Ibx[j]);
+    Iby[j] = fmaf(t, Qby[j], Iby[j]);
+    const float tbar = fmaf(Qbx[j], ex, Qby[j] * ey);
+    const float den = tb[j] - ta[j];
+    const float id2 = (den != 0.f && !degenerate) ? 1.f / (den * den) : 0.f;
+    const float abar = tbar * tb[j] * id2;
+    const float bbar = -tbar * ta[j] * id2;
+    Ibx[j] = fmaf(abar, G.x, Ibx[j]);
+    Iby[j] = fmaf(abar, G.y, Iby[j]);
+    Qbx[j + 1] = fmaf(bbar, G.x, Qbx[j + 1]);
+    Qby[j + 1] = fmaf(bbar, G.y, Qby[j + 1]);
+    rn_x[j] = fmaf(abar, Ix[j], fmaf(bbar, Qx[j + 1], rn_x[j]));
+    rn_y[j] = fmaf(abar, Iy[j], fmaf(bbar, Qy[j + 1], rn_y[j]));
+    rc[j] -= abar + bbar;
+  }
+  // image chain, reversed: I_j = I_{j-1} - 2 d n, d = n . I_{j-1} - c
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float dbar = -2.f * fmaf(Ibx[j], G.x, Iby[j] * G.y);
+    Ibx[j - 1] += fmaf(dbar, G.x, Ibx[j]);
+    Iby[j - 1] += fmaf(dbar, G.y, Iby[j]);
+    rn_x[j] = fmaf(-2.f * dimg[j], Ibx[j], fmaf(dbar, Ix[j - 1], rn_x[j]));
+    rn_y[j] = fmaf(-2.f * dimg[j], Iby[j], fmaf(dbar, Iy[j - 1], rn_y[j]));
+    rc[j] -= dbar;
+  }
+  txb_x += Qbx[0] + Ibx[0];
+  txb_y += Qby[0] + Iby[0];
+  if (WG && !UNI) {
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const bool any = (rn_x[j] != 0.f) | (rn_y[j] != 0.f) | (rc[j] != 0.f) |
+                       (rt0[j] != 0.f) | (rl[j] != 0.f);
+      if (any) {
+        float* dst = &s.acc[cd.w[j - 1] * VJP_SLOTS];
+        atomicAdd(dst + S_NX, rn_x[j]);
+        atomicAdd(dst + S_NY, rn_y[j]);
+        atomicAdd(dst + S_C, rc[j]);
+        atomicAdd(dst + S_T0, rt0[j]);
+        atomicAdd(dst + S_LEN, rl[j]);
+      }
+    }
+  }
+  if (WG && UNI) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const bool any = (rn_x[j] != 0.f) | (rn_y[j] != 0.f) | (rc[j] != 0.f) |
+                       (rt0[j] != 0.f) | (rl[j] != 0.f);
+      if (__any_sync(FULL, any)) {
+        const float a0 = warp_sum(rn_x[j]), a1 = warp_sum(rn_y[j]), a2 = warp_sum(rc[j]);
+        const float a3 = warp_sum(rt0[j]), a4 = warp_sum(rl[j]);
+        float v = a0;
+        int slot = S_NX;
+        if (lane == 1) { v = a1; slot = S_NY; }
+        if (lane == 2) { v = a2; slot = S_C; }
+        if (lane == 3) { v = a3; slot = S_T0; }
+        if (lane == 4) { v = a4; slot = S_LEN; }
+        if (lane < 5) atomicAdd(&s.acc[cd.w[j - 1] * VJP_SLOTS + slot], v);
+      }
+    }
+  }
+}
+
+}  // namespace drt
