@@ -191,7 +191,8 @@ typedef struct drt_batch_plan drt_batch_plan;
 
 /* Plans the work of a batch (host memory only): validates the host copies of
    the offsets, orders the forward work longest first, sizes the workspace.
-   tile: warps_per_cta (1..8) and ctas_per_sm are used; NULL for defaults.
+   tile: warps_per_cta (1..8), ctas_per_sm and the DRT_TILE_CULL_INVALID flag
+   are used; NULL for defaults.
    *plan receives a handle owned by the caller (drt_batch_plan_destroy). */
 drt_status drt_batch_plan_create(const drt_batch* batch, const drt_tile* tile,
                                  drt_batch_plan** plan);
@@ -210,12 +211,59 @@ drt_status drt_batch_bind(drt_batch_plan* plan, const drt_descent_state* state, 
    non-zero, direct kernel launches otherwise (same results). */
 drt_status drt_batch_run(drt_batch_plan* plan, int32_t n_steps, int32_t use_graph, void* stream);
 
+/* Evaluates the loss of every problem at its current TX (forward + min over
+   receivers, written to state->loss) without any update or step count.  With
+   tile flag DRT_TILE_CULL_INVALID the obstruction loop of paths whose validity
+   is exactly 0 for a whole warp is skipped (exact for hard sigmoid and step). */
+drt_status drt_batch_evaluate(drt_batch_plan* plan, void* stream);
+
 /* Plan facts (host out, 8 values): problems, forward units, adjoint units,
    forward CTAs, adjoint CTAs, largest W, receivers x starts, threads per CTA. */
 drt_status drt_batch_plan_info(const drt_batch_plan* plan, int64_t* info);
 
 /* Releases the plan (its graph and stream); NULL is accepted. */
 drt_status drt_batch_plan_destroy(drt_batch_plan* plan);
+
+/* ------------------------------------------------------------------------
+   Surrogate MLP of the objective over the TX position (no counterpart in the
+   paper; used to propose starting points for the exact descent).
+   x in [0,1]^2 -> Fourier features [sin(2 pi B x), cos(2 pi B x)] (B:
+   DRT_MLP_FREQS x 2) -> DRT_MLP_LAYERS x (Linear(DRT_MLP_WIDTH) + SiLU) ->
+   Linear(1).  BF16 weights and activations on the tensor cores, FP32
+   accumulation, FP32 master weights.  Flat FP32 parameter vector: W1
+   [256][64], b1 [256], W2..W4 [256][256], b2..b4 [256], w5 [256], b5 [1].
+   The BF16 "shadow" holds each W and its transpose, and w5.  batch must be a
+   positive multiple of 64.
+   ------------------------------------------------------------------------ */
+#define DRT_MLP_FREQS 32
+#define DRT_MLP_WIDTH 256
+#define DRT_MLP_LAYERS 4
+
+/* Parameter count, shadow bytes, and workspace bytes for `batch` (any NULL out is skipped). */
+drt_status drt_mlp_sizes(int32_t batch, int64_t* n_params, size_t* shadow_bytes,
+                         size_t* workspace_bytes);
+
+/* shadow <- BF16 copies of the weights of params (16-byte aligned shadow). */
+drt_status drt_mlp_shadow(const float* params, void* shadow, void* stream);
+
+/* y[b] = MLP(x[b]) for b < batch (x: [batch][2], freqs: [DRT_MLP_FREQS][2]);
+   params supplies the FP32 biases, shadow the BF16 weights (kept in sync by
+   drt_mlp_shadow / drt_mlp_adam).  workspace: 256-byte aligned, size from
+   drt_mlp_sizes. */
+drt_status drt_mlp_forward(const float* params, const void* shadow, const float* freqs,
+                           const float* x, int32_t batch, float* y, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
+/* loss[0] = mean_b (MLP(x[b]) - target[b])^2 and grad = d loss / d params
+   (flat, FP32, overwritten).  Deterministic. */
+drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const float* freqs,
+                             const float* x, const float* target, int32_t batch, float* loss,
+                             float* grad, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One Adam step on the FP32 master params with moments m, v and the device
+   step counter (incremented); refreshes the shadow when it is non-NULL. */
+drt_status drt_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t* step,
+                        float lr, float beta1, float beta2, float eps, void* shadow, void* stream);
 
 /* Size of the static device scratch array behind drt_forward_noalloc. */
 #define DRT_NOALLOC_SCRATCH_BYTES (8u << 20)

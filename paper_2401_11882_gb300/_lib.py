@@ -79,7 +79,14 @@ SIGNATURES = {
     "drt_batch_bind": (ctypes.c_int, [_P, _P, _P, _SZ, _P]),
     "drt_batch_run": (ctypes.c_int, [_P, _I32, _I32, _P]),
     "drt_batch_plan_info": (ctypes.c_int, [_P, _P]),
+    "drt_batch_evaluate": (ctypes.c_int, [_P, _P]),
     "drt_batch_plan_destroy": (ctypes.c_int, [_P]),
+    "drt_mlp_sizes": (ctypes.c_int, [_I32, _P, _P, _P]),
+    "drt_mlp_shadow": (ctypes.c_int, [_P, _P, _P]),
+    "drt_mlp_forward": (ctypes.c_int, [_P, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    "drt_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _SZ, _P]),
+    "drt_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, _P, _P]),
 }
 
 

@@ -78,6 +78,12 @@ class BatchedDescent:
         _lib.call("drt_batch_run", self._plan, int(n_steps), 1 if use_graph else 0,
                   ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
 
+    def evaluate(self) -> torch.Tensor:
+        """Loss of every problem at its current TX (no update); returns self.loss."""
+        _lib.call("drt_batch_evaluate", self._plan,
+                  ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+        return self.loss
+
     def info(self) -> dict:
         out = (ctypes.c_int64 * 8)()
         _lib.call("drt_batch_plan_info", self._plan, out)

@@ -54,6 +54,7 @@ struct BatchArgs {
   float* loss_hist;          // [hist_len][S*T] or null
   int hist_len;
   float lr, b1, b2, eps, lo_x, lo_y, hi_x, hi_y;
+  int cull;                      // skip the obstruction loop of warp-wide invalid paths (exact)
   // workspace
   unsigned long long* counter;   // [2]
   const int32_t* fwd_prob;       // [P] problems, longest forward first
@@ -133,10 +134,10 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const BatchArgs a) {
     for (long long c = warp; c < nc; c += nwarps) {
       const Cand cd = decode_candidate(c, W, K);
       switch (cd.k) {
-        case 0: acc += path_power<MODE, 0>(sw, W, txy, q, cd, alpha, a.gk[0], 0); break;
-        case 1: acc += path_power<MODE, 1>(sw, W, txy, q, cd, alpha, a.gk[1], 0); break;
-        case 2: acc += path_power<MODE, 2>(sw, W, txy, q, cd, alpha, a.gk[2], 0); break;
-        default: acc += path_power<MODE, 3>(sw, W, txy, q, cd, alpha, a.gk[3], 0); break;
+        case 0: acc += path_power<MODE, 0>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;
+        case 1: acc += path_power<MODE, 1>(sw, W, txy, q, cd, alpha, a.gk[1], a.cull); break;
+        case 2: acc += path_power<MODE, 2>(sw, W, txy, q, cd, alpha, a.gk[2], a.cull); break;
+        default: acc += path_power<MODE, 3>(sw, W, txy, q, cd, alpha, a.gk[3], a.cull); break;
       }
     }
     s_part[warp][lane] = acc;
@@ -319,7 +320,7 @@ struct BatchPlan {
   std::vector<int32_t> fwd_prob;
   std::vector<long long> fwd_prefix, adj_prefix, pw_off;
   long long n_fwd_units = 0, n_adj_units = 0, n_power = 0;
-  int ctas_fwd = 1, ctas_adj = 1, per_sm_req = 0;
+  int ctas_fwd = 1, ctas_adj = 1, per_sm_req = 0, cull = 0;
   size_t off_counter = 0, off_prob = 0, off_fprefix = 0, off_aprefix = 0, off_pwoff = 0,
          off_power = 0, off_argmin = 0, off_partial = 0, ws_bytes = 0;
   bool bound = false;
@@ -370,6 +371,22 @@ cudaError_t set_smem_limits(int Wmax) {
   return cudaSuccess;
 }
 
+cudaError_t launch_evaluate(BatchPlan* pl, cudaStream_t st) {
+  BatchArgs& a = pl->args;
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const size_t sf = batch_fwd_smem(pl->Wmax);
+  switch (pl->mode) {
+    case MODE_SIGMOID: batch_forward_kernel<MODE_SIGMOID><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
+    case MODE_HARD: batch_forward_kernel<MODE_HARD><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
+    default: batch_forward_kernel<MODE_STEP><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int ab = (int)std::min<long long>(((long long)pl->P * 32 + 255) / 256, 4096);
+  batch_argmin_kernel<<<std::max(ab, 1), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_step(BatchPlan* pl, cudaStream_t st) {
   BatchArgs& a = pl->args;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
@@ -415,6 +432,7 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
   pl->warps = (tile && tile->warps_per_cta) ? tile->warps_per_cta : 8;
   pl->threads = pl->warps * 32;
   pl->per_sm_req = tile ? tile->ctas_per_sm : 0;
+  pl->cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
   std::vector<double> cost(pl->P);
   std::vector<long long> tiles(pl->P), adj_units(pl->P);
   pl->pw_off.resize(pl->P);
@@ -549,6 +567,7 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
   a.lo_y = d->lo_y;
   a.hi_x = d->hi_x;
   a.hi_y = d->hi_y;
+  a.cull = pl->cull;
   a.counter = reinterpret_cast<unsigned long long*>(base + pl->off_counter);
   a.fwd_prob = reinterpret_cast<const int32_t*>(base + pl->off_prob);
   a.fwd_prefix = reinterpret_cast<const long long*>(base + pl->off_fprefix);
@@ -588,6 +607,19 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
     return DRT_ERR_CUDA;
   }
   pl->bound = true;
+  return DRT_OK;
+}
+
+drt_status batch_evaluate(BatchPlan* pl, cudaStream_t st, std::string* err) {
+  if (!pl->bound) {
+    *err = "plan is not bound";
+    return DRT_ERR_INVALID_ARG;
+  }
+  cudaError_t e = launch_evaluate(pl, st);
+  if (e != cudaSuccess) {
+    *err = cudaGetErrorString(e);
+    return DRT_ERR_CUDA;
+  }
   return DRT_OK;
 }
 
@@ -699,6 +731,13 @@ drt_status drt_batch_run(drt_batch_plan* plan, int32_t n_steps, int32_t use_grap
   if (n_steps < 0) return bad(DRT_ERR_INVALID_ARG, "n_steps < 0");
   std::string err;
   drt_status st = drt::batch_run(&plan->impl, n_steps, use_graph, static_cast<cudaStream_t>(stream), &err);
+  return st == DRT_OK ? st : bad(st, err);
+}
+
+drt_status drt_batch_evaluate(drt_batch_plan* plan, void* stream) {
+  if (!plan) return bad(DRT_ERR_INVALID_ARG, "plan is NULL");
+  std::string err;
+  drt_status st = drt::batch_evaluate(&plan->impl, static_cast<cudaStream_t>(stream), &err);
   return st == DRT_OK ? st : bad(st, err);
 }
 

@@ -79,7 +79,14 @@ def num_candidates(n_walls: int, max_order: int) -> int:
 def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
             refl_coef: float = 0.5, tile: TileConfig | None = None,
             out: torch.Tensor | None = None) -> torch.Tensor:
-    """Received power per receiver (float32 [R]) on the current stream."""
+    """Received power per receiver (float32 [R]) on the current stream.
+
+    ``tile``: a TileConfig, None (library defaults) or "auto" (autotuned, cached)."""
+    if isinstance(tile, str):
+        if tile != "auto":
+            raise ValueError("tile must be a TileConfig, None or 'auto'")
+        from . import autotune
+        tile = autotune.tune_forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
     sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
     dev = keep[0].device
     tl = tile.as_c() if tile else None

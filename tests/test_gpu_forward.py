@@ -168,3 +168,19 @@ def test_invalid_arguments_raise(drt):
         drt.forward(w, t, r, 1, -1.0)
     with pytest.raises(TypeError):
         drt.forward(w.double(), t, r, 1, 1.0)
+
+
+def test_autotuned_tile_is_cached_and_correct(drt, oracle_mod, tmp_path, monkeypatch):
+    from paper_2401_11882_gb300 import autotune
+    monkeypatch.setenv("DRT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    rng = np.random.default_rng(31)
+    sc = scenes.random_small_scene(rng, 12, 70, 2, 50.0, "hard_sigmoid", boundary=True)
+    dev = torch.device("cuda:0")
+    w, t, r = (torch.tensor(sc.walls, device=dev), torch.tensor(sc.tx, device=dev),
+               torch.tensor(sc.rx, device=dev))
+    cands = autotune.FORWARD_CANDIDATES[:4]
+    best = autotune.tune_forward(w, t, r, 2, 50.0, "hard_sigmoid", candidates=cands, reps=1)
+    assert best in cands
+    assert autotune.tune_forward(w, t, r, 2, 50.0, "hard_sigmoid", candidates=[], reps=1) == best
+    P = drt.forward(w, t, r, 2, 50.0, "hard_sigmoid", tile="auto").cpu().numpy()
+    assert_power_close(P, _ref(oracle_mod, sc))
