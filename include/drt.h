@@ -260,6 +260,18 @@ drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const floa
                              const float* x, const float* target, int32_t batch, float* loss,
                              float* grad, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Selects the tensor-core path of the MLP's dense layers for this process:
+   1 (default) = tcgen05.mma with the accumulator in tensor memory, for tiles
+   whose batch is a multiple of 128 (other shapes use the next path);
+   0 = mma.sync (warp-level MMA).  Both give the same function up to FP32
+   summation order. */
+drt_status drt_mlp_set_tensor_core_path(int32_t use_tcgen05);
+
+/* Synchronous: *timed_out = 1 if a tcgen05 kernel gave up waiting for its
+   MMAs since the last call (its outputs are then invalid), else 0; clears the
+   flag.  Returns DRT_ERR_TIMEOUT in the first case. */
+drt_status drt_mlp_tc_status(int32_t* timed_out);
+
 /* One Adam step on the FP32 master params with moments m, v and the device
    step counter (incremented); refreshes the shadow when it is non-NULL. */
 drt_status drt_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t* step,

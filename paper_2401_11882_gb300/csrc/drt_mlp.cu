@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <utility>
 
 #include "drt.h"
@@ -329,6 +331,17 @@ __global__ void increment_kernel(int32_t* step) {
 }
 
 }  // namespace mlp
+}  // namespace drt
+
+#include "drt_mlp_tc.cuh"
+
+namespace drt {
+namespace mlp {
+
+// timeout flag of the tcgen05 kernels (device-global; read and cleared by drt_mlp_tc_status)
+__device__ int g_tc_status;
+
+}  // namespace mlp
 
 // ------------------------------------------------------------------ host side
 namespace {
@@ -372,8 +385,48 @@ MlpWs carve(void* base, int B) {
   return w;
 }
 
+// Which tensor-core path the dense layers use: 1 = tcgen05 (TMEM accumulator),
+// 0 = mma.sync.  The tcgen05 path needs M a multiple of 128 and K of 64; other
+// shapes take the mma.sync path.
+std::atomic<int> g_tc_mode{1};
+std::mutex g_tc_mu;
+int* g_tc_status_ptr[64] = {};
+
+int* tc_status_ptr() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  if (!g_tc_status_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, mlp::g_tc_status) != cudaSuccess) return nullptr;
+    g_tc_status_ptr[dev] = static_cast<int*>(p);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  }
+  return g_tc_status_ptr[dev];
+}
+
 template <int EPI>
 cudaError_t gemm(const mlp::GemmArgs& g, cudaStream_t st) {
+  const bool tc_shape = (g.M % mlp::TC_BM == 0) && (g.K % mlp::TC_BK == 0) &&
+                        (g.N % 256 == 0 || g.N == 64);
+  int* status = (g_tc_mode.load() && tc_shape) ? tc_status_ptr() : nullptr;
+  if (status) {
+    // 100 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM columns) per SM
+    const size_t smem = 100 * 1024;
+    if (g.N % 256 == 0) {
+      dim3 grid(g.N / 256, g.M / mlp::TC_BM);
+      mlp::tc_gemm_nt_kernel<EPI, 256><<<grid, 128, smem, st>>>(g, status);
+    } else {
+      dim3 grid(1, g.M / mlp::TC_BM);
+      mlp::tc_gemm_nt_kernel<EPI, 64><<<grid, 128, smem, st>>>(g, status);
+    }
+    return cudaGetLastError();
+  }
   dim3 grid(g.N / 64, g.M / 64);
   mlp::gemm_nt_kernel<EPI><<<grid, 128, 0, st>>>(g);
   return cudaGetLastError();
@@ -529,6 +582,25 @@ drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const floa
     }
   }
   return e == cudaSuccess ? DRT_OK : mlp_fail(DRT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+drt_status drt_mlp_set_tensor_core_path(int32_t use_tcgen05) {
+  if (use_tcgen05 != 0 && use_tcgen05 != 1) return mlp_fail(DRT_ERR_INVALID_ARG, "use_tcgen05 must be 0 or 1");
+  g_tc_mode.store(use_tcgen05);
+  return DRT_OK;
+}
+
+drt_status drt_mlp_tc_status(int32_t* timed_out) {
+  if (!timed_out) return mlp_fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, mlp::g_tc_status, sizeof(int));
+  if (e == cudaSuccess) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(mlp::g_tc_status, &zero, sizeof(int));
+  }
+  if (e != cudaSuccess) return mlp_fail(DRT_ERR_CUDA, cudaGetErrorString(e));
+  *timed_out = v;
+  return v ? DRT_ERR_TIMEOUT : DRT_OK;
 }
 
 drt_status drt_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t* step,

@@ -1,0 +1,56 @@
+"""The tcgen05 (TMEM-accumulator) tensor-core path of the MLP's dense layers
+against the mma.sync path and the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_11882_gb300 import _lib, surrogate
+    yield _lib, surrogate
+    _lib.call("drt_mlp_set_tensor_core_path", 1)
+
+
+def _status(_lib):
+    flag = ctypes.c_int32(0)
+    _lib.load().drt_mlp_tc_status(ctypes.byref(flag))
+    return flag.value
+
+
+@pytest.mark.parametrize("batch", [128, 384])
+def test_forward_and_gradient_agree_across_paths(env, batch):
+    _lib, sur = env
+    rng = np.random.default_rng(batch)
+    theta = (M.init_params(7) + rng.normal(0, 0.02, M.n_params())).astype(np.float32)
+    x = torch.from_numpy(rng.uniform(0, 1, (batch, 2)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=batch).astype(np.float32)).cuda()
+    out = {}
+    for path in (1, 0):
+        _lib.call("drt_mlp_set_tensor_core_path", path)
+        m = sur.SurrogateMLP("cuda", seed=3, batch=batch)
+        m.set_params(theta)
+        y = m.forward(x).cpu().numpy()
+        loss, g = m.loss_grad(x, t)
+        torch.cuda.synchronize()
+        out[path] = (y, float(loss), g.cpu().numpy().copy(), m.freqs.cpu().numpy())
+    assert _status(_lib) == 0
+    y1, l1, g1, freqs = out[1]
+    y0, l0, g0, _ = out[0]
+    np.testing.assert_allclose(y1, y0, rtol=2e-3, atol=2e-3 * np.abs(y0).max())
+    assert l1 == pytest.approx(l0, rel=2e-3)
+    assert np.linalg.norm(g1 - g0) <= 1e-2 * np.linalg.norm(g0)
+    ref, _ = M.forward(theta.astype(np.float64), freqs, x.cpu().numpy(), emulate_bf16=True)
+    np.testing.assert_allclose(y1, ref, rtol=2e-3, atol=2e-3 * np.abs(ref).max())
+    _, gref = M.loss_grad(theta.astype(np.float64), freqs, x.cpu().numpy(), t.cpu().numpy(),
+                          emulate_bf16=True)
+    assert np.linalg.norm(g1 - gref) <= 1e-2 * np.linalg.norm(gref)
