@@ -183,8 +183,9 @@ typedef struct {
   int32_t history_len;
   const float* alpha_schedule;   /* device [n_alpha]: alpha of step i = schedule[min(i, n_alpha - 1)] */
   int32_t n_alpha;               /* >= 1 */
-  float lr, beta1, beta2, eps;   /* Adam */
+  float lr, beta1, beta2, eps;   /* Adam; the learning rate of step i is lr * lr_decay^i */
   float lo_x, lo_y, hi_x, hi_y;  /* the TX is clamped to this box after every update */
+  float lr_decay;                /* per-step factor of the learning rate, in (0, 1] */
 } drt_descent_state;
 
 typedef struct drt_batch_plan drt_batch_plan;

@@ -51,7 +51,7 @@ class DescentState(ctypes.Structure):
                 ("alpha_schedule", ctypes.c_void_p), ("n_alpha", ctypes.c_int32),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("lo_x", ctypes.c_float), ("lo_y", ctypes.c_float),
-                ("hi_x", ctypes.c_float), ("hi_y", ctypes.c_float)]
+                ("hi_x", ctypes.c_float), ("hi_y", ctypes.c_float), ("lr_decay", ctypes.c_float)]
 
 
 class DrtError(RuntimeError):

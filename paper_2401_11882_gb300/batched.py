@@ -22,12 +22,13 @@ class BatchedDescent:
 
     ``alpha`` is a float or a per-step schedule (the last value repeats);
     ``box`` = (lo_x, lo_y, hi_x, hi_y) clamps the TX after every step;
+    the learning rate of step i is ``lr * lr_decay**i``;
     ``history`` rows of per-step losses are kept on the device.
     """
 
     def __init__(self, batch, lr=1e-2, betas=(0.9, 0.999), eps=1e-8, alpha=100.0,
                  box=(0.0, 0.0, 1.0, 1.0), history=0, device="cuda",
-                 tile: TileConfig | None = None, tx0=None):
+                 tile: TileConfig | None = None, tx0=None, lr_decay: float = 1.0):
         self.device = torch.device(device)
         dev = self.device
         self.batch = batch
@@ -68,7 +69,7 @@ class BatchedDescent:
             self.loss.data_ptr(), self.history.data_ptr() if self.history is not None else None,
             history, self.alpha.data_ptr(), len(sched), float(lr), float(betas[0]),
             float(betas[1]), float(eps), float(box[0]), float(box[1]), float(box[2]),
-            float(box[3]))
+            float(box[3]), float(lr_decay))
         _lib.call("drt_batch_bind", self._plan, ctypes.byref(self._state),
                   ctypes.c_void_p(self.workspace.data_ptr()), ctypes.c_size_t(self.workspace.numel()),
                   ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))

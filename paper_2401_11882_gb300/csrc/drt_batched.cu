@@ -53,7 +53,7 @@ struct BatchArgs {
   float* loss;               // [S*T]
   float* loss_hist;          // [hist_len][S*T] or null
   int hist_len;
-  float lr, b1, b2, eps, lo_x, lo_y, hi_x, hi_y;
+  float lr, b1, b2, eps, lo_x, lo_y, hi_x, hi_y, lr_decay;
   int cull;                      // skip the obstruction loop of warp-wide invalid paths (exact)
   // workspace
   unsigned long long* counter;   // [2]
@@ -275,6 +275,7 @@ __global__ void batch_adam_kernel(const BatchArgs a) {
   const int P = a.S * a.T;
   const int t = *a.step + 1;   // Adam's 1-based step
   const float c1 = 1.f - powf(a.b1, (float)t), c2 = 1.f - powf(a.b2, (float)t);
+  const float lr = a.lr * powf(a.lr_decay, (float)(t - 1));
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     float gx = 0.f, gy = 0.f;
     for (long long u = a.adj_prefix[p]; u < a.adj_prefix[p + 1]; ++u) {
@@ -290,7 +291,7 @@ __global__ void batch_adam_kernel(const BatchArgs a) {
       a.m[2 * p + i] = m;
       a.v[2 * p + i] = v;
       const float mh = m / c1, vh = v / c2;
-      float x = a.tx[2 * p + i] - a.lr * mh / (sqrtf(vh) + a.eps);
+      float x = a.tx[2 * p + i] - lr * mh / (sqrtf(vh) + a.eps);
       x = fminf(fmaxf(x, lo[i]), hi[i]);
       a.tx[2 * p + i] = x;
     }
@@ -567,6 +568,7 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
   a.lo_y = d->lo_y;
   a.hi_x = d->hi_x;
   a.hi_y = d->hi_y;
+  a.lr_decay = d->lr_decay;
   a.cull = pl->cull;
   a.counter = reinterpret_cast<unsigned long long*>(base + pl->off_counter);
   a.fwd_prob = reinterpret_cast<const int32_t*>(base + pl->off_prob);
@@ -718,7 +720,7 @@ drt_status drt_batch_bind(drt_batch_plan* plan, const drt_descent_state* d, void
   if (d->loss_history && d->history_len < 0) return bad(DRT_ERR_INVALID_ARG, "history_len < 0");
   if (!(d->lr >= 0.f) || !std::isfinite(d->lr) || !(d->beta1 >= 0.f && d->beta1 < 1.f) ||
       !(d->beta2 >= 0.f && d->beta2 < 1.f) || !(d->eps > 0.f) || !(d->lo_x <= d->hi_x) ||
-      !(d->lo_y <= d->hi_y))
+      !(d->lo_y <= d->hi_y) || !(d->lr_decay > 0.f && d->lr_decay <= 1.f))
     return bad(DRT_ERR_INVALID_ARG, "Adam parameters or clamp box out of range");
   std::string err;
   drt_status st = drt::batch_bind(&plan->impl, d, workspace, workspace_bytes,

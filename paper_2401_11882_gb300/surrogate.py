@@ -169,17 +169,33 @@ def target_of(F: np.ndarray) -> np.ndarray:
     return -np.log(np.maximum(F, 0.0) + 1e-12)
 
 
-def separated_minima(points: np.ndarray, values: np.ndarray, k: int, min_sep: float) -> np.ndarray:
-    """Up to k points of lowest value, greedily keeping those at least min_sep apart."""
-    order = np.argsort(values, kind="stable")
-    chosen = []
+def separated_minima(points: np.ndarray, values: np.ndarray, k: int, min_sep: float,
+                     max_scan: int = 50000) -> np.ndarray:
+    """Up to k points of lowest value, greedily keeping those at least min_sep apart
+    (scanning at most max_scan candidates in order of value)."""
+    order = np.argsort(values, kind="stable")[:max_scan]
+    chosen = np.empty((0, 2), np.float64)
+    idx = []
     for i in order:
         p = points[i]
-        if all(np.hypot(*(p - points[j])) >= min_sep for j in chosen):
-            chosen.append(i)
-            if len(chosen) == k:
+        if chosen.shape[0] == 0 or np.min(np.hypot(*(chosen - p).T)) >= min_sep:
+            idx.append(i)
+            chosen = np.vstack([chosen, p])
+            if len(idx) == k:
                 break
-    return points[np.array(chosen, dtype=np.int64)]
+    return points[np.array(idx, dtype=np.int64)]
+
+
+def grid_local_minima(values: np.ndarray) -> np.ndarray:
+    """Mask of the points of a 2D grid not above any of their 8 neighbours."""
+    pad = np.pad(values, 1, mode="edge")
+    h, w = values.shape
+    mask = np.ones_like(values, dtype=bool)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy or dx:
+                mask &= values <= pad[1 + dy:1 + dy + h, 1 + dx:1 + dx + w]
+    return mask
 
 
 @dataclass
@@ -231,11 +247,20 @@ class SurrogateSearch:
         gx, gy = np.meshgrid(c, c, indexing="xy")
         pts = np.stack([gx.ravel(), gy.ravel()], 1).astype(np.float32)
         y = self.model.forward(torch.from_numpy(pts)).cpu().numpy()
-        return separated_minima(pts, y, k, min_sep)
+        # local minima of the surrogate first, then the best remaining separated points
+        m = grid_local_minima(y.reshape(grid, grid)).ravel()
+        props = separated_minima(pts[m], y[m], k, min_sep)
+        if props.shape[0] < k:
+            extra = separated_minima(pts, y, 4 * k, min_sep)
+            keep = [p for p in extra
+                    if props.shape[0] == 0 or np.min(np.hypot(*(props - p).T)) >= min_sep]
+            props = np.concatenate([props, np.asarray(keep, np.float32).reshape(-1, 2)])[:k]
+        return props.astype(np.float32)
 
 
 def descend(scene, starts: np.ndarray, n_steps: int, target_loss: float | None = None,
-            rel_tol: float = 1e-3, lr: float = 1e-2, device="cuda", check_every: int = 5):
+            rel_tol: float = 1e-3, lr: float = 1e-2, device="cuda", check_every: int = 5,
+            lr_decay: float = 1.0, box=(0.005, 0.005, 0.995, 0.995)):
     """Exact batched Adam from the given starts; stops once the best loss is within
     rel_tol of target_loss (checked every check_every steps).  Returns SearchResult-like
     (best_loss, best_tx, steps, seconds, reached, history)."""
@@ -246,7 +271,7 @@ def descend(scene, starts: np.ndarray, n_steps: int, target_loss: float | None =
                           np.asarray(starts, np.float32)[None], scene.alpha, scene.smoothing,
                           scene.refl_coef)
     dev = torch.device(device)
-    bd = BatchedDescent(b, lr=lr, device=dev, alpha=scene.alpha)
+    bd = BatchedDescent(b, lr=lr, device=dev, alpha=scene.alpha, lr_decay=lr_decay, box=box)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     steps, hist, reached = 0, [], False

@@ -1,0 +1,26 @@
+"""Small time-to-optimum study on GB300: both searches run, the reference
+optimum is verified by the FP64 oracle at its TX, and the seeded search is not
+worse than the plain one by more than its proposal overhead."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_small_study_and_oracle_verified_optimum(oracle_mod):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_11882_gb300 import experiments, scenes
+    r = experiments.time_to_optimum(scene_seed=0, n_samples=1 << 16, epochs=6, n_starts=32,
+                                    max_steps=200)
+    sc = scenes.surrogate_scene(seed=0)
+    tx = np.asarray(r["tx_star"], np.float32)
+    P = oracle_mod.power(sc.walls, tx, sc.rx, sc.max_order, sc.alpha, sc.smoothing)
+    # the reference optimum's loss is -min_r P_r at its TX (GPU FP32 vs oracle FP64)
+    assert -r["L_star"] == pytest.approx(P.min(), rel=1e-4, abs=1e-10 * P.max())
+    for k in ("seeded", "plain"):
+        assert r[k]["best_loss"] <= 0.0
+        assert r[k]["steps"] >= 1
+    assert r["seeded"]["best_loss"] >= r["L_star"] - 1e-3 * abs(r["L_star"])
