@@ -158,10 +158,20 @@ def file_hash(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+FORWARD_SOURCES = ("drt_forward.cu", "drt_path.cuh", "drt_common.cuh")
+
+
+def forward_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in FORWARD_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_11882_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def measured_traffic():
     """DRAM bytes per forward launch from the committed ncu summary, if it was taken on
-    the current forward kernel source (key: value lines)."""
-    src = os.path.join(ROOT, "paper_2401_11882_gb300", "csrc", "drt_forward.cu")
+    the current forward kernel sources (key: value lines)."""
     try:
         d = {}
         with open(TRAFFIC_FILE) as f:
@@ -169,7 +179,7 @@ def measured_traffic():
                 if ":" in line:
                     k, v = line.split(":", 1)
                     d[k.strip()] = v.strip()
-        if d.get("kernel_sha256_16") == file_hash(src):
+        if d.get("kernel_sha256_16") == forward_source_hash():
             return float(d["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         pass
@@ -346,6 +356,32 @@ def measure_extras(drt, dev, sc, w, t, r):
     gc = workload.num_candidates(g.n_walls, g.max_order)
     sf = timed(lambda: drt.forward(gw, gt, gr, 2, 100.0, "hard_sigmoid"), 2)
     sv = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", gp), 2)
+    # batched descent on the first 64 scenes of the 4096-scene batch (4 starts each)
+    from paper_2401_11882_gb300.batched import BatchedDescent
+    full = scenes.scene_batch(64, 0)
+    bd = BatchedDescent(full, history=0)
+    bd.run(1)
+    torch.cuda.synchronize(dev)
+    bs = timed(lambda: bd.run(1), 2)
+    bflops = sum(full.tx0.shape[1] * workload.forward_work(
+        int(full.wall_off[i + 1] - full.wall_off[i]), int(full.max_order[i]),
+        int(full.rx_off[i + 1] - full.rx_off[i]))["flops"] for i in range(full.n_scenes))
+    out["batched_descent_64_scenes"] = {
+        "workload": "first 64 scenes of the 4096-scene batch (W 8-256, R 64-4096, K 0-2), 4 starts "
+                    "each, alpha=100, hard sigmoid; one step = forward + argmin + adjoint + Adam",
+        "ms_per_step": bs * 1e3, "steps_per_s": 1.0 / bs,
+        "forward_tflops_by_convention": bflops / bs / 1e12}
+    bd.close()
+    # surrogate MLP (tcgen05 path), batch 8192
+    from paper_2401_11882_gb300.surrogate import SurrogateMLP
+    m = SurrogateMLP(dev, batch=8192)
+    xm = torch.rand(8192, 2, device=dev)
+    tm = torch.randn(8192, device=dev)
+    mf = timed(lambda: m.forward(xm), 20)
+    mb = timed(lambda: m.loss_grad(xm, tm), 20)
+    mlp_flops = 2 * 8192 * (64 * 256 + 3 * 256 * 256 + 256)
+    out["surrogate_mlp_batch_8192"] = {"forward_ms": mf * 1e3, "loss_grad_ms": mb * 1e3,
+                                       "forward_tflops": mlp_flops / mf / 1e12}
     out["gradient_scene_dense"] = {
         "workload": "128 random segments, 128x128 RX grid, K<=2 (16385 sequences), alpha=100, "
                     "hard sigmoid, dense g = 1/R, grad wrt TX and 512 wall coordinates",

@@ -273,6 +273,12 @@ drt_status drt_mlp_set_tensor_core_path(int32_t use_tcgen05);
    flag.  Returns DRT_ERR_TIMEOUT in the first case. */
 drt_status drt_mlp_tc_status(int32_t* timed_out);
 
+/* Test knob for the timeout path: while skip != 0, the tcgen05 kernels issue no
+   MMA and no commit, so their bounded mbarrier wait runs out with nothing in
+   flight; they then set the flag read by drt_mlp_tc_status, skip their
+   epilogue, free their tensor memory and return (outputs undefined). */
+drt_status drt_mlp_test_skip_mma(int32_t skip);
+
 /* One Adam step on the FP32 master params with moments m, v and the device
    step counter (incremented); refreshes the shadow when it is non-NULL. */
 drt_status drt_mlp_adam(float* params, float* m, float* v, const float* grad, int32_t* step,

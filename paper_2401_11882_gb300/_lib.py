@@ -87,6 +87,7 @@ SIGNATURES = {
     "drt_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _SZ, _P]),
     "drt_mlp_set_tensor_core_path": (ctypes.c_int, [_I32]),
     "drt_mlp_tc_status": (ctypes.c_int, [_P]),
+    "drt_mlp_test_skip_mma": (ctypes.c_int, [_I32]),
     "drt_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, _P, _P]),
 }

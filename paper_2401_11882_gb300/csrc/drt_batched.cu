@@ -131,13 +131,23 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const BatchArgs a) {
     const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + roff + r);
     const long long nc = n_candidates(W, K);
     float acc = 0.f;
+    const bool masked = alpha > FAST_SKIP_MAX_ALPHA;
     for (long long c = warp; c < nc; c += nwarps) {
       const Cand cd = decode_candidate(c, W, K);
-      switch (cd.k) {
-        case 0: acc += path_power<MODE, 0>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;
-        case 1: acc += path_power<MODE, 1>(sw, W, txy, q, cd, alpha, a.gk[1], a.cull); break;
-        case 2: acc += path_power<MODE, 2>(sw, W, txy, q, cd, alpha, a.gk[2], a.cull); break;
-        default: acc += path_power<MODE, 3>(sw, W, txy, q, cd, alpha, a.gk[3], a.cull); break;
+      if (!masked) {
+        switch (cd.k) {
+          case 0: acc += path_power<MODE, 0>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;
+          case 1: acc += path_power<MODE, 1>(sw, W, txy, q, cd, alpha, a.gk[1], a.cull); break;
+          case 2: acc += path_power<MODE, 2>(sw, W, txy, q, cd, alpha, a.gk[2], a.cull); break;
+          default: acc += path_power<MODE, 3>(sw, W, txy, q, cd, alpha, a.gk[3], a.cull); break;
+        }
+      } else {
+        switch (cd.k) {
+          case 0: acc += path_power<MODE, 0, true>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;
+          case 1: acc += path_power<MODE, 1, true>(sw, W, txy, q, cd, alpha, a.gk[1], a.cull); break;
+          case 2: acc += path_power<MODE, 2, true>(sw, W, txy, q, cd, alpha, a.gk[2], a.cull); break;
+          default: acc += path_power<MODE, 3, true>(sw, W, txy, q, cd, alpha, a.gk[3], a.cull); break;
+        }
       }
     }
     s_part[warp][lane] = acc;

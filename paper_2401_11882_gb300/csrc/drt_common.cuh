@@ -57,7 +57,7 @@ __device__ __forceinline__ Smooth3 smooth3(float x, float alpha) {
     // Eq. 4 with e = exp(-alpha |x|) in (0, 1]: s(|x|) = 1/(1+e), s(-|x|) = e/(1+e).
     const float z = x * (alpha * LOG2E);
     const float e = ex2_approx(-fabsf(z));
-    const float q = 1.0f / (1.0f + e);
+    const float q = rcp_approx(1.0f + e);   // 1 + e in (1, 2]: no special cases
     const float big = q, small = e * q;
     r.s = z >= 0.0f ? big : small;
     r.sb = z >= 0.0f ? small : big;

@@ -45,14 +45,24 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
     const long long c0 = chunk * a.chunk;
     const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
     float acc = 0.f;
+    const bool masked = a.alpha > FAST_SKIP_MAX_ALPHA;
     for (long long c = c0; c < c1; ++c) {
       const Cand cd = decode_candidate(c, a.W, a.K);
       float p;
-      switch (cd.k) {
-        case 0: p = path_power<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull); break;
-        case 1: p = path_power<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull); break;
-        case 2: p = path_power<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull); break;
-        default: p = path_power<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull); break;
+      if (!masked) {
+        switch (cd.k) {
+          case 0: p = path_power<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull); break;
+          case 1: p = path_power<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull); break;
+          case 2: p = path_power<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull); break;
+          default: p = path_power<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull); break;
+        }
+      } else {
+        switch (cd.k) {
+          case 0: p = path_power<MODE, 0, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull); break;
+          case 1: p = path_power<MODE, 1, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull); break;
+          case 2: p = path_power<MODE, 2, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull); break;
+          default: p = path_power<MODE, 3, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull); break;
+        }
       }
       acc += p;
     }

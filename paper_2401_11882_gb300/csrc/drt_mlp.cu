@@ -389,6 +389,7 @@ MlpWs carve(void* base, int B) {
 // 0 = mma.sync.  The tcgen05 path needs M a multiple of 128 and K of 64; other
 // shapes take the mma.sync path.
 std::atomic<int> g_tc_mode{1};
+std::atomic<int> g_tc_skip_mma{0};
 std::mutex g_tc_mu;
 int* g_tc_status_ptr[64] = {};
 
@@ -420,10 +421,10 @@ cudaError_t gemm(const mlp::GemmArgs& g, cudaStream_t st) {
     const size_t smem = 100 * 1024;
     if (g.N % 256 == 0) {
       dim3 grid(g.N / 256, g.M / mlp::TC_BM);
-      mlp::tc_gemm_nt_kernel<EPI, 256><<<grid, 128, smem, st>>>(g, status);
+      mlp::tc_gemm_nt_kernel<EPI, 256><<<grid, 128, smem, st>>>(g, status, g_tc_skip_mma.load());
     } else {
       dim3 grid(1, g.M / mlp::TC_BM);
-      mlp::tc_gemm_nt_kernel<EPI, 64><<<grid, 128, smem, st>>>(g, status);
+      mlp::tc_gemm_nt_kernel<EPI, 64><<<grid, 128, smem, st>>>(g, status, g_tc_skip_mma.load());
     }
     return cudaGetLastError();
   }
@@ -587,6 +588,11 @@ drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const floa
 drt_status drt_mlp_set_tensor_core_path(int32_t use_tcgen05) {
   if (use_tcgen05 != 0 && use_tcgen05 != 1) return mlp_fail(DRT_ERR_INVALID_ARG, "use_tcgen05 must be 0 or 1");
   g_tc_mode.store(use_tcgen05);
+  return DRT_OK;
+}
+
+drt_status drt_mlp_test_skip_mma(int32_t skip) {
+  g_tc_skip_mma.store(skip ? 1 : 0);
   return DRT_OK;
 }
 

@@ -8,8 +8,8 @@
 // (8-row x 16-byte core matrices; core matrices adjacent in K are 128 bytes
 // apart, adjacent 8-row groups 1024 bytes apart), and one thread issues four
 // tcgen05.mma (M = 128, N = BN, K = 16) and commits them to an mbarrier.  The
-// wait on that mbarrier is bounded: on timeout the kernel records an error
-// code, and still waits (bounded) before it frees TMEM.  After the last chunk
+// wait on that mbarrier is bounded (0.5 s of %globaltimer): on timeout the
+// kernel records an error code, and still waits (bounded) before it frees TMEM.  After the last chunk
 // every thread reads its accumulator row (warp w owns TMEM lanes 32w..32w+31)
 // with tcgen05.ld and runs the epilogue.
 #pragma once
@@ -23,7 +23,7 @@ namespace mlp {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
-constexpr long long TC_WAIT_LIMIT = 1LL << 22;   // mbarrier polls before giving up
+constexpr unsigned long long TC_WAIT_NS = 500000000ull;   // give up waiting after 0.5 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -54,22 +54,35 @@ __device__ __forceinline__ uint32_t tc_off(int r, int k) {
   return (uint32_t)((((r >> 3) * (TC_BK / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
+__device__ __forceinline__ uint64_t tc_now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Polls the mbarrier phase without blocking; gives up after TC_WAIT_NS.
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
-  for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+  const uint64_t t0 = tc_now_ns();
+  for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(mbar), "r"(phase)
         : "memory");
     if (done) return true;
+    if (tc_now_ns() - t0 > TC_WAIT_NS) return false;
+    __nanosleep(64);
   }
-  return false;
 }
 
+// skip_mma != 0 (test knob): no MMA and no commit is issued, so the bounded
+// wait runs out with nothing in flight; the kernel must then report the
+// timeout, skip its epilogue and still free its tensor memory.
 template <int EPI, int BN>
-__global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, int* status) {
+__global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, int* status,
+                                                            int skip_mma) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   uint8_t* sA = tc_smem;                                  // 128 x 64 bf16 = 16 KB
   uint8_t* sB = tc_smem + TC_BM * TC_BK * 2;              // BN x 64 bf16
@@ -116,7 +129,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, in
     // make the generic-proxy stores visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !skip_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int kk = 0; kk < TC_BK; kk += 16) {
@@ -180,7 +193,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, in
         }
       }
     }
-  } else {
+  } else if (!skip_mma) {
     // give an MMA that may still be running a last bounded chance to finish
     tc_wait(mbar_a, phase);
   }

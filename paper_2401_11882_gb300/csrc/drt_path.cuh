@@ -50,8 +50,15 @@ __device__ __forceinline__ float side(float z) {
   return z > 0.f ? 1.f : 0.f;
 }
 
+// Largest alpha for which the hard-sigmoid and sigmoid loops test every (leg,
+// wall) pair and divide the skipped pairs out afterwards: there a point lying on
+// a wall's line has s within 1/4 of 1/2 even after FP32 rounding of its
+// distance, so a skipped pair's factor is >= 1/2.  Above it (and for the unit
+// step) the skipped pairs are masked inside the loop.
+constexpr float FAST_SKIP_MAX_ALPHA = 1e4f;
+
 // Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
-template <int MODE, int K>
+template <int MODE, int K, bool MASKED = false>
 __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
                                             const Cand& cd, float alpha, float gk, int cull) {
   // --- image method (Sec. V-B): TX images in the walls of the sequence.
@@ -136,8 +143,51 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
 #pragma unroll
   for (int j = 0; j <= K; ++j) vis[j] = 1.f;
 
-  if constexpr (MODE != MODE_SIGMOID) {
-    // blocked = X(x1, y1) X(x2, y2) with X(x, y) = s(x) s(-y) + s(-x) s(y) = s_x + s_y (1 - 2 s_x).
+  if constexpr (MODE == MODE_HARD && !MASKED) {
+    // blocked = X(x1, y1) X(x2, y2) with X(a, b) = s(a) s(-b) + s(-a) s(b) = s_a + s_b (1 - 2 s_a).
+    // Every wall is tested against every leg here; the (leg, wall) pairs a leg must skip
+    // (the walls its own end points lie on) are divided out after the loop: one end point
+    // of such a pair lies on the wall's line, s = 1/2 there (C3), so its factor is >= 1/2.
+#pragma unroll 2
+    for (int w = 0; w < W; ++w) {
+      const float4 h = s.H[w];
+      const float4 e = s.E[w];
+      float sv[K + 2], uv[K + 2];
+      sv[0] = h.w;
+#pragma unroll
+      for (int i = 1; i <= K + 1; ++i) sv[i] = __saturatef(fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z)));
+#pragma unroll
+      for (int i = 1; i <= (K > 0 ? K : 1); ++i) uv[i] = fmaf(-2.f, sv[i], 1.f);
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        const float sa = __saturatef(fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j])));
+        const float sb = __saturatef(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
+        const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
+        const float x1 = (j == 0) ? fmaf(sv[0], uv[1], sv[1]) : fmaf(sv[j + 1], uv[j], sv[j]);
+        vis[j] = fmaf(-vis[j], x1 * x2, vis[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+#pragma unroll
+      for (int side_ = 0; side_ < 2; ++side_) {
+        // leg j skips w_j (side 0, j >= 1) and w_{j+1} (side 1, j < K)
+        if ((side_ == 0 && j >= 1) || (side_ == 1 && j < K)) {
+          const int w = cd.w[side_ == 0 ? j - 1 : j];
+          const float4 h = s.H[w];
+          const float4 e = s.E[w];
+          const float s0 = (j == 0) ? h.w : __saturatef(fmaf(h.x, Qx[j], fmaf(h.y, Qy[j], h.z)));
+          const float s1 = __saturatef(fmaf(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z)));
+          const float sa = __saturatef(fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j])));
+          const float sb = __saturatef(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
+          const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
+          const float x1 = (j == 0) ? fmaf(s0, fmaf(-2.f, s1, 1.f), s1) : fmaf(s1, fmaf(-2.f, s0, 1.f), s0);
+          vis[j] = __fdividef(vis[j], fmaf(-x1, x2, 1.f));
+        }
+      }
+    }
+  } else if constexpr (MODE != MODE_SIGMOID) {
+    // unit step (no 1/2 at 0), or a large alpha: the skipped pairs are masked inside the loop.
 #pragma unroll 2
     for (int w = 0; w < W; ++w) {
       const float4 h = s.H[w];
@@ -167,10 +217,36 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
     //   X = (same sign ? Ns : No) / D and 1 - X = (same sign ? No : Ns) / D,
     // and 1 - X1 X2 = (Xb1 D2 + X1 Xb2) / (D1 D2) in numerators: every term is a
     // sum of non-negative products, so a nearly blocked leg keeps its relative
-    // accuracy.  Numerator and denominator products are folded into vis every 8 walls.
+    // accuracy.  Numerator and denominator products are folded into vis every 8
+    // walls.  Skipped (leg, wall) pairs are divided out after the loop, as for the
+    // hard sigmoid (their factor is >= 1/2).
     float vn[K + 1], vd[K + 1];
 #pragma unroll
     for (int j = 0; j <= K; ++j) vn[j] = vd[j] = 1.f;
+    auto pair_factor = [&](const float4& h, const float4& e, int j, float& num, float& den) {
+      float ze0, ee0, ze1, ee1;
+      if (j == 0) {
+        ze0 = h.w;
+        ee0 = fabsf(h.w);
+      } else {
+        ze0 = fmaf(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
+        ee0 = ex2_approx(-fabsf(ze0));
+      }
+      ze1 = fmaf(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z));
+      ee1 = ex2_approx(-fabsf(ze1));
+      const float za = fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+      const float zb = fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
+      const float ea = ex2_approx(-fabsf(za));
+      const float eb = ex2_approx(-fabsf(zb));
+      const float ns1 = ee0 + ee1, no1 = fmaf(ee0, ee1, 1.f);
+      const bool same1 = (__float_as_int(ze0) ^ __float_as_int(ze1)) >= 0;
+      const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
+      const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
+      const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+      const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+      den = (ns1 + no1) * (ns2 + no2);
+      num = fmaf(xb1, ns2 + no2, x1 * xb2);
+    };
     for (int w0 = 0; w0 < W; w0 += 8) {
       const int w1 = min(w0 + 8, W);
       for (int w = w0; w < w1; ++w) {
@@ -202,8 +278,10 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
           const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
           const float den = (ns1 + no1) * (ns2 + no2);
           float num = fmaf(xb1, ns2 + no2, x1 * xb2);
-          const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
-          num = skip ? den : num;
+          if constexpr (MASKED) {
+            const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+            num = skip ? den : num;
+          }
           vn[j] *= num;
           vd[j] *= den;
         }
@@ -212,6 +290,18 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
       for (int j = 0; j <= K; ++j) {
         vis[j] *= __fdividef(vn[j], vd[j]);
         vn[j] = vd[j] = 1.f;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j <= (MASKED ? -1 : K); ++j) {
+#pragma unroll
+      for (int side_ = 0; side_ < 2; ++side_) {
+        if ((side_ == 0 && j >= 1) || (side_ == 1 && j < K)) {
+          const int w = cd.w[side_ == 0 ? j - 1 : j];
+          float num, den;
+          pair_factor(s.H[w], s.E[w], j, num, den);
+          vis[j] *= __fdividef(den, num);
+        }
       }
     }
   }

@@ -184,3 +184,18 @@ def test_autotuned_tile_is_cached_and_correct(drt, oracle_mod, tmp_path, monkeyp
     assert autotune.tune_forward(w, t, r, 2, 50.0, "hard_sigmoid", candidates=[], reps=1) == best
     P = drt.forward(w, t, r, 2, 50.0, "hard_sigmoid", tile="auto").cpu().numpy()
     assert_power_close(P, _ref(oracle_mod, sc))
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+def test_large_alpha_masked_path(drt, oracle_mod, smoothing):
+    # above the fast path's alpha limit the skipped (leg, wall) pairs are masked in the loop;
+    # both sides of the limit must agree with the oracle
+    from paper_2401_11882_gb300 import scenes as S
+    rng = np.random.default_rng(41)
+    sc = S.random_small_scene(rng, 8, 64, 2, 1.0, smoothing, boundary=True)
+    for alpha in (9.9e3, 1.01e4, 5e4):
+        s2 = sc.replace(alpha=alpha)
+        ref = _ref(oracle_mod, s2)
+        sens = fp32_sensitivity(lambda w, t, r: oracle_mod.power(w, t, r, 2, alpha, smoothing),
+                                s2.walls, s2.tx, s2.rx)
+        assert_power_close(_run(drt, s2), ref, sens=sens, min_strict=0.8)

@@ -54,3 +54,30 @@ def test_forward_and_gradient_agree_across_paths(env, batch):
     _, gref = M.loss_grad(theta.astype(np.float64), freqs, x.cpu().numpy(), t.cpu().numpy(),
                           emulate_bf16=True)
     assert np.linalg.norm(g1 - gref) <= 1e-2 * np.linalg.norm(gref)
+
+
+def test_bounded_wait_times_out_cleanly_and_context_survives(env):
+    """Failure detection without a fault: with the MMAs withheld, the kernel's
+    bounded mbarrier wait runs out; the host reads the timeout flag, and the next
+    (normal) call on the same context is correct."""
+    import time
+    _lib, sur = env
+    _lib.call("drt_mlp_set_tensor_core_path", 1)
+    m = sur.SurrogateMLP("cuda", seed=1, batch=128)
+    x = torch.rand(128, 2, device="cuda")
+    y_ok = m.forward(x).cpu().numpy()
+    assert _status(_lib) == 0
+    _lib.call("drt_mlp_test_skip_mma", 1)
+    try:
+        t0 = time.perf_counter()
+        m.forward(x)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t0
+    finally:
+        _lib.call("drt_mlp_test_skip_mma", 0)
+    assert _status(_lib) == 1
+    assert waited < 30.0
+    y_again = m.forward(x).cpu().numpy()
+    torch.cuda.synchronize()
+    assert _status(_lib) == 0
+    np.testing.assert_array_equal(y_again, y_ok)
