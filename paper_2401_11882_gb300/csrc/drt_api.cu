@@ -348,7 +348,11 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
   a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
   a.grad_tx = grad_tx;
   a.grad_walls = grad_walls;
-  cudaError_t e = launch_vjp(a, scene->smoothing, d.ctas, d.threads,
+  // one receiver: only ceil(N_K / 32) warps have work, so launch no more CTAs than
+  // that (fewer per-CTA tables for the final reduction to add up)
+  const long long busy = (a.n_units + d.threads / 32 - 1) / (d.threads / 32);
+  const int ctas = (int)std::max(1LL, std::min((long long)d.ctas, busy));
+  cudaError_t e = launch_vjp(a, scene->smoothing, ctas, d.threads,
                              static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "min-loss vjp launch");
   return DRT_OK;

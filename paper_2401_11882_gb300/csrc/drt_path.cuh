@@ -57,91 +57,16 @@ __device__ __forceinline__ float side(float z) {
 // step) the skipped pairs are masked inside the loop.
 constexpr float FAST_SKIP_MAX_ALPHA = 1e4f;
 
-// Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
-template <int MODE, int K, bool MASKED = false>
-__device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
-                                            const Cand& cd, float alpha, float gk, int cull) {
-  // --- image method (Sec. V-B): TX images in the walls of the sequence.
-  float Ix[K + 1], Iy[K + 1];
-  Ix[0] = tx.x;
-  Iy[0] = tx.y;
-#pragma unroll
-  for (int j = 1; j <= K; ++j) {
-    const float4 G = s.G[cd.w[j - 1]];
-    const float d = line_dist(G, Ix[j - 1], Iy[j - 1]);
-    Ix[j] = fmaf(-2.f * d, G.x, Ix[j - 1]);
-    Iy[j] = fmaf(-2.f * d, G.y, Iy[j - 1]);
-  }
-  // --- backtrace on the infinite lines: Q_{K+1} = RX, Q_j = line(Q_{j+1}, I_j) x wall j.
-  float Qx[K + 2], Qy[K + 2];
-  Qx[0] = tx.x;
-  Qy[0] = tx.y;
-  Qx[K + 1] = rx.x;
-  Qy[K + 1] = rx.y;
-  bool degenerate = false;
-#pragma unroll
-  for (int j = K; j >= 1; --j) {
-    const float4 G = s.G[cd.w[j - 1]];
-    const float a = line_dist(G, Ix[j], Iy[j]);
-    const float b = line_dist(G, Qx[j + 1], Qy[j + 1]);
-    // parallel lines (or a reflection point absurdly far away): no path
-    float t = __fdiv_rn(b, b - a);
-    if (!(fabsf(t) <= 1e8f)) {
-      degenerate = true;
-      t = 0.f;
-    }
-    Qx[j] = fmaf(t, Ix[j] - Qx[j + 1], Qx[j + 1]);
-    Qy[j] = fmaf(t, Iy[j] - Qy[j + 1], Qy[j + 1]);
-  }
-  // --- legs: length and the smoothing-ready normal form of each leg's line.
-  float L = 0.f;
-  float mx[K + 1], my[K + 1], mc[K + 1];
-#pragma unroll
-  for (int j = 0; j <= K; ++j) {
-    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
-    const float len2 = fmaf(dx, dx, dy * dy);
-    degenerate |= !(len2 > 0.f);
-    const float inv = rsqrtf(len2);
-    L = fmaf(len2, inv, L);
-    const float nx = -dy * inv, ny = dx * inv;
-    const float nq = fmaf(nx, Qx[j], ny * Qy[j]);
-    if (MODE == MODE_HARD) {
-      const float a6 = alpha * (1.0f / 6.0f);
-      mx[j] = nx * a6;
-      my[j] = ny * a6;
-      mc[j] = fmaf(-nq, a6, 0.5f);
-    } else if (MODE == MODE_STEP) {
-      mx[j] = nx;
-      my[j] = ny;
-      mc[j] = -nq;
-    } else {
-      const float kap = alpha * LOG2E;
-      mx[j] = nx * kap;
-      my[j] = ny * kap;
-      mc[j] = -nq * kap;
-    }
-  }
-  // --- continuous validity of each reflection (Sec. V-A): on the segment, and the
-  //     previous and next vertices on the same side of the wall's line.
-  float V = 1.f;
-#pragma unroll
-  for (int j = 1; j <= K; ++j) {
-    const int w = cd.w[j - 1];
-    const float4 G = s.G[w];
-    const float t0 = s.T[w].x;
-    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -t0));   // u = (ny, -nx)
-    const Smooth3 s1 = smooth3<MODE>(tau, alpha);
-    const Smooth3 s2 = smooth3<MODE>(G.w - tau, alpha);
-    const Smooth3 sp = smooth3<MODE>(line_dist(G, Qx[j - 1], Qy[j - 1]), alpha);
-    const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
-    V *= s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
-  }
-  // optional: skip the obstruction loop when the whole warp's validity is exactly 0
-  if (cull && __all_sync(0xffffffffu, V == 0.f || degenerate)) return 0.f;
-  // --- obstruction of every leg by every wall except the ones its end points lie on.
-  float vis[K + 1];
+// Visibility of each leg (obstruction by every wall except the ones its end points
+// lie on), written to vis[0..K].  Returns the smallest factor divided out for the
+// skipped (leg, wall) pairs (1 when they are masked instead).
+template <int MODE, int K, bool MASKED>
+__device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const Cand& cd,
+                                                const float* Qx, const float* Qy, const float* mx,
+                                                const float* my, const float* mc, float* vis) {
 #pragma unroll
   for (int j = 0; j <= K; ++j) vis[j] = 1.f;
+  float min_div = 1.f;
 
   if constexpr (MODE == MODE_HARD && !MASKED) {
     // blocked = X(x1, y1) X(x2, y2) with X(a, b) = s(a) s(-b) + s(-a) s(b) = s_a + s_b (1 - 2 s_a).
@@ -182,7 +107,9 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
           const float sb = __saturatef(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
           const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
           const float x1 = (j == 0) ? fmaf(s0, fmaf(-2.f, s1, 1.f), s1) : fmaf(s1, fmaf(-2.f, s0, 1.f), s0);
-          vis[j] = __fdividef(vis[j], fmaf(-x1, x2, 1.f));
+          const float f = fmaf(-x1, x2, 1.f);
+          min_div = fminf(min_div, f);
+          vis[j] = __fdividef(vis[j], f);
         }
       }
     }
@@ -300,10 +227,106 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
           const int w = cd.w[side_ == 0 ? j - 1 : j];
           float num, den;
           pair_factor(s.H[w], s.E[w], j, num, den);
+          min_div = fminf(min_div, __fdividef(num, den));
           vis[j] *= __fdividef(den, num);
         }
       }
     }
+  }
+  return min_div;
+}
+
+// Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
+template <int MODE, int K, bool MASKED = false>
+__device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
+                                            const Cand& cd, float alpha, float gk, int cull) {
+  // --- image method (Sec. V-B): TX images in the walls of the sequence.
+  float Ix[K + 1], Iy[K + 1];
+  Ix[0] = tx.x;
+  Iy[0] = tx.y;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float d = line_dist(G, Ix[j - 1], Iy[j - 1]);
+    Ix[j] = fmaf(-2.f * d, G.x, Ix[j - 1]);
+    Iy[j] = fmaf(-2.f * d, G.y, Iy[j - 1]);
+  }
+  // --- backtrace on the infinite lines: Q_{K+1} = RX, Q_j = line(Q_{j+1}, I_j) x wall j.
+  float Qx[K + 2], Qy[K + 2];
+  Qx[0] = tx.x;
+  Qy[0] = tx.y;
+  Qx[K + 1] = rx.x;
+  Qy[K + 1] = rx.y;
+  bool degenerate = false;
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 G = s.G[cd.w[j - 1]];
+    const float a = line_dist(G, Ix[j], Iy[j]);
+    const float b = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    // parallel lines (or a reflection point absurdly far away): no path
+    float t = __fdiv_rn(b, b - a);
+    if (!(fabsf(t) <= 1e8f)) {
+      degenerate = true;
+      t = 0.f;
+    }
+    Qx[j] = fmaf(t, Ix[j] - Qx[j + 1], Qx[j + 1]);
+    Qy[j] = fmaf(t, Iy[j] - Qy[j + 1], Qy[j + 1]);
+  }
+  // --- legs: length and the smoothing-ready normal form of each leg's line.
+  float L = 0.f;
+  float mx[K + 1], my[K + 1], mc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float len2 = fmaf(dx, dx, dy * dy);
+    degenerate |= !(len2 > 0.f);
+    const float inv = rsqrtf(len2);
+    L = fmaf(len2, inv, L);
+    const float nx = -dy * inv, ny = dx * inv;
+    const float nq = fmaf(nx, Qx[j], ny * Qy[j]);
+    if (MODE == MODE_HARD) {
+      const float a6 = alpha * (1.0f / 6.0f);
+      mx[j] = nx * a6;
+      my[j] = ny * a6;
+      mc[j] = fmaf(-nq, a6, 0.5f);
+    } else if (MODE == MODE_STEP) {
+      mx[j] = nx;
+      my[j] = ny;
+      mc[j] = -nq;
+    } else {
+      const float kap = alpha * LOG2E;
+      mx[j] = nx * kap;
+      my[j] = ny * kap;
+      mc[j] = -nq * kap;
+    }
+  }
+  // --- continuous validity of each reflection (Sec. V-A): on the segment, and the
+  //     previous and next vertices on the same side of the wall's line.
+  float V = 1.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 G = s.G[w];
+    const float t0 = s.T[w].x;
+    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -t0));   // u = (ny, -nx)
+    const Smooth3 s1 = smooth3<MODE>(tau, alpha);
+    const Smooth3 s2 = smooth3<MODE>(G.w - tau, alpha);
+    const Smooth3 sp = smooth3<MODE>(line_dist(G, Qx[j - 1], Qy[j - 1]), alpha);
+    const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
+    V *= s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+  }
+  // optional: skip the obstruction loop when the whole warp's validity is exactly 0
+  if (cull && __all_sync(0xffffffffu, V == 0.f || degenerate)) return 0.f;
+  // --- obstruction of every leg by every wall except the ones its end points lie on.
+  float vis[K + 1];
+  const float min_div = leg_visibility<MODE, K, MASKED>(s, W, cd, Qx, Qy, mx, my, mc, vis);
+  if constexpr (!MASKED && MODE != MODE_STEP) {
+    // A skipped pair's factor is >= 1/2 when its end point's distance to the wall's
+    // line is accurate; a relaxed reflection point far along the line (large
+    // backtrace ratio) can break that.  A warp with such a lane recomputes the
+    // candidate with the skipped pairs masked (same function up to rounding).
+    const bool bad = !degenerate && !(min_div >= 0.25f);
+    if (__any_sync(0xffffffffu, bad)) leg_visibility<MODE, K, true>(s, W, cd, Qx, Qy, mx, my, mc, vis);
   }
   float p = V * gk;
 #pragma unroll
