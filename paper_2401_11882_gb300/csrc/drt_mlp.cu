@@ -79,8 +79,9 @@ struct GemmArgs {
   int ldh;
   bf16* HT;            // transposed copy [N][ldht] (optional)
   int ldht;
-  float* C;            // DW: out [M][ldc]
+  float* C;            // DW: out [M][ldc]; with split-K, partial z at C + z * M * ldc
   int ldc;
+  int k_splits;        // DW: K is split into k_splits equal slices (blockIdx.z), >= 1
 };
 
 __device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* smem_ptr) {
@@ -117,7 +118,10 @@ __global__ void __launch_bounds__(128) gemm_nt_kernel(const GemmArgs g) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 
-  for (int k0 = 0; k0 < g.K; k0 += 32) {
+  const int kz = g.K / (g.k_splits > 0 ? g.k_splits : 1);
+  const int kbeg = blockIdx.z * kz, kend = kbeg + kz;
+  float* C = g.C ? g.C + (size_t)blockIdx.z * g.M * g.ldc : nullptr;
+  for (int k0 = kbeg; k0 < kend; k0 += 32) {
     for (int i = tid; i < 256; i += 128) {
       const int r = i >> 2, c = (i & 3) * 8;
       *reinterpret_cast<uint4*>(&As[r][c]) =
@@ -170,9 +174,20 @@ __global__ void __launch_bounds__(128) gemm_nt_kernel(const GemmArgs g) {
           g.H[(size_t)row * g.ldh + col] = dz;
           g.HT[(size_t)col * g.ldht + row] = dz;
         } else {
-          g.C[(size_t)row * g.ldc + col] = v;
+          C[(size_t)row * g.ldc + col] = v;
         }
       }
+}
+
+// out[i] = sum_z part[z][i] over the K splits, in split order
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, long long n,
+                                     float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + i];
+    out[i] = s;
+  }
 }
 
 // F[b] = (sin(2 pi B_j . x_b))_j, (cos(2 pi B_j . x_b))_j as BF16, row-major and transposed.
@@ -350,7 +365,8 @@ using mlp::bf16;
 
 struct MlpWs {
   bf16 *F, *FT, *H[DRT_MLP_LAYERS + 1], *HT[DRT_MLP_LAYERS + 1], *dZa, *dZTa, *dZb, *dZTb;
-  float *Z[DRT_MLP_LAYERS], *y, *dy;
+  float *Z[DRT_MLP_LAYERS], *y, *dy, *part;
+  int splits;
   size_t bytes;
 };
 
@@ -381,6 +397,10 @@ MlpWs carve(void* base, int B) {
   w.dZTa = reinterpret_cast<bf16*>(take(hb));
   w.dZb = reinterpret_cast<bf16*>(take(hb));
   w.dZTb = reinterpret_cast<bf16*>(take(hb));
+  // weight gradients reduce over the batch: split it into slices of >= 256 rows
+  w.splits = std::max(1, std::min(32, B / 256));
+  while (w.splits > 1 && (B % (w.splits * 64))) --w.splits;
+  w.part = reinterpret_cast<float*>(take((size_t)w.splits * mlp::WID * mlp::WID * 4));
   w.bytes = o;
   return w;
 }
@@ -393,6 +413,11 @@ std::atomic<int> g_tc_skip_mma{0};
 std::mutex g_tc_mu;
 int* g_tc_status_ptr[64] = {};
 
+// 72 KB of dynamic shared memory per CTA: the two 128 x 64 stages (or the FP32
+// output tile) fit, and at most three CTAs (3 x 128 TMEM columns) share an SM.
+constexpr int TC_SMEM = 72 * 1024;
+static_assert(mlp::TcSmem<128>::BYTES <= TC_SMEM && mlp::TcSmem<64>::BYTES <= TC_SMEM, "smem");
+
 int* tc_status_ptr() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
@@ -401,34 +426,32 @@ int* tc_status_ptr() {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, mlp::g_tc_status) != cudaSuccess) return nullptr;
     g_tc_status_ptr[dev] = static_cast<int*>(p);
-    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   }
   return g_tc_status_ptr[dev];
 }
 
 template <int EPI>
 cudaError_t gemm(const mlp::GemmArgs& g, cudaStream_t st) {
-  const bool tc_shape = (g.M % mlp::TC_BM == 0) && (g.K % mlp::TC_BK == 0) &&
-                        (g.N % 256 == 0 || g.N == 64);
+  const bool tc_shape = (g.M % mlp::TC_BM == 0) && (g.K % mlp::TC_BK == 0) && (g.N % 64 == 0);
   int* status = (g_tc_mode.load() && tc_shape) ? tc_status_ptr() : nullptr;
   if (status) {
-    // 100 KB of dynamic shared memory keeps at most two CTAs (2 x 256 TMEM columns) per SM
-    const size_t smem = 100 * 1024;
-    if (g.N % 256 == 0) {
-      dim3 grid(g.N / 256, g.M / mlp::TC_BM);
-      mlp::tc_gemm_nt_kernel<EPI, 256><<<grid, 128, smem, st>>>(g, status, g_tc_skip_mma.load());
+    const int z = (EPI == mlp::EPI_DW && g.k_splits > 1) ? g.k_splits : 1;
+    if (g.N % 128 == 0) {
+      dim3 grid(g.N / 128, g.M / mlp::TC_BM, z);
+      mlp::tc_gemm_nt_kernel<EPI, 128><<<grid, 128, TC_SMEM, st>>>(g, status, g_tc_skip_mma.load());
     } else {
-      dim3 grid(1, g.M / mlp::TC_BM);
-      mlp::tc_gemm_nt_kernel<EPI, 64><<<grid, 128, smem, st>>>(g, status, g_tc_skip_mma.load());
+      dim3 grid(g.N / 64, g.M / mlp::TC_BM, z);
+      mlp::tc_gemm_nt_kernel<EPI, 64><<<grid, 128, TC_SMEM, st>>>(g, status, g_tc_skip_mma.load());
     }
     return cudaGetLastError();
   }
-  dim3 grid(g.N / 64, g.M / 64);
+  dim3 grid(g.N / 64, g.M / 64, (EPI == mlp::EPI_DW && g.k_splits > 1) ? g.k_splits : 1);
   mlp::gemm_nt_kernel<EPI><<<grid, 128, 0, st>>>(g);
   return cudaGetLastError();
 }
@@ -556,9 +579,16 @@ drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const floa
     g.M = mlp::WID;
     g.N = L.k[l];
     g.K = B;
-    g.C = grad + L.w[l];
+    g.C = w.part;
     g.ldc = L.k[l];
+    g.k_splits = w.splits;
     if ((e = gemm<mlp::EPI_DW>(g, st)) != cudaSuccess) break;
+    {
+      const long long n = (long long)mlp::WID * L.k[l];
+      mlp::splitk_reduce_kernel<<<(int)std::min<long long>((n + 255) / 256, 1024), 256, 0, st>>>(
+          w.part, w.splits, n, grad + L.w[l]);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+    }
     mlp::row_sum_kernel<<<(mlp::WID * 32 + 255) / 256, 256, 0, st>>>(dZT, mlp::WID, B, nullptr,
                                                                      grad + L.b[l]);
     if ((e = cudaGetLastError()) != cudaSuccess) break;

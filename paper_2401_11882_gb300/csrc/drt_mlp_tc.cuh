@@ -2,7 +2,7 @@
 // C[M x N] = A[M x K] . Bt[N x K]^T with BF16 operands and an FP32 accumulator
 // in tensor memory (TMEM), the same three epilogues as the mma.sync kernel.
 //
-// One CTA (4 warps) computes a 128 x BN tile (BN = 64 or 256): it allocates BN
+// One CTA (4 warps) computes a 128 x BN tile (BN = 64 or 128): it allocates BN
 // TMEM columns, walks K in chunks of 64, copies the chunk of A (128 x 64) and
 // of Bt (BN x 64) into shared memory in the canonical no-swizzle K-major layout
 // (8-row x 16-byte core matrices; core matrices adjacent in K are 128 bytes
@@ -80,18 +80,34 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
 // skip_mma != 0 (test knob): no MMA and no commit is issued, so the bounded
 // wait runs out with nothing in flight; the kernel must then report the
 // timeout, skip its epilogue and still free its tensor memory.
+//
+// Pipeline: two shared-memory stages; the copy of chunk k+1 overlaps the MMAs of
+// chunk k, and a stage is refilled only after the commit of the MMAs that read it.
+// Epilogue: the accumulator goes TMEM -> registers (tcgen05.ld, one row per
+// thread) -> a shared-memory tile, from which the outputs are written with
+// consecutive threads on consecutive columns (row-major outputs) or rows (the
+// transposed copy), i.e. coalesced.
+template <int BN>
+struct TcSmem {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int TILE_LD = BN + 1;   // padded row of the FP32 tile
+  static constexpr int TILE = TC_BM * TILE_LD * 4;
+  static constexpr int BYTES = (2 * STAGE > TILE ? 2 * STAGE : TILE);
+};
+
 template <int EPI, int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, int* status,
                                                             int skip_mma) {
+  using SM = TcSmem<BN>;
   extern __shared__ __align__(1024) uint8_t tc_smem[];
-  uint8_t* sA = tc_smem;                                  // 128 x 64 bf16 = 16 KB
-  uint8_t* sB = tc_smem + TC_BM * TC_BK * 2;              // BN x 64 bf16
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
-  const uint32_t mbar_a = smem_u32(&mbar);
+  const uint32_t mb0 = smem_u32(&mbar[0]), mb1 = smem_u32(&mbar[1]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -102,7 +118,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, in
   }
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -111,11 +128,25 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, in
   const uint32_t tmem = tmem_base;
   constexpr uint32_t IDESC = tc_idesc<BN>();
 
-  uint32_t phase = 0;
-  const int n_chunks = g.K / TC_BK;
+  const int kz = g.K / (g.k_splits > 0 ? g.k_splits : 1);   // this CTA's K slice (split-K)
+  const int kbase = blockIdx.z * kz;
+  const int n_chunks = kz / TC_BK;
+  int last_issued = -1;
   for (int kc = 0; kc < n_chunks; ++kc) {
-    const int k0 = kc * TC_BK;
-    // A chunk: 128 rows x 8 pieces of 16 bytes; Bt chunk: BN rows x 8 pieces
+    const int st = kc & 1;
+    const uint32_t mb = st ? mb1 : mb0;
+    uint8_t* sA = tc_smem + st * SM::STAGE;
+    uint8_t* sB = sA + SM::A_BYTES;
+    if (kc >= 2) {
+      // the MMAs of chunk kc-2 read this stage: wait for their commit
+      if (!tc_wait(mb, ((kc - 2) >> 1) & 1)) {
+        s_fail = 1;
+        if (status) atomicExch(status, 1);
+      }
+      __syncthreads();
+      if (s_fail) break;
+    }
+    const int k0 = kbase + kc * TC_BK;
     for (int i = tid; i < TC_BM * 8; i += 128) {
       const int r = i >> 3, c = (i & 7) * 8;
       const uint4 v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + c);
@@ -143,23 +174,24 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, in
             : "memory");
       }
       asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              mbar_a)
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
           : "memory");
     }
-    // every thread waits: the chunk buffers are reused by the next iteration
-    if (!tc_wait(mbar_a, phase)) {
+    last_issued = kc;
+  }
+  // the last commit covers every MMA issued before it
+  if (!s_fail && last_issued >= 0) {
+    const uint32_t mb = (last_issued & 1) ? mb1 : mb0;
+    if (!tc_wait(mb, (last_issued >> 1) & 1)) {
       s_fail = 1;
       if (status) atomicExch(status, 1);
     }
-    __syncthreads();
-    if (s_fail) break;   // `phase` stays the one still pending
-    phase ^= 1u;
   }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   if (!s_fail) {
-    const int row = m0 + tid;
+    float* tile = reinterpret_cast<float*>(tc_smem);   // [128][BN + 1], the stages are free now
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -173,29 +205,41 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(const GemmArgs g, in
           : "r"(lane_addr + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = n0 + c0 + j;
-        const float acc = __uint_as_float(v[j]);
-        if (EPI == EPI_FWD) {
-          const float z = acc + g.bias[col];
-          if (g.Z) g.Z[(size_t)row * g.ldz + col] = z;
-          const bf16 h = __float2bfloat16(z * sigm(z));
-          g.H[(size_t)row * g.ldh + col] = h;
-          if (g.HT) g.HT[(size_t)col * g.ldht + row] = h;
-        } else if (EPI == EPI_DH) {
-          const float zp = g.Z[(size_t)row * g.ldz + col];
-          const float s = sigm(zp);
-          const bf16 dz = __float2bfloat16(acc * s * (1.f + zp * (1.f - s)));
-          g.H[(size_t)row * g.ldh + col] = dz;
-          g.HT[(size_t)col * g.ldht + row] = dz;
-        } else {
-          g.C[(size_t)row * g.ldc + col] = acc;
-        }
+      for (int j = 0; j < 16; ++j) tile[tid * SM::TILE_LD + c0 + j] = __uint_as_float(v[j]);
+    }
+    __syncthreads();
+    // row-major outputs: consecutive threads on consecutive columns
+    for (int idx = tid; idx < TC_BM * BN; idx += 128) {
+      const int r = idx / BN, c = idx % BN;
+      const int row = m0 + r, col = n0 + c;
+      const float acc = tile[r * SM::TILE_LD + c];
+      if (EPI == EPI_FWD) {
+        const float z = acc + g.bias[col];
+        if (g.Z) g.Z[(size_t)row * g.ldz + col] = z;
+        const float h = z * sigm(z);
+        g.H[(size_t)row * g.ldh + col] = __float2bfloat16(h);
+        tile[r * SM::TILE_LD + c] = h;
+      } else if (EPI == EPI_DH) {
+        const float zp = g.Z[(size_t)row * g.ldz + col];
+        const float s = sigm(zp);
+        const float dz = acc * s * (1.f + zp * (1.f - s));
+        g.H[(size_t)row * g.ldh + col] = __float2bfloat16(dz);
+        tile[r * SM::TILE_LD + c] = dz;
+      } else {
+        g.C[(size_t)blockIdx.z * g.M * g.ldc + (size_t)row * g.ldc + col] = acc;
       }
     }
-  } else if (!skip_mma) {
-    // give an MMA that may still be running a last bounded chance to finish
-    tc_wait(mbar_a, phase);
+    if (EPI != EPI_DW && g.HT) {
+      __syncthreads();
+      // transposed copy: consecutive threads on consecutive rows
+      for (int idx = tid; idx < TC_BM * BN; idx += 128) {
+        const int c = idx / TC_BM, r = idx % TC_BM;
+        g.HT[(size_t)(n0 + c) * g.ldht + m0 + r] = __float2bfloat16(tile[r * SM::TILE_LD + c]);
+      }
+    }
+  } else if (!skip_mma && last_issued >= 0) {
+    // give MMAs that may still be running a last bounded chance to finish
+    tc_wait((last_issued & 1) ? mb1 : mb0, (last_issued >> 1) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
