@@ -18,6 +18,10 @@ seeded search.  Data generation and training are reported separately, with
 the number of problems after which the surrogate pays for itself.
 
     python -m paper_2401_11882_gb300.experiments --seeds 0 1 2 --samples 1048576
+
+The annealing study (Sec. VII, convergence success with and without smoothing):
+
+    python -m paper_2401_11882_gb300.experiments --study annealing --scenes 256
 """
 from __future__ import annotations
 
@@ -89,13 +93,89 @@ def time_to_optimum(scene_seed=0, n_samples=1 << 20, epochs=20, n_starts=64, max
     }
 
 
+def _los_batch(rng, n_scenes, n_rx, n_walls, n_starts, smoothing, grid_tx=None):
+    """Square + n_walls random segments (lengths 0.1-0.4), n_rx receivers, K = 0."""
+    walls, rxs, w_off, r_off, txs = [], [], [0], [0], []
+    for _ in range(n_scenes):
+        w = np.concatenate([scenes.unit_square_walls(),
+                            scenes.random_segments(rng, n_walls, (0.1, 0.4))])
+        r = scenes.rx_uniform(rng, n_rx)
+        t = scenes.rx_uniform(rng, n_starts, 0.05, 0.95)
+        walls.append(w); rxs.append(r); txs.append(t if grid_tx is None else grid_tx)
+        w_off.append(w_off[-1] + w.shape[0]); r_off.append(r_off[-1] + n_rx)
+    return scenes.SceneBatch(np.concatenate(walls), np.asarray(w_off, np.int32), np.concatenate(rxs),
+                             np.asarray(r_off, np.int32), np.zeros(n_scenes, np.int32),
+                             np.stack(txs).astype(np.float32), 1.0, smoothing)
+
+
+def annealing_study(n_scenes=256, rx_counts=(2, 3, 4), n_starts=4, n_walls=5, steps=100,
+                    lr=2e-2, lr_decay=0.96, grid=128, tols=(1e-2, 5e-2), seed=0,
+                    device="cuda") -> dict:
+    """Sec. VII: TX placement by gradient descent on -min_r P_r (LOS only), with the
+    smoothing annealed as alpha_i = 100^(i/(steps-1)) (sigmoid) against no smoothing
+    (unit step); Adam with a learning rate decaying by lr_decay per step, so that a
+    run settles instead of circling the (non-smooth) max-min optimum.  A run
+    converges when the unsmoothed objective at its final TX is within tol
+    (relative) of the best value seen for that scene (a grid x grid scan and every
+    final point)."""
+    from .batched import BatchedDescent, geometric_alpha
+    out = {}
+    sched = geometric_alpha(1.0, 100.0, steps)
+    c = (np.arange(grid) + 0.5) / grid
+    gx, gy = np.meshgrid(c, c, indexing="xy")
+    grid_tx = np.stack([gx.ravel(), gy.ravel()], 1).astype(np.float32)
+    for n_rx in rx_counts:
+        rng = np.random.default_rng(seed + n_rx)
+        smooth = _los_batch(rng, n_scenes, n_rx, n_walls, n_starts, "sigmoid")
+        step = scenes.SceneBatch(smooth.walls, smooth.wall_off, smooth.rx, smooth.rx_off,
+                                 smooth.max_order, smooth.tx0, 1.0, "step")
+        # best unsmoothed objective per scene over the grid
+        scan = scenes.SceneBatch(smooth.walls, smooth.wall_off, smooth.rx, smooth.rx_off,
+                                 smooth.max_order,
+                                 np.broadcast_to(grid_tx, (n_scenes,) + grid_tx.shape).copy(),
+                                 1.0, "step")
+        bd = BatchedDescent(scan, device=device, alpha=1.0)
+        F_grid = (-bd.evaluate()).cpu().numpy().reshape(n_scenes, -1).max(axis=1)
+        bd.close()
+        finals = {}
+        for name, b, alpha in (("smoothed", smooth, sched), ("unsmoothed", step, 1.0)):
+            bd = BatchedDescent(b, lr=lr, alpha=alpha, device=device, lr_decay=lr_decay)
+            bd.run(steps)
+            tx = bd.tx.cpu().numpy().reshape(n_scenes, n_starts, 2)
+            bd.close()
+            ev = scenes.SceneBatch(b.walls, b.wall_off, b.rx, b.rx_off, b.max_order, tx, 1.0, "step")
+            e = BatchedDescent(ev, device=device, alpha=1.0)
+            finals[name] = (-e.evaluate()).cpu().numpy().reshape(n_scenes, n_starts)
+            e.close()
+        best = np.maximum(F_grid[:, None], np.maximum(finals["smoothed"].max(1, keepdims=True),
+                                                      finals["unsmoothed"].max(1, keepdims=True)))
+        res = {"runs": int(n_scenes * n_starts)}
+        for tol in tols:
+            ok = {k: v >= (1.0 - tol) * best for k, v in finals.items()}
+            n_ok_unsmoothed = int(ok["unsmoothed"].sum())
+            res[f"tol_{tol:g}"] = {
+                "success_smoothed": float(ok["smoothed"].mean()),
+                "success_unsmoothed": float(ok["unsmoothed"].mean()),
+                "ratio": float(ok["smoothed"].mean() / max(ok["unsmoothed"].mean(), 1e-12)),
+                "retained": (float((ok["smoothed"] & ok["unsmoothed"]).sum() / n_ok_unsmoothed)
+                             if n_ok_unsmoothed else None),
+            }
+        out[f"{n_rx}_rx"] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--seeds", type=int, nargs="+", default=[0])
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--starts", type=int, default=64)
+    ap.add_argument("--study", choices=["surrogate", "annealing"], default="surrogate")
+    ap.add_argument("--scenes", type=int, default=256)
     args = ap.parse_args()
+    if args.study == "annealing":
+        print(json.dumps(annealing_study(n_scenes=args.scenes)), flush=True)
+        return
     rows = []
     for s in args.seeds:
         r = time_to_optimum(s, args.samples, args.epochs, args.starts)

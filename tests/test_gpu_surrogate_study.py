@@ -24,3 +24,15 @@ def test_small_study_and_oracle_verified_optimum(oracle_mod):
         assert r[k]["best_loss"] <= 0.0
         assert r[k]["steps"] >= 1
     assert r["seeded"]["best_loss"] >= r["L_star"] - 1e-3 * abs(r["L_star"])
+
+
+def test_annealing_study_runs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_11882_gb300 import experiments
+    r = experiments.annealing_study(n_scenes=16, rx_counts=(2,), n_starts=2, steps=20, grid=32)
+    d = r["2_rx"]
+    assert d["runs"] == 32
+    for tol in ("tol_0.01", "tol_0.05"):
+        assert 0.0 <= d[tol]["success_smoothed"] <= 1.0
+        assert 0.0 <= d[tol]["success_unsmoothed"] <= 1.0
