@@ -132,8 +132,12 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const BatchArgs a) {
     const long long nc = n_candidates(W, K);
     float acc = 0.f;
     const bool masked = alpha > FAST_SKIP_MAX_ALPHA;
-    for (long long c = warp; c < nc; c += nwarps) {
-      const Cand cd = decode_candidate(c, W, K);
+    // each warp takes a contiguous block of candidates and steps through it
+    const long long cb = nc * warp / nwarps, ce = nc * (warp + 1) / nwarps;
+    Cand cd;
+    if (cb < ce) cd = decode_candidate(cb, W, K);
+    for (long long c = cb; c < ce; ++c) {
+      if (c > cb) next_candidate(cd, W);
       if (!masked) {
         switch (cd.k) {
           case 0: acc += path_power<MODE, 0>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;

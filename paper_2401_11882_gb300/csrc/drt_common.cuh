@@ -22,6 +22,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// a * b + c clamped to [0, 1] in one rounding (PTX fma with the .sat modifier)
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+  float y;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(c));
+  return y;
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -74,37 +81,70 @@ struct Cand {
   int w[KMAX > 0 ? KMAX : 1];
 };
 
-__device__ __forceinline__ Cand decode_candidate(long long c, int W, int K) {
+__device__ __forceinline__ Cand decode_candidate(long long c_in, int W, int K) {
+  // N_K < 2^31 for every supported (W, K), so 32-bit unsigned arithmetic suffices
+  unsigned c = (unsigned)c_in;
   Cand cd;
   cd.k = 0;
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) cd.w[j] = -1;
   if (c == 0) return cd;
   c -= 1;
-  long long block = W;      // number of candidates of order k: W (W-1)^(k-1)
+  const unsigned Wm1 = (unsigned)(W - 1);
+  unsigned block = (unsigned)W;   // number of candidates of order k: W (W-1)^(k-1)
+  unsigned stride = 1;            // (W-1)^(k-1)
   int k = 1;
   while (k < K && c >= block) {
     c -= block;
-    block *= (W - 1);
+    block *= Wm1;
+    stride *= Wm1;
     ++k;
   }
   cd.k = k;
   // first wall: c / (W-1)^(k-1); every later digit d in [0, W-2] skips the previous wall
-  long long stride = block / W;
   int prev = (int)(c / stride);
   cd.w[0] = prev;
-  long long rem = c - (long long)prev * stride;
+  unsigned rem = c - (unsigned)prev * stride;
 #pragma unroll
   for (int j = 1; j < KMAX; ++j) {
     if (j < k) {
-      stride /= (W - 1);
+      stride /= Wm1;
       const int d = (int)(rem / stride);
-      rem -= (long long)d * stride;
+      rem -= (unsigned)d * stride;
       prev = d < prev ? d : d + 1;
       cd.w[j] = prev;
     }
   }
   return cd;
+}
+
+// The candidate after cd in the same order (lexicographic increment of the wall
+// sequence, each position skipping the wall before it), or the first candidate
+// of the next order (0, 1, 0, 1, ...).  Only called while a next one exists.
+__device__ __forceinline__ void next_candidate(Cand& cd, int W) {
+  const int k = cd.k;
+  int jstar = -1;   // position incremented (positions after it are reset)
+#pragma unroll
+  for (int j = KMAX - 1; j >= 0; --j) {
+    if (jstar < 0 && j < k) {
+      const int prevw = (j > 0) ? cd.w[j > 0 ? j - 1 : 0] : -1;
+      int v = cd.w[j] + 1;
+      if (v == prevw) ++v;
+      if (v < W) {
+        cd.w[j] = v;
+        jstar = j;
+      }
+    }
+  }
+  if (jstar < 0) {   // order k exhausted: first sequence of order k + 1
+    cd.k = k + 1;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) cd.w[i] = (i < k + 1) ? (i & 1) : -1;
+    return;
+  }
+#pragma unroll
+  for (int i = 1; i < KMAX; ++i)
+    if (i > jstar && i < k) cd.w[i] = (cd.w[i - 1] == 0) ? 1 : 0;
 }
 
 // ------------------------------------------------------------ wall records

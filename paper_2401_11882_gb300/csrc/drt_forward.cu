@@ -42,12 +42,14 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
     const bool live = r < a.R;
     if (!live) r = a.R - 1;
     const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
-    const long long c0 = chunk * a.chunk;
-    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+    // N_K < 2^31 for every supported (W, K): candidate indices fit in 32 bits
+    const int c0 = (int)(chunk * a.chunk);
+    const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
     float acc = 0.f;
     const bool masked = a.alpha > FAST_SKIP_MAX_ALPHA;
-    for (long long c = c0; c < c1; ++c) {
-      const Cand cd = decode_candidate(c, a.W, a.K);
+    Cand cd = decode_candidate(c0, a.W, a.K);
+    for (int i = 0; i < nc; ++i) {
+      if (i > 0) next_candidate(cd, a.W);
       float p;
       if (!masked) {
         switch (cd.k) {

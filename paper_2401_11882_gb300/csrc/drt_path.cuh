@@ -50,6 +50,13 @@ __device__ __forceinline__ float side(float z) {
   return z > 0.f ? 1.f : 0.f;
 }
 
+// s() of (a b + c) for the H-record forms: one saturating FMA for the hard sigmoid
+template <int MODE>
+__device__ __forceinline__ float side_fma(float a, float b, float c) {
+  if (MODE == MODE_HARD) return fma_sat(a, b, c);
+  return fmaf(a, b, c) > 0.f ? 1.f : 0.f;
+}
+
 // Largest alpha for which the hard-sigmoid and sigmoid loops test every (leg,
 // wall) pair and divide the skipped pairs out afterwards: there a point lying on
 // a wall's line has s within 1/4 of 1/2 even after FP32 rounding of its
@@ -80,13 +87,13 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
       float sv[K + 2], uv[K + 2];
       sv[0] = h.w;
 #pragma unroll
-      for (int i = 1; i <= K + 1; ++i) sv[i] = __saturatef(fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z)));
+      for (int i = 1; i <= K + 1; ++i) sv[i] = fma_sat(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
 #pragma unroll
       for (int i = 1; i <= (K > 0 ? K : 1); ++i) uv[i] = fmaf(-2.f, sv[i], 1.f);
 #pragma unroll
       for (int j = 0; j <= K; ++j) {
-        const float sa = __saturatef(fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j])));
-        const float sb = __saturatef(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
+        const float sa = fma_sat(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+        const float sb = fma_sat(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
         const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
         const float x1 = (j == 0) ? fmaf(sv[0], uv[1], sv[1]) : fmaf(sv[j + 1], uv[j], sv[j]);
         vis[j] = fmaf(-vis[j], x1 * x2, vis[j]);
@@ -101,10 +108,10 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
           const int w = cd.w[side_ == 0 ? j - 1 : j];
           const float4 h = s.H[w];
           const float4 e = s.E[w];
-          const float s0 = (j == 0) ? h.w : __saturatef(fmaf(h.x, Qx[j], fmaf(h.y, Qy[j], h.z)));
-          const float s1 = __saturatef(fmaf(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z)));
-          const float sa = __saturatef(fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j])));
-          const float sb = __saturatef(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
+          const float s0 = (j == 0) ? h.w : fma_sat(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
+          const float s1 = fma_sat(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z));
+          const float sa = fma_sat(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+          const float sb = fma_sat(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
           const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
           const float x1 = (j == 0) ? fmaf(s0, fmaf(-2.f, s1, 1.f), s1) : fmaf(s1, fmaf(-2.f, s0, 1.f), s0);
           const float f = fmaf(-x1, x2, 1.f);
@@ -123,13 +130,13 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
       sv[0] = h.w;
       uv[0] = fmaf(-2.f, h.w, 1.f);
 #pragma unroll
-      for (int i = 1; i <= K + 1; ++i) sv[i] = side<MODE>(fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z)));
+      for (int i = 1; i <= K + 1; ++i) sv[i] = side_fma<MODE>(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
 #pragma unroll
       for (int i = 1; i <= K; ++i) uv[i] = fmaf(-2.f, sv[i], 1.f);
 #pragma unroll
       for (int j = 0; j <= K; ++j) {
-        const float sa = side<MODE>(fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j])));
-        const float sb = side<MODE>(fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j])));
+        const float sa = side_fma<MODE>(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+        const float sb = side_fma<MODE>(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
         const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
         const float x1 = fmaf(sv[j + 1], uv[j], sv[j]);
         float bl = x1 * x2;
@@ -264,7 +271,7 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
     const float a = line_dist(G, Ix[j], Iy[j]);
     const float b = line_dist(G, Qx[j + 1], Qy[j + 1]);
     // parallel lines (or a reflection point absurdly far away): no path
-    float t = __fdiv_rn(b, b - a);
+    float t = __fdividef(b, b - a);
     if (!(fabsf(t) <= 1e8f)) {
       degenerate = true;
       t = 0.f;
@@ -331,7 +338,7 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
   float p = V * gk;
 #pragma unroll
   for (int j = 0; j <= K; ++j) p *= vis[j];
-  p = __fdiv_rn(p, L * L);
+  p = __fdividef(p, L * L);
   return degenerate ? 0.f : p;
 }
 
