@@ -36,9 +36,10 @@ L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "forward_large_scene_traffic.txt")
 
 
-def workload_scene(rank: int = 0, rx_grid: int = 256):
+def workload_scene(rank: int = 0, rx_grid: int = 256, smoothing: str = "hard_sigmoid",
+                   alpha: float = 100.0):
     from paper_2401_11882_gb300 import scenes
-    sc = scenes.clutter_scene(60, rx_grid, 0, 100.0, "hard_sigmoid", 2, True)
+    sc = scenes.clutter_scene(60, rx_grid, 0, alpha, smoothing, 2, True)
     if rank:
         # an independent problem per rank: the TX moves along the grid's middle row
         sc = sc.replace(tx=np.array([0.5 + 0.011 * ((rank % 30) - 15), 0.2], np.float32))
@@ -124,7 +125,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2401_11882_gb300 import workload
-    sc = workload_scene(0, args.rx_grid)
+    sc = workload_scene(0, args.rx_grid, args.smoothing, args.alpha)
     n_cand = workload.num_candidates(sc.n_walls, sc.max_order)
     import oracle
     oracle.build()
@@ -209,7 +210,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    sc = workload_scene(rank, args.rx_grid)
+    sc = workload_scene(rank, args.rx_grid, args.smoothing, args.alpha)
     n_cand = drt.num_candidates(sc.n_walls, sc.max_order)
     work = workload.forward_work(sc.n_walls, sc.max_order, sc.n_rx)
     w = torch.tensor(sc.walls, device=dev)
@@ -309,7 +310,7 @@ def run_ours(args):
         "config": workload_config(sc, n_cand),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "forward_kernel<hard sigmoid> (+ its chunk-sum kernel)",
+                     "kernel": f"forward_kernel<{sc.smoothing}> (+ its chunk-sum kernel)",
                      "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
                                     f"FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "flops_per_launch": work["flops"], "ms_per_launch": fwd_avg_s * 1e3},
@@ -400,6 +401,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--rx-grid", type=int, default=256,
                     help="receiver grid side (256 = the benchmark workload; smaller for profiling)")
+    ap.add_argument("--smoothing", default="hard_sigmoid",
+                    choices=["hard_sigmoid", "sigmoid", "step"],
+                    help="smoothing of the timed step (hard_sigmoid = the benchmark workload)")
+    ap.add_argument("--alpha", type=float, default=100.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
