@@ -159,7 +159,7 @@ def file_hash(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-FORWARD_SOURCES = ("drt_forward.cu", "drt_path.cuh", "drt_common.cuh")
+FORWARD_SOURCES = ("drt_forward.cu", "drt_path.cuh", "drt_path_pair.cuh", "drt_common.cuh")
 
 
 def forward_source_hash() -> str:
@@ -310,7 +310,10 @@ def run_ours(args):
         "config": workload_config(sc, n_cand),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"forward_kernel<{sc.smoothing}> (+ its chunk-sum kernel)",
+                     "kernel": ((f"forward_pair_kernel<{sc.smoothing}>"
+                                 if sc.smoothing in ("hard_sigmoid", "sigmoid") and sc.alpha <= 1e4
+                                 else f"forward_kernel<{sc.smoothing}>")
+                                + " (+ its chunk-sum kernel)"),
                      "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
                                     f"FLOP x {sm_max:.0f} MHz (max SM clock)",
                      "flops_per_launch": work["flops"], "ms_per_launch": fwd_avg_s * 1e3},
@@ -347,9 +350,15 @@ def measure_extras(drt, dev, sc, w, t, r):
     ev = sc.n_rx * n_cand
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "sigmoid"))
     out["sigmoid_forward_evals_per_s"] = ev / s
+    s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "sigmoid",
+                                  tile=drt.TileConfig(single_rx=True)))
+    out["sigmoid_forward_one_rx_per_lane_evals_per_s"] = ev / s
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
                                   tile=drt.TileConfig(cull_invalid=True)))
     out["hard_forward_culled_evals_per_s"] = ev / s
+    s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
+                                  tile=drt.TileConfig(single_rx=True)))
+    out["hard_forward_one_rx_per_lane_evals_per_s"] = ev / s
     g = scenes.gradient_scene()
     gw, gt, gr = (torch.tensor(g.walls, device=dev), torch.tensor(g.tx, device=dev),
                   torch.tensor(g.rx, device=dev))

@@ -80,6 +80,13 @@ typedef struct {
    where s saturates at 0; a no-op for the sigmoid).  Off by default. */
 #define DRT_TILE_CULL_INVALID 1
 
+/* Hard sigmoid and sigmoid with alpha <= 1e4: the forward holds two receivers
+   per lane (tiles of 64 receivers) and runs its obstruction loop in packed FP32
+   pairs; the powers are the same, bit for bit.  This flag selects one receiver
+   per lane (tiles of 32) instead.  The unit step and alpha > 1e4 always use one
+   receiver per lane. */
+#define DRT_TILE_SINGLE_RX 2
+
 /* Human-readable name of a status code (static string). */
 const char* drt_status_string(drt_status status);
 

@@ -20,6 +20,7 @@ STATUS = {0: "DRT_OK", 1: "DRT_ERR_INVALID_ARG", 2: "DRT_ERR_UNSUPPORTED", 3: "D
 MAX_ORDER = 3
 MAX_WALLS = 1024
 TILE_CULL_INVALID = 1
+TILE_SINGLE_RX = 2
 
 
 class Scene(ctypes.Structure):

@@ -13,7 +13,7 @@ import json
 import math
 import os
 import threading
-from dataclasses import asdict
+from dataclasses import asdict, replace
 
 from .ops import TileConfig
 
@@ -92,6 +92,9 @@ def tune_forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "
             return TileConfig(**cache[key]["tile"])
     timer = timer or time_fn
     cands = candidates or FORWARD_CANDIDATES
+    if candidates is None and smoothing in ("hard_sigmoid", "sigmoid"):
+        # these smoothings have a one-receiver-per-lane variant of every shape
+        cands = cands + [replace(c, single_rx=True) for c in cands]
     timings = []
     for cfg in cands:
         ms = timer(lambda: ops.forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef,

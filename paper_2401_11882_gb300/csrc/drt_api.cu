@@ -130,12 +130,14 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   if (chunk > (1LL << 30)) chunk = 1LL << 30;
   d->chunk = (int)chunk;
   d->n_chunks = (d->n_cand + chunk - 1) / chunk;
-  d->n_tiles = (R + 31) / 32;
+  d->pairs = (kern == FWD) &&
+             forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0);
+  d->n_tiles = d->pairs ? (R + 63) / 64 : (R + 31) / 32;
   d->n_units = d->n_tiles * d->n_chunks;
   int per_sm = (t && t->ctas_per_sm) ? t->ctas_per_sm : 0;
   if (per_sm == 0) {
     const int mode = sc->smoothing;
-    cudaError_t e = (kern == FWD) ? forward_occupancy(mode, d->threads, W, &per_sm)
+    cudaError_t e = (kern == FWD) ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
                                   : vjp_occupancy(mode, true, d->threads, W, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
@@ -228,6 +230,7 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
   a.n_tiles = d.n_tiles;
   a.n_units = d.n_units;
   a.cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  a.pairs = d.pairs;
   a.partial = static_cast<float*>(workspace);
   a.power = power;
   cudaError_t e = launch_forward(a, scene->smoothing, d.ctas, d.threads,

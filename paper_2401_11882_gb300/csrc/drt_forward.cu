@@ -18,6 +18,7 @@
 #include "drt_common.cuh"
 #include "drt_internal.h"
 #include "drt_path.cuh"
+#include "drt_path_pair.cuh"
 
 namespace drt {
 
@@ -69,6 +70,52 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
       acc += p;
     }
     if (live) a.partial[chunk * a.R + r] = acc;
+  }
+}
+
+// Hard sigmoid and sigmoid, two receivers per lane (tiles of 64 receivers:
+// lane l holds receivers l and l + 32 of its tile); the walls' paired records
+// follow the four single-receiver arrays in shared memory.
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
+  extern __shared__ float4 smem[];
+  SmemWalls s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
+  SmemPairs pr{smem + 4 * a.W, smem + 5 * a.W, smem + 6 * a.W, smem + 7 * a.W};
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
+  __syncthreads();
+  stage_pairs<MODE>(s, a.W, pr);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
+       u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    const long long r0 = tile * 64 + lane, r1 = r0 + 32;
+    const bool live0 = r0 < a.R, live1 = r1 < a.R;
+    const float2 q0 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live0 ? r0 : a.R - 1));
+    const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live1 ? r1 : a.R - 1));
+    const int c0 = (int)(chunk * a.chunk);
+    const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
+    float acc0 = 0.f, acc1 = 0.f;
+    Cand cd = decode_candidate(c0, a.W, a.K);
+    for (int i = 0; i < nc; ++i) {
+      if (i > 0) next_candidate(cd, a.W);
+      float2 p;
+      switch (cd.k) {
+        case 0: p = path_power_pair<MODE, 0>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], a.cull); break;
+        case 1: p = path_power_pair<MODE, 1>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], a.cull); break;
+        case 2: p = path_power_pair<MODE, 2>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], a.cull); break;
+        default: p = path_power_pair<MODE, 3>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], a.cull); break;
+      }
+      acc0 += p.x;
+      acc1 += p.y;
+    }
+    if (live0) a.partial[chunk * a.R + r0] = acc0;
+    if (live1) a.partial[chunk * a.R + r1] = acc1;
   }
 }
 
@@ -145,11 +192,23 @@ __global__ void loss_backward_kernel(const int32_t* __restrict__ argmin,
 
 }  // namespace
 
-size_t forward_smem_bytes(int W) { return (size_t)4 * W * sizeof(float4); }
+size_t forward_smem_bytes(int W, bool pairs) { return (size_t)(pairs ? 8 : 4) * W * sizeof(float4); }
+
+bool forward_uses_pairs(int mode, float alpha, int flags) {
+  return (mode == MODE_HARD || mode == MODE_SIGMOID) && !(alpha > FAST_SKIP_MAX_ALPHA) &&
+         !(flags & DRT_TILE_SINGLE_RX);
+}
 
 cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
-  const size_t smem = forward_smem_bytes(a.W);
-  if (a.n_units > 0) {
+  const size_t smem = forward_smem_bytes(a.W, a.pairs);
+  if (a.n_units > 0 && a.pairs) {
+    if (mode == MODE_SIGMOID)
+      forward_pair_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);
+    else
+      forward_pair_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if (a.n_units > 0) {
     switch (mode) {
       case MODE_SIGMOID:
         forward_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);
@@ -172,8 +231,14 @@ cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cu
   return cudaGetLastError();
 }
 
-cudaError_t forward_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
-  const size_t smem = forward_smem_bytes(W);
+cudaError_t forward_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = forward_smem_bytes(W, pairs);
+  if (pairs)
+    return mode == MODE_SIGMOID
+               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     ctas_per_sm, forward_pair_kernel<MODE_SIGMOID>, threads, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     ctas_per_sm, forward_pair_kernel<MODE_HARD>, threads, smem);
   switch (mode) {
     case MODE_SIGMOID:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm,
@@ -188,8 +253,15 @@ cudaError_t forward_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
 }
 
 cudaError_t forward_set_smem_limit(int W) {
-  const int smem = (int)forward_smem_bytes(W);
+  const int smem = (int)forward_smem_bytes(W, false);
   cudaError_t e;
+  const int psmem = (int)forward_smem_bytes(W, true);
+  e = cudaFuncSetAttribute(forward_pair_kernel<MODE_HARD>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(forward_pair_kernel<MODE_SIGMOID>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(forward_kernel<MODE_SIGMOID>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

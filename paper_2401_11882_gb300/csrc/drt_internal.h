@@ -10,9 +10,11 @@
 namespace drt {
 
 // Work decomposition shared by the forward and adjoint kernels: a unit is
-// (32 receivers) x (`chunk` consecutive candidates); unit u covers receiver
-// tile u % n_tiles and candidate chunk u / n_tiles.
+// (32 receivers, or 64 for the two-receivers-per-lane forward) x (`chunk`
+// consecutive candidates); unit u covers receiver tile u % n_tiles and candidate
+// chunk u / n_tiles.
 struct Decomp {
+  bool pairs;   // forward with two receivers per lane (64-receiver tiles)
   long long n_cand;
   int chunk;
   long long n_chunks, n_tiles, n_units;
@@ -33,6 +35,7 @@ struct FwdArgs {
   int chunk;
   long long n_chunks, n_tiles, n_units;
   int cull;
+  bool pairs;       // two receivers per lane (n_tiles counts 64-receiver tiles)
   float* partial;   // [n_chunks][R]
   float* power;     // [R]
 };
@@ -65,9 +68,11 @@ constexpr int VJP_SLOTS = 9;
 // Sets the message drt_last_error() returns on this host thread.
 void set_error_message(const char* msg);
 
-size_t forward_smem_bytes(int W);
+size_t forward_smem_bytes(int W, bool pairs);
+// whether the forward runs two receivers per lane for this smoothing, alpha and tile flags
+bool forward_uses_pairs(int mode, float alpha, int flags);
 cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cudaStream_t st);
-cudaError_t forward_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t forward_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);
 cudaError_t forward_set_smem_limit(int W);
 cudaError_t launch_loss(const float* power, int R, float* loss, int32_t* argmin, cudaStream_t st);
 cudaError_t launch_loss_backward(const int32_t* argmin, const float* grad_loss, int R,

@@ -64,6 +64,92 @@ __device__ __forceinline__ float side_fma(float a, float b, float c) {
 // step) the skipped pairs are masked inside the loop.
 constexpr float FAST_SKIP_MAX_ALPHA = 1e4f;
 
+// Hard sigmoid: divides out of vis[0..K] the factors of the (leg, wall) pairs a
+// leg must skip (the walls its own end points lie on), which the wall loop
+// multiplied in; returns the smallest factor divided out.
+template <int K>
+__device__ __forceinline__ float hard_skip_divide(const SmemWalls& s, const Cand& cd,
+                                                  const float* Qx, const float* Qy, const float* mx,
+                                                  const float* my, const float* mc, float* vis) {
+  float min_div = 1.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+#pragma unroll
+    for (int side_ = 0; side_ < 2; ++side_) {
+      // leg j skips w_j (side 0, j >= 1) and w_{j+1} (side 1, j < K)
+      if ((side_ == 0 && j >= 1) || (side_ == 1 && j < K)) {
+        const int w = cd.w[side_ == 0 ? j - 1 : j];
+        const float4 h = s.H[w];
+        const float4 e = s.E[w];
+        const float s0 = (j == 0) ? h.w : fma_sat(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
+        const float s1 = fma_sat(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z));
+        const float sa = fma_sat(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+        const float sb = fma_sat(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
+        const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
+        const float x1 = (j == 0) ? fmaf(s0, fmaf(-2.f, s1, 1.f), s1) : fmaf(s1, fmaf(-2.f, s0, 1.f), s0);
+        const float f = fmaf(-x1, x2, 1.f);
+        min_div = fminf(min_div, f);
+        vis[j] = __fdividef(vis[j], f);
+      }
+    }
+  }
+  return min_div;
+}
+
+// Sigmoid: the factor 1 - X1 X2 of leg j and one wall as (numerator,
+// denominator), in the product form of the sigmoid loop below.
+template <int K>
+__device__ __forceinline__ void sigmoid_pair_factor(const float4& h, const float4& e, int j,
+                                                    const float* Qx, const float* Qy,
+                                                    const float* mx, const float* my,
+                                                    const float* mc, float& num, float& den) {
+  float ze0, ee0, ze1, ee1;
+  if (j == 0) {
+    ze0 = h.w;
+    ee0 = fabsf(h.w);
+  } else {
+    ze0 = fmaf(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
+    ee0 = ex2_approx(-fabsf(ze0));
+  }
+  ze1 = fmaf(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z));
+  ee1 = ex2_approx(-fabsf(ze1));
+  const float za = fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
+  const float zb = fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
+  const float ea = ex2_approx(-fabsf(za));
+  const float eb = ex2_approx(-fabsf(zb));
+  const float ns1 = ee0 + ee1, no1 = fmaf(ee0, ee1, 1.f);
+  const bool same1 = (__float_as_int(ze0) ^ __float_as_int(ze1)) >= 0;
+  const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
+  const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
+  const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+  const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+  den = (ns1 + no1) * (ns2 + no2);
+  num = fmaf(xb1, ns2 + no2, x1 * xb2);
+}
+
+// Sigmoid counterpart of hard_skip_divide.
+template <int K>
+__device__ __forceinline__ float sigmoid_skip_divide(const SmemWalls& s, const Cand& cd,
+                                                     const float* Qx, const float* Qy,
+                                                     const float* mx, const float* my,
+                                                     const float* mc, float* vis) {
+  float min_div = 1.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+#pragma unroll
+    for (int side_ = 0; side_ < 2; ++side_) {
+      if ((side_ == 0 && j >= 1) || (side_ == 1 && j < K)) {
+        const int w = cd.w[side_ == 0 ? j - 1 : j];
+        float num, den;
+        sigmoid_pair_factor<K>(s.H[w], s.E[w], j, Qx, Qy, mx, my, mc, num, den);
+        min_div = fminf(min_div, __fdividef(num, den));
+        vis[j] *= __fdividef(den, num);
+      }
+    }
+  }
+  return min_div;
+}
+
 // Visibility of each leg (obstruction by every wall except the ones its end points
 // lie on), written to vis[0..K].  Returns the smallest factor divided out for the
 // skipped (leg, wall) pairs (1 when they are masked instead).
@@ -99,27 +185,7 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
         vis[j] = fmaf(-vis[j], x1 * x2, vis[j]);
       }
     }
-#pragma unroll
-    for (int j = 0; j <= K; ++j) {
-#pragma unroll
-      for (int side_ = 0; side_ < 2; ++side_) {
-        // leg j skips w_j (side 0, j >= 1) and w_{j+1} (side 1, j < K)
-        if ((side_ == 0 && j >= 1) || (side_ == 1 && j < K)) {
-          const int w = cd.w[side_ == 0 ? j - 1 : j];
-          const float4 h = s.H[w];
-          const float4 e = s.E[w];
-          const float s0 = (j == 0) ? h.w : fma_sat(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
-          const float s1 = fma_sat(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z));
-          const float sa = fma_sat(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
-          const float sb = fma_sat(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
-          const float x2 = fmaf(sb, fmaf(-2.f, sa, 1.f), sa);
-          const float x1 = (j == 0) ? fmaf(s0, fmaf(-2.f, s1, 1.f), s1) : fmaf(s1, fmaf(-2.f, s0, 1.f), s0);
-          const float f = fmaf(-x1, x2, 1.f);
-          min_div = fminf(min_div, f);
-          vis[j] = __fdividef(vis[j], f);
-        }
-      }
-    }
+    min_div = hard_skip_divide<K>(s, cd, Qx, Qy, mx, my, mc, vis);
   } else if constexpr (MODE != MODE_SIGMOID) {
     // unit step (no 1/2 at 0), or a large alpha: the skipped pairs are masked inside the loop.
 #pragma unroll 2
@@ -157,30 +223,6 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
     float vn[K + 1], vd[K + 1];
 #pragma unroll
     for (int j = 0; j <= K; ++j) vn[j] = vd[j] = 1.f;
-    auto pair_factor = [&](const float4& h, const float4& e, int j, float& num, float& den) {
-      float ze0, ee0, ze1, ee1;
-      if (j == 0) {
-        ze0 = h.w;
-        ee0 = fabsf(h.w);
-      } else {
-        ze0 = fmaf(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
-        ee0 = ex2_approx(-fabsf(ze0));
-      }
-      ze1 = fmaf(h.x, Qx[j + 1], fmaf(h.y, Qy[j + 1], h.z));
-      ee1 = ex2_approx(-fabsf(ze1));
-      const float za = fmaf(mx[j], e.x, fmaf(my[j], e.y, mc[j]));
-      const float zb = fmaf(mx[j], e.z, fmaf(my[j], e.w, mc[j]));
-      const float ea = ex2_approx(-fabsf(za));
-      const float eb = ex2_approx(-fabsf(zb));
-      const float ns1 = ee0 + ee1, no1 = fmaf(ee0, ee1, 1.f);
-      const bool same1 = (__float_as_int(ze0) ^ __float_as_int(ze1)) >= 0;
-      const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
-      const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
-      const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
-      const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
-      den = (ns1 + no1) * (ns2 + no2);
-      num = fmaf(xb1, ns2 + no2, x1 * xb2);
-    };
     for (int w0 = 0; w0 < W; w0 += 8) {
       const int w1 = min(w0 + 8, W);
       for (int w = w0; w < w1; ++w) {
@@ -226,29 +268,16 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
         vn[j] = vd[j] = 1.f;
       }
     }
-#pragma unroll
-    for (int j = 0; j <= (MASKED ? -1 : K); ++j) {
-#pragma unroll
-      for (int side_ = 0; side_ < 2; ++side_) {
-        if ((side_ == 0 && j >= 1) || (side_ == 1 && j < K)) {
-          const int w = cd.w[side_ == 0 ? j - 1 : j];
-          float num, den;
-          pair_factor(s.H[w], s.E[w], j, num, den);
-          min_div = fminf(min_div, __fdividef(num, den));
-          vis[j] *= __fdividef(den, num);
-        }
-      }
-    }
+    if constexpr (!MASKED) min_div = sigmoid_skip_divide<K>(s, cd, Qx, Qy, mx, my, mc, vis);
   }
   return min_div;
 }
 
-// Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
-template <int MODE, int K, bool MASKED = false>
-__device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
-                                            const Cand& cd, float alpha, float gk, int cull) {
-  // --- image method (Sec. V-B): TX images in the walls of the sequence.
-  float Ix[K + 1], Iy[K + 1];
+// TX image chain of a candidate (Sec. V-B): I_0 = TX, I_j = mirror of I_{j-1} in
+// the line of wall w_j.  Independent of the receiver.
+template <int K>
+__device__ __forceinline__ void tx_images(const SmemWalls& s, float2 tx, const Cand& cd, float* Ix,
+                                          float* Iy) {
   Ix[0] = tx.x;
   Iy[0] = tx.y;
 #pragma unroll
@@ -258,88 +287,121 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
     Ix[j] = fmaf(-2.f * d, G.x, Ix[j - 1]);
     Iy[j] = fmaf(-2.f * d, G.y, Iy[j - 1]);
   }
-  // --- backtrace on the infinite lines: Q_{K+1} = RX, Q_j = line(Q_{j+1}, I_j) x wall j.
+}
+
+// Receiver-dependent geometry of one path: the reflection points (backtrace on
+// the walls' infinite lines), each leg's line in smoothing-ready normal form,
+// the path length L and the product V of the reflections' validities.
+template <int MODE, int K>
+struct PathGeom {
   float Qx[K + 2], Qy[K + 2];
-  Qx[0] = tx.x;
-  Qy[0] = tx.y;
-  Qx[K + 1] = rx.x;
-  Qy[K + 1] = rx.y;
-  bool degenerate = false;
+  float mx[K + 1], my[K + 1], mc[K + 1];
+  float L, V;
+  bool degenerate;
+};
+
+template <int MODE, int K>
+__device__ __forceinline__ void path_geometry(const SmemWalls& s, const float* Ix, const float* Iy,
+                                              float2 tx, float2 rx, const Cand& cd, float alpha,
+                                              PathGeom<MODE, K>& g) {
+  // --- backtrace on the infinite lines: Q_{K+1} = RX, Q_j = line(Q_{j+1}, I_j) x wall j.
+  g.Qx[0] = tx.x;
+  g.Qy[0] = tx.y;
+  g.Qx[K + 1] = rx.x;
+  g.Qy[K + 1] = rx.y;
+  g.degenerate = false;
 #pragma unroll
   for (int j = K; j >= 1; --j) {
     const float4 G = s.G[cd.w[j - 1]];
     const float a = line_dist(G, Ix[j], Iy[j]);
-    const float b = line_dist(G, Qx[j + 1], Qy[j + 1]);
+    const float b = line_dist(G, g.Qx[j + 1], g.Qy[j + 1]);
     // parallel lines (or a reflection point absurdly far away): no path
     float t = __fdividef(b, b - a);
     if (!(fabsf(t) <= 1e8f)) {
-      degenerate = true;
+      g.degenerate = true;
       t = 0.f;
     }
-    Qx[j] = fmaf(t, Ix[j] - Qx[j + 1], Qx[j + 1]);
-    Qy[j] = fmaf(t, Iy[j] - Qy[j + 1], Qy[j + 1]);
+    g.Qx[j] = fmaf(t, Ix[j] - g.Qx[j + 1], g.Qx[j + 1]);
+    g.Qy[j] = fmaf(t, Iy[j] - g.Qy[j + 1], g.Qy[j + 1]);
   }
   // --- legs: length and the smoothing-ready normal form of each leg's line.
-  float L = 0.f;
-  float mx[K + 1], my[K + 1], mc[K + 1];
+  g.L = 0.f;
 #pragma unroll
   for (int j = 0; j <= K; ++j) {
-    const float dx = Qx[j + 1] - Qx[j], dy = Qy[j + 1] - Qy[j];
+    const float dx = g.Qx[j + 1] - g.Qx[j], dy = g.Qy[j + 1] - g.Qy[j];
     const float len2 = fmaf(dx, dx, dy * dy);
-    degenerate |= !(len2 > 0.f);
+    g.degenerate |= !(len2 > 0.f);
     const float inv = rsqrtf(len2);
-    L = fmaf(len2, inv, L);
+    g.L = fmaf(len2, inv, g.L);
     const float nx = -dy * inv, ny = dx * inv;
-    const float nq = fmaf(nx, Qx[j], ny * Qy[j]);
+    const float nq = fmaf(nx, g.Qx[j], ny * g.Qy[j]);
     if (MODE == MODE_HARD) {
       const float a6 = alpha * (1.0f / 6.0f);
-      mx[j] = nx * a6;
-      my[j] = ny * a6;
-      mc[j] = fmaf(-nq, a6, 0.5f);
+      g.mx[j] = nx * a6;
+      g.my[j] = ny * a6;
+      g.mc[j] = fmaf(-nq, a6, 0.5f);
     } else if (MODE == MODE_STEP) {
-      mx[j] = nx;
-      my[j] = ny;
-      mc[j] = -nq;
+      g.mx[j] = nx;
+      g.my[j] = ny;
+      g.mc[j] = -nq;
     } else {
       const float kap = alpha * LOG2E;
-      mx[j] = nx * kap;
-      my[j] = ny * kap;
-      mc[j] = -nq * kap;
+      g.mx[j] = nx * kap;
+      g.my[j] = ny * kap;
+      g.mc[j] = -nq * kap;
     }
   }
   // --- continuous validity of each reflection (Sec. V-A): on the segment, and the
   //     previous and next vertices on the same side of the wall's line.
-  float V = 1.f;
+  g.V = 1.f;
 #pragma unroll
   for (int j = 1; j <= K; ++j) {
     const int w = cd.w[j - 1];
     const float4 G = s.G[w];
     const float t0 = s.T[w].x;
-    const float tau = fmaf(G.y, Qx[j], fmaf(-G.x, Qy[j], -t0));   // u = (ny, -nx)
+    const float tau = fmaf(G.y, g.Qx[j], fmaf(-G.x, g.Qy[j], -t0));   // u = (ny, -nx)
     const Smooth3 s1 = smooth3<MODE>(tau, alpha);
     const Smooth3 s2 = smooth3<MODE>(G.w - tau, alpha);
-    const Smooth3 sp = smooth3<MODE>(line_dist(G, Qx[j - 1], Qy[j - 1]), alpha);
-    const Smooth3 sq = smooth3<MODE>(line_dist(G, Qx[j + 1], Qy[j + 1]), alpha);
-    V *= s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+    const Smooth3 sp = smooth3<MODE>(line_dist(G, g.Qx[j - 1], g.Qy[j - 1]), alpha);
+    const Smooth3 sq = smooth3<MODE>(line_dist(G, g.Qx[j + 1], g.Qy[j + 1]), alpha);
+    g.V *= s1.s * s2.s * fmaf(sp.s, sq.s, sp.sb * sq.sb);
   }
+}
+
+// Path power from the geometry and the legs' visibilities (Eq. 7 term).
+template <int MODE, int K>
+__device__ __forceinline__ float path_power_of(const PathGeom<MODE, K>& g, const float* vis,
+                                               float gk) {
+  float p = g.V * gk;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) p *= vis[j];
+  p = __fdividef(p, g.L * g.L);
+  return g.degenerate ? 0.f : p;
+}
+
+// Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
+template <int MODE, int K, bool MASKED = false>
+__device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
+                                            const Cand& cd, float alpha, float gk, int cull) {
+  float Ix[K + 1], Iy[K + 1];
+  tx_images<K>(s, tx, cd, Ix, Iy);
+  PathGeom<MODE, K> g;
+  path_geometry<MODE, K>(s, Ix, Iy, tx, rx, cd, alpha, g);
   // optional: skip the obstruction loop when the whole warp's validity is exactly 0
-  if (cull && __all_sync(0xffffffffu, V == 0.f || degenerate)) return 0.f;
+  if (cull && __all_sync(0xffffffffu, g.V == 0.f || g.degenerate)) return 0.f;
   // --- obstruction of every leg by every wall except the ones its end points lie on.
   float vis[K + 1];
-  const float min_div = leg_visibility<MODE, K, MASKED>(s, W, cd, Qx, Qy, mx, my, mc, vis);
+  const float min_div = leg_visibility<MODE, K, MASKED>(s, W, cd, g.Qx, g.Qy, g.mx, g.my, g.mc, vis);
   if constexpr (!MASKED && MODE != MODE_STEP) {
     // A skipped pair's factor is >= 1/2 when its end point's distance to the wall's
     // line is accurate; a relaxed reflection point far along the line (large
     // backtrace ratio) can break that.  A warp with such a lane recomputes the
     // candidate with the skipped pairs masked (same function up to rounding).
-    const bool bad = !degenerate && !(min_div >= 0.25f);
-    if (__any_sync(0xffffffffu, bad)) leg_visibility<MODE, K, true>(s, W, cd, Qx, Qy, mx, my, mc, vis);
+    const bool bad = !g.degenerate && !(min_div >= 0.25f);
+    if (__any_sync(0xffffffffu, bad))
+      leg_visibility<MODE, K, true>(s, W, cd, g.Qx, g.Qy, g.mx, g.my, g.mc, vis);
   }
-  float p = V * gk;
-#pragma unroll
-  for (int j = 0; j <= K; ++j) p *= vis[j];
-  p = __fdividef(p, L * L);
-  return degenerate ? 0.f : p;
+  return path_power_of<MODE, K>(g, vis, gk);
 }
 
 }  // namespace drt

@@ -23,10 +23,12 @@ class TileConfig:
     cands_per_unit: int = 0
     ctas_per_sm: int = 0
     cull_invalid: bool = False
+    single_rx: bool = False   # (hard) sigmoid forward: one receiver per lane instead of two
 
     def as_c(self) -> _lib.Tile:
-        return _lib.Tile(self.warps_per_cta, self.cands_per_unit, self.ctas_per_sm,
-                         _lib.TILE_CULL_INVALID if self.cull_invalid else 0)
+        flags = ((_lib.TILE_CULL_INVALID if self.cull_invalid else 0)
+                 | (_lib.TILE_SINGLE_RX if self.single_rx else 0))
+        return _lib.Tile(self.warps_per_cta, self.cands_per_unit, self.ctas_per_sm, flags)
 
 
 def _stream_ptr(device) -> ctypes.c_void_p:

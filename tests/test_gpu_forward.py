@@ -79,6 +79,52 @@ def test_cull_option_is_exact_for_hard_sigmoid(drt):
     np.testing.assert_array_equal(a, b)
 
 
+PAIR_CASES = [
+    # (seed, W, R, K, alpha): receiver counts around the 64-receiver tile of the
+    # two-receivers-per-lane kernel (a lone receiver, half tiles, ragged tails)
+    (20, 5, 1, 0, 50.0),
+    (21, 9, 33, 1, 30.0),
+    (22, 12, 63, 2, 100.0),
+    (23, 12, 64, 2, 300.0),
+    (24, 12, 65, 2, 1000.0),
+    (25, 6, 130, 3, 40.0),
+    (26, 40, 200, 2, 0.0),
+    (27, 16, 97, 2, 1e4),
+]
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+@pytest.mark.parametrize("seed,W,R,K,alpha", PAIR_CASES)
+def test_two_receivers_per_lane_equal_one_per_lane_bitwise(drt, oracle_mod, seed, W, R, K, alpha,
+                                                            smoothing):
+    # the paired kernel does the same FP32 operations in the same order (packed
+    # f32x2 FMA rounds each half like the scalar FMA), so the powers are identical
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, smoothing, boundary=(seed % 2 == 0))
+    a = _run(drt, sc)
+    b = _run(drt, sc, drt.TileConfig(single_rx=True))
+    np.testing.assert_array_equal(a, b)
+    # another chunking (another order of the chunk sums), with the exact cull
+    c = _run(drt, sc, drt.TileConfig(warps_per_cta=3, cands_per_unit=5, cull_invalid=True))
+    d = _run(drt, sc, drt.TileConfig(warps_per_cta=3, cands_per_unit=5, cull_invalid=True,
+                                     single_rx=True))
+    np.testing.assert_array_equal(c, d)
+    assert_power_close(a, _ref(oracle_mod, sc),
+                       sens=fp32_sensitivity(lambda w, t, r: oracle_mod.power(
+                           w, t, r, K, alpha, smoothing), sc.walls, sc.tx, sc.rx)
+                       if alpha >= 1000 else None, min_strict=0.9 if alpha >= 1000 else 1.0)
+
+
+@pytest.mark.parametrize("alpha,smoothing", [(100.0, "hard_sigmoid"), (1000.0, "hard_sigmoid"),
+                                             (100.0, "sigmoid")])
+def test_two_receivers_per_lane_bitwise_on_benchmark_scene(drt, alpha, smoothing):
+    # full benchmark launch (64 walls, 65536 receivers, 4097 sequences), both kernels
+    sc = scenes.large_scene(alpha=alpha, smoothing=smoothing)
+    a = _run(drt, sc)
+    b = _run(drt, sc, drt.TileConfig(single_rx=True))
+    np.testing.assert_array_equal(a, b)
+
+
 def test_deterministic(drt):
     sc = scenes.clutter_scene(20, 16, seed=2, max_order=2)
     a, b = _run(drt, sc), _run(drt, sc)
