@@ -30,22 +30,18 @@ namespace {
 template <int MODE, bool WG>
 __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
   extern __shared__ float4 smem[];
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
   VSmem s;
   s.G = smem;
   s.E = smem + a.W;
   s.T = smem + 2 * a.W;
-  s.acc = reinterpret_cast<float*>(smem + 3 * a.W);
-  for (int w = threadIdx.x; w < a.W; w += blockDim.x) {
-    const WallGeom g = wall_geometry(a.walls[w]);
-    s.G[w] = g.G;
-    s.E[w] = g.E;
-    s.T[w] = g.T;
-  }
+  s.H = smem + 3 * a.W;
+  s.acc = reinterpret_cast<float*>(smem + 4 * a.W);
+  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, SmemWalls{s.G, s.E, s.T, s.H});
   if (WG)
     for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) s.acc[i] = 0.f;
   __syncthreads();
 
-  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
   const int lane = threadIdx.x & 31;
   const long long warps_per_cta = blockDim.x >> 5;
   const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
@@ -94,22 +90,18 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
 template <int MODE, bool WG>
 __global__ void __launch_bounds__(256) vjp_rx_kernel(const VjpArgs a) {
   extern __shared__ float4 smem[];
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
   VSmem s;
   s.G = smem;
   s.E = smem + a.W;
   s.T = smem + 2 * a.W;
-  s.acc = reinterpret_cast<float*>(smem + 3 * a.W);
-  for (int w = threadIdx.x; w < a.W; w += blockDim.x) {
-    const WallGeom g = wall_geometry(a.walls[w]);
-    s.G[w] = g.G;
-    s.E[w] = g.E;
-    s.T[w] = g.T;
-  }
+  s.H = smem + 3 * a.W;
+  s.acc = reinterpret_cast<float*>(smem + 4 * a.W);
+  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, SmemWalls{s.G, s.E, s.T, s.H});
   if (WG)
     for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) s.acc[i] = 0.f;
   __syncthreads();
 
-  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
   int ri = __ldg(a.rx_index);
   ri = ri < 0 ? 0 : (ri >= a.R ? (int)a.R - 1 : ri);
   const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + ri);
@@ -235,7 +227,7 @@ void launch_vjp_t(const VjpArgs& a, int ctas, int threads, size_t smem, cudaStre
 }  // namespace
 
 size_t vjp_smem_bytes(int W, bool wall_grad) {
-  return (size_t)3 * W * sizeof(float4) + (wall_grad ? (size_t)W * VJP_SLOTS * sizeof(float) : 0);
+  return (size_t)4 * W * sizeof(float4) + (wall_grad ? (size_t)W * VJP_SLOTS * sizeof(float) : 0);
 }
 
 cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {

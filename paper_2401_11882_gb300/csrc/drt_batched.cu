@@ -5,8 +5,10 @@
 // A "problem" is (scene s, start t).  One descent step is five kernels:
 //   1. batch_forward_kernel: received power of every receiver of every problem.
 //      Persistent CTAs take work units from a global counter; a unit is
-//      (problem, 32-receiver tile) with all of the scene's path candidates
-//      split over the CTA's warps, and units are ordered longest first.
+//      (problem, 64-receiver tile, two receivers per lane with the packed
+//      wall loop of drt_path_pair.cuh; 32 receivers for the unit step) with all
+//      of the scene's path candidates split over the CTA's warps, and units are
+//      ordered longest first.
 //      The CTA stages the scene's walls in shared memory for each unit and
 //      adds the warps' partial sums in warp order (deterministic).
 //   2. batch_argmin_kernel: loss = -min_r P_r and its argmin per problem.
@@ -29,6 +31,7 @@
 #include "drt_common.cuh"
 #include "drt_internal.h"
 #include "drt_path.cuh"
+#include "drt_path_pair.cuh"
 #include "drt_path_vjp.cuh"
 
 namespace drt {
@@ -93,15 +96,36 @@ __device__ __forceinline__ int find_unit(const long long* prefix, int n, long lo
   return lo;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) batch_forward_kernel(const BatchArgs a) {
+template <int MODE, int K>
+__device__ __forceinline__ float batch_path_power(const SmemWalls& sw, int W, float2 txy, float2 q,
+                                                  const Cand& cd, float alpha, float gk, int cull,
+                                                  bool masked) {
+  return masked ? path_power<MODE, K, true>(sw, W, txy, q, cd, alpha, gk, cull)
+                : path_power<MODE, K>(sw, W, txy, q, cd, alpha, gk, cull);
+}
+
+template <int MODE, int K>
+__device__ __forceinline__ float2 batch_path_power2(const SmemWalls& sw, const SmemPairs& pr, int W,
+                                                    float2 txy, float2 q0, float2 q1,
+                                                    const Cand& cd, float alpha, float gk,
+                                                    int cull, bool masked) {
+  if (masked)   // alpha above the packed loop's range: one receiver at a time, masked
+    return make_float2(path_power<MODE, K, true>(sw, W, txy, q0, cd, alpha, gk, cull),
+                       path_power<MODE, K, true>(sw, W, txy, q1, cd, alpha, gk, cull));
+  return path_power_pair<MODE, K>(sw, pr, W, txy, q0, q1, cd, alpha, gk, cull);
+}
+
+// PAIRS: lane l holds receivers l and l + 32 of a 64-receiver tile.
+template <int MODE, bool PAIRS>
+__global__ void __launch_bounds__(256, PAIRS ? 2 : 1) batch_forward_kernel(const BatchArgs a) {
   extern __shared__ float4 smem[];
   __shared__ long long s_unit;
   __shared__ int s_info[2];   // problem, sorted index
-  __shared__ float s_part[BATCH_MAX_WARPS][32];
+  __shared__ float s_part[BATCH_MAX_WARPS][PAIRS ? 64 : 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float alpha = step_alpha(a);
   const int P = a.S * a.T;
+  constexpr int TILE = PAIRS ? 64 : 32;
   for (;;) {
     if (threadIdx.x == 0) {
       const long long u = (long long)atomicAdd(a.counter, 1ULL);
@@ -123,14 +147,19 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const BatchArgs a) {
     const int K = a.order[s];
     const float2 txy = reinterpret_cast<const float2*>(a.tx)[p];
     SmemWalls sw{smem, smem + W, smem + 2 * W, smem + 3 * W};
+    SmemPairs pr{smem + 4 * W, smem + 5 * W, smem + 6 * W, smem + 7 * W};
     stage_walls<MODE>(a.walls + woff, W, txy, alpha, sw);
     __syncthreads();
-    int r = (int)(tile * 32) + lane;
-    const bool live = r < R;
-    if (!live) r = R - 1;
-    const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + roff + r);
+    if (PAIRS) {
+      stage_pairs<MODE>(sw, W, pr);
+      __syncthreads();
+    }
+    const int r0 = (int)(tile * TILE) + lane, r1 = r0 + 32;
+    const bool live0 = r0 < R, live1 = PAIRS && r1 < R;
+    const float2 q0 = __ldg(reinterpret_cast<const float2*>(a.rx) + roff + (live0 ? r0 : R - 1));
+    const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.rx) + roff + (live1 ? r1 : R - 1));
     const long long nc = n_candidates(W, K);
-    float acc = 0.f;
+    float acc0 = 0.f, acc1 = 0.f;
     const bool masked = alpha > FAST_SKIP_MAX_ALPHA;
     // each warp takes a contiguous block of candidates and steps through it
     const long long cb = nc * warp / nwarps, ce = nc * (warp + 1) / nwarps;
@@ -138,28 +167,36 @@ __global__ void __launch_bounds__(256) batch_forward_kernel(const BatchArgs a) {
     if (cb < ce) cd = decode_candidate(cb, W, K);
     for (long long c = cb; c < ce; ++c) {
       if (c > cb) next_candidate(cd, W);
-      if (!masked) {
+      if (PAIRS) {
+        float2 pp;
         switch (cd.k) {
-          case 0: acc += path_power<MODE, 0>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;
-          case 1: acc += path_power<MODE, 1>(sw, W, txy, q, cd, alpha, a.gk[1], a.cull); break;
-          case 2: acc += path_power<MODE, 2>(sw, W, txy, q, cd, alpha, a.gk[2], a.cull); break;
-          default: acc += path_power<MODE, 3>(sw, W, txy, q, cd, alpha, a.gk[3], a.cull); break;
+          case 0: pp = batch_path_power2<MODE, 0>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[0], a.cull, masked); break;
+          case 1: pp = batch_path_power2<MODE, 1>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[1], a.cull, masked); break;
+          case 2: pp = batch_path_power2<MODE, 2>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[2], a.cull, masked); break;
+          default: pp = batch_path_power2<MODE, 3>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[3], a.cull, masked); break;
         }
+        acc0 += pp.x;
+        acc1 += pp.y;
       } else {
         switch (cd.k) {
-          case 0: acc += path_power<MODE, 0, true>(sw, W, txy, q, cd, alpha, a.gk[0], a.cull); break;
-          case 1: acc += path_power<MODE, 1, true>(sw, W, txy, q, cd, alpha, a.gk[1], a.cull); break;
-          case 2: acc += path_power<MODE, 2, true>(sw, W, txy, q, cd, alpha, a.gk[2], a.cull); break;
-          default: acc += path_power<MODE, 3, true>(sw, W, txy, q, cd, alpha, a.gk[3], a.cull); break;
+          case 0: acc0 += batch_path_power<MODE, 0>(sw, W, txy, q0, cd, alpha, a.gk[0], a.cull, masked); break;
+          case 1: acc0 += batch_path_power<MODE, 1>(sw, W, txy, q0, cd, alpha, a.gk[1], a.cull, masked); break;
+          case 2: acc0 += batch_path_power<MODE, 2>(sw, W, txy, q0, cd, alpha, a.gk[2], a.cull, masked); break;
+          default: acc0 += batch_path_power<MODE, 3>(sw, W, txy, q0, cd, alpha, a.gk[3], a.cull, masked); break;
         }
       }
     }
-    s_part[warp][lane] = acc;
+    s_part[warp][lane] = acc0;
+    if (PAIRS) s_part[warp][lane + 32 * PAIRS] = acc1;
     __syncthreads();
     if (warp == 0) {
-      float sum = 0.f;
-      for (int w2 = 0; w2 < nwarps; ++w2) sum += s_part[w2][lane];
-      if (live) a.power[a.pw_off[p] + r] = sum;
+      float sum0 = 0.f, sum1 = 0.f;
+      for (int w2 = 0; w2 < nwarps; ++w2) {
+        sum0 += s_part[w2][lane];
+        if (PAIRS) sum1 += s_part[w2][lane + 32 * PAIRS];
+      }
+      if (live0) a.power[a.pw_off[p] + r0] = sum0;
+      if (live1) a.power[a.pw_off[p] + r1] = sum1;
     }
     __syncthreads();
   }
@@ -225,19 +262,15 @@ __global__ void __launch_bounds__(256) batch_adjoint_kernel(const BatchArgs a) {
     const int woff = a.wall_off[s], W = a.wall_off[s + 1] - woff;
     const int roff = a.rx_off[s];
     const int K = a.order[s];
+    const float2 txy = reinterpret_cast<const float2*>(a.tx)[p];
     VSmem vs;
     vs.G = smem;
     vs.E = smem + W;
     vs.T = smem + 2 * W;
+    vs.H = smem + 3 * W;
     vs.acc = nullptr;
-    for (int w = threadIdx.x; w < W; w += blockDim.x) {
-      const WallGeom g = wall_geometry(a.walls[woff + w]);
-      vs.G[w] = g.G;
-      vs.E[w] = g.E;
-      vs.T[w] = g.T;
-    }
+    stage_walls<MODE>(a.walls + woff, W, txy, alpha, SmemWalls{vs.G, vs.E, vs.T, vs.H});
     __syncthreads();
-    const float2 txy = reinterpret_cast<const float2*>(a.tx)[p];
     const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + roff + a.argmin[p]);
     const long long nc = n_candidates(W, K);
     const long long base = chunk * nwarps * 32 + (long long)warp * 32;
@@ -336,6 +369,7 @@ struct BatchPlan {
   std::vector<long long> fwd_prefix, adj_prefix, pw_off;
   long long n_fwd_units = 0, n_adj_units = 0, n_power = 0;
   int ctas_fwd = 1, ctas_adj = 1, per_sm_req = 0, cull = 0;
+  bool pairs = false;   // forward with two receivers per lane (64-receiver tiles)
   size_t off_counter = 0, off_prob = 0, off_fprefix = 0, off_aprefix = 0, off_pwoff = 0,
          off_power = 0, off_argmin = 0, off_partial = 0, ws_bytes = 0;
   bool bound = false;
@@ -367,18 +401,20 @@ double host_forward_cost(int W, int K, int R) {
   return c * R;
 }
 
-size_t batch_fwd_smem(int Wmax) { return (size_t)4 * Wmax * sizeof(float4); }
-size_t batch_adj_smem(int Wmax) { return (size_t)3 * Wmax * sizeof(float4); }
+size_t batch_fwd_smem(int Wmax, bool pairs) { return (size_t)(pairs ? 8 : 4) * Wmax * sizeof(float4); }
+size_t batch_adj_smem(int Wmax) { return (size_t)4 * Wmax * sizeof(float4); }
 
 cudaError_t set_smem_limits(int Wmax) {
-  const int s1 = (int)batch_fwd_smem(std::max(Wmax, 1)), s2 = (int)batch_adj_smem(std::max(Wmax, 1));
+  const int s1 = (int)batch_fwd_smem(std::max(Wmax, 1), true), s2 = (int)batch_adj_smem(std::max(Wmax, 1));
   cudaError_t e;
 #define DRT_B(K_, S_)                                                                     \
   e = cudaFuncSetAttribute(K_, cudaFuncAttributeMaxDynamicSharedMemorySize, S_);         \
   if (e != cudaSuccess) return e;
-  DRT_B(batch_forward_kernel<MODE_SIGMOID>, s1)
-  DRT_B(batch_forward_kernel<MODE_HARD>, s1)
-  DRT_B(batch_forward_kernel<MODE_STEP>, s1)
+  DRT_B((batch_forward_kernel<MODE_SIGMOID, true>), s1)
+  DRT_B((batch_forward_kernel<MODE_HARD, true>), s1)
+  DRT_B((batch_forward_kernel<MODE_SIGMOID, false>), s1)
+  DRT_B((batch_forward_kernel<MODE_HARD, false>), s1)
+  DRT_B((batch_forward_kernel<MODE_STEP, false>), s1)
   DRT_B(batch_adjoint_kernel<MODE_SIGMOID>, s2)
   DRT_B(batch_adjoint_kernel<MODE_HARD>, s2)
   DRT_B(batch_adjoint_kernel<MODE_STEP>, s2)
@@ -386,16 +422,26 @@ cudaError_t set_smem_limits(int Wmax) {
   return cudaSuccess;
 }
 
+void launch_batch_forward(BatchPlan* pl, size_t sf, cudaStream_t st) {
+  const BatchArgs& a = pl->args;
+  if (pl->pairs && pl->mode == MODE_SIGMOID)
+    batch_forward_kernel<MODE_SIGMOID, true><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
+  else if (pl->pairs)
+    batch_forward_kernel<MODE_HARD, true><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
+  else if (pl->mode == MODE_SIGMOID)
+    batch_forward_kernel<MODE_SIGMOID, false><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
+  else if (pl->mode == MODE_HARD)
+    batch_forward_kernel<MODE_HARD, false><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
+  else
+    batch_forward_kernel<MODE_STEP, false><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
+}
+
 cudaError_t launch_evaluate(BatchPlan* pl, cudaStream_t st) {
   BatchArgs& a = pl->args;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  const size_t sf = batch_fwd_smem(pl->Wmax);
-  switch (pl->mode) {
-    case MODE_SIGMOID: batch_forward_kernel<MODE_SIGMOID><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
-    case MODE_HARD: batch_forward_kernel<MODE_HARD><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
-    default: batch_forward_kernel<MODE_STEP><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
-  }
+  const size_t sf = batch_fwd_smem(pl->Wmax, pl->pairs);
+  launch_batch_forward(pl, sf, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int ab = (int)std::min<long long>(((long long)pl->P * 32 + 255) / 256, 4096);
   batch_argmin_kernel<<<std::max(ab, 1), 256, 0, st>>>(a);
@@ -406,12 +452,8 @@ cudaError_t launch_step(BatchPlan* pl, cudaStream_t st) {
   BatchArgs& a = pl->args;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  const size_t sf = batch_fwd_smem(pl->Wmax), sa = batch_adj_smem(pl->Wmax);
-  switch (pl->mode) {
-    case MODE_SIGMOID: batch_forward_kernel<MODE_SIGMOID><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
-    case MODE_HARD: batch_forward_kernel<MODE_HARD><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
-    default: batch_forward_kernel<MODE_STEP><<<pl->ctas_fwd, pl->threads, sf, st>>>(a); break;
-  }
+  const size_t sf = batch_fwd_smem(pl->Wmax, pl->pairs), sa = batch_adj_smem(pl->Wmax);
+  launch_batch_forward(pl, sf, st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int ab = (int)std::min<long long>(((long long)pl->P * 32 + 255) / 256, 4096);
   batch_argmin_kernel<<<std::max(ab, 1), 256, 0, st>>>(a);
@@ -448,6 +490,8 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
   pl->threads = pl->warps * 32;
   pl->per_sm_req = tile ? tile->ctas_per_sm : 0;
   pl->cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  pl->pairs = (pl->mode == MODE_HARD || pl->mode == MODE_SIGMOID) &&
+              !(tile && (tile->flags & DRT_TILE_SINGLE_RX));
   std::vector<double> cost(pl->P);
   std::vector<long long> tiles(pl->P), adj_units(pl->P);
   pl->pw_off.resize(pl->P);
@@ -472,7 +516,7 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
     for (int t = 0; t < pl->T; ++t) {
       const int p = s * pl->T + t;
       cost[p] = host_forward_cost(W, K, R);
-      tiles[p] = (R + 31) / 32;
+      tiles[p] = pl->pairs ? (R + 63) / 64 : (R + 31) / 32;
       adj_units[p] = (nc + pl->threads - 1) / pl->threads;
       pl->pw_off[p] = pw;
       pw += R;
@@ -518,18 +562,21 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
     return DRT_ERR_CUDA;
   }
   int occ_f = 0, occ_a = 0;
+  const size_t sf = batch_fwd_smem(pl->Wmax, pl->pairs), sa = batch_adj_smem(pl->Wmax);
   switch (pl->mode) {
     case MODE_SIGMOID:
-      e = occupancy(batch_forward_kernel<MODE_SIGMOID>, pl->threads, batch_fwd_smem(pl->Wmax), &occ_f);
-      if (e == cudaSuccess) e = occupancy(batch_adjoint_kernel<MODE_SIGMOID>, pl->threads, batch_adj_smem(pl->Wmax), &occ_a);
+      e = pl->pairs ? occupancy(batch_forward_kernel<MODE_SIGMOID, true>, pl->threads, sf, &occ_f)
+                    : occupancy(batch_forward_kernel<MODE_SIGMOID, false>, pl->threads, sf, &occ_f);
+      if (e == cudaSuccess) e = occupancy(batch_adjoint_kernel<MODE_SIGMOID>, pl->threads, sa, &occ_a);
       break;
     case MODE_HARD:
-      e = occupancy(batch_forward_kernel<MODE_HARD>, pl->threads, batch_fwd_smem(pl->Wmax), &occ_f);
-      if (e == cudaSuccess) e = occupancy(batch_adjoint_kernel<MODE_HARD>, pl->threads, batch_adj_smem(pl->Wmax), &occ_a);
+      e = pl->pairs ? occupancy(batch_forward_kernel<MODE_HARD, true>, pl->threads, sf, &occ_f)
+                    : occupancy(batch_forward_kernel<MODE_HARD, false>, pl->threads, sf, &occ_f);
+      if (e == cudaSuccess) e = occupancy(batch_adjoint_kernel<MODE_HARD>, pl->threads, sa, &occ_a);
       break;
     default:
-      e = occupancy(batch_forward_kernel<MODE_STEP>, pl->threads, batch_fwd_smem(pl->Wmax), &occ_f);
-      if (e == cudaSuccess) e = occupancy(batch_adjoint_kernel<MODE_STEP>, pl->threads, batch_adj_smem(pl->Wmax), &occ_a);
+      e = occupancy(batch_forward_kernel<MODE_STEP, false>, pl->threads, sf, &occ_f);
+      if (e == cudaSuccess) e = occupancy(batch_adjoint_kernel<MODE_STEP>, pl->threads, sa, &occ_a);
       break;
   }
   if (e != cudaSuccess || occ_f < 1 || occ_a < 1) {

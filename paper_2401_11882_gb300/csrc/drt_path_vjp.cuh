@@ -6,6 +6,7 @@
 
 #include "drt_common.cuh"
 #include "drt_internal.h"
+#include "drt_path.cuh"
 
 namespace drt {
 
@@ -20,10 +21,106 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Slots of the per-wall accumulator.
 enum : int { S_NX = 0, S_NY, S_C, S_AX, S_AY, S_BX, S_BY, S_T0, S_LEN };
 
+// Staged walls (the forward's records: G, E, T and the mode's H record, see
+// stage_walls) and the per-CTA wall-gradient accumulator.
 struct VSmem {
-  float4 *G, *E, *T;
+  float4 *G, *E, *T, *H;
   float* acc;   // [W][VJP_SLOTS] (wall gradient only)
 };
+
+// Sums v[0..7] over the warp by recursive halving: lane l ends with the warp
+// total of v[(l >> 2) & 7] (each total held by 4 lanes); 9 shuffles instead of
+// 40 for eight separate butterfly sums.
+__device__ __forceinline__ float warp_reduce_scatter8(const float* v) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float a[4], c[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float keep = b4 ? v[k + 4] : v[k], send = b4 ? v[k] : v[k + 4];
+    a[k] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float keep = b3 ? a[k + 2] : a[k], send = b3 ? a[k] : a[k + 2];
+    c[k] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  float d = (b2 ? c[1] : c[0]) + __shfl_xor_sync(FULL, b2 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(FULL, d, 2);
+  d += __shfl_xor_sync(FULL, d, 1);
+  return d;
+}
+
+// Adds the warp's adjoints of one wall's (n, c, A, B) into the CTA table (the
+// wall is the same in every lane, whatever candidate each lane holds).
+__device__ __forceinline__ void add_wall_adjoint(const VSmem& s, int w, float nbx, float nby,
+                                                 float cb, float Abx, float Aby, float Bbx,
+                                                 float Bby) {
+  const float v[8] = {nbx, nby, cb, Abx, Aby, Bbx, Bby, 0.f};   // slots S_NX .. S_BY
+  const float t = warp_reduce_scatter8(v);
+  const int lane = threadIdx.x & 31, slot = (lane >> 2) & 7;
+  if ((lane & 3) == 0 && slot <= S_BY) atomicAdd(&s.acc[w * VJP_SLOTS + slot], t);
+}
+
+// Sigmoid, sweep 1 of the adjoint: each leg's visibility as (product of the
+// non-zero factors, number of exactly-zero factors), in the forward's product
+// form (e = 2^-|z|, numerator and denominator products folded every 8 walls),
+// the leg's own walls masked.  mxk, myk, mck: the leg's line scaled by
+// alpha log2(e), as the forward's.
+template <int K>
+__device__ __forceinline__ void sigmoid_vis_sweep(const VSmem& s, int W, const Cand& cd,
+                                                  const float* Qx, const float* Qy,
+                                                  const float* mxk, const float* myk,
+                                                  const float* mck, float* nz, int* zc) {
+  float vn[K + 1], vd[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    nz[j] = vn[j] = vd[j] = 1.f;
+    zc[j] = 0;
+  }
+  for (int w0 = 0; w0 < W; w0 += 8) {
+    const int w1 = min(w0 + 8, W);
+    for (int w = w0; w < w1; ++w) {
+      const float4 h = s.H[w];
+      const float4 e = s.E[w];
+      float ze[K + 2], ee[K + 2];
+      ze[0] = h.w;
+      ee[0] = fabsf(h.w);
+#pragma unroll
+      for (int i = 1; i <= K + 1; ++i) {
+        ze[i] = fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
+        ee[i] = ex2_approx(-fabsf(ze[i]));
+      }
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+        if (skip) continue;
+        const float za = fmaf(mxk[j], e.x, fmaf(myk[j], e.y, mck[j]));
+        const float zb = fmaf(mxk[j], e.z, fmaf(myk[j], e.w, mck[j]));
+        const float ea = ex2_approx(-fabsf(za)), eb = ex2_approx(-fabsf(zb));
+        const float ns1 = ee[j] + ee[j + 1], no1 = fmaf(ee[j], ee[j + 1], 1.f);
+        const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+        const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
+        const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
+        const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+        const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+        const float d2 = ns2 + no2;
+        const float num = fmaf(xb1, d2, x1 * xb2);
+        if (num == 0.f) {
+          zc[j] += 1;
+        } else {
+          vn[j] *= num;
+          vd[j] *= (ns1 + no1) * d2;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      nz[j] *= __fdividef(vn[j], vd[j]);
+      vn[j] = vd[j] = 1.f;
+    }
+  }
+}
 
 // One leg x wall factor f = 1 - X(x1, y1) X(x2, y2), written as
 // Xb1 + X1 Xb2 with Xb = 1 - X = s(x) s(y) + s(-x) s(-y), and its partials.
@@ -135,11 +232,19 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
   // sweep 1: visibility as (product of non-zero factors, number of zero factors)
   float nz[K + 1];
   int zc[K + 1];
+  float mxk[K + 1], myk[K + 1], mck[K + 1];   // sigmoid: the leg lines scaled by alpha log2(e)
 #pragma unroll
   for (int j = 0; j <= K; ++j) {
     nz[j] = 1.f;
     zc[j] = 0;
+    const float kap = alpha * LOG2E;
+    mxk[j] = mx[j] * kap;
+    myk[j] = my[j] * kap;
+    mck[j] = -mq[j] * kap;
   }
+  if constexpr (MODE == MODE_SIGMOID) {
+    sigmoid_vis_sweep<K>(s, W, cd, Qx, Qy, mxk, myk, mck, nz, zc);
+  } else {
   for (int w = 0; w < W; ++w) {
     const float4 G = s.G[w];
     const float4 E = s.E[w];
@@ -159,6 +264,7 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
         nz[j] *= f;
       }
     }
+  }
   }
 #pragma unroll
   for (int j = 0; j <= K; ++j) dead |= (zc[j] != 0);
@@ -200,6 +306,83 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
 #pragma unroll
   for (int j = 0; j <= K; ++j) mAx[j] = mAy[j] = sm[j] = 0.f;
 
+  if constexpr (MODE == MODE_SIGMOID) {
+    // Rational form of each factor's derivatives: with e = 2^-|z| per smoothed
+    // distance, E = 1 + e, F = 1 - e^2 and D = E_x E_y per pair,
+    //   dX/dx = -alpha sign(y) e_x F_y / D^2   (and symmetrically in y),
+    // so the adjoint of factor f = 1 - X1 X2 = num / (D1 D2) reaches the four
+    // distances through one reciprocal 1 / (num D1 D2) and the per-vertex e, F.
+    float Wa[K + 1];
+#pragma unroll
+    for (int j = 0; j <= K; ++j) Wa[j] = (zc[j] == 0) ? visb[j] * nz[j] * alpha : 0.f;
+    for (int w = 0; w < W; ++w) {
+      const float4 G = s.G[w];
+      const float4 E = s.E[w];
+      const float4 h = s.H[w];
+      float ze[K + 2], ev[K + 2], Ev[K + 2], sF[K + 2], vb[K + 2];
+      ze[0] = h.w;
+      ev[0] = fabsf(h.w);
+#pragma unroll
+      for (int i = 1; i <= K + 1; ++i) {
+        ze[i] = fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
+        ev[i] = ex2_approx(-fabsf(ze[i]));
+      }
+#pragma unroll
+      for (int i = 0; i <= K + 1; ++i) {
+        Ev[i] = 1.f + ev[i];
+        sF[i] = copysignf(fmaf(-ev[i], ev[i], 1.f), ze[i]);
+        vb[i] = 0.f;
+      }
+      float Abx = 0.f, Aby = 0.f, Bbx = 0.f, Bby = 0.f;
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+        if (skip || !live_leg[j]) continue;
+        const float za = fmaf(mxk[j], E.x, fmaf(myk[j], E.y, mck[j]));
+        const float zb = fmaf(mxk[j], E.z, fmaf(myk[j], E.w, mck[j]));
+        const float ea = ex2_approx(-fabsf(za)), eb = ex2_approx(-fabsf(zb));
+        const float ns1 = ev[j] + ev[j + 1], no1 = fmaf(ev[j], ev[j + 1], 1.f);
+        const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+        const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
+        const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
+        const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+        const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+        const float D1 = Ev[j] * Ev[j + 1], D2 = (1.f + ea) * (1.f + eb);
+        const float num = fmaf(xb1, D2, x1 * xb2);
+        const float q = num * (D1 * D2);
+        // q == 0 only in a lane with an exactly-zero factor on this leg (weight 0)
+        const float t = q > 0.f ? Wa[j] * rcp_approx(q) : 0.f;
+        const float c1 = t * x2 * D2, c2 = t * x1 * D1;
+        vb[j] = fmaf(c1 * ev[j], sF[j + 1], vb[j]);
+        vb[j + 1] = fmaf(c1 * ev[j + 1], sF[j], vb[j + 1]);
+        const float sFa = copysignf(fmaf(-ea, ea, 1.f), za);
+        const float sFb = copysignf(fmaf(-eb, eb, 1.f), zb);
+        const float x2b = c2 * ea * sFb, y2b = c2 * eb * sFa;
+        // x2 = m . (A - Q_j), y2 = m . (B - Q_j)
+        mAx[j] = fmaf(x2b, E.x, fmaf(y2b, E.z, mAx[j]));
+        mAy[j] = fmaf(x2b, E.y, fmaf(y2b, E.w, mAy[j]));
+        sm[j] += x2b + y2b;
+        if (WG) {
+          Abx = fmaf(x2b, mx[j], Abx);
+          Aby = fmaf(x2b, my[j], Aby);
+          Bbx = fmaf(y2b, mx[j], Bbx);
+          Bby = fmaf(y2b, my[j], Bby);
+        }
+      }
+      float nbx = 0.f, nby = 0.f, cb = 0.f;
+#pragma unroll
+      for (int i = 0; i <= K + 1; ++i) {
+        Qbx[i] = fmaf(vb[i], G.x, Qbx[i]);
+        Qby[i] = fmaf(vb[i], G.y, Qby[i]);
+        if (WG) {
+          nbx = fmaf(vb[i], Qx[i], nbx);
+          nby = fmaf(vb[i], Qy[i], nby);
+          cb -= vb[i];
+        }
+      }
+      if (WG) add_wall_adjoint(s, w, nbx, nby, cb, Abx, Aby, Bbx, Bby);
+    }
+  } else {
   for (int w = 0; w < W; ++w) {
     const float4 G = s.G[w];
     const float4 E = s.E[w];
@@ -254,25 +437,10 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
     if (WG) {
       const bool any = (nbx != 0.f) | (nby != 0.f) | (cb != 0.f) | (Abx != 0.f) |
                        (Aby != 0.f) | (Bbx != 0.f) | (Bby != 0.f);
-      if (__any_sync(FULL, any)) {
-        nbx = warp_sum(nbx);
-        nby = warp_sum(nby);
-        cb = warp_sum(cb);
-        Abx = warp_sum(Abx);
-        Aby = warp_sum(Aby);
-        Bbx = warp_sum(Bbx);
-        Bby = warp_sum(Bby);
-        const int lane = threadIdx.x & 31;
-        float v = nbx;
-        v = lane == S_NY ? nby : v;
-        v = lane == S_C ? cb : v;
-        v = lane == S_AX ? Abx : v;
-        v = lane == S_AY ? Aby : v;
-        v = lane == S_BX ? Bbx : v;
-        v = lane == S_BY ? Bby : v;
-        if (lane <= S_BY) atomicAdd(&s.acc[w * VJP_SLOTS + lane], v);
-      }
+      if (__any_sync(FULL, any)) add_wall_adjoint(s, w, nbx, nby, cb, Abx, Aby, Bbx, Bby);
     }
+  }
+
   }
 
   // ------------------------------------------------ legs: normals and lengths

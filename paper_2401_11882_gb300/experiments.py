@@ -22,6 +22,11 @@ the number of problems after which the surrogate pays for itself.
 The annealing study (Sec. VII, convergence success with and without smoothing):
 
     python -m paper_2401_11882_gb300.experiments --study annealing --scenes 256
+
+The batched-descent study (4096 uneven scenes x 4 starts: full-batch step time;
+200 Adam steps on the first 256 scenes):
+
+    python -m paper_2401_11882_gb300.experiments --study batch
 """
 from __future__ import annotations
 
@@ -164,17 +169,112 @@ def annealing_study(n_scenes=256, rx_counts=(2, 3, 4), n_starts=4, n_walls=5, st
     return out
 
 
+def batch_study(n_scenes=4096, timed_steps=3, conv_scenes=256, conv_steps=200, seed=0,
+                device="cuda") -> dict:
+    """Batched descent on the 4096-scene batch (W 8-256, R 64-4096, K 0-2, 4 starts,
+    alpha = 100, hard sigmoid, Adam lr 1e-2): (1) time of full-batch steps after one
+    warm-up step; (2) 200 steps on the first conv_scenes scenes, with the loss
+    trajectory and the final TX of every problem (the batched losses themselves are
+    checked against the oracle by the GPU tests)."""
+    from . import workload
+    full = scenes.scene_batch(n_scenes, seed)
+    dev = torch.device(device)
+    T = full.tx0.shape[1]
+
+    def fwd_flops(b):
+        return sum(T * workload.forward_work(int(b.wall_off[i + 1] - b.wall_off[i]),
+                                             int(b.max_order[i]),
+                                             int(b.rx_off[i + 1] - b.rx_off[i]))["flops"]
+                   for i in range(b.n_scenes))
+
+    out = {"batch": {"scenes": n_scenes, "starts": T,
+                     "evaluations_per_step": sum(
+                         T * int(full.rx_off[i + 1] - full.rx_off[i]) *
+                         int(workload.num_candidates(int(full.wall_off[i + 1] - full.wall_off[i]),
+                                                     int(full.max_order[i])))
+                         for i in range(n_scenes))}}
+    if timed_steps > 0:
+        out["full_batch"] = _time_full_batch(full, timed_steps, fwd_flops(full),
+                                             out["batch"]["evaluations_per_step"], dev)
+    if conv_steps > 0:
+        out["convergence"] = _convergence_run(full, conv_scenes, conv_steps, dev)
+    return out
+
+
+def _time_full_batch(full, timed_steps, fl, evals, dev):
+    from .batched import BatchedDescent
+    bd = BatchedDescent(full, device=dev)
+    bd.run(1)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    bd.run(timed_steps)
+    b.record()
+    torch.cuda.synchronize(dev)
+    s_step = a.elapsed_time(b) / 1e3 / timed_steps
+    res = {"timed_steps": timed_steps, "s_per_step": s_step, "steps_per_s": 1.0 / s_step,
+           "forward_flop_per_step_convention": fl, "tflops_by_convention": fl / s_step / 1e12,
+           "evals_per_s": evals / s_step, "info": bd.info()}
+    bd.close()
+    return res
+
+
+def _convergence_run(full, n, conv_steps, dev):
+    """conv_steps Adam steps on the first n scenes.  A problem whose minimum power is
+    exactly 0 (a receiver in full hard-sigmoid shadow) has loss 0 and gradient 0:
+    the statistics of improvement are taken over the problems with a non-zero loss."""
+    from .batched import BatchedDescent
+    T = full.tx0.shape[1]
+    sub = scenes.SceneBatch(full.walls[:full.wall_off[n]], full.wall_off[:n + 1],
+                            full.rx[:full.rx_off[n]], full.rx_off[:n + 1], full.max_order[:n],
+                            full.tx0[:n], full.alpha, full.smoothing, full.refl_coef)
+    bd = BatchedDescent(sub, history=conv_steps, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    bd.run(conv_steps)
+    torch.cuda.synchronize(dev)
+    secs = time.perf_counter() - t0
+    hist = bd.history.cpu().numpy()            # [steps][P], loss before each step's update
+    final = bd.evaluate().cpu().numpy().copy()  # loss at the final TX
+    tx = bd.tx.cpu().numpy().reshape(n, T, 2)
+    bd.close()
+    first = hist[0]
+    rows = {str(i): float(np.mean(hist[i])) for i in (0, 49, 99, 149, conv_steps - 1)}
+    rows["final"] = float(np.mean(final))
+    best_start = final.reshape(n, T).min(axis=1)
+    live = first < 0
+    rel = (first[live] - final[live]) / np.abs(first[live])
+    return {
+        "scenes": n, "problems": int(n * T), "steps": conv_steps, "seconds": secs,
+        "s_per_step": secs / conv_steps,
+        "mean_loss_by_step": rows,
+        "problems_with_nonzero_initial_loss": int(live.sum()),
+        "problems_with_nonzero_final_loss": int((final < 0).sum()),
+        "fraction_improved_of_nonzero": float(np.mean(final[live] < first[live])) if live.any() else None,
+        "median_relative_improvement_of_nonzero": float(np.median(rel)) if live.any() else None,
+        "mean_best_of_starts_loss": float(np.mean(best_start)),
+        "last_10_steps_mean_abs_change": float(np.mean(np.abs(np.diff(hist[-10:], axis=0)))),
+        "final_tx_first_8_problems": tx.reshape(-1, 2)[:8].tolist(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--seeds", type=int, nargs="+", default=[0])
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--starts", type=int, default=64)
-    ap.add_argument("--study", choices=["surrogate", "annealing"], default="surrogate")
+    ap.add_argument("--study", choices=["surrogate", "annealing", "batch"], default="surrogate")
     ap.add_argument("--scenes", type=int, default=256)
+    ap.add_argument("--timed-steps", type=int, default=3, help="batch study: full-batch steps timed")
+    ap.add_argument("--conv-steps", type=int, default=200, help="batch study: convergence steps")
     args = ap.parse_args()
     if args.study == "annealing":
         print(json.dumps(annealing_study(n_scenes=args.scenes)), flush=True)
+        return
+    if args.study == "batch":
+        print(json.dumps(batch_study(timed_steps=args.timed_steps, conv_scenes=args.scenes,
+                                     conv_steps=args.conv_steps)), flush=True)
         return
     rows = []
     for s in args.seeds:

@@ -120,6 +120,26 @@ def test_graph_and_direct_launch_agree_and_are_deterministic(drt):
         o.close()
 
 
+@pytest.mark.parametrize("smoothing,alpha", [("hard_sigmoid", 100.0), ("sigmoid", 60.0),
+                                             ("hard_sigmoid", 2e4)])
+def test_two_receivers_per_lane_match_one_per_lane_bitwise(drt, smoothing, alpha):
+    # the batched forward's 64-receiver tiles (packed loop; above alpha = 1e4 two
+    # masked single-receiver calls) against 32-receiver tiles: same operations per
+    # receiver, same candidate blocks per warp, same sum order
+    from paper_2401_11882_gb300.batched import BatchedDescent
+    batch = _small_batch(4, n=7, smoothing=smoothing, alpha=alpha)
+    a = BatchedDescent(batch, history=4, alpha=alpha)
+    b = BatchedDescent(batch, history=4, alpha=alpha, tile=drt.TileConfig(single_rx=True))
+    assert a.info()["forward_units"] < b.info()["forward_units"]
+    a.run(4)
+    b.run(4)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.history.cpu().numpy(), b.history.cpu().numpy())
+    np.testing.assert_array_equal(a.tx.cpu().numpy(), b.tx.cpu().numpy())
+    a.close()
+    b.close()
+
+
 def test_checkpoint_resume_is_bitwise(drt, tmp_path):
     from paper_2401_11882_gb300.batched import BatchedDescent
     batch = _small_batch(3)
