@@ -366,6 +366,8 @@ def measure_extras(drt, dev, sc, w, t, r):
     gc = workload.num_candidates(g.n_walls, g.max_order)
     sf = timed(lambda: drt.forward(gw, gt, gr, 2, 100.0, "hard_sigmoid"), 2)
     sv = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", gp), 2)
+    sfs = timed(lambda: drt.forward(gw, gt, gr, 2, 100.0, "sigmoid"), 1)
+    svs = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "sigmoid", gp), 1)
     # batched descent on the first 64 scenes of the 4096-scene batch (4 starts each)
     from paper_2401_11882_gb300.batched import BatchedDescent
     full = scenes.scene_batch(64, 0)
@@ -396,7 +398,9 @@ def measure_extras(drt, dev, sc, w, t, r):
         "workload": "128 random segments, 128x128 RX grid, K<=2 (16385 sequences), alpha=100, "
                     "hard sigmoid, dense g = 1/R, grad wrt TX and 512 wall coordinates",
         "fwd_ms": sf * 1e3, "vjp_ms": sv * 1e3,
-        "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sf + sv)}
+        "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sf + sv),
+        "sigmoid": {"fwd_ms": sfs * 1e3, "vjp_ms": svs * 1e3,
+                    "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sfs + svs)}}
     return out
 
 
