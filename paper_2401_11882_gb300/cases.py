@@ -1,0 +1,61 @@
+"""Runs one named workload a few times and prints its CUDA-event timings, so that
+a profiler can capture a chosen launch of it (e.g. ``ncu -k regex:vjp_kernel -s 2
+-c 1 python -m paper_2401_11882_gb300.cases vjp --rx-grid 32``).
+
+    forward   drt.forward on the scene
+    vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
+
+Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload)
+and ``large`` (square + 60 segments, K <= 2, the benchmark workload), each on an
+n x n receiver grid.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import ops, scenes
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("op", choices=["forward", "vjp"])
+    ap.add_argument("--scene", choices=["gradient", "large"], default="gradient")
+    ap.add_argument("--smoothing", default="sigmoid", choices=["hard_sigmoid", "sigmoid", "step"])
+    ap.add_argument("--alpha", type=float, default=100.0)
+    ap.add_argument("--rx-grid", type=int, default=32)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    dev = torch.device("cuda:0")
+    sc = (scenes.gradient_scene if args.scene == "gradient" else scenes.large_scene)(
+        alpha=args.alpha, smoothing=args.smoothing)
+    rx = scenes.rx_grid(args.rx_grid)
+    w, t, r = (torch.tensor(x, device=dev) for x in (sc.walls, sc.tx, rx))
+    g = torch.full((r.shape[0],), 1.0 / r.shape[0], device=dev)
+
+    def run():
+        if args.op == "forward":
+            return ops.forward(w, t, r, sc.max_order, args.alpha, args.smoothing)
+        return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g)
+
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.reps):
+        out = run()
+    b.record()
+    torch.cuda.synchronize(dev)
+    res = {"op": args.op, "scene": args.scene, "smoothing": args.smoothing, "alpha": args.alpha,
+           "n_rx": int(r.shape[0]), "ms": a.elapsed_time(b) / args.reps}
+    if args.op == "vjp":
+        res["grad_tx"] = out[0].tolist()
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -47,6 +47,8 @@ CASES = [
     (4, 7, 40, 2, 1.0, "step"),
     (5, 5, 36, 3, 15.0, "sigmoid"),
     (6, 10, 64, 2, 100.0, "hard_sigmoid"),
+    (7, 9, 50, 2, 100.0, "sigmoid"),
+    (8, 6, 40, 2, 0.0, "sigmoid"),
 ]
 
 
@@ -101,11 +103,12 @@ def test_against_central_differences(drt, oracle_mod):
     assert_grad_close(np.concatenate([gtx, gw.ravel()]), fd, "adjoint vs central FD")
 
 
-def test_gradient_scene_sampled(drt, oracle_mod):
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+def test_gradient_scene_sampled(drt, oracle_mod, smoothing):
     # 128 random walls, 128 x 128 receivers, K <= 2 (16385 sequences): the VJP is linear in g,
     # so g = indicator of 8 sampled receivers is checked against the oracle's derivative of
     # their summed power, for the TX and 10 sampled wall coordinates.
-    sc = scenes.gradient_scene(alpha=100.0, smoothing="hard_sigmoid")
+    sc = scenes.gradient_scene(alpha=100.0, smoothing=smoothing)
     rng = np.random.default_rng(0)
     idx = rng.choice(sc.n_rx, 8, replace=False)
     g = np.zeros(sc.n_rx)
