@@ -112,6 +112,21 @@ drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* ti
 drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* Autotuner probe for drt_forward (the work decomposition does not change the
+   result beyond the order of the per-chunk sums): runs drt_forward on `scene`
+   with each of the n_cand tiles of `cands` (host array), one untimed launch
+   then `reps` launches timed with CUDA events on `stream`, and writes the
+   fastest tile to *best (host; ties go to the earlier candidate) and, when
+   ms_out is not NULL, each candidate's mean milliseconds per launch to
+   ms_out[0..n_cand) (host; +inf for a candidate whose workspace need exceeds
+   workspace_bytes, which is skipped).  power: [n_rx] device, receives the last
+   timed candidate's result.  Requires n_rx >= 1 and reps >= 1.  Waits for the
+   stream (it reads the events), so it is not for hot paths or stream capture;
+   DRT_ERR_WORKSPACE if no candidate fits. */
+drt_status drt_tune_forward(const drt_scene* scene, const drt_tile* cands, int32_t n_cand,
+                            int32_t reps, float* power, void* workspace, size_t workspace_bytes,
+                            drt_tile* best, float* ms_out, void* stream);
+
 /* Loss of the antenna-placement problem (Eq. 8 and Sec. III):
      loss[0] = -min_r power[r],  argmin[0] = the smallest r attaining the min.
    power: [n_rx] with n_rx >= 1; loss: [1]; argmin: [1] (int32). */

@@ -1,8 +1,9 @@
 """Autotuner for the path kernels' work decomposition.
 
 Times a set of candidate tile shapes (warps per CTA, candidates per work
-unit, resident CTAs per SM) with CUDA events on the current stream and keeps
-the fastest.  Results are cached on disk, keyed by GPU name, smoothing, order
+unit, resident CTAs per SM, one or two receivers per lane) with CUDA events on
+the current stream (inside the library: drt_tune_forward) and keeps the
+fastest.  Results are cached on disk, keyed by GPU name, smoothing, order
 K and the power-of-two buckets of the wall and receiver counts; a later call
 with a key in the cache costs no timing.  Cache file: $DRT_TUNE_CACHE, else
 ~/.cache/drt_gb300/tune.json.
@@ -90,16 +91,21 @@ def tune_forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "
         cache = load_cache() if use_cache else {}
         if key in cache:
             return TileConfig(**cache[key]["tile"])
-    timer = timer or time_fn
     cands = candidates or FORWARD_CANDIDATES
     if candidates is None and smoothing in ("hard_sigmoid", "sigmoid"):
         # these smoothings have a one-receiver-per-lane variant of every shape
         cands = cands + [replace(c, single_rx=True) for c in cands]
-    timings = []
-    for cfg in cands:
-        ms = timer(lambda: ops.forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef,
-                                       tile=cfg), reps)
-        timings.append((cfg, ms))
+    if timer is None:
+        # timed inside the library (drt_tune_forward, CUDA events)
+        _, ms = ops.tune_forward_timings(walls, tx, rx, max_order, alpha, smoothing, cands,
+                                         refl_coef, reps)
+        timings = list(zip(cands, ms))
+    else:
+        timings = []
+        for cfg in cands:
+            ms = timer(lambda: ops.forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef,
+                                           tile=cfg), reps)
+            timings.append((cfg, ms))
     best = pick_best(timings)
     if use_cache:
         with _lock:

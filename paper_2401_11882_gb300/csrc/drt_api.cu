@@ -239,6 +239,65 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
   return DRT_OK;
 }
 
+drt_status drt_tune_forward(const drt_scene* scene, const drt_tile* cands, int32_t n_cand,
+                            int32_t reps, float* power, void* workspace, size_t workspace_bytes,
+                            drt_tile* best, float* ms_out, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if (!cands || n_cand < 1 || !best || !power)
+    return fail(DRT_ERR_INVALID_ARG, "cands, n_cand >= 1, best and power are required");
+  if (reps < 1) return fail(DRT_ERR_INVALID_ARG, "reps = %d < 1", reps);
+  if (scene->n_rx < 1) return fail(DRT_ERR_INVALID_ARG, "n_rx must be >= 1 to time the forward");
+  for (int i = 0; i < n_cand; ++i)
+    if ((st = check_tile(&cands[i])) != DRT_OK) return st;
+  cudaStream_t strm = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e != cudaSuccess) {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  float best_ms = INFINITY;
+  int bi = -1;
+  st = DRT_OK;
+  for (int i = 0; i < n_cand && st == DRT_OK; ++i) {
+    float ms = INFINITY;
+    size_t need = 0;
+    if ((st = drt_forward_workspace_size(scene, &cands[i], &need)) != DRT_OK) break;
+    if (workspace && need <= workspace_bytes) {
+      if ((st = drt_forward(scene, &cands[i], power, workspace, workspace_bytes, stream)) != DRT_OK)
+        break;
+      if ((e = cudaEventRecord(ev[0], strm)) != cudaSuccess) {
+        st = cuda_fail(e, "cudaEventRecord");
+        break;
+      }
+      for (int r = 0; r < reps && st == DRT_OK; ++r)
+        st = drt_forward(scene, &cands[i], power, workspace, workspace_bytes, stream);
+      if (st != DRT_OK) break;
+      if ((e = cudaEventRecord(ev[1], strm)) != cudaSuccess ||
+          (e = cudaEventSynchronize(ev[1])) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, ev[0], ev[1])) != cudaSuccess) {
+        st = cuda_fail(e, "timing events");
+        break;
+      }
+      ms /= (float)reps;
+      if (ms < best_ms) {
+        best_ms = ms;
+        bi = i;
+      }
+    }
+    if (ms_out) ms_out[i] = ms;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (st != DRT_OK) return st;
+  if (bi < 0) return fail(DRT_ERR_WORKSPACE, "no candidate tile fits %zu workspace bytes",
+                          workspace_bytes);
+  *best = cands[bi];
+  return DRT_OK;
+}
+
 drt_status drt_loss(const float* power, int32_t n_rx, float* loss, int32_t* argmin,
                     void* stream) {
   if (!power || !loss || !argmin) return fail(DRT_ERR_INVALID_ARG, "NULL pointer");

@@ -102,6 +102,33 @@ def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
     return power
 
 
+def tune_forward_timings(walls, tx, rx, max_order: int, alpha: float, smoothing: str,
+                         candidates, refl_coef: float = 0.5, reps: int = 3):
+    """Times drt_forward with each TileConfig of ``candidates`` in the library
+    (drt_tune_forward: CUDA events on the current stream) and returns
+    (fastest TileConfig, [ms per launch for each candidate])."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    cands = list(candidates)
+    arr = (_lib.Tile * len(cands))(*[c.as_c() for c in cands])
+    need = 0
+    for c in arr:
+        nbytes = ctypes.c_size_t()
+        _lib.call("drt_forward_workspace_size", ctypes.byref(sc), ctypes.byref(c),
+                  ctypes.byref(nbytes))
+        need = max(need, nbytes.value)
+    ws = _workspace(dev, need)
+    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    best = _lib.Tile()
+    ms = (ctypes.c_float * len(cands))()
+    _lib.call("drt_tune_forward", ctypes.byref(sc), arr, len(cands), int(reps), _ptr(power),
+              _ptr(ws), ctypes.c_size_t(ws.numel()), ctypes.byref(best), ms, _stream_ptr(dev))
+    key = (best.warps_per_cta, best.cands_per_unit, best.ctas_per_sm, best.flags)
+    i = next(i for i, c in enumerate(arr)
+             if (c.warps_per_cta, c.cands_per_unit, c.ctas_per_sm, c.flags) == key)
+    return cands[i], list(ms)
+
+
 def min_loss(power: torch.Tensor):
     """(loss, argmin): loss = -min_r power[r] (float32 [1]), argmin int32 [1]."""
     power = _as_f32(power.reshape(-1, 1), 1, "power", 4)

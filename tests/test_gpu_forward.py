@@ -232,6 +232,35 @@ def test_autotuned_tile_is_cached_and_correct(drt, oracle_mod, tmp_path, monkeyp
     assert_power_close(P, _ref(oracle_mod, sc))
 
 
+def test_native_tuner(drt, oracle_mod):
+    import ctypes
+    from paper_2401_11882_gb300 import _lib, ops
+    rng = np.random.default_rng(32)
+    sc = scenes.random_small_scene(rng, 10, 150, 2, 40.0, "sigmoid", boundary=True)
+    dev = torch.device("cuda:0")
+    w, t, r = (torch.tensor(sc.walls, device=dev), torch.tensor(sc.tx, device=dev),
+               torch.tensor(sc.rx, device=dev))
+    cands = [drt.TileConfig(8, 64), drt.TileConfig(4, 16), drt.TileConfig(8, 64, single_rx=True),
+             drt.TileConfig(2, 5, 1)]
+    best, ms = ops.tune_forward_timings(w, t, r, 2, 40.0, "sigmoid", cands, reps=2)
+    assert best in cands and len(ms) == len(cands)
+    assert all(np.isfinite(ms)) and min(ms) > 0 and ms[cands.index(best)] == min(ms)
+    P = drt.forward(w, t, r, 2, 40.0, "sigmoid", tile=best).cpu().numpy()
+    assert_power_close(P, _ref(oracle_mod, sc))
+    # a workspace too small for every candidate: nothing fits
+    scd, keep = ops.make_scene(w, t, r, 2, 40.0, "sigmoid")
+    arr = (_lib.Tile * 1)(cands[0].as_c())
+    out = torch.empty(sc.n_rx, device=dev)
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    bt = _lib.Tile()
+    msa = (ctypes.c_float * 1)()
+    with pytest.raises(_lib.DrtError) as ei:
+        _lib.call("drt_tune_forward", ctypes.byref(scd), arr, 1, 1, ctypes.c_void_p(out.data_ptr()),
+                  ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(256), ctypes.byref(bt), msa,
+                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert ei.value.status == 5 and np.isinf(msa[0])
+
+
 @pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
 def test_large_alpha_masked_path(drt, oracle_mod, smoothing):
     # above the fast path's alpha limit the skipped (leg, wall) pairs are masked in the loop;
