@@ -316,7 +316,11 @@ def run_ours(args):
                                 + " (+ its chunk-sum kernel)"),
                      "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
                                     f"FLOP x {sm_max:.0f} MHz (max SM clock)",
-                     "flops_per_launch": work["flops"], "ms_per_launch": fwd_avg_s * 1e3},
+                     "flops_per_launch": work["flops"], "ms_per_launch": fwd_avg_s * 1e3,
+                     "note": "achieved counts the frozen convention's 40 FLOP per leg x wall "
+                             "test; the kernel needs fewer FMA-pipe operations per test, so the "
+                             "hardware view is the ncu FMA-pipe utilisation in "
+                             "profiles/forward_large_scene.md (75% busy for the hard sigmoid)"},
         "cpu_baseline": cpu,
         "e2e": {"value": world * args.steps * evals / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -348,6 +352,9 @@ def measure_extras(drt, dev, sc, w, t, r):
     out = {}
     n_cand = workload.num_candidates(sc.n_walls, sc.max_order)
     ev = sc.n_rx * n_cand
+    for a_ in (10.0, 1000.0):
+        s = timed(lambda: drt.forward(w, t, r, sc.max_order, a_, sc.smoothing))
+        out[f"forward_alpha_{a_:g}_evals_per_s"] = ev / s
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "sigmoid"))
     out["sigmoid_forward_evals_per_s"] = ev / s
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "sigmoid",
