@@ -62,6 +62,7 @@ struct BatchArgs {
   unsigned long long* counter;   // [2]
   const int32_t* fwd_prob;       // [P] problems, longest forward first
   const long long* fwd_prefix;   // [P+1] tiles, in that order
+  const int32_t* fwd_unit;       // [n_fwd_units] position in that order of each unit's problem
   long long n_fwd_units;
   const long long* adj_prefix;   // [P+1] adjoint units per problem (natural order)
   long long n_adj_units;
@@ -124,14 +125,13 @@ __global__ void __launch_bounds__(256, PAIRS ? 2 : 1) batch_forward_kernel(const
   __shared__ float s_part[BATCH_MAX_WARPS][PAIRS ? 64 : 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float alpha = step_alpha(a);
-  const int P = a.S * a.T;
   constexpr int TILE = PAIRS ? 64 : 32;
   for (;;) {
     if (threadIdx.x == 0) {
       const long long u = (long long)atomicAdd(a.counter, 1ULL);
       s_unit = u;
       if (u < a.n_fwd_units) {
-        const int i = find_unit(a.fwd_prefix, P, u);
+        const int i = a.fwd_unit[u];
         s_info[0] = a.fwd_prob[i];
         s_info[1] = i;
       }
@@ -365,11 +365,12 @@ struct BatchPlan {
   const float* rx = nullptr;
   const int32_t* rx_off = nullptr;
   const int32_t* order = nullptr;
-  std::vector<int32_t> fwd_prob;
+  std::vector<int32_t> fwd_prob, fwd_unit;
   std::vector<long long> fwd_prefix, adj_prefix, pw_off;
   long long n_fwd_units = 0, n_adj_units = 0, n_power = 0;
   int ctas_fwd = 1, ctas_adj = 1, per_sm_req = 0, cull = 0;
   bool pairs = false;   // forward with two receivers per lane (64-receiver tiles)
+  size_t off_funit = 0;
   size_t off_counter = 0, off_prob = 0, off_fprefix = 0, off_aprefix = 0, off_pwoff = 0,
          off_power = 0, off_argmin = 0, off_partial = 0, ws_bytes = 0;
   bool bound = false;
@@ -532,11 +533,17 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
   pl->adj_prefix.assign(pl->P + 1, 0);
   for (int p = 0; p < pl->P; ++p) pl->adj_prefix[p + 1] = pl->adj_prefix[p] + adj_units[p];
   pl->n_fwd_units = pl->fwd_prefix[pl->P];
+  // unit -> its problem's position in the sorted order (one load per unit fetch
+  // instead of a binary search over the prefix sums)
+  pl->fwd_unit.resize(pl->n_fwd_units);
+  for (int i = 0; i < pl->P; ++i)
+    std::fill(pl->fwd_unit.begin() + pl->fwd_prefix[i], pl->fwd_unit.begin() + pl->fwd_prefix[i + 1], i);
   pl->n_adj_units = pl->adj_prefix[pl->P];
   size_t off = 0;
   pl->off_counter = off; off = align_up(off + 2 * sizeof(unsigned long long));
   pl->off_prob = off; off = align_up(off + (size_t)pl->P * sizeof(int32_t));
   pl->off_fprefix = off; off = align_up(off + (size_t)(pl->P + 1) * sizeof(long long));
+  pl->off_funit = off; off = align_up(off + (size_t)pl->n_fwd_units * sizeof(int32_t));
   pl->off_aprefix = off; off = align_up(off + (size_t)(pl->P + 1) * sizeof(long long));
   pl->off_pwoff = off; off = align_up(off + (size_t)pl->P * sizeof(long long));
   pl->off_power = off; off = align_up(off + (size_t)pl->n_power * sizeof(float));
@@ -595,6 +602,8 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(base + pl->off_fprefix, pl->fwd_prefix.data(),
                            (pl->P + 1) * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(base + pl->off_funit, pl->fwd_unit.data(),
+                           pl->n_fwd_units * sizeof(int32_t), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(base + pl->off_aprefix, pl->adj_prefix.data(),
                            (pl->P + 1) * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(base + pl->off_pwoff, pl->pw_off.data(), pl->P * sizeof(long long),
@@ -634,6 +643,7 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
   a.counter = reinterpret_cast<unsigned long long*>(base + pl->off_counter);
   a.fwd_prob = reinterpret_cast<const int32_t*>(base + pl->off_prob);
   a.fwd_prefix = reinterpret_cast<const long long*>(base + pl->off_fprefix);
+  a.fwd_unit = reinterpret_cast<const int32_t*>(base + pl->off_funit);
   a.n_fwd_units = pl->n_fwd_units;
   a.adj_prefix = reinterpret_cast<const long long*>(base + pl->off_aprefix);
   a.n_adj_units = pl->n_adj_units;

@@ -81,6 +81,20 @@ def random_segments(rng: np.random.Generator, n: int,
     return np.concatenate([mid - half, mid + half], axis=1).astype(np.float32)
 
 
+def spatial_order(points: np.ndarray, bits: int = 16) -> np.ndarray:
+    """Permutation that sorts 2D points in [0, 1]^2 along a Z-order (Morton) curve,
+    so that consecutive points (the lanes of a warp) are near each other."""
+    q = np.clip(np.asarray(points, np.float64), 0.0, 1.0)
+    n = (1 << bits) - 1
+    ix = np.round(q[:, 0] * n).astype(np.uint64)
+    iy = np.round(q[:, 1] * n).astype(np.uint64)
+    key = np.zeros(len(q), np.uint64)
+    for b in range(bits):
+        key |= ((ix >> np.uint64(b)) & np.uint64(1)) << np.uint64(2 * b)
+        key |= ((iy >> np.uint64(b)) & np.uint64(1)) << np.uint64(2 * b + 1)
+    return np.argsort(key, kind="stable")
+
+
 def rx_grid(n: int) -> np.ndarray:
     """RX at the cell centres ((i + 1/2)/n, (j + 1/2)/n), row-major in (j, i)."""
     c = (np.arange(n, dtype=np.float64) + 0.5) / n

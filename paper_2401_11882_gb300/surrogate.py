@@ -147,14 +147,21 @@ class SurrogateMLP:
 
 def sample_objective(scene, tx: np.ndarray, device="cuda", cull: bool = True,
                      chunk: int = 1 << 18) -> np.ndarray:
-    """F(tx_i) = min_r P_r(tx_i) for every row of tx [N, 2] (exact, batched forward)."""
+    """F(tx_i) = min_r P_r(tx_i) for every row of tx [N, 2] (exact, batched forward).
+
+    F does not depend on the order of the receivers, so they are passed in
+    Z-order: the receivers of one warp are then near each other, and the exact
+    invalid-path skip (a path whose validity is 0 for every receiver of the
+    warp) applies far more often.  One warp per CTA: a work unit (one sample, 64
+    receivers) is then never split between warps that wait for each other."""
     from . import scenes
     from .batched import BatchedDescent
     out = np.empty(tx.shape[0], np.float32)
-    tile = TileConfig(cull_invalid=cull and scene.smoothing != "sigmoid")
+    tile = TileConfig(warps_per_cta=1, cull_invalid=cull and scene.smoothing != "sigmoid")
+    rx = np.ascontiguousarray(scene.rx[scenes.spatial_order(scene.rx)])
     for s in range(0, tx.shape[0], chunk):
         part = np.asarray(tx[s:s + chunk], np.float32)
-        b = scenes.SceneBatch(scene.walls, np.array([0, scene.n_walls], np.int32), scene.rx,
+        b = scenes.SceneBatch(scene.walls, np.array([0, scene.n_walls], np.int32), rx,
                               np.array([0, scene.n_rx], np.int32),
                               np.array([scene.max_order], np.int32), part[None], scene.alpha,
                               scene.smoothing, scene.refl_coef)

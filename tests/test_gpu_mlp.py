@@ -117,6 +117,25 @@ def test_sample_objective_matches_single_scene_and_oracle(sur, oracle_mod):
         assert F[i] == pytest.approx(Pref.min(), rel=1e-4, abs=1e-10 * Pref.max())
 
 
+def test_sample_objective_receiver_order_does_not_change_F(sur):
+    # the sampler passes the receivers in Z-order; F = min over receivers is the
+    # same bit for bit as with the original order and the same tile
+    from paper_2401_11882_gb300.batched import BatchedDescent
+    from paper_2401_11882_gb300.ops import TileConfig
+    rng = np.random.default_rng(5)
+    sc = scenes.clutter_scene(16, 1, seed=8, max_order=2, alpha=100.0,
+                              rx=rng.uniform(0.05, 0.95, (200, 2)).astype(np.float32))
+    tx = rng.uniform(0.05, 0.95, (300, 2)).astype(np.float32)
+    F = sur.sample_objective(sc, tx)
+    b = scenes.SceneBatch(sc.walls, np.array([0, sc.n_walls], np.int32), sc.rx,
+                          np.array([0, sc.n_rx], np.int32), np.array([2], np.int32), tx[None],
+                          sc.alpha, sc.smoothing, sc.refl_coef)
+    bd = BatchedDescent(b, tile=TileConfig(warps_per_cta=1, cull_invalid=True), alpha=sc.alpha)
+    F0 = (-bd.evaluate()).cpu().numpy()
+    bd.close()
+    np.testing.assert_array_equal(F, F0)
+
+
 def test_surrogate_proposals_beat_random_points(sur):
     sc = scenes.clutter_scene(12, 4, seed=6, max_order=1, alpha=50.0)
     search = sur.SurrogateSearch(sc, batch=512, seed=1)
