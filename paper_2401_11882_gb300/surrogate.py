@@ -270,15 +270,21 @@ def descend(scene, starts: np.ndarray, n_steps: int, target_loss: float | None =
             lr_decay: float = 1.0, box=(0.005, 0.005, 0.995, 0.995)):
     """Exact batched Adam from the given starts; stops once the best loss is within
     rel_tol of target_loss (checked every check_every steps).  Returns SearchResult-like
-    (best_loss, best_tx, steps, seconds, reached, history)."""
+    (best_loss, best_tx, steps, seconds, reached, history).
+
+    As in sample_objective, the receivers go in Z-order and the forward skips, per
+    warp, the obstruction loop of paths whose validity is exactly 0 (the loss, a
+    min over receivers, and its gradient are unchanged)."""
     from . import scenes
     from .batched import BatchedDescent
-    b = scenes.SceneBatch(scene.walls, np.array([0, scene.n_walls], np.int32), scene.rx,
+    rx = np.ascontiguousarray(scene.rx[scenes.spatial_order(scene.rx)])
+    b = scenes.SceneBatch(scene.walls, np.array([0, scene.n_walls], np.int32), rx,
                           np.array([0, scene.n_rx], np.int32), np.array([scene.max_order], np.int32),
                           np.asarray(starts, np.float32)[None], scene.alpha, scene.smoothing,
                           scene.refl_coef)
     dev = torch.device(device)
-    bd = BatchedDescent(b, lr=lr, device=dev, alpha=scene.alpha, lr_decay=lr_decay, box=box)
+    bd = BatchedDescent(b, lr=lr, device=dev, alpha=scene.alpha, lr_decay=lr_decay, box=box,
+                        tile=TileConfig(cull_invalid=True))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     steps, hist, reached = 0, [], False
