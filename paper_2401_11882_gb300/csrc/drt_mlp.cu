@@ -36,8 +36,17 @@ typedef __nv_bfloat16 bf16;
 struct Layout {
   long long w[NL], b[NL], w5, b5, total;
   long long sw[NL], swt[NL], sw5, stotal;
+  long long swc[NL];   // W_l in 256 x 32 K-chunks, each in the tensor-core smem layout
   int k[NL];
 };
+
+// K-chunk width of the chunked weight copy, and the byte offset of element
+// (n, k) of a [256 x 32] chunk in the canonical no-swizzle K-major layout of the
+// tcgen05 operands (8-row x 16-byte core matrices, four along K per 8-row group).
+constexpr int WCHUNK_K = 32;
+__host__ __device__ constexpr unsigned chunk_woff(int n, int k) {
+  return (unsigned)((((n >> 3) * (WCHUNK_K / 8) + (k >> 3)) << 7) + ((n & 7) << 4) + ((k & 7) << 1));
+}
 
 __host__ __device__ inline Layout layout() {
   Layout L{};
@@ -60,6 +69,10 @@ __host__ __device__ inline Layout layout() {
   L.total = o;
   L.sw5 = so;
   so += WID;
+  for (int l = 0; l < NL; ++l) {
+    L.swc[l] = so;
+    so += (long long)WID * L.k[l];
+  }
   L.stotal = so;
   return L;
 }
@@ -294,6 +307,25 @@ __global__ void row_sum_kernel(const bf16* __restrict__ X, int rows, int cols,
 }
 
 // Adam on the FP32 master vector; refreshes the BF16 shadows (W, W^T, w5).
+// BF16 copies of parameter i (value v) in the shadow: W_l row-major, its
+// transpose, its K-chunked tensor-core layout, and w5.
+__device__ __forceinline__ void write_shadow(const Layout& L, bf16* __restrict__ shadow, long long i,
+                                             float v) {
+  for (int l = 0; l < NL; ++l) {
+    const long long n_w = (long long)WID * L.k[l];
+    if (i >= L.w[l] && i < L.w[l] + n_w) {
+      const long long e = i - L.w[l];
+      const int n = (int)(e / L.k[l]), k = (int)(e % L.k[l]);
+      const bf16 b = __float2bfloat16(v);
+      shadow[L.sw[l] + e] = b;
+      shadow[L.swt[l] + (long long)k * WID + n] = b;
+      shadow[L.swc[l] + (long long)(k / WCHUNK_K) * WID * WCHUNK_K +
+             chunk_woff(n, k % WCHUNK_K) / 2] = b;
+    }
+  }
+  if (i >= L.w5 && i < L.w5 + WID) shadow[L.sw5 + (i - L.w5)] = __float2bfloat16(v);
+}
+
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, const int32_t* __restrict__ step, float lr,
                             float b1, float b2, float eps, bf16* __restrict__ shadow) {
@@ -309,36 +341,15 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float*
     v[i] = vi;
     const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     p[i] = pi;
-    if (shadow) {
-      for (int l = 0; l < NL; ++l) {
-        const long long n_w = (long long)WID * L.k[l];
-        if (i >= L.w[l] && i < L.w[l] + n_w) {
-          const long long e = i - L.w[l];
-          const long long n = e / L.k[l], k = e % L.k[l];
-          shadow[L.sw[l] + e] = __float2bfloat16(pi);
-          shadow[L.swt[l] + k * WID + n] = __float2bfloat16(pi);
-        }
-      }
-      if (i >= L.w5 && i < L.w5 + WID) shadow[L.sw5 + (i - L.w5)] = __float2bfloat16(pi);
-    }
+    if (shadow) write_shadow(L, shadow, i, pi);
   }
 }
 
 __global__ void shadow_kernel(const float* __restrict__ p, bf16* __restrict__ shadow) {
   const Layout L = layout();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.total;
-       i += (long long)gridDim.x * blockDim.x) {
-    for (int l = 0; l < NL; ++l) {
-      const long long n_w = (long long)WID * L.k[l];
-      if (i >= L.w[l] && i < L.w[l] + n_w) {
-        const long long e = i - L.w[l];
-        const long long n = e / L.k[l], k = e % L.k[l];
-        shadow[L.sw[l] + e] = __float2bfloat16(p[i]);
-        shadow[L.swt[l] + k * WID + n] = __float2bfloat16(p[i]);
-      }
-    }
-    if (i >= L.w5 && i < L.w5 + WID) shadow[L.sw5 + (i - L.w5)] = __float2bfloat16(p[i]);
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    write_shadow(L, shadow, i, p[i]);
 }
 
 __global__ void increment_kernel(int32_t* step) {
@@ -349,6 +360,7 @@ __global__ void increment_kernel(int32_t* step) {
 }  // namespace drt
 
 #include "drt_mlp_tc.cuh"
+#include "drt_mlp_fused.cuh"
 
 namespace drt {
 namespace mlp {
@@ -432,6 +444,8 @@ int* tc_status_ptr() {
     cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_FWD, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DH, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     cudaFuncSetAttribute(mlp::tc_gemm_nt_kernel<mlp::EPI_DW, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(mlp::tc_mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         mlp::FZ_SMEM);
   }
   return g_tc_status_ptr[dev];
 }
@@ -475,7 +489,7 @@ cudaError_t mlp_hidden_forward(const float* params, const bf16* shadow, const fl
     g.N = mlp::WID;
     g.K = L.k[l];
     g.bias = params + L.b[l];
-    g.Z = w.Z[l];
+    g.Z = with_train ? w.Z[l] : nullptr;   // pre-activations: only the backward pass reads them
     g.ldz = mlp::WID;
     g.H = w.H[l + 1];
     g.ldh = mlp::WID;
@@ -533,6 +547,28 @@ drt_status drt_mlp_forward(const float* params, const void* shadow, const float*
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mlp::Layout L = mlp::layout();
   const mlp::bf16* sh = static_cast<const mlp::bf16*>(shadow);
+  int* status = g_tc_mode.load() ? tc_status_ptr() : nullptr;
+  if (status) {
+    // tcgen05 path: the whole network in one kernel, activations on chip
+    mlp::FusedArgs fa{};
+    fa.params = params;
+    fa.shadow = sh;
+    fa.freqs = freqs;
+    fa.x = x;
+    fa.y = y;
+    fa.batch = batch;
+    for (int l = 0; l < mlp::NL; ++l) {
+      fa.swc[l] = L.swc[l];
+      fa.b[l] = L.b[l];
+    }
+    fa.sw5 = L.sw5;
+    fa.b5 = L.b5;
+    const int grid = (batch + mlp::FZ_ROWS - 1) / mlp::FZ_ROWS;
+    mlp::tc_mlp_forward_kernel<<<grid, mlp::FZ_ROWS, mlp::FZ_SMEM, st>>>(fa, status,
+                                                                        g_tc_skip_mma.load());
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DRT_OK : mlp_fail(DRT_ERR_CUDA, cudaGetErrorString(e));
+  }
   cudaError_t e = mlp_hidden_forward(params, sh, freqs, x, batch, w, false, st);
   if (e == cudaSuccess) {
     mlp::out_layer_kernel<<<std::min(4096, (batch * 32 + 255) / 256), 256, 0, st>>>(

@@ -1,5 +1,6 @@
-"""The tcgen05 (TMEM-accumulator) tensor-core path of the MLP's dense layers
-against the mma.sync path and the FP64 oracle."""
+"""The tcgen05 (TMEM-accumulator) tensor-core path of the MLP (the fused
+inference kernel and the training GEMMs) against the mma.sync path and the
+FP64 oracle."""
 import ctypes
 
 import numpy as np
@@ -27,7 +28,7 @@ def _status(_lib):
     return flag.value
 
 
-@pytest.mark.parametrize("batch", [128, 384])
+@pytest.mark.parametrize("batch", [128, 192, 384, 4096])
 def test_forward_and_gradient_agree_across_paths(env, batch):
     _lib, sur = env
     rng = np.random.default_rng(batch)
@@ -50,7 +51,14 @@ def test_forward_and_gradient_agree_across_paths(env, batch):
     assert l1 == pytest.approx(l0, rel=2e-3)
     assert np.linalg.norm(g1 - g0) <= 1e-2 * np.linalg.norm(g0)
     ref, _ = M.forward(theta.astype(np.float64), freqs, x.cpu().numpy(), emulate_bf16=True)
-    np.testing.assert_allclose(y1, ref, rtol=2e-3, atol=2e-3 * np.abs(ref).max())
+    # The oracle rounds to BF16 at the same points; a different FP32 accumulation
+    # order can still flip one activation's BF16 rounding (2^-8 relative) and move
+    # that row's output by about that much.  Over many rows a few such flips occur:
+    # at least 99.5% of the rows meet the tight bound, all rows a 10x looser one.
+    err = np.abs(y1 - ref)
+    tight = 2e-3 * np.abs(ref) + 2e-3 * np.abs(ref).max()
+    assert np.mean(err <= tight) >= 0.995
+    assert np.all(err <= 10 * tight)
     _, gref = M.loss_grad(theta.astype(np.float64), freqs, x.cpu().numpy(), t.cpu().numpy(),
                           emulate_bf16=True)
     assert np.linalg.norm(g1 - gref) <= 1e-2 * np.linalg.norm(gref)
