@@ -401,6 +401,15 @@ def measure_extras(drt, dev, sc, w, t, r):
     mlp_flops = 2 * 8192 * (64 * 256 + 3 * 256 * 256 + 256)
     out["surrogate_mlp_batch_8192"] = {"forward_ms": mf * 1e3, "loss_grad_ms": mb * 1e3,
                                        "forward_tflops": mlp_flops / mf / 1e12}
+    # inference on the 512 x 512 proposal grid: the fused tcgen05 kernel
+    mg = SurrogateMLP(dev, batch=512 * 512)
+    xg = torch.rand(512 * 512, 2, device=dev)
+    mgf = timed(lambda: mg.forward(xg), 20)
+    pk_bf16 = float(peaks().get("bf16_tflops") or 1899.4)
+    gfl = 2 * 512 * 512 * (64 * 256 + 3 * 256 * 256 + 256)
+    out["surrogate_mlp_inference_512x512"] = {
+        "kernel": "tc_mlp_forward_kernel (fused, tcgen05)", "forward_ms": mgf * 1e3,
+        "tflops": gfl / mgf / 1e12, "frac_of_measured_bf16_peak": gfl / mgf / 1e12 / pk_bf16}
     out["gradient_scene_dense"] = {
         "workload": "128 random segments, 128x128 RX grid, K<=2 (16385 sequences), alpha=100, "
                     "hard sigmoid, dense g = 1/R, grad wrt TX and 512 wall coordinates",

@@ -4,6 +4,7 @@ a profiler can capture a chosen launch of it (e.g. ``ncu -k regex:vjp_kernel -s 
 
     forward   drt.forward on the scene
     vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
+    mlp       the surrogate MLP's inference on --batch random points
 
 Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload)
 and ``large`` (square + 60 segments, K <= 2, the benchmark workload), each on an
@@ -21,7 +22,8 @@ from . import ops, scenes
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["forward", "vjp"])
+    ap.add_argument("op", choices=["forward", "vjp", "mlp"])
+    ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--scene", choices=["gradient", "large"], default="gradient")
     ap.add_argument("--smoothing", default="sigmoid", choices=["hard_sigmoid", "sigmoid", "step"])
     ap.add_argument("--alpha", type=float, default=100.0)
@@ -29,6 +31,21 @@ def main() -> int:
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     dev = torch.device("cuda:0")
+    if args.op == "mlp":
+        from .surrogate import SurrogateMLP
+        m = SurrogateMLP(dev, batch=args.batch)
+        xm = torch.rand(args.batch, 2, device=dev)
+        for _ in range(2):
+            m.forward(xm)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.reps):
+            m.forward(xm)
+        b.record()
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"op": "mlp", "batch": args.batch, "ms": a.elapsed_time(b) / args.reps}))
+        return 0
     sc = (scenes.gradient_scene if args.scene == "gradient" else scenes.large_scene)(
         alpha=args.alpha, smoothing=args.smoothing)
     rx = scenes.rx_grid(args.rx_grid)
