@@ -564,7 +564,7 @@ drt_status drt_mlp_forward(const float* params, const void* shadow, const float*
     fa.sw5 = L.sw5;
     fa.b5 = L.b5;
     const int grid = (batch + mlp::FZ_ROWS - 1) / mlp::FZ_ROWS;
-    mlp::tc_mlp_forward_kernel<<<grid, mlp::FZ_ROWS, mlp::FZ_SMEM, st>>>(fa, status,
+    mlp::tc_mlp_forward_kernel<<<grid, mlp::FZ_THREADS, mlp::FZ_SMEM, st>>>(fa, status,
                                                                         g_tc_skip_mma.load());
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DRT_OK : mlp_fail(DRT_ERR_CUDA, cudaGetErrorString(e));
