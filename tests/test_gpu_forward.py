@@ -178,6 +178,12 @@ def test_single_wall_and_max_walls(drt, oracle_mod):
                               rx=np.array([[0.31, 0.62], [0.77, 0.18]], np.float32))
     assert sc.n_walls == 1024
     assert_power_close(_run(drt, sc), _ref(oracle_mod, sc))
+    # the largest wall count with the sigmoid, and both kernels (shared memory
+    # holds 8 records per wall for the two-receivers-per-lane kernel: 128 KB here)
+    sg = sc.replace(smoothing="sigmoid", alpha=30.0)
+    a = _run(drt, sg)
+    np.testing.assert_array_equal(a, _run(drt, sg, drt.TileConfig(single_rx=True)))
+    assert_power_close(a, _ref(oracle_mod, sg))
 
 
 def test_loss_and_argmin(drt, oracle_mod):

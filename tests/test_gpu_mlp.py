@@ -87,6 +87,21 @@ def test_adam_step_and_shadow(sur):
     W1 = m.params.cpu().numpy()[:256 * 64].reshape(256, 64)
     np.testing.assert_array_equal(sh[:256 * 64].reshape(256, 64), M.bf16(W1))
     np.testing.assert_array_equal(sh[256 * 64:2 * 256 * 64].reshape(64, 256), M.bf16(W1).T)
+    # ... and, after w5, every W again in 256 x 32 K-chunks laid out for the tensor
+    # cores: element (n, k) of a chunk at byte ((n//8)*4 + k//8)*128 + (n%8)*16 + (k%8)*2
+    p_all = m.params.cpu().numpy()
+    ks = [64, 256, 256, 256]
+    off_w, off_s = 0, sum(2 * 256 * k for k in ks) + 256
+    n = np.arange(256)[:, None]
+    for k_l in ks:
+        W = p_all[off_w:off_w + 256 * k_l].reshape(256, k_l)
+        for q in range(k_l // 32):
+            k = np.arange(32)[None, :]
+            idx = ((n // 8) * 4 + k // 8) * 64 + (n % 8) * 8 + (k % 8)
+            chunk = sh[off_s + q * 256 * 32: off_s + (q + 1) * 256 * 32]
+            np.testing.assert_array_equal(chunk[idx], M.bf16(W[:, q * 32:(q + 1) * 32]))
+        off_w += 256 * k_l + 256
+        off_s += 256 * k_l
 
 
 def test_fit_learns_a_smooth_function(sur):
