@@ -101,42 +101,48 @@ __device__ __forceinline__ void sigmoid_visibility_pair(const SmemWalls& s, cons
   float2 vn[K + 1], vd[K + 1];
 #pragma unroll
   for (int j = 0; j <= K; ++j) vis[j] = vn[j] = vd[j] = one;
+  // one wall's factors for every leg, folded into vn, vd
+  auto wall = [&](int w) {
+    const float4 A = p.A[w], B = p.B[w], C = p.C[w], D = p.D[w];
+    const float zt = s.H[w].w;   // signed TX-side value: only its sign is used
+    const float2 hx = f2(A.x, A.y), hy = f2(A.z, A.w), hz = f2(B.x, B.y);
+    const float2 ax = f2(C.x, C.y), ay = f2(C.z, C.w), bx = f2(D.x, D.y), by = f2(D.z, D.w);
+    float2 ze[K + 2], ee[K + 2];
+    ze[0] = f2(zt, zt);
+    ee[0] = f2(B.z, B.w);
+#pragma unroll
+    for (int i = 1; i <= K + 1; ++i) {
+      ze[i] = fma2(hx, Qx[i], fma2(hy, Qy[i], hz));
+      ee[i] = ex2_pair(ze[i]);
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const float2 za = fma2(mx[j], ax, fma2(my[j], ay, mc[j]));
+      const float2 zb = fma2(mx[j], bx, fma2(my[j], by, mc[j]));
+      const float2 ea = ex2_pair(za), eb = ex2_pair(zb);
+      const float2 ns1 = add2(ee[j], ee[j + 1]);
+      const float2 no1 = fma2(ee[j], ee[j + 1], one);
+      const bool s1x = same_sign(ze[j].x, ze[j + 1].x), s1y = same_sign(ze[j].y, ze[j + 1].y);
+      const float2 x1 = f2(s1x ? ns1.x : no1.x, s1y ? ns1.y : no1.y);
+      const float2 xb1 = f2(s1x ? no1.x : ns1.x, s1y ? no1.y : ns1.y);
+      const float2 ns2 = add2(ea, eb);
+      const float2 no2 = fma2(ea, eb, one);
+      const bool s2x = same_sign(za.x, zb.x), s2y = same_sign(za.y, zb.y);
+      const float2 x2 = f2(s2x ? ns2.x : no2.x, s2y ? ns2.y : no2.y);
+      const float2 xb2 = f2(s2x ? no2.x : ns2.x, s2y ? no2.y : ns2.y);
+      const float2 d2 = add2(ns2, no2);
+      const float2 den = mul2(add2(ns1, no1), d2);
+      const float2 num = fma2(xb1, d2, mul2(x1, xb2));
+      vn[j] = mul2(vn[j], num);
+      vd[j] = mul2(vd[j], den);
+    }
+  };
   for (int w0 = 0; w0 < W; w0 += 8) {
-    const int w1 = min(w0 + 8, W);
-    for (int w = w0; w < w1; ++w) {
-      const float4 A = p.A[w], B = p.B[w], C = p.C[w], D = p.D[w];
-      const float zt = s.H[w].w;   // signed TX-side value: only its sign is used
-      const float2 hx = f2(A.x, A.y), hy = f2(A.z, A.w), hz = f2(B.x, B.y);
-      const float2 ax = f2(C.x, C.y), ay = f2(C.z, C.w), bx = f2(D.x, D.y), by = f2(D.z, D.w);
-      float2 ze[K + 2], ee[K + 2];
-      ze[0] = f2(zt, zt);
-      ee[0] = f2(B.z, B.w);
+    if (w0 + 8 <= W) {   // a full block of 8 walls: unrolled, for independent work
 #pragma unroll
-      for (int i = 1; i <= K + 1; ++i) {
-        ze[i] = fma2(hx, Qx[i], fma2(hy, Qy[i], hz));
-        ee[i] = ex2_pair(ze[i]);
-      }
-#pragma unroll
-      for (int j = 0; j <= K; ++j) {
-        const float2 za = fma2(mx[j], ax, fma2(my[j], ay, mc[j]));
-        const float2 zb = fma2(mx[j], bx, fma2(my[j], by, mc[j]));
-        const float2 ea = ex2_pair(za), eb = ex2_pair(zb);
-        const float2 ns1 = add2(ee[j], ee[j + 1]);
-        const float2 no1 = fma2(ee[j], ee[j + 1], one);
-        const bool s1x = same_sign(ze[j].x, ze[j + 1].x), s1y = same_sign(ze[j].y, ze[j + 1].y);
-        const float2 x1 = f2(s1x ? ns1.x : no1.x, s1y ? ns1.y : no1.y);
-        const float2 xb1 = f2(s1x ? no1.x : ns1.x, s1y ? no1.y : ns1.y);
-        const float2 ns2 = add2(ea, eb);
-        const float2 no2 = fma2(ea, eb, one);
-        const bool s2x = same_sign(za.x, zb.x), s2y = same_sign(za.y, zb.y);
-        const float2 x2 = f2(s2x ? ns2.x : no2.x, s2y ? ns2.y : no2.y);
-        const float2 xb2 = f2(s2x ? no2.x : ns2.x, s2y ? no2.y : ns2.y);
-        const float2 d2 = add2(ns2, no2);
-        const float2 den = mul2(add2(ns1, no1), d2);
-        const float2 num = fma2(xb1, d2, mul2(x1, xb2));
-        vn[j] = mul2(vn[j], num);
-        vd[j] = mul2(vd[j], den);
-      }
+      for (int i = 0; i < 8; ++i) wall(w0 + i);
+    } else {
+      for (int w = w0; w < W; ++w) wall(w);
     }
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
