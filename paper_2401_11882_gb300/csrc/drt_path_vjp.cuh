@@ -78,41 +78,47 @@ __device__ __forceinline__ void sigmoid_vis_sweep(const VSmem& s, int W, const C
     nz[j] = vn[j] = vd[j] = 1.f;
     zc[j] = 0;
   }
+  // one wall's factors for every leg (the leg's own walls masked)
+  auto wall = [&](int w) {
+    const float4 h = s.H[w];
+    const float4 e = s.E[w];
+    float ze[K + 2], ee[K + 2];
+    ze[0] = h.w;
+    ee[0] = fabsf(h.w);
+#pragma unroll
+    for (int i = 1; i <= K + 1; ++i) {
+      ze[i] = fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
+      ee[i] = ex2_approx(-fabsf(ze[i]));
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
+      if (skip) continue;
+      const float za = fmaf(mxk[j], e.x, fmaf(myk[j], e.y, mck[j]));
+      const float zb = fmaf(mxk[j], e.z, fmaf(myk[j], e.w, mck[j]));
+      const float ea = ex2_approx(-fabsf(za)), eb = ex2_approx(-fabsf(zb));
+      const float ns1 = ee[j] + ee[j + 1], no1 = fmaf(ee[j], ee[j + 1], 1.f);
+      const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+      const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
+      const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
+      const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+      const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+      const float d2 = ns2 + no2;
+      const float num = fmaf(xb1, d2, x1 * xb2);
+      if (num == 0.f) {
+        zc[j] += 1;
+      } else {
+        vn[j] *= num;
+        vd[j] *= (ns1 + no1) * d2;
+      }
+    }
+  };
   for (int w0 = 0; w0 < W; w0 += 8) {
-    const int w1 = min(w0 + 8, W);
-    for (int w = w0; w < w1; ++w) {
-      const float4 h = s.H[w];
-      const float4 e = s.E[w];
-      float ze[K + 2], ee[K + 2];
-      ze[0] = h.w;
-      ee[0] = fabsf(h.w);
+    if (w0 + 8 <= W) {   // a full block of 8 walls: unrolled, for independent work
 #pragma unroll
-      for (int i = 1; i <= K + 1; ++i) {
-        ze[i] = fmaf(h.x, Qx[i], fmaf(h.y, Qy[i], h.z));
-        ee[i] = ex2_approx(-fabsf(ze[i]));
-      }
-#pragma unroll
-      for (int j = 0; j <= K; ++j) {
-        const bool skip = (j >= 1 && w == cd.w[j - 1]) || (j < K && w == cd.w[j]);
-        if (skip) continue;
-        const float za = fmaf(mxk[j], e.x, fmaf(myk[j], e.y, mck[j]));
-        const float zb = fmaf(mxk[j], e.z, fmaf(myk[j], e.w, mck[j]));
-        const float ea = ex2_approx(-fabsf(za)), eb = ex2_approx(-fabsf(zb));
-        const float ns1 = ee[j] + ee[j + 1], no1 = fmaf(ee[j], ee[j + 1], 1.f);
-        const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
-        const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
-        const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
-        const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
-        const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
-        const float d2 = ns2 + no2;
-        const float num = fmaf(xb1, d2, x1 * xb2);
-        if (num == 0.f) {
-          zc[j] += 1;
-        } else {
-          vn[j] *= num;
-          vd[j] *= (ns1 + no1) * d2;
-        }
-      }
+      for (int i = 0; i < 8; ++i) wall(w0 + i);
+    } else {
+      for (int w = w0; w < W; ++w) wall(w);
     }
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
