@@ -19,13 +19,15 @@
 //     epilogue (the tensor pipe on one tile, the XU/FMA pipes on the other), so
 //     each layer's weights stream once per tile.  Per tile, mbarriers carry the
 //     hand-offs: "accumulator full" (an MMA commit) to the epilogue warps, and
-//     "activations ready" (128 arrivals after the BF16 rows are in shared
-//     memory and the accumulator has been read) back to the issuing thread;
-//   * the epilogue reads each row back (tcgen05.ld, 32 columns at a time), adds
+//     "activations ready" (256 arrivals, two per row, after the BF16 rows are
+//     in shared memory and the accumulator has been read) back to the issuing
+//     thread; biases and w5 are staged in shared memory once per CTA;
+//   * the epilogue reads its half row back (tcgen05.ld, 32 columns at a time), adds
 //     the bias, applies SiLU z / (1 + 2^(-z log2 e)) (ex2.approx, rcp.approx),
 //     rounds to BF16 and writes the row over the activation buffer as the next
 //     layer's A operand; after the last layer it takes the dot product with w5
-//     instead, and only y leaves the chip.
+//     instead (the two halves meet through shared memory at a per-tile named
+//     barrier), and only y leaves the chip.
 // BF16 rounding points are those of the layer-by-layer path.  Every wait is
 // bounded (TC_WAIT_NS) and also ends once another thread of the CTA has given
 // up: the CTA then records an error code, drains its bulk copies and MMAs in
