@@ -321,6 +321,7 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
     float Wa[K + 1];
 #pragma unroll
     for (int j = 0; j <= K; ++j) Wa[j] = (zc[j] == 0) ? visb[j] * nz[j] * alpha : 0.f;
+#pragma unroll 2
     for (int w = 0; w < W; ++w) {
       const float4 G = s.G[w];
       const float4 E = s.E[w];
