@@ -170,14 +170,14 @@ def annealing_study(n_scenes=256, rx_counts=(2, 3, 4), n_starts=4, n_walls=5, st
 
 
 def batch_study(n_scenes=4096, timed_steps=3, conv_scenes=256, conv_steps=200, seed=0,
-                device="cuda") -> dict:
+                device="cuda", smoothing="hard_sigmoid") -> dict:
     """Batched descent on the 4096-scene batch (W 8-256, R 64-4096, K 0-2, 4 starts,
     alpha = 100, hard sigmoid, Adam lr 1e-2): (1) time of full-batch steps after one
     warm-up step; (2) 200 steps on the first conv_scenes scenes, with the loss
     trajectory and the final TX of every problem (the batched losses themselves are
     checked against the oracle by the GPU tests)."""
     from . import workload
-    full = scenes.scene_batch(n_scenes, seed)
+    full = scenes.scene_batch(n_scenes, seed, smoothing=smoothing)
     dev = torch.device(device)
     T = full.tx0.shape[1]
 
@@ -239,7 +239,9 @@ def _convergence_run(full, n, conv_steps, dev):
     tx = bd.tx.cpu().numpy().reshape(n, T, 2)
     bd.close()
     first = hist[0]
-    rows = {str(i): float(np.mean(hist[i])) for i in (0, 49, 99, 149, conv_steps - 1)}
+    marks = sorted({0, conv_steps // 4 - 1, conv_steps // 2 - 1, 3 * conv_steps // 4 - 1,
+                    conv_steps - 1} - {-1})
+    rows = {str(i): float(np.mean(hist[i])) for i in marks}
     rows["final"] = float(np.mean(final))
     best_start = final.reshape(n, T).min(axis=1)
     live = first < 0
@@ -268,12 +270,15 @@ def main():
     ap.add_argument("--scenes", type=int, default=256)
     ap.add_argument("--timed-steps", type=int, default=3, help="batch study: full-batch steps timed")
     ap.add_argument("--conv-steps", type=int, default=200, help="batch study: convergence steps")
+    ap.add_argument("--smoothing", default="hard_sigmoid", choices=["hard_sigmoid", "sigmoid"],
+                    help="batch study: smoothing of the descent")
     args = ap.parse_args()
     if args.study == "annealing":
         print(json.dumps(annealing_study(n_scenes=args.scenes)), flush=True)
         return
     if args.study == "batch":
         print(json.dumps(batch_study(timed_steps=args.timed_steps, conv_scenes=args.scenes,
+                                     smoothing=args.smoothing,
                                      conv_steps=args.conv_steps)), flush=True)
         return
     rows = []
