@@ -18,6 +18,8 @@ Functions and the passages they follow:
 * ``gradient``          sum_r g_r dP_r/dtheta, assembled from ``power_jvp``
 * ``paths``             per-candidate vertices, validity, visibility, length and power for one receiver
 * ``candidates``        the candidate table of Sec. V (no wall twice in a row)
+* ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
+                        finders' convergence check compares with zero (``oracle/mpt.py``)
 
 Readings of the paper that the oracle fixes (the paper leaves them open):
 incoherent scalar power p = Gamma^k V / L^2 with Gamma = 0.5; smoothing
