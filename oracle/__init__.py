@@ -18,6 +18,7 @@ Functions and the passages they follow:
 * ``gradient``          sum_r g_r dP_r/dtheta, assembled from ``power_jvp``
 * ``paths``             per-candidate vertices, validity, visibility, length and power for one receiver
 * ``candidates``        the candidate table of Sec. V (no wall twice in a row)
+* ``field``           Eq. 7 read as a coherent sum of path fields (Fresnel TE reflection)
 * ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
                         finders' convergence check compares with zero (``oracle/mpt.py``)
 
@@ -75,6 +76,7 @@ def _load():
         lib.drt_oracle_power_jvp.argtypes = [p, i, p, p, i, i, d, i, d, p, p, i, p, p]
         lib.drt_oracle_power_cstep.argtypes = [p, i, p, p, i, i, d, i, d, p, p, d, i, p]
         lib.drt_oracle_paths.argtypes = [p, i, p, p, i, d, i, d, p, p, p, p, p, p]
+        lib.drt_oracle_field.argtypes = [p, i, p, p, i, i, d, i, d, d, d, i, p]
         _lib = lib
         return lib
 
@@ -194,6 +196,23 @@ def gradient(walls, tx, rx, max_order, alpha, smoothing, g, params="all", refl_c
                           threads)
         out[n] = float(np.dot(g_nz, dP))
     return out
+
+
+def field(walls, tx, rx, max_order: int, alpha: float, smoothing, wavelength: float,
+          eps_r: float, refl_coef: float = 0.5, threads=None) -> np.ndarray:
+    """Coherent field E_r (complex128 [R]): Eq. 7's sum of path fields, each
+    prod_j C_j V vis exp(-2 pi i L / wavelength) / L with C_j the Fresnel TE
+    coefficient of relative permittivity ``eps_r`` at reflection j, or the
+    constant -sqrt(refl_coef) when ``eps_r`` is 0.  |E_r|^2 is the coherent power."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    out = np.zeros(2 * rx.shape[0], dtype=np.float64)
+    rc = _load().drt_oracle_field(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx), rx.shape[0],
+                                  int(max_order), float(alpha), _kind(smoothing),
+                                  float(refl_coef), float(wavelength), float(eps_r),
+                                  _threads(threads), _ptr(out))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return out[0::2] + 1j * out[1::2]
 
 
 def loss(P) -> tuple[float, int]:

@@ -191,10 +191,22 @@ struct PathRecord {
   double power;          // p
 };
 
-// Power of one path candidate `seq` (k = seq.size()) from tx to rx.
+// Geometry, validity and visibility of one path candidate `seq` (k = seq.size()).
 template <class T>
-T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& rx,
-             const std::vector<int>& seq, const Params& P, PathRecord* rec) {
+struct PathTerms {
+  bool degenerate;
+  T validity;                // prod_j V_j
+  T visibility;              // prod_j vis_j
+  T L;                       // sum of the leg lengths
+  std::vector<T> cos_in;     // |cos| of the angle between leg j-1 and wall j's normal
+};
+
+template <class T>
+PathTerms<T> path_terms(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& rx,
+                        const std::vector<int>& seq, const Params& P, PathRecord* rec) {
+  PathTerms<T> out;
+  out.degenerate = true;
+  out.validity = out.visibility = out.L = T(0.0);
   const int k = (int)seq.size();
   const int W = (int)walls.size();
   // images I_0..I_k
@@ -235,7 +247,7 @@ T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& 
   }
   if (degenerate) {
     if (rec) { rec->validity = 0; rec->length = 0; rec->power = 0; }
-    return T(0.0);
+    return out;
   }
   const double a = P.alpha;
   const int kind = P.kind;
@@ -277,15 +289,65 @@ T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& 
   }
   T L = T(0.0);
   for (int j = 0; j <= k; ++j) L = L + leg_len[j];
-  double gk = 1.0;
-  for (int j = 0; j < k; ++j) gk *= P.gamma;
-  T power = gk * validity * visibility / (L * L);
+  // incidence at each reflection: the incoming leg j-1 is Q_{j-1} -> Q_j, whose unit
+  // normal is leg_normal[j-1]; |u_w . m| = |n_w . d| / |d| for the leg direction d
+  out.cos_in.resize(k);
+  for (int j = 1; j <= k; ++j) {
+    const Wall<T>& w = walls[seq[j - 1]];
+    T c = dot(w.u, leg_normal[j - 1]);
+    out.cos_in[j - 1] = re(c) < 0.0 ? T(-c) : c;
+  }
+  out.degenerate = false;
+  out.validity = validity;
+  out.visibility = visibility;
+  out.L = L;
   if (rec) {
     rec->validity = re(validity);
     rec->length = re(L);
-    rec->power = re(power);
   }
+  return out;
+}
+
+// Power of one path candidate `seq` (k = seq.size()) from tx to rx.
+template <class T>
+T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& rx,
+             const std::vector<int>& seq, const Params& P, PathRecord* rec) {
+  const int k = (int)seq.size();
+  PathTerms<T> t = path_terms(walls, tx, rx, seq, P, rec);
+  if (t.degenerate) return T(0.0);
+  const T& validity = t.validity;
+  const T& visibility = t.visibility;
+  const T& L = t.L;
+  double gk = 1.0;
+  for (int j = 0; j < k; ++j) gk *= P.gamma;
+  T power = gk * validity * visibility / (L * L);
+  if (rec) rec->power = re(power);
   return power;
+}
+
+// Fresnel reflection coefficient for a field normal to the plane of incidence
+// (TE): (c - sqrt(eps - s^2)) / (c + sqrt(eps - s^2)), with c the cosine of the
+// angle of incidence, s^2 = 1 - c^2 and eps the wall's relative permittivity.
+double fresnel_te(double c, double eps) {
+  const double r = std::sqrt(eps - (1.0 - c * c));
+  return (c - r) / (c + r);
+}
+
+// Eq. 7 read as a coherent sum of scalar fields (field normal to the scene plane,
+// free-space spreading 1/L of the unfolded path): the field of one path is
+//   prod_j C_j * V * vis * exp(-i 2 pi L / lambda) / L,
+// with C_j the Fresnel TE coefficient at reflection j (eps > 0), or the constant
+// amplitude -sqrt(Gamma) (eps == 0), whose square is the power coefficient Gamma.
+Cplx path_field(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
+                const Vec<double>& rx, const std::vector<int>& seq, const Params& P,
+                double wavelength, double eps) {
+  PathTerms<double> t = path_terms(walls, tx, rx, seq, P, nullptr);
+  if (t.degenerate) return Cplx(0.0, 0.0);
+  double coef = 1.0;
+  for (double c : t.cos_in) coef *= (eps > 0.0) ? fresnel_te(c, eps) : -std::sqrt(P.gamma);
+  const double amp = coef * t.validity * t.visibility / t.L;
+  const double phase = 2.0 * M_PI * t.L / wavelength;
+  return Cplx(amp * std::cos(phase), -amp * std::sin(phase));
 }
 
 template <class T>
@@ -412,6 +474,29 @@ int drt_oracle_power_cstep(const double* walls_xy, int W, const double* tx, cons
     Vec<Cplx> q{Cplx(rx[2 * r]), Cplx(rx[2 * r + 1])};
     Cplx v = received_power(walls, t, q, cands, prm);
     dP[r] = v.imag() / h;
+  }
+  return 0;
+}
+
+// Coherent field E[r] (re, im interleaved) summed over the candidate table in order.
+int drt_oracle_field(const double* walls_xy, int W, const double* tx, const double* rx, int R,
+                     int K, double alpha, int kind, double gamma, double wavelength, double eps,
+                     int nthreads, double* E) {
+  if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind)) return 1;
+  if (!(wavelength > 0.0) || !(eps == 0.0 || eps >= 1.0) || !(gamma >= 0.0)) return 1;
+  set_threads(nthreads);
+  std::vector<double> xy(walls_xy, walls_xy + 4 * W);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<double> t{tx[0], tx[1]};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    Vec<double> q{rx[2 * r], rx[2 * r + 1]};
+    Cplx sum(0.0, 0.0);
+    for (const auto& seq : cands) sum += path_field(walls, t, q, seq, prm, wavelength, eps);
+    E[2 * r] = sum.real();
+    E[2 * r + 1] = sum.imag();
   }
   return 0;
 }

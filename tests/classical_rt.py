@@ -67,12 +67,13 @@ def fermat_points(walls, tx, rx, seq):
     return pts(best.x), best.x
 
 
-def classical_power(walls, tx, rx, max_order, gamma=0.5):
-    """(P, min_margin) for one receiver."""
+def classical_paths(walls, tx, rx, max_order):
+    """(paths, min_margin) for one receiver: every specular, unobstructed path as
+    (wall sequence, vertices [TX, X_1 .. X_k, RX])."""
     walls = [np.asarray(w, dtype=np.float64) for w in walls]
     tx = np.asarray(tx, np.float64)
     rx = np.asarray(rx, np.float64)
-    total, margin = 0.0, np.inf
+    paths, margin = [], np.inf
     for seq in sequences(len(walls), max_order):
         k = len(seq)
         P, t = fermat_points(walls, tx, rx, seq)
@@ -111,11 +112,44 @@ def classical_power(walls, tx, rx, max_order, gamma=0.5):
                 if o1 * o2 < 0 and o3 * o4 < 0:
                     ok = False
         margin = min(margin, m)
-        if not ok:
-            continue
-        L = sum(np.hypot(*(P[j + 1] - P[j])) for j in range(k + 1))
-        total += gamma ** k / L ** 2
-    return total, margin
+        if ok:
+            paths.append((seq, P))
+    return paths, margin
+
+
+def _length(P):
+    return sum(np.hypot(*(P[j + 1] - P[j])) for j in range(len(P) - 1))
+
+
+def classical_power(walls, tx, rx, max_order, gamma=0.5):
+    """(P, min_margin) for one receiver."""
+    paths, margin = classical_paths(walls, tx, rx, max_order)
+    return sum(gamma ** len(seq) / _length(P) ** 2 for seq, P in paths), margin
+
+
+def classical_field(walls, tx, rx, max_order, wavelength, eps_r, gamma=0.5):
+    """(E, min_margin) for one receiver: the coherent sum over the specular paths of
+    prod_j C_j exp(-2 pi i L / wavelength) / L, C_j the Fresnel coefficient for a field
+    normal to the plane of incidence, from the angle between the incoming leg and the
+    wall's normal (eps_r > 0), or -sqrt(gamma) (eps_r = 0)."""
+    paths, margin = classical_paths(walls, tx, rx, max_order)
+    E = 0j
+    for seq, P in paths:
+        coef = 1.0
+        for j, w in enumerate(seq, start=1):
+            if eps_r > 0:
+                a, b = np.asarray(walls[w][:2], np.float64), np.asarray(walls[w][2:], np.float64)
+                d = P[j] - P[j - 1]
+                # cosine of incidence from the normal, via the 2D cross product
+                e = b - a
+                c = abs(e[0] * d[1] - e[1] * d[0]) / (np.hypot(*e) * np.hypot(*d))
+                root = np.sqrt(eps_r - (1.0 - c * c))
+                coef *= (c - root) / (c + root)
+            else:
+                coef *= -np.sqrt(gamma)
+        L = _length(P)
+        E += coef * np.exp(-2j * np.pi * L / wavelength) / L
+    return E, margin
 
 
 def mirror_point(p, a, b):

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "drt_oracle.cpp")
 PIN_FILES = ["tests/test_oracle_smoothing.py", "tests/test_oracle_candidates.py",
              "tests/test_oracle_geometry.py", "tests/test_oracle_bruteforce.py",
-             "tests/test_oracle_gradients.py"]
+             "tests/test_oracle_gradients.py", "tests/test_oracle_field.py"]
 
 MUTANTS = {
     "mirror sign": ("return Vec<T>{p.x - 2.0 * d * w.n.x", "return Vec<T>{p.x + 2.0 * d * w.n.x"),
@@ -52,6 +52,16 @@ MUTANTS = {
     "dual quotient rule": ("(a.d * b.v - a.v * b.d) / (b.v * b.v)",
                            "(a.d * b.v + a.v * b.d) / (b.v * b.v)"),
     "dual exp": ("return Dual(e, a.d * e);", "return Dual(e, a.d);"),
+    "field phase sign": ("return Cplx(amp * std::cos(phase), -amp * std::sin(phase));",
+                         "return Cplx(amp * std::cos(phase), amp * std::sin(phase));"),
+    "field wavelength factor": ("const double phase = 2.0 * M_PI * t.L / wavelength;",
+                                "const double phase = M_PI * t.L / wavelength;"),
+    "field spreading squared": ("const double amp = coef * t.validity * t.visibility / t.L;",
+                                "const double amp = coef * t.validity * t.visibility / (t.L * t.L);"),
+    "fresnel numerator sign": ("return (c - r) / (c + r);", "return (r - c) / (c + r);"),
+    "fresnel sine for cosine": ("const double r = std::sqrt(eps - (1.0 - c * c));",
+                                "const double r = std::sqrt(eps - c * c);"),
+    "constant coefficient sign": (": -std::sqrt(P.gamma);", ": std::sqrt(P.gamma);"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
