@@ -366,6 +366,11 @@ def measure_extras(drt, dev, sc, w, t, r):
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
                                   tile=drt.TileConfig(single_rx=True)))
     out["hard_forward_one_rx_per_lane_evals_per_s"] = ev / s
+    # coherent field (Eq. 7 with complex path fields, Fresnel TE, eps_r 5, wavelength 0.02)
+    s = timed(lambda: drt.field(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid", 0.02, 5.0))
+    out["coherent_field_hard_evals_per_s"] = ev / s
+    s = timed(lambda: drt.field(w, t, r, sc.max_order, sc.alpha, "sigmoid", 0.02, 5.0))
+    out["coherent_field_sigmoid_evals_per_s"] = ev / s
     g = scenes.gradient_scene()
     gw, gt, gr = (torch.tensor(g.walls, device=dev), torch.tensor(g.tx, device=dev),
                   torch.tensor(g.rx, device=dev))

@@ -112,6 +112,29 @@ drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* ti
 drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* Coherent field per receiver: Eq. 7 read as a sum of complex path fields (the
+   field normal to the scene plane, free-space spreading 1/L of the unfolded path):
+     E_r = sum over the candidates of  prod_j C_j * V * vis * exp(-2 pi i L / wavelength) / L
+   with V, vis and L as in drt_forward (Sec. V-A smoothing, same candidates) and
+   C_j the reflection coefficient at reflection j:
+     eps_r >= 1: Fresnel TE (c - sqrt(eps_r - 1 + c^2)) / (c + sqrt(eps_r - 1 + c^2)),
+                 c the cosine of the angle between the arriving leg and the wall's
+                 normal (0 at eps_r = 1 and grazing incidence);
+     eps_r == 0: the constant -sqrt(scene->refl_coef) (refl_coef >= 0), whose square
+                 is drt_forward's power coefficient.
+   wavelength: > 0, in the scene's length unit.  The phase carries the FP32 path
+   length's rounding: its error grows as 2 pi (L / wavelength) times a few units
+   of 2^-24.
+   field: [n_rx][2] device (re, im; 8-byte aligned), overwritten.
+   power: [n_rx] device receiving |E_r|^2, or NULL.
+   workspace: device scratch of at least drt_field_workspace_size bytes.
+   tile: as for drt_forward (always one receiver per lane; DRT_TILE_SINGLE_RX is
+   implied).  Enqueued on `stream`; never synchronises. */
+drt_status drt_field_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes);
+drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelength, float eps_r,
+                     float* field, float* power, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
 /* Autotuner probe for drt_forward (the work decomposition does not change the
    result beyond the order of the per-chunk sums): runs drt_forward on `scene`
    with each of the n_cand tiles of `cands` (host array), one untimed launch

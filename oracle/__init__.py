@@ -76,7 +76,7 @@ def _load():
         lib.drt_oracle_power_jvp.argtypes = [p, i, p, p, i, i, d, i, d, p, p, i, p, p]
         lib.drt_oracle_power_cstep.argtypes = [p, i, p, p, i, i, d, i, d, p, p, d, i, p]
         lib.drt_oracle_paths.argtypes = [p, i, p, p, i, d, i, d, p, p, p, p, p, p]
-        lib.drt_oracle_field.argtypes = [p, i, p, p, i, i, d, i, d, d, d, i, p]
+        lib.drt_oracle_field.argtypes = [p, i, p, p, i, i, d, i, d, d, d, i, p, p, p]
         _lib = lib
         return lib
 
@@ -199,20 +199,27 @@ def gradient(walls, tx, rx, max_order, alpha, smoothing, g, params="all", refl_c
 
 
 def field(walls, tx, rx, max_order: int, alpha: float, smoothing, wavelength: float,
-          eps_r: float, refl_coef: float = 0.5, threads=None) -> np.ndarray:
+          eps_r: float, refl_coef: float = 0.5, threads=None, scales: bool = False):
     """Coherent field E_r (complex128 [R]): Eq. 7's sum of path fields, each
     prod_j C_j V vis exp(-2 pi i L / wavelength) / L with C_j the Fresnel TE
     coefficient of relative permittivity ``eps_r`` at reflection j, or the
-    constant -sqrt(refl_coef) when ``eps_r`` is 0.  |E_r|^2 is the coherent power."""
+    constant -sqrt(refl_coef) when ``eps_r`` is 0.  |E_r|^2 is the coherent power.
+
+    With ``scales``: (E, mag, lmax), mag_r the sum of the path fields' magnitudes
+    and lmax_r the longest length among the paths with a non-zero field."""
     walls, tx, rx = _scene_args(walls, tx, rx)
-    out = np.zeros(2 * rx.shape[0], dtype=np.float64)
-    rc = _load().drt_oracle_field(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx), rx.shape[0],
+    R = rx.shape[0]
+    out = np.zeros(2 * R, dtype=np.float64)
+    mag = np.zeros(R)
+    lmax = np.zeros(R)
+    rc = _load().drt_oracle_field(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx), R,
                                   int(max_order), float(alpha), _kind(smoothing),
                                   float(refl_coef), float(wavelength), float(eps_r),
-                                  _threads(threads), _ptr(out))
+                                  _threads(threads), _ptr(out), _ptr(mag), _ptr(lmax))
     if rc:
         raise ValueError("oracle rejected the arguments")
-    return out[0::2] + 1j * out[1::2]
+    E = out[0::2] + 1j * out[1::2]
+    return (E, mag, lmax) if scales else E
 
 
 def loss(P) -> tuple[float, int]:

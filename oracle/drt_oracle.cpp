@@ -327,9 +327,11 @@ T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& 
 
 // Fresnel reflection coefficient for a field normal to the plane of incidence
 // (TE): (c - sqrt(eps - s^2)) / (c + sqrt(eps - s^2)), with c the cosine of the
-// angle of incidence, s^2 = 1 - c^2 and eps the wall's relative permittivity.
+// angle of incidence, s^2 = 1 - c^2 and eps the wall's relative permittivity.  At
+// eps = 1 the coefficient is 0 for every c > 0; c = 0 (grazing) keeps that value.
 double fresnel_te(double c, double eps) {
   const double r = std::sqrt(eps - (1.0 - c * c));
+  if (c + r == 0.0) return 0.0;
   return (c - r) / (c + r);
 }
 
@@ -340,8 +342,9 @@ double fresnel_te(double c, double eps) {
 // amplitude -sqrt(Gamma) (eps == 0), whose square is the power coefficient Gamma.
 Cplx path_field(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
                 const Vec<double>& rx, const std::vector<int>& seq, const Params& P,
-                double wavelength, double eps) {
+                double wavelength, double eps, double* length) {
   PathTerms<double> t = path_terms(walls, tx, rx, seq, P, nullptr);
+  *length = t.degenerate ? 0.0 : t.L;
   if (t.degenerate) return Cplx(0.0, 0.0);
   double coef = 1.0;
   for (double c : t.cos_in) coef *= (eps > 0.0) ? fresnel_te(c, eps) : -std::sqrt(P.gamma);
@@ -478,10 +481,12 @@ int drt_oracle_power_cstep(const double* walls_xy, int W, const double* tx, cons
   return 0;
 }
 
-// Coherent field E[r] (re, im interleaved) summed over the candidate table in order.
+// Coherent field E[r] (re, im interleaved) summed over the candidate table in order;
+// optionally mag[r] = sum of the path fields' magnitudes and lmax[r] = the longest
+// path length with a non-zero field (the scales of FP32 rounding in E).
 int drt_oracle_field(const double* walls_xy, int W, const double* tx, const double* rx, int R,
                      int K, double alpha, int kind, double gamma, double wavelength, double eps,
-                     int nthreads, double* E) {
+                     int nthreads, double* E, double* mag, double* lmax) {
   if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind)) return 1;
   if (!(wavelength > 0.0) || !(eps == 0.0 || eps >= 1.0) || !(gamma >= 0.0)) return 1;
   set_threads(nthreads);
@@ -494,9 +499,18 @@ int drt_oracle_field(const double* walls_xy, int W, const double* tx, const doub
   for (int r = 0; r < R; ++r) {
     Vec<double> q{rx[2 * r], rx[2 * r + 1]};
     Cplx sum(0.0, 0.0);
-    for (const auto& seq : cands) sum += path_field(walls, t, q, seq, prm, wavelength, eps);
+    double m = 0.0, lm = 0.0;
+    for (const auto& seq : cands) {
+      double len = 0.0;
+      const Cplx f = path_field(walls, t, q, seq, prm, wavelength, eps, &len);
+      sum += f;
+      m += std::abs(f);
+      if (std::abs(f) > 0.0 && len > lm) lm = len;
+    }
     E[2 * r] = sum.real();
     E[2 * r + 1] = sum.imag();
+    if (mag) mag[r] = m;
+    if (lmax) lmax[r] = lm;
   }
   return 0;
 }

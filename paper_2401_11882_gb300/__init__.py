@@ -6,12 +6,14 @@ Public calls (PyTorch tensors on a CUDA device, float32):
   receiver, differentiable in ``walls`` and ``tx`` (hand-written adjoint).
 * ``loss(power)``: -min over receivers; ``objective(...)`` = loss(power(...)).
 * ``forward``, ``vjp``, ``min_loss``: the raw C-ABI calls.
+* ``field(...)``: the coherent reading of Eq. 7 (complex path fields, Fresnel
+  reflection), field and power per receiver.
 
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
-from .ops import (TileConfig, forward, loss, min_loss, min_loss_backward, min_loss_vjp,
+from .ops import (TileConfig, field, forward, loss, min_loss, min_loss_backward, min_loss_vjp,
                   num_candidates, objective, objective_host, power, vjp)
 
-__all__ = ["TileConfig", "forward", "loss", "min_loss", "min_loss_backward", "min_loss_vjp",
-           "num_candidates", "objective", "objective_host", "power", "vjp"]
+__all__ = ["TileConfig", "field", "forward", "loss", "min_loss", "min_loss_backward",
+           "min_loss_vjp", "num_candidates", "objective", "objective_host", "power", "vjp"]

@@ -4,6 +4,7 @@ a profiler can capture a chosen launch of it (e.g. ``ncu -k regex:vjp_kernel -s 
 
     forward   drt.forward on the scene
     vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
+    field     drt.field (coherent field, Fresnel TE, --eps-r, --wavelength)
     mlp       the surrogate MLP's inference on --batch random points
 
 Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload)
@@ -22,13 +23,15 @@ from . import ops, scenes
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["forward", "vjp", "mlp"])
+    ap.add_argument("op", choices=["forward", "vjp", "mlp", "field"])
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--scene", choices=["gradient", "large"], default="gradient")
     ap.add_argument("--smoothing", default="sigmoid", choices=["hard_sigmoid", "sigmoid", "step"])
     ap.add_argument("--alpha", type=float, default=100.0)
     ap.add_argument("--rx-grid", type=int, default=32)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--wavelength", type=float, default=0.02)
+    ap.add_argument("--eps-r", type=float, default=5.0)
     args = ap.parse_args()
     dev = torch.device("cuda:0")
     if args.op == "mlp":
@@ -55,6 +58,9 @@ def main() -> int:
     def run():
         if args.op == "forward":
             return ops.forward(w, t, r, sc.max_order, args.alpha, args.smoothing)
+        if args.op == "field":
+            return ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
+                             args.eps_r)
         return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g)
 
     for _ in range(2):
@@ -67,7 +73,9 @@ def main() -> int:
     b.record()
     torch.cuda.synchronize(dev)
     res = {"op": args.op, "scene": args.scene, "smoothing": args.smoothing, "alpha": args.alpha,
-           "n_rx": int(r.shape[0]), "ms": a.elapsed_time(b) / args.reps}
+           "n_rx": int(r.shape[0]), "ms": a.elapsed_time(b) / args.reps,
+           "evals_per_s": int(r.shape[0]) * ops.num_candidates(sc.walls.shape[0], sc.max_order)
+           / (a.elapsed_time(b) / args.reps / 1e3)}
     if args.op == "vjp":
         res["grad_tx"] = out[0].tolist()
     print(json.dumps(res), flush=True)

@@ -61,6 +61,8 @@ drt_status device_info(int* sms) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(forward)");
     e = vjp_set_smem_limit(DRT_MAX_WALLS);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(vjp)");
+    e = field_set_smem_limit(DRT_MAX_WALLS);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(field)");
     d.smem_set = true;
   }
   *sms = d.sms;
@@ -111,7 +113,7 @@ drt_status check_tile(const drt_tile* t) {
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
 
-enum Kernel { FWD, VJP };
+enum Kernel { FWD, VJP, FIELD };
 
 drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
   int sms = 0;
@@ -123,7 +125,7 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   d->threads = warps * 32;
   d->n_cand = num_candidates(W, K);
   long long chunk = (t && t->cands_per_unit) ? t->cands_per_unit : 64;
-  if (kern == FWD && R > 0) {
+  if (kern != VJP && R > 0) {
     const long long max_chunks = std::max(1LL, MAX_PARTIALS / R);
     chunk = std::max(chunk, (d->n_cand + max_chunks - 1) / max_chunks);
   }
@@ -137,14 +139,15 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   int per_sm = (t && t->ctas_per_sm) ? t->ctas_per_sm : 0;
   if (per_sm == 0) {
     const int mode = sc->smoothing;
-    cudaError_t e = (kern == FWD) ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
-                                  : vjp_occupancy(mode, true, d->threads, W, &per_sm);
+    cudaError_t e = (kern == FWD)     ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
+                    : (kern == FIELD) ? field_occupancy(mode, d->threads, W, &per_sm)
+                                      : vjp_occupancy(mode, true, d->threads, W, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
   }
   long long ctas = (long long)sms * per_sm;
   const long long needed = (d->n_units + warps - 1) / warps;
-  if (kern == FWD) ctas = std::min(ctas, std::max(1LL, needed));
+  if (kern != VJP) ctas = std::min(ctas, std::max(1LL, needed));
   d->ctas = (int)std::max(1LL, ctas);
   return DRT_OK;
 }
@@ -236,6 +239,66 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
   cudaError_t e = launch_forward(a, scene->smoothing, d.ctas, d.threads,
                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return DRT_OK;
+}
+
+drt_status drt_field_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(scene, tile, FIELD, &d)) != DRT_OK) return st;
+  *bytes = (size_t)d.n_chunks * (size_t)scene->n_rx * 2 * sizeof(float);
+  return DRT_OK;
+}
+
+drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelength, float eps_r,
+                     float* field, float* power, void* workspace, size_t workspace_bytes,
+                     void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!(wavelength > 0.f) || !std::isfinite(wavelength))
+    return fail(DRT_ERR_INVALID_ARG, "wavelength must be finite and > 0");
+  if (!(eps_r == 0.f || eps_r >= 1.f) || !std::isfinite(eps_r))
+    return fail(DRT_ERR_INVALID_ARG, "eps_r must be 0 (constant coefficient) or finite and >= 1");
+  if (eps_r == 0.f && !(scene->refl_coef >= 0.f))
+    return fail(DRT_ERR_INVALID_ARG, "refl_coef must be >= 0 for the constant coefficient");
+  if (scene->n_rx > 0 && (!field || !aligned(field, 8)))
+    return fail(DRT_ERR_INVALID_ARG, "field must be an 8-byte aligned device pointer");
+  if (scene->n_rx == 0) return DRT_OK;
+  Decomp d;
+  if ((st = decompose(scene, tile, FIELD, &d)) != DRT_OK) return st;
+  const size_t need = (size_t)d.n_chunks * (size_t)scene->n_rx * 2 * sizeof(float);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 8))
+    return fail(DRT_ERR_WORKSPACE, "field needs %zu 8-byte aligned workspace bytes, got %zu",
+                need, workspace_bytes);
+  FieldArgs a;
+  a.walls = reinterpret_cast<const float4*>(scene->walls);
+  a.W = scene->n_walls;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  a.refl_amp = eps_r == 0.f ? -(float)std::sqrt((double)scene->refl_coef) : 0.f;
+  a.eps_r = eps_r;
+  const double inv = 1.0 / (double)wavelength;
+  a.inv_lambda_hi = (float)inv;
+  a.inv_lambda_lo = (float)(inv - (double)a.inv_lambda_hi);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  a.partial = static_cast<float2*>(workspace);
+  a.field = reinterpret_cast<float2*>(field);
+  a.power = power;
+  cudaError_t e = launch_field(a, scene->smoothing, d.ctas, d.threads,
+                               static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "field launch");
   return DRT_OK;
 }
 

@@ -1,0 +1,189 @@
+// Coherent field per receiver: Eq. 7 read as a sum of complex path fields,
+//   E_r = sum over candidates of  prod_j C_j * V * vis * exp(-2 pi i L / lambda) / L,
+// with the field normal to the scene plane, C_j the Fresnel reflection
+// coefficient for that polarisation (TE) at the angle of incidence of the leg
+// arriving at reflection j, or a constant amplitude coefficient, and the
+// coherent power |E_r|^2.
+//
+// The geometry, validity and obstruction of each (receiver, candidate) are the
+// forward pass's (path_geometry, leg_visibility): the obstruction loop is the
+// cost and is unchanged.  Only the per-path epilogue differs: it recomputes the
+// path length with correctly rounded leg lengths (the phase 2 pi L / lambda
+// magnifies any error in L by L / lambda), takes 1/lambda as a float pair so
+// the cycle count's only rounding is L's own, and reduces the cycle count to
+// [-1/2, 1/2] before sincospi.  Work decomposition, determinism and the chunk
+// reduction follow drt_forward.cu with (re, im) partial sums.
+#include <cuda_runtime.h>
+
+#include "drt_common.cuh"
+#include "drt_internal.h"
+#include "drt_path.cuh"
+
+namespace drt {
+
+namespace {
+
+// Field (re, im) of one path candidate of order K for this lane's receiver.
+template <int MODE, int K, bool MASKED>
+__device__ __forceinline__ float2 path_field(const SmemWalls& s, const FieldArgs& a, float2 tx,
+                                             float2 rx, const Cand& cd) {
+  float Ix[K + 1], Iy[K + 1];
+  tx_images<K>(s, tx, cd, Ix, Iy);
+  PathGeom<MODE, K> g;
+  path_geometry<MODE, K>(s, Ix, Iy, tx, rx, cd, a.alpha, g);
+  if (a.cull && __all_sync(0xffffffffu, g.V == 0.f || g.degenerate)) return make_float2(0.f, 0.f);
+  float vis[K + 1];
+  const float min_div =
+      leg_visibility<MODE, K, MASKED>(s, a.W, cd, g.Qx, g.Qy, g.mx, g.my, g.mc, vis);
+  if constexpr (!MASKED && MODE != MODE_STEP) {
+    // as in path_power: an unreliable divided-out factor recomputes with masking
+    const bool bad = !g.degenerate && !(min_div >= 0.25f);
+    if (__any_sync(0xffffffffu, bad))
+      leg_visibility<MODE, K, true>(s, a.W, cd, g.Qx, g.Qy, g.mx, g.my, g.mc, vis);
+  }
+  float L = 0.f, coef = 1.f, amp = g.V;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = g.Qx[j + 1] - g.Qx[j], dy = g.Qy[j + 1] - g.Qy[j];
+    const float len = __fsqrt_rn(fmaf(dx, dx, dy * dy));
+    L += len;
+    amp *= vis[j];
+    if (j < K) {
+      // leg j arrives at reflection j + 1 on wall w_{j+1}: cosine of incidence
+      // |n . d| / |d| with n the wall's unit normal
+      const float4 G = s.G[cd.w[j]];
+      const float c = fminf(__fdiv_rn(fabsf(fmaf(G.x, dx, G.y * dy)), len), 1.f);
+      float r = a.refl_amp;
+      if (a.eps_r > 0.f) {
+        const float root = __fsqrt_rn(fmaf(c, c, a.eps_r - 1.f));
+        const float den = c + root;
+        r = den > 0.f ? __fdiv_rn(c - root, den) : 0.f;   // eps_r = 1 at grazing: 0
+      }
+      coef *= r;
+    }
+  }
+  // cycles L / lambda = L * (hi + lo): the product's rounding error is recovered
+  // by an FMA, so the fractional part carries only L's own error
+  const float p = L * a.inv_lambda_hi;
+  const float e = fmaf(L, a.inv_lambda_hi, -p);
+  const float frac = (p - rintf(p)) + fmaf(L, a.inv_lambda_lo, e);
+  float sn, cs;
+  sincospif(2.f * frac, &sn, &cs);
+  const float m = __fdiv_rn(amp * coef, L);
+  return g.degenerate ? make_float2(0.f, 0.f) : make_float2(m * cs, -m * sn);
+}
+
+template <int MODE, bool MASKED>
+__device__ __forceinline__ float2 field_of(const SmemWalls& s, const FieldArgs& a, float2 tx,
+                                           float2 q, const Cand& cd) {
+  switch (cd.k) {
+    case 0: return path_field<MODE, 0, MASKED>(s, a, tx, q, cd);
+    case 1: return path_field<MODE, 1, MASKED>(s, a, tx, q, cd);
+    case 2: return path_field<MODE, 2, MASKED>(s, a, tx, q, cd);
+    default: return path_field<MODE, 3, MASKED>(s, a, tx, q, cd);
+  }
+}
+
+// One receiver per lane; a unit is (32 receivers) x (a chunk of candidates), as in
+// the forward kernel, with one (re, im) partial sum per (chunk, receiver).
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 2 : 3) field_kernel(const FieldArgs a) {
+  extern __shared__ float4 smem[];
+  SmemWalls s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  const bool masked = a.alpha > FAST_SKIP_MAX_ALPHA;
+  for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
+       u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    long long r = tile * 32 + lane;
+    const bool live = r < a.R;
+    if (!live) r = a.R - 1;
+    const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
+    const int c0 = (int)(chunk * a.chunk);
+    const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
+    float2 acc = make_float2(0.f, 0.f);
+    Cand cd = decode_candidate(c0, a.W, a.K);
+    for (int i = 0; i < nc; ++i) {
+      if (i > 0) next_candidate(cd, a.W);
+      const float2 f = masked ? field_of<MODE, true>(s, a, tx, q, cd)
+                              : field_of<MODE, false>(s, a, tx, q, cd);
+      acc.x += f.x;
+      acc.y += f.y;
+    }
+    if (live) a.partial[chunk * a.R + r] = acc;
+  }
+}
+
+// field[r] = sum over chunks of partial[chunk][r] in chunk order; power[r] = |field[r]|^2.
+__global__ void reduce_field_kernel(const float2* __restrict__ partial, long long n_chunks,
+                                    long long R, float2* __restrict__ field,
+                                    float* __restrict__ power) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (long long c = 0; c < n_chunks; ++c) {
+      const float2 v = partial[c * R + r];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    field[r] = acc;
+    if (power) power[r] = fmaf(acc.x, acc.x, acc.y * acc.y);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
+  const size_t smem = forward_smem_bytes(a.W, false);
+  if (a.n_units > 0) {
+    switch (mode) {
+      case MODE_SIGMOID: field_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_HARD: field_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a); break;
+      default: field_kernel<MODE_STEP><<<ctas, threads, smem, st>>>(a); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.R > 0) {
+    const long long nb = (a.R + 255) / 256;
+    const int rb = (int)(nb < 4096 ? nb : 4096);
+    reduce_field_kernel<<<rb, 256, 0, st>>>(a.partial, a.n_chunks, a.R, a.field, a.power);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t field_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = forward_smem_bytes(W, false);
+  switch (mode) {
+    case MODE_SIGMOID:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_kernel<MODE_SIGMOID>,
+                                                           threads, smem);
+    case MODE_HARD:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_kernel<MODE_HARD>,
+                                                           threads, smem);
+    default:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_kernel<MODE_STEP>,
+                                                           threads, smem);
+  }
+}
+
+cudaError_t field_set_smem_limit(int W) {
+  const int smem = (int)forward_smem_bytes(W, false);
+  cudaError_t e = cudaFuncSetAttribute(field_kernel<MODE_SIGMOID>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(field_kernel<MODE_HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(field_kernel<MODE_STEP>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace drt

@@ -102,6 +102,29 @@ def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
     return power
 
 
+def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
+          eps_r: float, refl_coef: float = 0.5, tile: TileConfig | None = None):
+    """Coherent field and power per receiver on the current stream:
+    (field float32 [R, 2] = (re, im), power float32 [R] = |field|^2).
+
+    Eq. 7 as a sum of complex path fields prod_j C_j V vis exp(-2 pi i L / wavelength) / L,
+    C_j the Fresnel TE coefficient of relative permittivity ``eps_r`` (>= 1) at
+    each reflection, or -sqrt(refl_coef) when ``eps_r`` is 0 (drt_field)."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_field_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    E = torch.empty(sc.n_rx, 2, dtype=torch.float32, device=dev)
+    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    _lib.call("drt_field", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
+              ctypes.c_float(eps_r), _ptr(E), _ptr(power), _ptr(ws),
+              ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return E, power
+
+
 def tune_forward_timings(walls, tx, rx, max_order: int, alpha: float, smoothing: str,
                          candidates, refl_coef: float = 0.5, reps: int = 3):
     """Times drt_forward with each TileConfig of ``candidates`` in the library

@@ -84,3 +84,25 @@ def test_loss_rejects_bad_args(lib):
     assert lib.drt_loss(None, 4, p, p, None) == 1
     assert lib.drt_loss(p, 0, p, p, None) == 1
     assert lib.drt_loss_backward(None, None, 4, p, None) == 1
+
+
+@pytest.mark.parametrize("wavelength,eps_r,refl,field_ptr", [
+    (0.0, 5.0, 0.5, 256), (-1.0, 5.0, 0.5, 256), (float("nan"), 5.0, 0.5, 256),
+    (float("inf"), 5.0, 0.5, 256), (0.1, 0.5, 0.5, 256), (0.1, -2.0, 0.5, 256),
+    (0.1, float("inf"), 0.5, 256), (0.1, 0.0, -0.5, 256), (0.1, 5.0, 0.5, 0),
+    (0.1, 5.0, 0.5, 260)])
+def test_field_rejects_bad_args_before_any_launch(lib, wavelength, eps_r, refl, field_ptr):
+    # Rejected on the host (wavelength, permittivity, coefficient, field pointer).
+    sc = _scene(refl_coef=refl)
+    p = ctypes.c_void_p(256)
+    st = lib.drt_field(ctypes.byref(sc), None, ctypes.c_float(wavelength), ctypes.c_float(eps_r),
+                       ctypes.c_void_p(field_ptr), None, p, 1 << 20, None)
+    assert st == 1 and len(lib.drt_last_error()) > 0
+
+
+def test_field_rejects_bad_scene_before_any_launch(lib):
+    sc = _scene(n_walls=0)
+    out = ctypes.c_size_t()
+    assert lib.drt_field_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == 1
+    assert lib.drt_field(ctypes.byref(sc), None, ctypes.c_float(0.1), ctypes.c_float(5.0),
+                         ctypes.c_void_p(256), None, None, 0, None) == 1

@@ -1,0 +1,149 @@
+"""CUDA coherent field (drt_field: Eq. 7 as a sum of complex path fields) against the
+FP64 oracle.
+
+Bound per receiver (derived from the FP32 arithmetic): each path field may carry
+the forward's relative tolerance 1e-4 on its magnitude, and its phase the FP32
+error of the path length, a few units of 2^-24 of L, magnified by 2 pi L / lambda:
+
+    |E_gpu - E_ref| <= mag * (1e-4 + 2 pi (lmax / lambda) * 16 * 2^-24)
+
+with mag the oracle's sum of path-field magnitudes and lmax its longest
+contributing path.  Where the field is ill-conditioned in FP32 (large alpha:
+two FP32 roundings of the inputs move the oracle's own FP64 field further), at
+least 99% of receivers meet that bound and all meet 4x the field's measured
+sensitivity.  The power |E|^2 follows: |dP| <= 2 |E| |dE| + |dE|^2.
+"""
+import numpy as np
+import pytest
+
+from paper_2401_11882_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+AMP_RTOL = 1e-4
+LEN_ULPS = 16 * 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def drt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_11882_gb300 as m
+    return m
+
+
+def _gpu(drt, walls, tx, rx, K, alpha, smoothing, lam, eps, refl=0.5, tile=None):
+    dev = torch.device("cuda:0")
+    w = torch.tensor(np.asarray(walls, np.float32), device=dev)
+    t = torch.tensor(np.asarray(tx, np.float32), device=dev)
+    r = torch.tensor(np.asarray(rx, np.float32), device=dev)
+    E, P = drt.field(w, t, r, K, alpha, smoothing, lam, eps, refl, tile=tile)
+    torch.cuda.synchronize()
+    E = E.cpu().numpy().astype(np.float64)
+    return E[:, 0] + 1j * E[:, 1], P.cpu().numpy().astype(np.float64)
+
+
+def _sensitivity(oracle_mod, walls, tx, rx, K, alpha, smoothing, lam, eps, refl=0.5, seed=0):
+    rng = np.random.default_rng(seed)
+    walls, tx, rx = (np.asarray(a, np.float64) for a in (walls, tx, rx))
+    base = oracle_mod.field(walls, tx, rx, K, alpha, smoothing, lam, eps, refl)
+    out = np.zeros(base.shape)
+
+    def jit(a):
+        return a + rng.uniform(-2.0 ** -23, 2.0 ** -23, a.shape) * np.maximum(np.abs(a), 1.0)
+
+    for _ in range(4):
+        out = np.maximum(out, np.abs(oracle_mod.field(jit(walls), jit(tx), jit(rx), K, alpha,
+                                                      smoothing, lam, eps, refl) - base))
+    return out
+
+
+def _check(oracle_mod, E, P, walls, tx, rx, K, alpha, smoothing, lam, eps, refl=0.5,
+           min_strict=1.0):
+    ref, mag, lmax = oracle_mod.field(np.asarray(walls, np.float64), np.asarray(tx, np.float64),
+                                      np.asarray(rx, np.float64), K, alpha, smoothing, lam, eps,
+                                      refl, scales=True)
+    bound = mag * (AMP_RTOL + 2 * np.pi * (lmax / lam) * LEN_ULPS) + 1e-30
+    err = np.abs(E - ref)
+    strict = err <= bound
+    if strict.mean() < 1.0:
+        sens = _sensitivity(oracle_mod, walls, tx, rx, K, alpha, smoothing, lam, eps, refl)
+        wide = np.maximum(bound, 4 * sens)
+        bad = np.nonzero(err > wide)[0]
+        assert bad.size == 0, (bad[:5], err[bad[:5]], wide[bad[:5]], ref[bad[:5]])
+        assert strict.mean() >= min_strict, strict.mean()
+    dP = 2 * np.abs(ref) * np.maximum(bound, err) + np.maximum(bound, err) ** 2
+    assert np.all(np.abs(P - np.abs(ref) ** 2) <= 1.01 * dP + 1e-6 * np.abs(ref) ** 2 + 1e-30)
+    return ref
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid", "step"])
+@pytest.mark.parametrize("eps", [0.0, 5.0])
+def test_tiny_scene(drt, oracle_mod, smoothing, eps):
+    sc = scenes.tiny_scene(alpha=100.0, smoothing=smoothing)
+    E, P = _gpu(drt, sc.walls, sc.tx, sc.rx, sc.max_order, sc.alpha, smoothing, 0.05, eps)
+    _check(oracle_mod, E, P, sc.walls, sc.tx, sc.rx, sc.max_order, sc.alpha, smoothing, 0.05, eps)
+
+
+CASES = [
+    # (seed, W, R, K, alpha, smoothing, wavelength, eps_r): ragged 32-receiver tiles
+    (0, 5, 77, 0, 50.0, "hard_sigmoid", 0.013, 4.0),
+    (1, 9, 100, 1, 30.0, "sigmoid", 0.1, 0.0),
+    (2, 12, 33, 2, 100.0, "hard_sigmoid", 0.02, 15.0),
+    (3, 12, 65, 2, 20.0, "sigmoid", 0.05, 2.5),
+    (4, 10, 40, 2, 1.0, "step", 0.01, 81.0),
+    (5, 6, 31, 3, 40.0, "hard_sigmoid", 0.07, 0.0),
+    (6, 6, 45, 3, 15.0, "sigmoid", 0.03, 6.0),
+    (7, 16, 50, 2, 3e4, "hard_sigmoid", 0.04, 3.0),
+]
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha,smoothing,lam,eps", CASES)
+def test_random_scenes(drt, oracle_mod, seed, W, R, K, alpha, smoothing, lam, eps):
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, smoothing, boundary=(seed % 2 == 0))
+    E, P = _gpu(drt, sc.walls, sc.tx, sc.rx, K, alpha, smoothing, lam, eps)
+    _check(oracle_mod, E, P, sc.walls, sc.tx, sc.rx, K, alpha, smoothing, lam, eps,
+           min_strict=0.99)
+
+
+def test_benchmark_scene_sampled_receivers(drt, oracle_mod):
+    # the 64-wall scene on its full 256 x 256 receiver grid, in the launch configuration
+    # the benchmark times; 96 receivers sampled for the oracle
+    sc = scenes.large_scene(alpha=100.0, smoothing="hard_sigmoid")
+    lam, eps = 0.02, 5.0
+    E, P = _gpu(drt, sc.walls, sc.tx, sc.rx, sc.max_order, sc.alpha, sc.smoothing, lam, eps)
+    idx = np.random.default_rng(5).choice(sc.rx.shape[0], 96, replace=False)
+    _check(oracle_mod, E[idx], P[idx], sc.walls, sc.tx, sc.rx[idx], sc.max_order, sc.alpha,
+           sc.smoothing, lam, eps, min_strict=0.99)
+    assert np.all(np.isfinite(E)) and np.all(P >= 0)
+
+
+def test_unit_permittivity_leaves_the_line_of_sight(drt):
+    # eps_r = 1: every reflection coefficient is 0, so K = 2 gives exactly the K = 0 field
+    rng = np.random.default_rng(12)
+    sc = scenes.random_small_scene(rng, 10, 70, 2, 60.0, "hard_sigmoid", boundary=True)
+    E2, P2 = _gpu(drt, sc.walls, sc.tx, sc.rx, 2, 60.0, "hard_sigmoid", 0.03, 1.0)
+    E0, P0 = _gpu(drt, sc.walls, sc.tx, sc.rx, 0, 60.0, "hard_sigmoid", 0.03, 1.0)
+    np.testing.assert_array_equal(E2, E0)
+    np.testing.assert_array_equal(P2, P0)
+
+
+def test_tile_shapes_agree_up_to_sum_order(drt, oracle_mod):
+    rng = np.random.default_rng(13)
+    sc = scenes.random_small_scene(rng, 10, 90, 2, 60.0, "sigmoid", boundary=True)
+    base, _ = _gpu(drt, sc.walls, sc.tx, sc.rx, 2, 60.0, "sigmoid", 0.05, 4.0)
+    for kw in (dict(warps_per_cta=1, cands_per_unit=1), dict(warps_per_cta=8, cands_per_unit=1000)):
+        E, P = _gpu(drt, sc.walls, sc.tx, sc.rx, 2, 60.0, "sigmoid", 0.05, 4.0,
+                    tile=drt.TileConfig(**kw))
+        _check(oracle_mod, E, P, sc.walls, sc.tx, sc.rx, 2, 60.0, "sigmoid", 0.05, 4.0)
+        assert np.max(np.abs(E - base)) <= 1e-5 * np.max(np.abs(base))
+
+
+def test_empty_receiver_set(drt):
+    sc = scenes.tiny_scene(alpha=100.0, smoothing="hard_sigmoid")
+    E, P = _gpu(drt, sc.walls, sc.tx, np.zeros((0, 2), np.float32), 1, 100.0, "hard_sigmoid",
+                0.05, 5.0)
+    assert E.shape == (0,) and P.shape == (0,)

@@ -33,6 +33,9 @@ def test_line_of_sight_is_a_spherical_wave(oracle_mod):
             E = _E(oracle_mod, walls, tx, rx, 0, alpha, fn, lam, 5.0)
             np.testing.assert_allclose(E, np.exp(-2j * np.pi * d / lam) / d, rtol=1e-13)
             np.testing.assert_allclose(np.abs(E) ** 2, 1.0 / d ** 2, rtol=1e-13)
+    E, mag, lmax = oracle_mod.field(walls, tx, rx, 0, 1.0, "step", 0.05, 5.0, GAMMA, scales=True)
+    np.testing.assert_allclose(mag, 1.0 / d, rtol=1e-13)
+    np.testing.assert_allclose(lmax, d, rtol=1e-13)
 
 
 @pytest.mark.parametrize("eps", [2.0, 15.0, 81.0])
