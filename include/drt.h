@@ -128,8 +128,9 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
    field: [n_rx][2] device (re, im; 8-byte aligned), overwritten.
    power: [n_rx] device receiving |E_r|^2, or NULL.
    workspace: device scratch of at least drt_field_workspace_size bytes.
-   tile: as for drt_forward (always one receiver per lane; DRT_TILE_SINGLE_RX is
-   implied).  Enqueued on `stream`; never synchronises. */
+   tile: as for drt_forward, including two receivers per lane for the hard
+   sigmoid and the sigmoid at alpha <= 1e4 unless DRT_TILE_SINGLE_RX is set.
+   Enqueued on `stream`; never synchronises. */
 drt_status drt_field_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes);
 drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelength, float eps_r,
                      float* field, float* power, void* workspace, size_t workspace_bytes,

@@ -32,6 +32,7 @@ def main() -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--wavelength", type=float, default=0.02)
     ap.add_argument("--eps-r", type=float, default=5.0)
+    ap.add_argument("--single-rx", action="store_true", help="one receiver per lane")
     args = ap.parse_args()
     dev = torch.device("cuda:0")
     if args.op == "mlp":
@@ -56,11 +57,12 @@ def main() -> int:
     g = torch.full((r.shape[0],), 1.0 / r.shape[0], device=dev)
 
     def run():
+        tile = ops.TileConfig(single_rx=True) if args.single_rx else None
         if args.op == "forward":
-            return ops.forward(w, t, r, sc.max_order, args.alpha, args.smoothing)
+            return ops.forward(w, t, r, sc.max_order, args.alpha, args.smoothing, tile=tile)
         if args.op == "field":
             return ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
-                             args.eps_r)
+                             args.eps_r, tile=tile)
         return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g)
 
     for _ in range(2):
@@ -73,6 +75,7 @@ def main() -> int:
     b.record()
     torch.cuda.synchronize(dev)
     res = {"op": args.op, "scene": args.scene, "smoothing": args.smoothing, "alpha": args.alpha,
+           "single_rx": args.single_rx,
            "n_rx": int(r.shape[0]), "ms": a.elapsed_time(b) / args.reps,
            "evals_per_s": int(r.shape[0]) * ops.num_candidates(sc.walls.shape[0], sc.max_order)
            / (a.elapsed_time(b) / args.reps / 1e3)}

@@ -132,7 +132,7 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   if (chunk > (1LL << 30)) chunk = 1LL << 30;
   d->chunk = (int)chunk;
   d->n_chunks = (d->n_cand + chunk - 1) / chunk;
-  d->pairs = (kern == FWD) &&
+  d->pairs = (kern != VJP) &&
              forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0);
   d->n_tiles = d->pairs ? (R + 63) / 64 : (R + 31) / 32;
   d->n_units = d->n_tiles * d->n_chunks;
@@ -140,7 +140,7 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   if (per_sm == 0) {
     const int mode = sc->smoothing;
     cudaError_t e = (kern == FWD)     ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
-                    : (kern == FIELD) ? field_occupancy(mode, d->threads, W, &per_sm)
+                    : (kern == FIELD) ? field_occupancy(mode, d->pairs, d->threads, W, &per_sm)
                                       : vjp_occupancy(mode, true, d->threads, W, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
@@ -282,8 +282,9 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
   a.tx = scene->tx;
   a.K = scene->max_order;
   a.alpha = scene->alpha;
+  // eps_r = 1: the Fresnel coefficient is 0 at every angle; pass it as that constant
   a.refl_amp = eps_r == 0.f ? -(float)std::sqrt((double)scene->refl_coef) : 0.f;
-  a.eps_r = eps_r;
+  a.eps_r = eps_r == 1.f ? 0.f : eps_r;
   const double inv = 1.0 / (double)wavelength;
   a.inv_lambda_hi = (float)inv;
   a.inv_lambda_lo = (float)(inv - (double)a.inv_lambda_hi);
@@ -293,6 +294,7 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
   a.n_tiles = d.n_tiles;
   a.n_units = d.n_units;
   a.cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  a.pairs = d.pairs;
   a.partial = static_cast<float2*>(workspace);
   a.field = reinterpret_cast<float2*>(field);
   a.power = power;

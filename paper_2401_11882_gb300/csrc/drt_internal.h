@@ -40,8 +40,8 @@ struct FwdArgs {
   float* power;     // [R]
 };
 
-// Coherent field (drt_field.cu): the forward's decomposition with one receiver
-// per lane and (re, im) partial sums.
+// Coherent field (drt_field.cu): the forward's decomposition (one or two
+// receivers per lane) with (re, im) partial sums.
 struct FieldArgs {
   const float4* walls;
   int W;
@@ -51,13 +51,14 @@ struct FieldArgs {
   int K;
   float alpha;
   float refl_amp;        // constant amplitude coefficient per reflection (eps_r == 0)
-  float eps_r;           // > 0: Fresnel TE coefficient of this relative permittivity
+  float eps_r;           // > 1: Fresnel TE coefficient of this relative permittivity; 0: refl_amp
   float inv_lambda_hi;   // 1/lambda = hi + lo
   float inv_lambda_lo;
   long long n_cand;
   int chunk;
   long long n_chunks, n_tiles, n_units;
   int cull;
+  bool pairs;        // two receivers per lane (n_tiles counts 64-receiver tiles)
   float2* partial;   // [n_chunks][R]
   float2* field;     // [R]
   float* power;      // [R] or null
@@ -102,7 +103,7 @@ cudaError_t launch_loss_backward(const int32_t* argmin, const float* grad_loss, 
                                  float* grad_power, cudaStream_t st);
 
 cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st);
-cudaError_t field_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t field_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);
 cudaError_t field_set_smem_limit(int W);
 
 size_t vjp_smem_bytes(int W, bool wall_grad);
