@@ -19,6 +19,8 @@ Functions and the passages they follow:
 * ``paths``             per-candidate vertices, validity, visibility, length and power for one receiver
 * ``candidates``        the candidate table of Sec. V (no wall twice in a row)
 * ``field``           Eq. 7 read as a coherent sum of path fields (Fresnel TE reflection)
+* ``field_jvp``, ``field_gradient``  its exact forward-mode derivative, and the gradient of
+                        sum_r g_r |E_r|^2
 * ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
                         finders' convergence check compares with zero (``oracle/mpt.py``)
 
@@ -77,6 +79,7 @@ def _load():
         lib.drt_oracle_power_cstep.argtypes = [p, i, p, p, i, i, d, i, d, p, p, d, i, p]
         lib.drt_oracle_paths.argtypes = [p, i, p, p, i, d, i, d, p, p, p, p, p, p]
         lib.drt_oracle_field.argtypes = [p, i, p, p, i, i, d, i, d, d, d, i, p, p, p]
+        lib.drt_oracle_field_jvp.argtypes = [p, i, p, p, i, i, d, i, d, d, d, p, p, i, p, p]
         _lib = lib
         return lib
 
@@ -220,6 +223,52 @@ def field(walls, tx, rx, max_order: int, alpha: float, smoothing, wavelength: fl
         raise ValueError("oracle rejected the arguments")
     E = out[0::2] + 1j * out[1::2]
     return (E, mag, lmax) if scales else E
+
+
+def field_jvp(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, dwalls, dtx,
+              refl_coef=0.5, threads=None):
+    """(E, dE) complex128 [R]: the coherent field and its derivative along (dwalls, dtx)."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    dwalls, dtx = _f64(dwalls).reshape(walls.shape), _f64(dtx).reshape(2)
+    R = rx.shape[0]
+    E = np.zeros(2 * R)
+    dE = np.zeros(2 * R)
+    rc = _load().drt_oracle_field_jvp(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx), R,
+                                      int(max_order), float(alpha), _kind(smoothing),
+                                      float(refl_coef), float(wavelength), float(eps_r),
+                                      _ptr(dwalls), _ptr(dtx), _threads(threads), _ptr(E),
+                                      _ptr(dE))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return E[0::2] + 1j * E[1::2], dE[0::2] + 1j * dE[1::2]
+
+
+def field_gradient(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, g,
+                   params="all", refl_coef=0.5, threads=None):
+    """sum_r g_r d|E_r|^2 / dtheta (= sum_r g_r 2 Re(conj(E_r) dE_r)); ``params`` as
+    for ``gradient``."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    g = _f64(g).reshape(-1)
+    nz = np.nonzero(g)[0]
+    rx_nz, g_nz = rx[nz], g[nz]
+    W = walls.shape[0]
+    if isinstance(params, str):
+        idx = list(range(2)) if params == "tx" else list(range(2 + 4 * W))
+    else:
+        idx = list(params)
+    out = np.zeros(len(idx))
+    for n, p in enumerate(idx):
+        dtx = np.zeros(2); dw = np.zeros(4 * W)
+        if p < 2:
+            dtx[p] = 1.0
+        else:
+            dw[p - 2] = 1.0
+        if rx_nz.shape[0] == 0:
+            continue
+        E, dE = field_jvp(walls, tx, rx_nz, max_order, alpha, smoothing, wavelength, eps_r, dw,
+                          dtx, refl_coef, threads)
+        out[n] = float(np.dot(g_nz, 2.0 * (E.real * dE.real + E.imag * dE.imag)))
+    return out
 
 
 def loss(P) -> tuple[float, int]:

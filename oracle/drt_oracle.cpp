@@ -73,6 +73,8 @@ inline Dual operator/(double a, Dual b) { return Dual(a) / b; }
 inline Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
 inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, a.d * e); }
 inline Dual sqrt(Dual a) { double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
+inline Dual cos(Dual a) { return Dual(std::cos(a.v), -a.d * std::sin(a.v)); }
+inline Dual sin(Dual a) { return Dual(std::sin(a.v), a.d * std::cos(a.v)); }
 
 typedef std::complex<double> Cplx;
 
@@ -80,7 +82,9 @@ inline double re(double x) { return x; }
 inline double re(const Dual& x) { return x.v; }
 inline double re(const Cplx& x) { return x.real(); }
 
+using std::cos;
 using std::exp;
+using std::sin;
 using std::sqrt;
 
 // ---------------------------------------------------------------- smoothing
@@ -329,9 +333,10 @@ T path_power(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& 
 // (TE): (c - sqrt(eps - s^2)) / (c + sqrt(eps - s^2)), with c the cosine of the
 // angle of incidence, s^2 = 1 - c^2 and eps the wall's relative permittivity.  At
 // eps = 1 the coefficient is 0 for every c > 0; c = 0 (grazing) keeps that value.
-double fresnel_te(double c, double eps) {
-  const double r = std::sqrt(eps - (1.0 - c * c));
-  if (c + r == 0.0) return 0.0;
+template <class T>
+T fresnel_te(const T& c, double eps) {
+  const T r = sqrt(eps - (1.0 - c * c));
+  if (re(c) + re(r) == 0.0) return T(0.0);
   return (c - r) / (c + r);
 }
 
@@ -340,17 +345,19 @@ double fresnel_te(double c, double eps) {
 //   prod_j C_j * V * vis * exp(-i 2 pi L / lambda) / L,
 // with C_j the Fresnel TE coefficient at reflection j (eps > 0), or the constant
 // amplitude -sqrt(Gamma) (eps == 0), whose square is the power coefficient Gamma.
-Cplx path_field(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
-                const Vec<double>& rx, const std::vector<int>& seq, const Params& P,
-                double wavelength, double eps, double* length) {
-  PathTerms<double> t = path_terms(walls, tx, rx, seq, P, nullptr);
-  *length = t.degenerate ? 0.0 : t.L;
-  if (t.degenerate) return Cplx(0.0, 0.0);
-  double coef = 1.0;
-  for (double c : t.cos_in) coef *= (eps > 0.0) ? fresnel_te(c, eps) : -std::sqrt(P.gamma);
-  const double amp = coef * t.validity * t.visibility / t.L;
-  const double phase = 2.0 * M_PI * t.L / wavelength;
-  return Cplx(amp * std::cos(phase), -amp * std::sin(phase));
+// Returned as (re, im).
+template <class T>
+Vec<T> path_field(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec<T>& rx,
+                  const std::vector<int>& seq, const Params& P, double wavelength, double eps,
+                  double* length) {
+  PathTerms<T> t = path_terms(walls, tx, rx, seq, P, nullptr);
+  *length = t.degenerate ? 0.0 : re(t.L);
+  if (t.degenerate) return Vec<T>{T(0.0), T(0.0)};
+  T coef = T(1.0);
+  for (const T& c : t.cos_in) coef = coef * ((eps > 0.0) ? fresnel_te(c, eps) : T(-std::sqrt(P.gamma)));
+  const T amp = coef * t.validity * t.visibility / t.L;
+  const T phase = (2.0 * M_PI / wavelength) * t.L;
+  return Vec<T>{amp * cos(phase), -(amp * sin(phase))};
 }
 
 template <class T>
@@ -498,19 +505,54 @@ int drt_oracle_field(const double* walls_xy, int W, const double* tx, const doub
 #pragma omp parallel for schedule(dynamic, 1)
   for (int r = 0; r < R; ++r) {
     Vec<double> q{rx[2 * r], rx[2 * r + 1]};
-    Cplx sum(0.0, 0.0);
+    double sre = 0.0, sim = 0.0;
     double m = 0.0, lm = 0.0;
     for (const auto& seq : cands) {
       double len = 0.0;
-      const Cplx f = path_field(walls, t, q, seq, prm, wavelength, eps, &len);
-      sum += f;
-      m += std::abs(f);
-      if (std::abs(f) > 0.0 && len > lm) lm = len;
+      const Vec<double> f = path_field(walls, t, q, seq, prm, wavelength, eps, &len);
+      sre += f.x;
+      sim += f.y;
+      const double af = std::hypot(f.x, f.y);
+      m += af;
+      if (af > 0.0 && len > lm) lm = len;
     }
-    E[2 * r] = sum.real();
-    E[2 * r + 1] = sum.imag();
+    E[2 * r] = sre;
+    E[2 * r + 1] = sim;
     if (mag) mag[r] = m;
     if (lmax) lmax[r] = lm;
+  }
+  return 0;
+}
+
+// Forward-mode derivative of the coherent field along (dwalls [W][4], dtx [2]):
+// E and dE (re, im interleaved) for every receiver.
+int drt_oracle_field_jvp(const double* walls_xy, int W, const double* tx, const double* rx,
+                         int R, int K, double alpha, int kind, double gamma, double wavelength,
+                         double eps, const double* dwalls, const double* dtx, int nthreads,
+                         double* E, double* dE) {
+  if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind) || !dwalls || !dtx) return 1;
+  if (!(wavelength > 0.0) || !(eps == 0.0 || eps >= 1.0) || !(gamma >= 0.0)) return 1;
+  set_threads(nthreads);
+  std::vector<Dual> xy(4 * W);
+  for (int i = 0; i < 4 * W; ++i) xy[i] = Dual(walls_xy[i], dwalls[i]);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<Dual> t{Dual(tx[0], dtx[0]), Dual(tx[1], dtx[1])};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    Vec<Dual> q{Dual(rx[2 * r]), Dual(rx[2 * r + 1])};
+    Dual sre(0.0), sim(0.0);
+    for (const auto& seq : cands) {
+      double len = 0.0;
+      const Vec<Dual> f = path_field(walls, t, q, seq, prm, wavelength, eps, &len);
+      sre = sre + f.x;
+      sim = sim + f.y;
+    }
+    E[2 * r] = sre.v;
+    E[2 * r + 1] = sim.v;
+    dE[2 * r] = sre.d;
+    dE[2 * r + 1] = sim.d;
   }
   return 0;
 }

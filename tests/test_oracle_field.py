@@ -107,3 +107,56 @@ def test_reciprocity_in_the_hard_limit(oracle_mod, eps):
         a = _E(oracle_mod, walls, tx, rx[r], 2, 1.0, "step", 0.02, eps)[0]
         b = _E(oracle_mod, walls, rx[r], tx, 2, 1.0, "step", 0.02, eps)[0]
         assert abs(a - b) <= 1e-12 * max(abs(a), 1e-300)
+
+
+def _two_ray_power_cs(tx, ground_y, rx, lam, eps):
+    """|E|^2 of the two-ray model as a real-analytic expression of (tx, ground height),
+    so complex-step differentiation applies (no abs, no conjugate)."""
+    ht, hr = tx[1] - ground_y, rx[1] - ground_y
+    dx = rx[0] - tx[0]
+    d0 = np.sqrt(dx * dx + (ht - hr) ** 2)
+    d1 = np.sqrt(dx * dx + (ht + hr) ** 2)
+    c = (ht + hr) / d1
+    root = np.sqrt(eps - 1.0 + c * c)
+    gam = (c - root) / (c + root)
+    k = 2 * np.pi / lam
+    re = np.cos(k * d0) / d0 + gam * np.cos(k * d1) / d1
+    im = -np.sin(k * d0) / d0 - gam * np.sin(k * d1) / d1
+    return re * re + im * im
+
+
+@pytest.mark.parametrize("eps", [2.0, 15.0])
+def test_field_gradient_of_the_two_ray_model(oracle_mod, eps):
+    # d|E|^2 / d(TX x, TX y, ground height) against complex-step derivatives of the
+    # closed form (an independent expression of the same model)
+    tx = np.array([0.1, 0.3])
+    rx = np.array([[0.9, 0.25]])
+    lam, gy = 0.05, 0.0
+    ground = np.array([[-50.0, gy, 50.0, gy]])
+    g = np.array([1.0])
+    # parameters: TX x, TX y, and the wall's two y coordinates (flat indices 2 + 1, 2 + 3)
+    got = oracle_mod.field_gradient(ground, tx, rx, 1, 1.0, "step", lam, eps, g, [0, 1, 3, 5],
+                                    GAMMA)
+    h = 1e-30
+    ref_tx = [_two_ray_power_cs(tx + 1j * h * e, gy, rx[0], lam, eps).imag / h
+              for e in np.eye(2)]
+    ref_gy = _two_ray_power_cs(tx, gy + 1j * h, rx[0], lam, eps).imag / h
+    np.testing.assert_allclose(got[:2], ref_tx, rtol=1e-9)
+    assert got[2] + got[3] == pytest.approx(ref_gy, rel=1e-9)
+
+
+@pytest.mark.parametrize("fn,alpha", [("sigmoid", 30.0), ("hard_sigmoid", 40.0)])
+@pytest.mark.parametrize("eps", [0.0, 4.0])
+def test_field_jvp_equals_central_differences(oracle_mod, fn, alpha, eps):
+    walls, tx, rx = _scene(8, 4, 3)
+    lam = 0.06
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        dw = rng.normal(size=walls.shape)
+        dtx = rng.normal(size=2)
+        E, dE = oracle_mod.field_jvp(walls, tx, rx, 2, alpha, fn, lam, eps, dw, dtx, GAMMA)
+        h = 1e-6
+        Ep = oracle_mod.field(walls + h * dw, tx + h * dtx, rx, 2, alpha, fn, lam, eps, GAMMA)
+        Em = oracle_mod.field(walls - h * dw, tx - h * dtx, rx, 2, alpha, fn, lam, eps, GAMMA)
+        fd = (Ep - Em) / (2 * h)
+        np.testing.assert_allclose(dE, fd, rtol=2e-5, atol=2e-5 * np.abs(fd).max())

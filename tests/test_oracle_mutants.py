@@ -52,16 +52,20 @@ MUTANTS = {
     "dual quotient rule": ("(a.d * b.v - a.v * b.d) / (b.v * b.v)",
                            "(a.d * b.v + a.v * b.d) / (b.v * b.v)"),
     "dual exp": ("return Dual(e, a.d * e);", "return Dual(e, a.d);"),
-    "field phase sign": ("return Cplx(amp * std::cos(phase), -amp * std::sin(phase));",
-                         "return Cplx(amp * std::cos(phase), amp * std::sin(phase));"),
-    "field wavelength factor": ("const double phase = 2.0 * M_PI * t.L / wavelength;",
-                                "const double phase = M_PI * t.L / wavelength;"),
-    "field spreading squared": ("const double amp = coef * t.validity * t.visibility / t.L;",
-                                "const double amp = coef * t.validity * t.visibility / (t.L * t.L);"),
+    "field phase sign": ("return Vec<T>{amp * cos(phase), -(amp * sin(phase))};",
+                         "return Vec<T>{amp * cos(phase), amp * sin(phase)};"),
+    "field wavelength factor": ("const T phase = (2.0 * M_PI / wavelength) * t.L;",
+                                "const T phase = (M_PI / wavelength) * t.L;"),
+    "field spreading squared": ("const T amp = coef * t.validity * t.visibility / t.L;",
+                                "const T amp = coef * t.validity * t.visibility / (t.L * t.L);"),
     "fresnel numerator sign": ("return (c - r) / (c + r);", "return (r - c) / (c + r);"),
-    "fresnel sine for cosine": ("const double r = std::sqrt(eps - (1.0 - c * c));",
-                                "const double r = std::sqrt(eps - c * c);"),
-    "constant coefficient sign": (": -std::sqrt(P.gamma);", ": std::sqrt(P.gamma);"),
+    "fresnel sine for cosine": ("const T r = sqrt(eps - (1.0 - c * c));",
+                                "const T r = sqrt(eps - c * c);"),
+    "constant coefficient sign": ("T(-std::sqrt(P.gamma))", "T(std::sqrt(P.gamma))"),
+    "dual cosine derivative": ("return Dual(std::cos(a.v), -a.d * std::sin(a.v));",
+                               "return Dual(std::cos(a.v), a.d * std::sin(a.v));"),
+    "dual sine derivative": ("return Dual(std::sin(a.v), a.d * std::cos(a.v));",
+                             "return Dual(std::sin(a.v), a.d * std::sin(a.v));"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
