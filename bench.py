@@ -380,6 +380,12 @@ def measure_extras(drt, dev, sc, w, t, r):
     sv = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", gp), 2)
     sfs = timed(lambda: drt.forward(gw, gt, gr, 2, 100.0, "sigmoid"), 1)
     svs = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "sigmoid", gp), 1)
+    # coherent field and its adjoint (lambda 0.02, eps_r 5) on the same scene
+    fE, _ = drt.field(gw, gt, gr, 2, 100.0, "hard_sigmoid", 0.02, 5.0)
+    ffh = timed(lambda: drt.field(gw, gt, gr, 2, 100.0, "hard_sigmoid", 0.02, 5.0), 2)
+    fvh = timed(lambda: drt.field_vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", 0.02, 5.0, fE, gp), 2)
+    fEs, _ = drt.field(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0)
+    fvs = timed(lambda: drt.field_vjp(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0, fEs, gp), 1)
     # batched descent on the first 64 scenes of the 4096-scene batch (4 starts each)
     from paper_2401_11882_gb300.batched import BatchedDescent
     full = scenes.scene_batch(64, 0)
@@ -421,7 +427,9 @@ def measure_extras(drt, dev, sc, w, t, r):
         "fwd_ms": sf * 1e3, "vjp_ms": sv * 1e3,
         "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sf + sv),
         "sigmoid": {"fwd_ms": sfs * 1e3, "vjp_ms": svs * 1e3,
-                    "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sfs + svs)}}
+                    "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sfs + svs)},
+        "coherent_field": {"wavelength": 0.02, "eps_r": 5.0, "hard_fwd_ms": ffh * 1e3,
+                           "hard_vjp_ms": fvh * 1e3, "sigmoid_vjp_ms": fvs * 1e3}}
     return out
 
 

@@ -136,6 +136,23 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
                      float* field, float* power, void* workspace, size_t workspace_bytes,
                      void* stream);
 
+/* Vector-Jacobian product of drt_field's power: grad_power^T d|E|^2 / d(tx, walls)
+   = sum_r grad_power[r] 2 Re(conj(E_r) dE_r / d(tx, walls)) (reverse mode through
+   the path fields' amplitude, phase, Fresnel coefficients and the geometry; the
+   geometry is recomputed, nothing is stored).
+   field: [n_rx][2] device, the E drt_field returned for the same scene, wavelength
+   and eps_r (8-byte aligned).  grad_power: [n_rx] device.
+   grad_tx: [2] device, overwritten.  grad_walls: [n_walls][4] device (16-byte
+   aligned), overwritten, or NULL to skip the wall gradient.
+   workspace: at least drt_field_vjp_workspace_size bytes, 16-byte aligned.
+   Arguments and errors as for drt_field and drt_vjp. */
+drt_status drt_field_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                        size_t* bytes);
+drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                         float eps_r, const float* field, const float* grad_power,
+                         float* grad_tx, float* grad_walls, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
 /* Autotuner probe for drt_forward (the work decomposition does not change the
    result beyond the order of the per-chunk sums): runs drt_forward on `scene`
    with each of the n_cand tiles of `cands` (host array), one untimed launch

@@ -7,13 +7,16 @@ Public calls (PyTorch tensors on a CUDA device, float32):
 * ``loss(power)``: -min over receivers; ``objective(...)`` = loss(power(...)).
 * ``forward``, ``vjp``, ``min_loss``: the raw C-ABI calls.
 * ``field(...)``: the coherent reading of Eq. 7 (complex path fields, Fresnel
-  reflection), field and power per receiver.
+  reflection), field and power per receiver; ``field_power(...)`` is its power
+  |E|^2, differentiable in ``walls`` and ``tx``; ``field_vjp`` the raw adjoint.
 
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
-from .ops import (TileConfig, field, forward, loss, min_loss, min_loss_backward, min_loss_vjp,
-                  num_candidates, objective, objective_host, power, vjp)
+from .ops import (TileConfig, field, field_power, field_vjp, forward, loss, min_loss,
+                  min_loss_backward, min_loss_vjp, num_candidates, objective, objective_host,
+                  power, vjp)
 
-__all__ = ["TileConfig", "field", "forward", "loss", "min_loss", "min_loss_backward",
-           "min_loss_vjp", "num_candidates", "objective", "objective_host", "power", "vjp"]
+__all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "loss", "min_loss",
+           "min_loss_backward", "min_loss_vjp", "num_candidates", "objective", "objective_host",
+           "power", "vjp"]

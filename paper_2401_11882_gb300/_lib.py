@@ -72,6 +72,9 @@ SIGNATURES = {
     "drt_tune_forward": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P, _SZ, _P, _P, _P]),
     "drt_field_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_field": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _SZ, _P]),
+    "drt_field_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt_field_vjp": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P, _P,
+                                     _SZ, _P]),
     "drt_loss": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "drt_loss_backward": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "drt_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),

@@ -5,6 +5,7 @@ a profiler can capture a chosen launch of it (e.g. ``ncu -k regex:vjp_kernel -s 
     forward   drt.forward on the scene
     vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
     field     drt.field (coherent field, Fresnel TE, --eps-r, --wavelength)
+    field_vjp drt.field_vjp with dense g = 1/R (after one drt.field)
     mlp       the surrogate MLP's inference on --batch random points
 
 Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload)
@@ -23,7 +24,7 @@ from . import ops, scenes
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["forward", "vjp", "mlp", "field"])
+    ap.add_argument("op", choices=["forward", "vjp", "mlp", "field", "field_vjp"])
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--scene", choices=["gradient", "large"], default="gradient")
     ap.add_argument("--smoothing", default="sigmoid", choices=["hard_sigmoid", "sigmoid", "step"])
@@ -55,6 +56,10 @@ def main() -> int:
     rx = scenes.rx_grid(args.rx_grid)
     w, t, r = (torch.tensor(x, device=dev) for x in (sc.walls, sc.tx, rx))
     g = torch.full((r.shape[0],), 1.0 / r.shape[0], device=dev)
+    E = None
+    if args.op == "field_vjp":
+        E, _ = ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
+                         args.eps_r)
 
     def run():
         tile = ops.TileConfig(single_rx=True) if args.single_rx else None
@@ -63,6 +68,9 @@ def main() -> int:
         if args.op == "field":
             return ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
                              args.eps_r, tile=tile)
+        if args.op == "field_vjp":
+            return ops.field_vjp(w, t, r, sc.max_order, args.alpha, args.smoothing,
+                                 args.wavelength, args.eps_r, E, g)
         return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g)
 
     for _ in range(2):
@@ -79,7 +87,7 @@ def main() -> int:
            "n_rx": int(r.shape[0]), "ms": a.elapsed_time(b) / args.reps,
            "evals_per_s": int(r.shape[0]) * ops.num_candidates(sc.walls.shape[0], sc.max_order)
            / (a.elapsed_time(b) / args.reps / 1e3)}
-    if args.op == "vjp":
+    if args.op in ("vjp", "field_vjp"):
         res["grad_tx"] = out[0].tolist()
     print(json.dumps(res), flush=True)
     return 0

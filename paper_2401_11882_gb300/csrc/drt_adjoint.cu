@@ -81,6 +81,73 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
   }
 }
 
+// Adjoint of the coherent field's power |E_r|^2 with cotangent g_r: the same
+// mapping as vjp_kernel, each lane weighing its paths' fields by w = 2 g_r conj(E_r)
+// (E_r from drt_field, one load per unit).
+template <int MODE, bool WG>
+__global__ void __launch_bounds__(256, WG ? 2 : 1) field_vjp_kernel(const VjpArgs a) {
+  extern __shared__ float4 smem[];
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  VSmem s;
+  s.G = smem;
+  s.E = smem + a.W;
+  s.T = smem + 2 * a.W;
+  s.H = smem + 3 * a.W;
+  s.acc = reinterpret_cast<float*>(smem + 4 * a.W);
+  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, SmemWalls{s.G, s.E, s.T, s.H});
+  if (WG)
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) s.acc[i] = 0.f;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  FieldW fw;
+  fw.inv_lambda_hi = a.inv_lambda_hi;
+  fw.inv_lambda_lo = a.inv_lambda_lo;
+  fw.k2pi = a.k2pi;
+  fw.eps_r = a.eps_r;
+  fw.refl_amp = a.refl_amp;
+  float txb_x = 0.f, txb_y = 0.f;
+  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    long long r = tile * 32 + lane;
+    const bool live = r < a.R;
+    if (!live) r = a.R - 1;
+    const float gp = live ? __ldg(a.grad_power + r) : 0.f;
+    const float2 E = __ldg(a.field + r);
+    fw.wre = 2.f * gp * E.x;
+    fw.wim = -2.f * gp * E.y;
+    const float g = (fw.wre != 0.f || fw.wim != 0.f) ? 1.f : 0.f;
+    if (__all_sync(FULL, g == 0.f)) continue;
+    const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
+    const long long c0 = chunk * a.chunk;
+    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+    for (long long c = c0; c < c1; ++c) {
+      const Cand cd = decode_candidate(c, a.W, a.K);
+      switch (cd.k) {
+        case 0: path_vjp<MODE, 0, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
+        case 1: path_vjp<MODE, 1, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
+        case 2: path_vjp<MODE, 2, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
+        default: path_vjp<MODE, 3, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
+      }
+    }
+  }
+  txb_x = warp_sum(txb_x);
+  txb_y = warp_sum(txb_y);
+  if (lane == 0) {
+    a.warp_tx[2 * gwarp] = txb_x;
+    a.warp_tx[2 * gwarp + 1] = txb_y;
+  }
+  if (WG) {
+    __syncthreads();
+    float* out = a.cta_walls + (size_t)blockIdx.x * a.W * VJP_SLOTS;
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) out[i] = s.acc[i];
+  }
+}
+
 // Adjoint of the min-power loss: loss = -P[argmin], so the gradient is
 // -grad_loss * dP[argmin]/d(tx, walls) for one receiver.  Here the lanes of a
 // warp hold 32 consecutive candidates of that receiver (one unit = 32
@@ -249,6 +316,43 @@ cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaSt
   return cudaGetLastError();
 }
 
+cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
+  const bool wg = a.grad_walls != nullptr;
+  const size_t smem = vjp_smem_bytes(a.W, wg);
+  switch (mode * 2 + (wg ? 1 : 0)) {
+    case MODE_SIGMOID * 2: field_vjp_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a); break;
+    case MODE_SIGMOID * 2 + 1: field_vjp_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a); break;
+    case MODE_HARD * 2: field_vjp_kernel<MODE_HARD, false><<<ctas, threads, smem, st>>>(a); break;
+    case MODE_HARD * 2 + 1: field_vjp_kernel<MODE_HARD, true><<<ctas, threads, smem, st>>>(a); break;
+    case MODE_STEP * 2: field_vjp_kernel<MODE_STEP, false><<<ctas, threads, smem, st>>>(a); break;
+    default: field_vjp_kernel<MODE_STEP, true><<<ctas, threads, smem, st>>>(a); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_warps = ctas * (threads / 32);
+  const int fb = wg ? (a.W + 255) / 256 : 1;
+  vjp_finalize_kernel<<<fb, 256, 0, st>>>(a, ctas, n_warps, wg ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t field_vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = vjp_smem_bytes(W, wg);
+  switch (mode * 2 + (wg ? 1 : 0)) {
+    case MODE_SIGMOID * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_SIGMOID, false>, threads, smem);
+    case MODE_SIGMOID * 2 + 1:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_SIGMOID, true>, threads, smem);
+    case MODE_HARD * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_HARD, false>, threads, smem);
+    case MODE_HARD * 2 + 1:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_HARD, true>, threads, smem);
+    case MODE_STEP * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_STEP, false>, threads, smem);
+    default:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_STEP, true>, threads, smem);
+  }
+}
+
 cudaError_t vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas_per_sm) {
   const size_t smem = vjp_smem_bytes(W, wg);
   switch (mode * 2 + (wg ? 1 : 0)) {
@@ -274,6 +378,8 @@ cudaError_t vjp_set_smem_limit(int W) {
   e = cudaFuncSetAttribute(vjp_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
   if (e != cudaSuccess) return e;                                                           \
   e = cudaFuncSetAttribute(vjp_rx_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
+  if (e != cudaSuccess) return e;                                                           \
+  e = cudaFuncSetAttribute(field_vjp_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
   if (e != cudaSuccess) return e;
   DRT_SET(MODE_SIGMOID, false, s0)
   DRT_SET(MODE_SIGMOID, true, s1)

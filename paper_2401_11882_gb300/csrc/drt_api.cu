@@ -113,7 +113,7 @@ drt_status check_tile(const drt_tile* t) {
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
 
-enum Kernel { FWD, VJP, FIELD };
+enum Kernel { FWD, VJP, FIELD, FIELD_VJP };
 
 drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
   int sms = 0;
@@ -125,29 +125,30 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   d->threads = warps * 32;
   d->n_cand = num_candidates(W, K);
   long long chunk = (t && t->cands_per_unit) ? t->cands_per_unit : 64;
-  if (kern != VJP && R > 0) {
+  if ((kern == FWD || kern == FIELD) && R > 0) {
     const long long max_chunks = std::max(1LL, MAX_PARTIALS / R);
     chunk = std::max(chunk, (d->n_cand + max_chunks - 1) / max_chunks);
   }
   if (chunk > (1LL << 30)) chunk = 1LL << 30;
   d->chunk = (int)chunk;
   d->n_chunks = (d->n_cand + chunk - 1) / chunk;
-  d->pairs = (kern != VJP) &&
+  d->pairs = (kern == FWD || kern == FIELD) &&
              forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0);
   d->n_tiles = d->pairs ? (R + 63) / 64 : (R + 31) / 32;
   d->n_units = d->n_tiles * d->n_chunks;
   int per_sm = (t && t->ctas_per_sm) ? t->ctas_per_sm : 0;
   if (per_sm == 0) {
     const int mode = sc->smoothing;
-    cudaError_t e = (kern == FWD)     ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
-                    : (kern == FIELD) ? field_occupancy(mode, d->pairs, d->threads, W, &per_sm)
-                                      : vjp_occupancy(mode, true, d->threads, W, &per_sm);
+    cudaError_t e = (kern == FWD)         ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
+                    : (kern == FIELD)     ? field_occupancy(mode, d->pairs, d->threads, W, &per_sm)
+                    : (kern == FIELD_VJP) ? field_vjp_occupancy(mode, true, d->threads, W, &per_sm)
+                                          : vjp_occupancy(mode, true, d->threads, W, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
   }
   long long ctas = (long long)sms * per_sm;
   const long long needed = (d->n_units + warps - 1) / warps;
-  if (kern != VJP) ctas = std::min(ctas, std::max(1LL, needed));
+  if (kern == FWD || kern == FIELD) ctas = std::min(ctas, std::max(1LL, needed));
   d->ctas = (int)std::max(1LL, ctas);
   return DRT_OK;
 }
@@ -409,7 +410,7 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
   if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
     return fail(DRT_ERR_WORKSPACE, "vjp needs %zu aligned workspace bytes, got %zu", need,
                 workspace_bytes);
-  VjpArgs a;
+  VjpArgs a{};
   a.rx_index = nullptr;
   a.grad_loss = nullptr;
   a.walls = reinterpret_cast<const float4*>(scene->walls);
@@ -437,6 +438,78 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
   return DRT_OK;
 }
 
+drt_status drt_field_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                        size_t* bytes) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(scene, tile, FIELD_VJP, &d)) != DRT_OK) return st;
+  *bytes = vjp_workspace(scene, d);
+  return DRT_OK;
+}
+
+drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                         float eps_r, const float* field, const float* grad_power,
+                         float* grad_tx, float* grad_walls, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!(wavelength > 0.f) || !std::isfinite(wavelength))
+    return fail(DRT_ERR_INVALID_ARG, "wavelength must be finite and > 0");
+  if (!(eps_r == 0.f || eps_r >= 1.f) || !std::isfinite(eps_r))
+    return fail(DRT_ERR_INVALID_ARG, "eps_r must be 0 (constant coefficient) or finite and >= 1");
+  if (eps_r == 0.f && !(scene->refl_coef >= 0.f))
+    return fail(DRT_ERR_INVALID_ARG, "refl_coef must be >= 0 for the constant coefficient");
+  if (!grad_tx || (scene->n_rx > 0 && (!grad_power || !field)))
+    return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  if (field && !aligned(field, 8)) return fail(DRT_ERR_INVALID_ARG, "field must be 8-byte aligned");
+  if (grad_walls && !aligned(grad_walls, 16))
+    return fail(DRT_ERR_INVALID_ARG, "grad_walls must be 16-byte aligned");
+  Decomp d;
+  if ((st = decompose(scene, tile, FIELD_VJP, &d)) != DRT_OK) return st;
+  const size_t need = vjp_workspace(scene, d);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
+    return fail(DRT_ERR_WORKSPACE, "field vjp needs %zu aligned workspace bytes, got %zu", need,
+                workspace_bytes);
+  VjpArgs a{};
+  a.rx_index = nullptr;
+  a.grad_loss = nullptr;
+  a.walls = reinterpret_cast<const float4*>(scene->walls);
+  a.W = scene->n_walls;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.grad_power = grad_power;
+  float* ws = static_cast<float*>(workspace);
+  a.cta_walls = ws;
+  a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.grad_tx = grad_tx;
+  a.grad_walls = grad_walls;
+  a.field = reinterpret_cast<const float2*>(field);
+  const double inv = 1.0 / (double)wavelength;
+  a.inv_lambda_hi = (float)inv;
+  a.inv_lambda_lo = (float)(inv - (double)a.inv_lambda_hi);
+  a.k2pi = (float)(2.0 * M_PI * inv);
+  // as in drt_field: eps_r = 1 is the zero coefficient
+  a.refl_amp = eps_r == 0.f ? -(float)std::sqrt((double)scene->refl_coef) : 0.f;
+  a.eps_r = eps_r == 1.f ? 0.f : eps_r;
+  cudaError_t e = launch_field_vjp(a, scene->smoothing, d.ctas, d.threads,
+                                   static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "field vjp launch");
+  return DRT_OK;
+}
+
 drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const int32_t* argmin,
                             const float* grad_loss, float* grad_tx, float* grad_walls,
                             void* workspace, size_t workspace_bytes, void* stream) {
@@ -453,7 +526,7 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
   if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
     return fail(DRT_ERR_WORKSPACE, "min-loss vjp needs %zu aligned workspace bytes, got %zu",
                 need, workspace_bytes);
-  VjpArgs a;
+  VjpArgs a{};
   a.walls = reinterpret_cast<const float4*>(scene->walls);
   a.W = scene->n_walls;
   a.rx = scene->rx;

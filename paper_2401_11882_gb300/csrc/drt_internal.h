@@ -83,6 +83,10 @@ struct VjpArgs {
   float* warp_tx;            // [ctas * warps_per_cta][2]
   float* grad_tx;            // [2]
   float* grad_walls;         // [W][4] or null
+  // coherent-field adjoint only (drt_field_vjp): the field E [R] from drt_field and
+  // the field's constants; grad_power then weighs |E_r|^2
+  const float2* field;
+  float inv_lambda_hi, inv_lambda_lo, k2pi, eps_r, refl_amp;
 };
 
 // number of float slots per wall in the adjoint's accumulators:
@@ -110,5 +114,7 @@ size_t vjp_smem_bytes(int W, bool wall_grad);
 cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t vjp_occupancy(int mode, bool wall_grad, int threads, int W, int* ctas_per_sm);
 cudaError_t vjp_set_smem_limit(int W);
+cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t field_vjp_occupancy(int mode, bool wall_grad, int threads, int W, int* ctas_per_sm);
 
 }  // namespace drt

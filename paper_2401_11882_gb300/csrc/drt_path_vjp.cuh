@@ -154,13 +154,27 @@ __device__ __forceinline__ LegWall leg_wall(float x1, float y1, float x2, float 
   return r;
 }
 
+// Coherent field (FIELD): this lane's weight w = 2 g conj(E) on the path fields
+// a = prod_j C_j V vis exp(-i 2 pi L / lambda) / L (the adjoint of |E|^2 with
+// cotangent g is Re(w da)), and the field's constants.
+struct FieldW {
+  float wre, wim;                        // w = wre + i wim
+  float inv_lambda_hi, inv_lambda_lo;    // 1 / lambda as a float pair
+  float k2pi;                            // 2 pi / lambda
+  float eps_r;                           // > 1: Fresnel TE; 0: the constant refl_amp
+  float refl_amp;
+};
+
 // UNI: the candidate is the same in all 32 lanes (lanes hold receivers), so the
 // adjoints of the reflecting walls can be summed over the warp; otherwise (lanes
 // hold different candidates of one receiver) each lane adds its own.
-template <int MODE, int K, bool WG, bool UNI>
+// FIELD: the adjoint of the coherent field's |E|^2 instead of the power (fw
+// holds the lane's weight; g is 1 or 0).
+template <int MODE, int K, bool WG, bool UNI, bool FIELD = false>
 __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float2 rx,
                                          const Cand& cd, float alpha, float gk, float g,
-                                         float& txb_x, float& txb_y) {
+                                         float& txb_x, float& txb_y,
+                                         const FieldW* fw = nullptr) {
   // ------------------------------------------------ forward recompute (guarded)
   float Ix[K + 1], Iy[K + 1], dimg[K + 1];
   Ix[0] = tx.x;
@@ -291,15 +305,63 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
   suf[NF] = 1.f;
 #pragma unroll
   for (int i = NF - 1; i >= 0; --i) suf[i] = suf[i + 1] * F[i];
-  const float C = __fdiv_rn(gk, L * L);
-  const float p = C * pre[NF];
-  const float gC = g * C;
+  float gC, Lb, p = 0.f;
+  float cosb[K + 1];   // FIELD: adjoints of the incidence cosines c_1..c_K
+  if constexpr (!FIELD) {
+    const float C = __fdiv_rn(gk, L * L);
+    p = C * pre[NF];
+    gC = g * C;
+  } else {
+    // a = A exp(-i phi), A = prod_j C_j(c_j) prod(F) / L, phi = 2 pi L / lambda:
+    // Re(w da) = A_bar dA + phi_bar dphi with A_bar = Re(w e^{-i phi}) and
+    // phi_bar = A Im(w e^{-i phi}).  c_j = |n_j . d| / |d| for the leg d arriving
+    // at reflection j; C_j the Fresnel TE coefficient, dC/dc = 2 (eps - 1) / (r (c + r)^2)
+    // with r = sqrt(eps - 1 + c^2), or the constant (dC/dc = 0).
+    float Cj[K + 1], dC[K + 1];
+    float Cf = 1.f;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const float4 G = s.G[cd.w[j - 1]];
+      const float dx = Qx[j] - Qx[j - 1], dy = Qy[j] - Qy[j - 1];
+      const float il = len[j - 1] > 0.f ? __frcp_rn(len[j - 1]) : 0.f;
+      const float c = fminf(fabsf(fmaf(G.x, dx, G.y * dy)) * il, 1.f);
+      Cj[j] = fw->refl_amp;
+      dC[j] = 0.f;
+      if (fw->eps_r > 0.f) {
+        const float x = fmaf(c, c, fw->eps_r - 1.f);
+        const float root = x > 0.f ? x * rsqrtf(x) : 0.f;
+        const float den = c + root;
+        Cj[j] = den > 0.f ? __fdividef(c - root, den) : 0.f;
+        dC[j] = root > 0.f ? __fdividef(2.f * (fw->eps_r - 1.f), root * den * den) : 0.f;
+      }
+      Cf *= Cj[j];
+    }
+    const float iL = __frcp_rn(L);
+    const float A = Cf * pre[NF] * iL;
+    const float cyc = L * fw->inv_lambda_hi;
+    const float cer = fmaf(L, fw->inv_lambda_hi, -cyc);
+    const float frac = (cyc - rintf(cyc)) + fmaf(L, fw->inv_lambda_lo, cer);
+    float sph, cph;
+    sincospif(2.f * frac, &sph, &cph);
+    const float Ab = g * fmaf(fw->wre, cph, fw->wim * sph);
+    const float phb = g * A * fmaf(fw->wim, cph, -fw->wre * sph);
+    gC = Ab * Cf * iL;
+    Lb = fmaf(-Ab, A * iL, phb * fw->k2pi);
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      float others = 1.f;
+#pragma unroll
+      for (int i = 1; i <= K; ++i)
+        if (i != j) others *= Cj[i];
+      cosb[j] = Ab * others * pre[NF] * iL * dC[j];
+    }
+  }
   float Vb[K + 1], visb[K + 1];
 #pragma unroll
   for (int j = 1; j <= K; ++j) Vb[j] = gC * pre[j - 1] * suf[j];
 #pragma unroll
   for (int j = 0; j <= K; ++j) visb[j] = gC * pre[K + j] * suf[K + j + 1];
-  const float Lb = -2.f * g * __fdiv_rn(p, L);
+  if constexpr (!FIELD) Lb = -2.f * g * __fdiv_rn(p, L);
 
   // ------------------------------------------------ sweep 2: obstruction adjoint
   // legs whose visibility adjoint is zero in every lane contribute nothing here
@@ -501,6 +563,27 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
     rn_x[j] = fmaf(pb, Qx[j - 1], fmaf(qb, Qx[j + 1], rn_x[j]));
     rn_y[j] = fmaf(pb, Qy[j - 1], fmaf(qb, Qy[j + 1], rn_y[j]));
     rc[j] = -(pb + qb);
+  }
+  if constexpr (FIELD) {
+    // c_j = |n . d| / |d|, d = Q_j - Q_{j-1}:
+    //   dc/dd = sign(n . d) (n - (n . d) d / |d|^2) / |d|,  dc/dn = sign(n . d) d / |d|
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const float4 G = s.G[cd.w[j - 1]];
+      const float dx = Qx[j] - Qx[j - 1], dy = Qy[j] - Qy[j - 1];
+      const float il = len[j - 1] > 0.f ? __frcp_rn(len[j - 1]) : 0.f;
+      const float sd = fmaf(G.x, dx, G.y * dy);
+      const float k = cosb[j] * il * copysignf(1.f, sd);
+      const float proj = sd * il * il;
+      const float Dbx = k * fmaf(-proj, dx, G.x);
+      const float Dby = k * fmaf(-proj, dy, G.y);
+      Qbx[j] += Dbx;
+      Qby[j] += Dby;
+      Qbx[j - 1] -= Dbx;
+      Qby[j - 1] -= Dby;
+      rn_x[j] = fmaf(k, dx, rn_x[j]);
+      rn_y[j] = fmaf(k, dy, rn_y[j]);
+    }
   }
   float Ibx[K + 1], Iby[K + 1];
 #pragma unroll

@@ -125,6 +125,31 @@ def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelengt
     return E, power
 
 
+def field_vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
+              eps_r: float, field_values: torch.Tensor, grad_power: torch.Tensor,
+              refl_coef: float = 0.5, wall_grad: bool = True, tile: TileConfig | None = None):
+    """(grad_tx [2], grad_walls [W, 4] or None) = grad_power^T d|E|^2 / d(tx, walls), with
+    ``field_values`` the [R, 2] field that ``field`` returned for the same arguments."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    gp = _as_f32(grad_power.reshape(-1, 1), 1, "grad_power", 4)
+    E = _as_f32(field_values, 2, "field", 8)
+    if gp.shape[0] != sc.n_rx or E.shape[0] != sc.n_rx:
+        raise ValueError("grad_power and field must have one entry per receiver")
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_field_vjp_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    gtx = torch.empty(2, dtype=torch.float32, device=dev)
+    gw = torch.empty(sc.n_walls, 4, dtype=torch.float32, device=dev) if wall_grad else None
+    _lib.call("drt_field_vjp", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
+              ctypes.c_float(eps_r), _ptr(E), _ptr(gp), _ptr(gtx),
+              None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+              _stream_ptr(dev))
+    return gtx, gw
+
+
 def tune_forward_timings(walls, tx, rx, max_order: int, alpha: float, smoothing: str,
                          candidates, refl_coef: float = 0.5, reps: int = 3):
     """Times drt_forward with each TileConfig of ``candidates`` in the library
@@ -278,6 +303,39 @@ class MinLossFunction(torch.autograd.Function):
     def backward(ctx, grad_loss):
         (arg,) = ctx.saved_tensors
         return min_loss_backward(arg, grad_loss.reshape(1).float().contiguous(), ctx.n)
+
+
+class FieldPowerFunction(torch.autograd.Function):
+    """|E|^2 of the coherent field, with drt_field_vjp as backward (the field E is
+    saved; the geometry is recomputed)."""
+
+    @staticmethod
+    def forward(ctx, walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef,
+                tile):
+        E, P = field(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef,
+                     tile)
+        ctx.save_for_backward(walls, tx, rx, E)
+        ctx.args = (max_order, alpha, smoothing, wavelength, eps_r, refl_coef, tile)
+        return P
+
+    @staticmethod
+    def backward(ctx, grad_power):
+        walls, tx, rx, E = ctx.saved_tensors
+        max_order, alpha, smoothing, wavelength, eps_r, refl_coef, tile = ctx.args
+        need_w, need_tx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_w or need_tx):
+            return (None,) * 10
+        gtx, gw = field_vjp(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, E,
+                            grad_power.contiguous(), refl_coef, wall_grad=need_w, tile=tile)
+        return (gw if need_w else None, gtx.reshape(tx.shape) if need_tx else None,
+                None, None, None, None, None, None, None, None)
+
+
+def field_power(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
+                eps_r: float, refl_coef: float = 0.5, tile: TileConfig | None = None):
+    """Differentiable (in walls and tx) coherent power |E_r|^2 per receiver."""
+    return FieldPowerFunction.apply(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r,
+                                    refl_coef, tile)
 
 
 def power(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",

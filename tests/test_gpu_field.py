@@ -162,3 +162,97 @@ def test_two_receivers_per_lane_equal_one_bit_for_bit(drt, smoothing, alpha):
                       tile=drt.TileConfig(single_rx=True))
         np.testing.assert_array_equal(Ep, Es)
         np.testing.assert_array_equal(Pp, Ps)
+
+
+# --------------------------------------------------------------------------- adjoint
+# Gradient bar for the coherent power: norm-wise 1e-3 relative (as for the power's
+# gradient); per element 1e-3 |ref| + 1e-4 max|ref|: a component is a sum of path
+# terms whose phases differ, so a small component is a near-cancellation of large
+# terms of both signs, and FP32 rounding of those terms sets its absolute error.
+FGRAD_FLOOR = 1e-4
+
+
+def _assert_field_grad_close(gpu, ref, what):
+    gpu = np.asarray(gpu, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    assert np.linalg.norm(gpu - ref) <= 1e-3 * np.linalg.norm(ref), (what, gpu, ref)
+    tol = 1e-3 * np.abs(ref) + FGRAD_FLOOR * np.abs(ref).max()
+    bad = np.nonzero(np.abs(gpu - ref) > tol)[0]
+    assert bad.size == 0, (what, bad[:5], gpu[bad[:5]], ref[bad[:5]])
+
+
+def _field_vjp(drt, walls, tx, rx, K, alpha, smoothing, lam, eps, g, wall_grad=True):
+    dev = torch.device("cuda:0")
+    w = torch.tensor(np.asarray(walls, np.float32), device=dev)
+    t = torch.tensor(np.asarray(tx, np.float32), device=dev)
+    r = torch.tensor(np.asarray(rx, np.float32), device=dev)
+    E, _ = drt.field(w, t, r, K, alpha, smoothing, lam, eps)
+    gp = torch.tensor(np.asarray(g, np.float32), device=dev)
+    gtx, gw = drt.field_vjp(w, t, r, K, alpha, smoothing, lam, eps, E, gp, wall_grad=wall_grad)
+    torch.cuda.synchronize()
+    return gtx.cpu().numpy(), (gw.cpu().numpy() if gw is not None else None)
+
+
+FVJP_CASES = [
+    # (seed, W, R, K, alpha, smoothing, wavelength, eps_r)
+    (0, 6, 45, 1, 20.0, "sigmoid", 0.05, 4.0),
+    (1, 8, 40, 2, 10.0, "sigmoid", 0.08, 0.0),
+    (2, 8, 33, 2, 40.0, "hard_sigmoid", 0.05, 6.0),
+    (3, 5, 70, 0, 30.0, "hard_sigmoid", 0.03, 0.0),
+    (4, 7, 40, 2, 1.0, "step", 0.05, 3.0),
+    (5, 5, 36, 3, 15.0, "sigmoid", 0.1, 2.0),
+    (6, 9, 50, 2, 100.0, "hard_sigmoid", 0.02, 15.0),
+]
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha,smoothing,lam,eps", FVJP_CASES)
+def test_field_vjp_all_parameters(drt, oracle_mod, seed, W, R, K, alpha, smoothing, lam, eps):
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, smoothing, boundary=(seed % 2 == 1))
+    g = rng.normal(size=sc.n_rx)
+    gtx, gw = _field_vjp(drt, sc.walls, sc.tx, sc.rx, K, alpha, smoothing, lam, eps, g)
+    ref = oracle_mod.field_gradient(sc.walls, sc.tx, sc.rx, K, alpha, smoothing, lam, eps,
+                                    g.astype(np.float32).astype(np.float64), "all", 0.5)
+    _assert_field_grad_close(gtx, ref[:2], "grad_tx")
+    _assert_field_grad_close(gw.ravel(), ref[2:], "grad_walls")
+
+
+def test_field_vjp_tx_only_matches_full(drt):
+    rng = np.random.default_rng(31)
+    sc = scenes.random_small_scene(rng, 8, 60, 2, 50.0, "sigmoid", boundary=True)
+    g = rng.normal(size=sc.n_rx)
+    a, _ = _field_vjp(drt, sc.walls, sc.tx, sc.rx, 2, 50.0, "sigmoid", 0.04, 5.0, g, False)
+    b, _ = _field_vjp(drt, sc.walls, sc.tx, sc.rx, 2, 50.0, "sigmoid", 0.04, 5.0, g, True)
+    np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6 * np.abs(b).max())
+
+
+def test_field_power_autograd(drt, oracle_mod):
+    rng = np.random.default_rng(32)
+    sc = scenes.random_small_scene(rng, 7, 50, 2, 30.0, "hard_sigmoid", boundary=True)
+    dev = torch.device("cuda:0")
+    w = torch.tensor(sc.walls, device=dev, requires_grad=True)
+    t = torch.tensor(sc.tx, device=dev, requires_grad=True)
+    r = torch.tensor(sc.rx, device=dev)
+    P = drt.field_power(w, t, r, 2, 30.0, "hard_sigmoid", 0.05, 4.0)
+    g = torch.tensor(rng.normal(size=sc.n_rx).astype(np.float32), device=dev)
+    (P * g).sum().backward()
+    ref = oracle_mod.field_gradient(sc.walls, sc.tx, sc.rx, 2, 30.0, "hard_sigmoid", 0.05, 4.0,
+                                    g.cpu().numpy().astype(np.float64), "all", 0.5)
+    _assert_field_grad_close(t.grad.cpu().numpy(), ref[:2], "grad_tx")
+    _assert_field_grad_close(w.grad.cpu().numpy().ravel(), ref[2:], "grad_walls")
+
+
+def test_field_vjp_benchmark_scene_sampled(drt, oracle_mod):
+    # full 256 x 256 launch with g on 12 sampled receivers; TX and 8 wall coordinates
+    sc = scenes.large_scene(alpha=100.0, smoothing="hard_sigmoid")
+    lam, eps = 0.02, 5.0
+    rng = np.random.default_rng(33)
+    idx = rng.choice(sc.n_rx, 12, replace=False)
+    g = np.zeros(sc.n_rx)
+    g[idx] = rng.normal(size=12)
+    gtx, gw = _field_vjp(drt, sc.walls, sc.tx, sc.rx, 2, 100.0, "hard_sigmoid", lam, eps, g)
+    params = [0, 1] + [2 + 4 * w + c for w in (4, 20, 40) for c in (0, 3)] + [2 + 4 * 63, 2 + 4 * 63 + 1]
+    ref = oracle_mod.field_gradient(sc.walls, sc.tx, sc.rx[idx], 2, 100.0, "hard_sigmoid", lam,
+                                    eps, g[idx], params, 0.5)
+    got = np.concatenate([gtx, gw.ravel()])[params]
+    _assert_field_grad_close(got, ref, "sampled gradient")
