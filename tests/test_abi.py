@@ -106,3 +106,19 @@ def test_field_rejects_bad_scene_before_any_launch(lib):
     assert lib.drt_field_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == 1
     assert lib.drt_field(ctypes.byref(sc), None, ctypes.c_float(0.1), ctypes.c_float(5.0),
                          ctypes.c_void_p(256), None, None, 0, None) == 1
+
+
+@pytest.mark.parametrize("wavelength,eps_r,field_ptr,gp_ptr,gtx_ptr,gw_ptr", [
+    (0.0, 5.0, 256, 256, 256, None), (0.1, 0.5, 256, 256, 256, None),
+    (0.1, float("nan"), 256, 256, 256, None), (0.1, 5.0, 0, 256, 256, None),
+    (0.1, 5.0, 260, 256, 256, None), (0.1, 5.0, 256, 0, 256, None),
+    (0.1, 5.0, 256, 256, 0, None), (0.1, 5.0, 256, 256, 256, 264)])
+def test_field_vjp_rejects_bad_args_before_any_launch(lib, wavelength, eps_r, field_ptr, gp_ptr,
+                                                      gtx_ptr, gw_ptr):
+    sc = _scene()
+    st = lib.drt_field_vjp(ctypes.byref(sc), None, ctypes.c_float(wavelength),
+                           ctypes.c_float(eps_r), ctypes.c_void_p(field_ptr),
+                           ctypes.c_void_p(gp_ptr), ctypes.c_void_p(gtx_ptr),
+                           None if gw_ptr is None else ctypes.c_void_p(gw_ptr),
+                           ctypes.c_void_p(256), 1 << 20, None)
+    assert st == 1 and len(lib.drt_last_error()) > 0
