@@ -102,7 +102,7 @@ __device__ __forceinline__ void sigmoid_vis_sweep(const VSmem& s, int W, const C
       const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
       const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
       const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
-      const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
+      const float xb2 = same2 ? no2 : ns2;
       const float d2 = ns2 + no2;
       const float num = fmaf(xb1, d2, x1 * xb2);
       if (num == 0.f) {
