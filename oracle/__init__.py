@@ -21,6 +21,7 @@ Functions and the passages they follow:
 * ``field``           Eq. 7 read as a coherent sum of path fields (Fresnel TE reflection)
 * ``field_jvp``, ``field_gradient``  its exact forward-mode derivative, and the gradient of
                         sum_r g_r |E_r|^2
+* ``power3``          Sec. VI's 3D extension for triangle walls (same steps, planes for lines)
 * ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
                         finders' convergence check compares with zero (``oracle/mpt.py``)
 
@@ -80,6 +81,7 @@ def _load():
         lib.drt_oracle_paths.argtypes = [p, i, p, p, i, d, i, d, p, p, p, p, p, p]
         lib.drt_oracle_field.argtypes = [p, i, p, p, i, i, d, i, d, d, d, i, p, p, p]
         lib.drt_oracle_field_jvp.argtypes = [p, i, p, p, i, i, d, i, d, d, d, p, p, i, p, p]
+        lib.drt_oracle_power3.argtypes = [p, i, p, p, i, i, d, i, d, i, p]
         _lib = lib
         return lib
 
@@ -268,6 +270,23 @@ def field_gradient(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r
         E, dE = field_jvp(walls, tx, rx_nz, max_order, alpha, smoothing, wavelength, eps_r, dw,
                           dtx, refl_coef, threads)
         out[n] = float(np.dot(g_nz, 2.0 * (E.real * dE.real + E.imag * dE.imag)))
+    return out
+
+
+def power3(tris, tx, rx, max_order: int, alpha: float, smoothing, refl_coef: float = 0.5,
+           threads=None) -> np.ndarray:
+    """Received power of a 3D scene of triangle walls (float64 [R]): tris [W, 9]
+    (corners A, B, C), tx [3], rx [R, 3]; the reading of the method for triangles
+    stated in drt_oracle.cpp (plane distances, in-plane edge distances)."""
+    tris = _f64(tris).reshape(-1, 9)
+    tx = _f64(tx).reshape(3)
+    rx = _f64(rx).reshape(-1, 3)
+    out = np.zeros(rx.shape[0])
+    rc = _load().drt_oracle_power3(_ptr(tris), tris.shape[0], _ptr(tx), _ptr(rx), rx.shape[0],
+                                   int(max_order), float(alpha), _kind(smoothing),
+                                   float(refl_coef), _threads(threads), _ptr(out))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
     return out
 
 

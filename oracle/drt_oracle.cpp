@@ -393,9 +393,141 @@ void set_threads(int nthreads) {
 #endif
 }
 
+// ---------------------------------------------------------------- 3D scenes
+// Sec. VI: the method is not tied to two dimensions.  Read for triangle walls:
+//   plane of triangle (A, B, C): unit normal n along (B - A) x (C - A), offset
+//   c = n . A, signed distance d(p) = n . p - c; edge k (A->B, B->C, C->A) has the
+//   in-plane unit normal m_k = n x e_k / |e_k| (pointing into the triangle) and the
+//   signed in-plane distance delta_k(p) = m_k . (p - start of edge k).
+//   image method and backtrace: as in 2D with planes for lines;
+//   on the object: prod_k s(delta_k(Q_j)) (the 2D on-segment test has two ends);
+//   same side: s(p) s(q) + s(-p) s(-q) with plane distances;
+//   obstruction of leg Q_j -> Q_{j+1} by triangle w (not one its end points lie
+//   on): X(x, y) * prod_k s(delta_k(P)), x = d_w(Q_j), y = d_w(Q_{j+1}), P the
+//   intersection of the leg's line with w's plane (no intersection: not blocked);
+//   path power Gamma^k V vis / L^2 as in 2D.
+struct V3 {
+  double x, y, z;
+};
+V3 operator+(const V3& a, const V3& b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+V3 operator-(const V3& a, const V3& b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 operator*(double s, const V3& a) { return V3{s * a.x, s * a.y, s * a.z}; }
+double dot(const V3& a, const V3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+V3 cross(const V3& a, const V3& b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+double norm(const V3& a) { return std::sqrt(dot(a, a)); }
+
+struct Tri {
+  V3 v[3];   // corners A, B, C
+  V3 n;      // unit normal
+  double c;  // n . A
+  V3 m[3];   // in-plane unit normals of the edges, pointing inside
+};
+
+Tri make_tri(const double* p) {
+  Tri t;
+  for (int i = 0; i < 3; ++i) t.v[i] = V3{p[3 * i], p[3 * i + 1], p[3 * i + 2]};
+  V3 nn = cross(t.v[1] - t.v[0], t.v[2] - t.v[0]);
+  t.n = (1.0 / norm(nn)) * nn;
+  t.c = dot(t.n, t.v[0]);
+  for (int k = 0; k < 3; ++k) {
+    V3 e = t.v[(k + 1) % 3] - t.v[k];
+    t.m[k] = (1.0 / norm(e)) * cross(t.n, e);
+  }
+  return t;
+}
+
+double plane_dist(const Tri& t, const V3& p) { return dot(t.n, p) - t.c; }
+double edge_dist(const Tri& t, int k, const V3& p) { return dot(t.m[k], p - t.v[k]); }
+
+// prod_k s(delta_k(p)): p (on the plane) inside the triangle
+double inside(const Tri& t, const V3& p, double alpha, int kind) {
+  double r = 1.0;
+  for (int k = 0; k < 3; ++k) r *= smooth(edge_dist(t, k, p), alpha, kind);
+  return r;
+}
+
+double path_power3(const std::vector<Tri>& tris, const V3& tx, const V3& rx,
+                   const std::vector<int>& seq, const Params& P) {
+  const int k = (int)seq.size();
+  const int W = (int)tris.size();
+  std::vector<V3> img(k + 1);
+  img[0] = tx;
+  for (int j = 1; j <= k; ++j) {
+    const Tri& t = tris[seq[j - 1]];
+    img[j] = img[j - 1] - (2.0 * plane_dist(t, img[j - 1])) * t.n;
+  }
+  std::vector<V3> Q(k + 2);
+  Q[0] = tx;
+  Q[k + 1] = rx;
+  for (int j = k; j >= 1; --j) {
+    const Tri& t = tris[seq[j - 1]];
+    const double a = plane_dist(t, img[j]);
+    const double b = plane_dist(t, Q[j + 1]);
+    if (b - a == 0.0) return 0.0;
+    Q[j] = Q[j + 1] + (b / (b - a)) * (img[j] - Q[j + 1]);
+  }
+  double L = 0.0;
+  for (int j = 0; j <= k; ++j) {
+    const double l = norm(Q[j + 1] - Q[j]);
+    if (l == 0.0) return 0.0;
+    L += l;
+  }
+  const double al = P.alpha;
+  const int kind = P.kind;
+  double validity = 1.0;
+  for (int j = 1; j <= k; ++j) {
+    const Tri& t = tris[seq[j - 1]];
+    const double p = plane_dist(t, Q[j - 1]), q = plane_dist(t, Q[j + 1]);
+    const double same_side = smooth(p, al, kind) * smooth(q, al, kind) +
+                             smooth(-p, al, kind) * smooth(-q, al, kind);
+    validity *= inside(t, Q[j], al, kind) * same_side;
+  }
+  double visibility = 1.0;
+  for (int j = 0; j <= k; ++j) {
+    const int skip_a = (j >= 1) ? seq[j - 1] : -1;
+    const int skip_b = (j + 1 <= k) ? seq[j] : -1;
+    for (int wi = 0; wi < W; ++wi) {
+      if (wi == skip_a || wi == skip_b) continue;
+      const Tri& t = tris[wi];
+      const double x = plane_dist(t, Q[j]), y = plane_dist(t, Q[j + 1]);
+      const double cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +
+                                 smooth(-x, al, kind) * smooth(y, al, kind);
+      if (x - y == 0.0) continue;   // the leg's line never meets the plane
+      const V3 hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);
+      visibility *= 1.0 - cross_plane * inside(t, hit, al, kind);
+    }
+  }
+  double gk = 1.0;
+  for (int j = 0; j < k; ++j) gk *= P.gamma;
+  return gk * validity * visibility / (L * L);
+}
+
 }  // namespace
 
 extern "C" {
+
+// Received power of a 3D triangle scene: tris [W][9] (A, B, C corners), tx [3], rx [R][3].
+int drt_oracle_power3(const double* tris_xyz, int W, const double* tx, const double* rx, int R,
+                      int K, double alpha, int kind, double gamma, int nthreads, double* Pw) {
+  if (check_args(tris_xyz, W, tx, rx, R, K, alpha, kind)) return 1;
+  set_threads(nthreads);
+  std::vector<Tri> tris;
+  for (int i = 0; i < W; ++i) tris.push_back(make_tri(tris_xyz + 9 * i));
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  const V3 t{tx[0], tx[1], tx[2]};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    const V3 q{rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]};
+    double sum = 0.0;
+    for (const auto& seq : cands) sum += path_power3(tris, t, q, seq, prm);
+    Pw[r] = sum;
+  }
+  return 0;
+}
+
 
 // Number of path candidates for W walls and maximum order K.
 long long drt_oracle_num_candidates(int W, int K) {

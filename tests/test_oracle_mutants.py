@@ -17,7 +17,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "drt_oracle.cpp")
 PIN_FILES = ["tests/test_oracle_smoothing.py", "tests/test_oracle_candidates.py",
              "tests/test_oracle_geometry.py", "tests/test_oracle_bruteforce.py",
-             "tests/test_oracle_gradients.py", "tests/test_oracle_field.py"]
+             "tests/test_oracle_gradients.py", "tests/test_oracle_field.py",
+             "tests/test_oracle_3d.py"]
 
 MUTANTS = {
     "mirror sign": ("return Vec<T>{p.x - 2.0 * d * w.n.x", "return Vec<T>{p.x + 2.0 * d * w.n.x"),
@@ -66,6 +67,18 @@ MUTANTS = {
                                "return Dual(std::cos(a.v), a.d * std::sin(a.v));"),
     "dual sine derivative": ("return Dual(std::sin(a.v), a.d * std::cos(a.v));",
                              "return Dual(std::sin(a.v), a.d * std::sin(a.v));"),
+    "3d mirror sign": ("img[j] = img[j - 1] - (2.0 * plane_dist(t, img[j - 1])) * t.n;",
+                       "img[j] = img[j - 1] + (2.0 * plane_dist(t, img[j - 1])) * t.n;"),
+    "3d inside tests two edges": ("for (int k = 0; k < 3; ++k) r *= smooth(edge_dist(t, k, p), alpha, kind);",
+                                  "for (int k = 0; k < 2; ++k) r *= smooth(edge_dist(t, k, p), alpha, kind);"),
+    "3d edge normals outward": ("t.m[k] = (1.0 / norm(e)) * cross(t.n, e);",
+                                "t.m[k] = (1.0 / norm(e)) * cross(e, t.n);"),
+    "3d crossing point": ("const V3 hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);",
+                          "const V3 hit = Q[j] + (y / (x - y)) * (Q[j + 1] - Q[j]);"),
+    "3d crossing test sign": ("const double cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +",
+                              "const double cross_plane = smooth(x, al, kind) * smooth(y, al, kind) +"),
+    "3d same-side term": ("smooth(-p, al, kind) * smooth(-q, al, kind);",
+                          "smooth(-p, al, kind) * smooth(q, al, kind);"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
