@@ -153,6 +153,48 @@ drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wav
                          float* grad_tx, float* grad_walls, void* workspace,
                          size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+   3D scenes (Sec. VI: the method does not depend on the dimension).  Walls are
+   triangles; planes replace lines, and a point lies on a triangle when its three
+   in-plane edge distances pass the smoothed comparison:
+     plane of (A, B, C): unit normal n along (B - A) x (C - A), d(p) = n . (p - A);
+     edge k (A->B, B->C, C->A): delta_k(p) = m_k . (p - start of k), m_k = n x e_k / |e_k|;
+     reflection j valid: prod_k s(delta_k(Q_j)) (s(p) s(q) + s(-p) s(-q)) with p, q the
+       plane distances of the neighbouring vertices;
+     leg Q_j -> Q_{j+1} blocked by triangle w (not one in the plane of a triangle
+       its end points lie on: the leg meets that plane only at the end point):
+       X(x, y) prod_k s(delta_k(P)), X(x, y) = s(x) s(-y) + s(-x) s(y), x, y the end
+       points' plane distances, P where the leg's line meets w's plane (a line
+       parallel to the plane, or meeting it more than 1e8 leg lengths away, is not
+       blocked);
+     path power Gamma^k V vis / L^2 over the same candidates as in 2D; two
+       consecutive reflections on triangles of one plane (normals parallel and
+       offsets equal to within 1e-5) make a degenerate path, which contributes 0.
+   ------------------------------------------------------------------------ */
+typedef struct {
+  const float* tris;      /* [n_tris][9] device: corners A, B, C as x, y, z (4-byte aligned) */
+  int32_t n_tris;         /* W, 1..DRT_MAX_WALLS; no zero-area triangle */
+  const float* rx;        /* [n_rx][3] device */
+  int32_t n_rx;           /* R >= 0 */
+  const float* tx;        /* [3] device */
+  int32_t max_order;      /* K, 0..DRT_MAX_ORDER */
+  float alpha;            /* >= 0 */
+  drt_smoothing smoothing;
+  float refl_coef;        /* Gamma */
+} drt3_scene;
+
+/* Bytes of device workspace drt3_forward needs (host out). */
+drt_status drt3_forward_workspace_size(const drt3_scene* scene, const drt_tile* tile,
+                                       size_t* bytes);
+
+/* Received power per receiver of a 3D scene: power [n_rx] device, overwritten.
+   Paths with an exactly-zero validity in all 32 receivers of a warp skip their
+   obstruction loop (their power is exactly 0 either way).  tile: as for
+   drt_forward (one receiver per lane; the cull flag is implied).  Enqueued on
+   `stream`; never synchronises. */
+drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* power,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
 /* Autotuner probe for drt_forward (the work decomposition does not change the
    result beyond the order of the per-chunk sums): runs drt_forward on `scene`
    with each of the n_cand tiles of `cands` (host array), one untimed launch

@@ -402,10 +402,13 @@ void set_threads(int nthreads) {
 //   image method and backtrace: as in 2D with planes for lines;
 //   on the object: prod_k s(delta_k(Q_j)) (the 2D on-segment test has two ends);
 //   same side: s(p) s(q) + s(-p) s(-q) with plane distances;
-//   obstruction of leg Q_j -> Q_{j+1} by triangle w (not one its end points lie
-//   on): X(x, y) * prod_k s(delta_k(P)), x = d_w(Q_j), y = d_w(Q_{j+1}), P the
+//   obstruction of leg Q_j -> Q_{j+1} by triangle w (not one in the plane of a
+//   triangle its end points lie on: the leg meets that plane only at the end
+//   point): X(x, y) * prod_k s(delta_k(P)), x = d_w(Q_j), y = d_w(Q_{j+1}), P the
 //   intersection of the leg's line with w's plane (no intersection: not blocked);
-//   path power Gamma^k V vis / L^2 as in 2D.
+//   path power Gamma^k V vis / L^2 as in 2D;
+//   two consecutive reflections on triangles of one plane (normals parallel and
+//   offsets equal to within 1e-5): a degenerate path (zero-length leg), power 0.
 struct V3 {
   double x, y, z;
 };
@@ -448,6 +451,12 @@ double inside(const Tri& t, const V3& p, double alpha, int kind) {
   return r;
 }
 
+// Triangles a and b lie in one plane (normals parallel, offsets equal, to 1e-5).
+bool coplanar(const Tri& ta, const Tri& tb) {
+  const double nn = dot(ta.n, tb.n);
+  return std::fabs(nn) >= 1.0 - 1e-5 && std::fabs(ta.c - nn * tb.c) <= 1e-5 * (1.0 + std::fabs(ta.c));
+}
+
 double path_power3(const std::vector<Tri>& tris, const V3& tx, const V3& rx,
                    const std::vector<int>& seq, const Params& P) {
   const int k = (int)seq.size();
@@ -458,6 +467,10 @@ double path_power3(const std::vector<Tri>& tris, const V3& tx, const V3& rx,
     const Tri& t = tris[seq[j - 1]];
     img[j] = img[j - 1] - (2.0 * plane_dist(t, img[j - 1])) * t.n;
   }
+  // two consecutive reflections in one plane (two triangles of one flat face): the
+  // leg between them has zero length, so the path is degenerate
+  for (int j = 1; j < k; ++j)
+    if (coplanar(tris[seq[j - 1]], tris[seq[j]])) return 0.0;
   std::vector<V3> Q(k + 2);
   Q[0] = tx;
   Q[k + 1] = rx;
@@ -484,13 +497,14 @@ double path_power3(const std::vector<Tri>& tris, const V3& tx, const V3& rx,
                              smooth(-p, al, kind) * smooth(-q, al, kind);
     validity *= inside(t, Q[j], al, kind) * same_side;
   }
+  // a leg meets the plane of an end point's triangle only at that end point: it is
+  // not tested against any triangle of that plane
   double visibility = 1.0;
   for (int j = 0; j <= k; ++j) {
-    const int skip_a = (j >= 1) ? seq[j - 1] : -1;
-    const int skip_b = (j + 1 <= k) ? seq[j] : -1;
     for (int wi = 0; wi < W; ++wi) {
-      if (wi == skip_a || wi == skip_b) continue;
       const Tri& t = tris[wi];
+      if (j >= 1 && coplanar(t, tris[seq[j - 1]])) continue;
+      if (j + 1 <= k && coplanar(t, tris[seq[j]])) continue;
       const double x = plane_dist(t, Q[j]), y = plane_dist(t, Q[j + 1]);
       const double cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +
                                  smooth(-x, al, kind) * smooth(y, al, kind);

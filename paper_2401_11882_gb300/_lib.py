@@ -31,6 +31,14 @@ class Scene(ctypes.Structure):
                 ("refl_coef", ctypes.c_float)]
 
 
+class Scene3(ctypes.Structure):
+    _fields_ = [("tris", ctypes.c_void_p), ("n_tris", ctypes.c_int32),
+                ("rx", ctypes.c_void_p), ("n_rx", ctypes.c_int32),
+                ("tx", ctypes.c_void_p), ("max_order", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("smoothing", ctypes.c_int32),
+                ("refl_coef", ctypes.c_float)]
+
+
 class Tile(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int32), ("cands_per_unit", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("flags", ctypes.c_int32)]
@@ -72,6 +80,8 @@ SIGNATURES = {
     "drt_tune_forward": (ctypes.c_int, [_P, _P, _I32, _I32, _P, _P, _SZ, _P, _P, _P]),
     "drt_field_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_field": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _SZ, _P]),
+    "drt3_forward_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt3_forward": (ctypes.c_int, [_P, _P, _P, _P, _SZ, _P]),
     "drt_field_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_field_vjp": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P, _P,
                                      _SZ, _P]),

@@ -63,6 +63,8 @@ drt_status device_info(int* sms) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(vjp)");
     e = field_set_smem_limit(DRT_MAX_WALLS);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(field)");
+    e = forward3_set_smem_limit(DRT_MAX_WALLS);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(forward3)");
     d.smem_set = true;
   }
   *sms = d.sms;
@@ -113,7 +115,7 @@ drt_status check_tile(const drt_tile* t) {
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
 
-enum Kernel { FWD, VJP, FIELD, FIELD_VJP };
+enum Kernel { FWD, VJP, FIELD, FIELD_VJP, FWD3 };
 
 drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
   int sms = 0;
@@ -125,7 +127,7 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   d->threads = warps * 32;
   d->n_cand = num_candidates(W, K);
   long long chunk = (t && t->cands_per_unit) ? t->cands_per_unit : 64;
-  if ((kern == FWD || kern == FIELD) && R > 0) {
+  if ((kern == FWD || kern == FIELD || kern == FWD3) && R > 0) {
     const long long max_chunks = std::max(1LL, MAX_PARTIALS / R);
     chunk = std::max(chunk, (d->n_cand + max_chunks - 1) / max_chunks);
   }
@@ -142,13 +144,14 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
     cudaError_t e = (kern == FWD)         ? forward_occupancy(mode, d->pairs, d->threads, W, &per_sm)
                     : (kern == FIELD)     ? field_occupancy(mode, d->pairs, d->threads, W, &per_sm)
                     : (kern == FIELD_VJP) ? field_vjp_occupancy(mode, true, d->threads, W, &per_sm)
+                    : (kern == FWD3)      ? forward3_occupancy(mode, d->threads, W, &per_sm)
                                           : vjp_occupancy(mode, true, d->threads, W, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
   }
   long long ctas = (long long)sms * per_sm;
   const long long needed = (d->n_units + warps - 1) / warps;
-  if (kern == FWD || kern == FIELD) ctas = std::min(ctas, std::max(1LL, needed));
+  if (kern == FWD || kern == FIELD || kern == FWD3) ctas = std::min(ctas, std::max(1LL, needed));
   d->ctas = (int)std::max(1LL, ctas);
   return DRT_OK;
 }
@@ -302,6 +305,85 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
   cudaError_t e = launch_field(a, scene->smoothing, d.ctas, d.threads,
                                static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "field launch");
+  return DRT_OK;
+}
+
+// The 3D scene's counts and options in a drt_scene, for the shared decomposition.
+drt_status check_scene3(const drt3_scene* sc, drt_scene* flat) {
+  if (!sc) return fail(DRT_ERR_INVALID_ARG, "scene is NULL");
+  if (sc->n_tris < 1 || sc->n_tris > DRT_MAX_WALLS)
+    return fail(sc->n_tris > DRT_MAX_WALLS ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
+                "n_tris = %d outside 1..%d", sc->n_tris, DRT_MAX_WALLS);
+  if (sc->n_rx < 0) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 0", sc->n_rx);
+  if (sc->max_order < 0 || sc->max_order > DRT_MAX_ORDER)
+    return fail(sc->max_order > DRT_MAX_ORDER ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
+                "max_order = %d outside 0..%d", sc->max_order, DRT_MAX_ORDER);
+  if (!(sc->alpha >= 0.f) || !std::isfinite(sc->alpha))
+    return fail(DRT_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+  if (!std::isfinite(sc->refl_coef)) return fail(DRT_ERR_INVALID_ARG, "refl_coef must be finite");
+  if (sc->smoothing < 0 || sc->smoothing > 2)
+    return fail(DRT_ERR_INVALID_ARG, "unknown smoothing %d", sc->smoothing);
+  if (!sc->tris || !aligned(sc->tris, 4))
+    return fail(DRT_ERR_INVALID_ARG, "tris must be a 4-byte aligned device pointer");
+  if (!sc->tx || !aligned(sc->tx, 4)) return fail(DRT_ERR_INVALID_ARG, "tx pointer");
+  if (sc->n_rx > 0 && (!sc->rx || !aligned(sc->rx, 4)))
+    return fail(DRT_ERR_INVALID_ARG, "rx must be a 4-byte aligned device pointer");
+  *flat = drt_scene{};
+  flat->n_walls = sc->n_tris;
+  flat->n_rx = sc->n_rx;
+  flat->max_order = sc->max_order;
+  flat->alpha = sc->alpha;
+  flat->smoothing = sc->smoothing;
+  flat->refl_coef = sc->refl_coef;
+  return DRT_OK;
+}
+
+drt_status drt3_forward_workspace_size(const drt3_scene* scene, const drt_tile* tile,
+                                       size_t* bytes) {
+  drt_scene flat;
+  drt_status st = check_scene3(scene, &flat);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(&flat, tile, FWD3, &d)) != DRT_OK) return st;
+  *bytes = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  return DRT_OK;
+}
+
+drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* power,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  drt_scene flat;
+  drt_status st = check_scene3(scene, &flat);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (scene->n_rx > 0 && !power) return fail(DRT_ERR_INVALID_ARG, "power is NULL");
+  if (scene->n_rx == 0) return DRT_OK;
+  Decomp d;
+  if ((st = decompose(&flat, tile, FWD3, &d)) != DRT_OK) return st;
+  const size_t need = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  if (!workspace || workspace_bytes < need)
+    return fail(DRT_ERR_WORKSPACE, "3D forward needs %zu workspace bytes, got %zu", need,
+                workspace_bytes);
+  Fwd3Args a;
+  a.tris = scene->tris;
+  a.W = scene->n_tris;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.partial = static_cast<float*>(workspace);
+  a.power = power;
+  cudaError_t e = launch_forward3(a, scene->smoothing, d.ctas, d.threads,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "3D forward launch");
   return DRT_OK;
 }
 

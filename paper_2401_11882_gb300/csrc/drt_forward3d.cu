@@ -1,0 +1,286 @@
+// Forward pass of the method in 3D (Sec. VI: the framework does not depend on the
+// dimension): walls are triangles, lines become planes, and a point lies on an
+// object when its three in-plane edge distances pass the smoothed comparison.
+//
+//   plane of triangle (A, B, C): unit normal n along (B - A) x (C - A), c = n . A,
+//   d(p) = n . p - c; edge k (A->B, B->C, C->A): in-plane unit normal
+//   m_k = n x e_k / |e_k| (pointing inside), delta_k(p) = m_k . p - m_k . (start of k);
+//   image method and backtrace as in 2D with planes for lines;
+//   validity of reflection j: prod_k s(delta_k(Q_j)) (s(p) s(q) + s(-p) s(-q));
+//   obstruction of leg Q_j -> Q_{j+1} by triangle w (not one in the plane of a
+//   triangle its end points lie on, which the leg meets only at that end point):
+//   X(x, y) prod_k s(delta_k(P)), x, y the end points' plane distances and P
+//   the point where the leg's line meets the plane, whose edge distances are the
+//   end points' ones interpolated at t = x / (x - y) (delta_k is affine);
+//   path power Gamma^k V vis / L^2, summed over the candidates;
+//   two consecutive reflections on triangles of one plane make a degenerate path:
+//   the leg between them has zero length, and in floating point its rounding-sized
+//   length would make the path's power an arbitrary function of the rounding.
+//   "One plane": normals parallel and offsets equal, both to 1e-5.
+//
+// Mapping as in drt_forward.cu: lanes are receivers, the candidate is
+// warp-uniform, the triangles' plane and edge records sit in shared memory and
+// are read as broadcasts; per triangle, the plane and edge distances of every
+// path vertex are computed once and shared by the two legs meeting there.  Units
+// of (32 receivers) x (a chunk of candidates), per-chunk partial sums added in
+// chunk order: deterministic.
+#include <cuda_runtime.h>
+
+#include "drt_common.cuh"
+#include "drt_internal.h"
+
+namespace drt {
+
+namespace {
+
+// Triangle records in shared memory, 4 float4 per triangle:
+//   P  {nx, ny, nz, c}            plane: d(p) = n . p - c
+//   Mk {mx, my, mz, o_k}, k=0..2  edge k: delta_k(p) = m_k . p - o_k
+struct SmemTris {
+  float4 *P, *M0, *M1, *M2;
+};
+
+__device__ __forceinline__ float dot3(float4 r, float3 p) {
+  return fmaf(r.x, p.x, fmaf(r.y, p.y, r.z * p.z));
+}
+
+__device__ void stage_tris(const float* __restrict__ tris, int W, SmemTris s) {
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    const float* t = tris + 9 * (size_t)w;
+    const float3 a = make_float3(t[0], t[1], t[2]);
+    const float3 b = make_float3(t[3], t[4], t[5]);
+    const float3 c = make_float3(t[6], t[7], t[8]);
+    const float3 e1 = make_float3(b.x - a.x, b.y - a.y, b.z - a.z);
+    const float3 e2 = make_float3(c.x - a.x, c.y - a.y, c.z - a.z);
+    float3 n = make_float3(fmaf(e1.y, e2.z, -e1.z * e2.y), fmaf(e1.z, e2.x, -e1.x * e2.z),
+                           fmaf(e1.x, e2.y, -e1.y * e2.x));
+    const float nl = __fsqrt_rn(fmaf(n.x, n.x, fmaf(n.y, n.y, n.z * n.z)));
+    n = make_float3(__fdiv_rn(n.x, nl), __fdiv_rn(n.y, nl), __fdiv_rn(n.z, nl));
+    const float4 P = make_float4(n.x, n.y, n.z, fmaf(n.x, a.x, fmaf(n.y, a.y, n.z * a.z)));
+    s.P[w] = P;
+    const float3 v[3] = {a, b, c};
+    float4* M[3] = {s.M0, s.M1, s.M2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float3 p = v[k], q = v[(k + 1) % 3];
+      const float3 e = make_float3(q.x - p.x, q.y - p.y, q.z - p.z);
+      float3 m = make_float3(fmaf(n.y, e.z, -n.z * e.y), fmaf(n.z, e.x, -n.x * e.z),
+                             fmaf(n.x, e.y, -n.y * e.x));
+      const float ml = __fsqrt_rn(fmaf(m.x, m.x, fmaf(m.y, m.y, m.z * m.z)));
+      m = make_float3(__fdiv_rn(m.x, ml), __fdiv_rn(m.y, ml), __fdiv_rn(m.z, ml));
+      M[k][w] = make_float4(m.x, m.y, m.z, fmaf(m.x, p.x, fmaf(m.y, p.y, m.z * p.z)));
+    }
+  }
+}
+
+// Power of one candidate of order K for this lane's receiver.
+template <int MODE, int K>
+__device__ __forceinline__ float path_power3(const SmemTris& s, int W, float3 tx, float3 rx,
+                                             const Cand& cd, float alpha, float gk) {
+  // images (warp-uniform)
+  float3 I[K + 1];
+  I[0] = tx;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 P = s.P[cd.w[j - 1]];
+    const float d2 = 2.f * (dot3(P, I[j - 1]) - P.w);
+    I[j] = make_float3(fmaf(-d2, P.x, I[j - 1].x), fmaf(-d2, P.y, I[j - 1].y),
+                       fmaf(-d2, P.z, I[j - 1].z));
+  }
+  // two consecutive reflections in one plane (two triangles of one flat face): the
+  // leg between them has zero length, the path is degenerate (warp-uniform test)
+  bool degenerate = false;
+#pragma unroll
+  for (int j = 1; j < K; ++j) {
+    const float4 Pa = s.P[cd.w[j - 1]], Pb = s.P[cd.w[j]];
+    const float nn = fmaf(Pa.x, Pb.x, fmaf(Pa.y, Pb.y, Pa.z * Pb.z));
+    if (fabsf(nn) >= 1.f - 1e-5f && fabsf(fmaf(-nn, Pb.w, Pa.w)) <= 1e-5f * (1.f + fabsf(Pa.w)))
+      degenerate = true;
+  }
+  // backtrace on the planes: Q_{K+1} = RX, Q_j = line(Q_{j+1}, I_j) x plane j
+  float3 Q[K + 2];
+  Q[0] = tx;
+  Q[K + 1] = rx;
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 P = s.P[cd.w[j - 1]];
+    const float a = dot3(P, I[j]) - P.w;
+    const float b = dot3(P, Q[j + 1]) - P.w;
+    float t = __fdividef(b, b - a);
+    if (!(fabsf(t) <= 1e8f)) {
+      degenerate = true;
+      t = 0.f;
+    }
+    Q[j] = make_float3(fmaf(t, I[j].x - Q[j + 1].x, Q[j + 1].x),
+                       fmaf(t, I[j].y - Q[j + 1].y, Q[j + 1].y),
+                       fmaf(t, I[j].z - Q[j + 1].z, Q[j + 1].z));
+  }
+  float L = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = Q[j + 1].x - Q[j].x, dy = Q[j + 1].y - Q[j].y, dz = Q[j + 1].z - Q[j].z;
+    const float len2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    degenerate |= !(len2 > 0.f);
+    L += __fsqrt_rn(len2);
+  }
+  // validity: on the triangle, and the neighbours on the same side of its plane
+  float V = 1.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 P = s.P[w];
+    const Smooth3 sp = smooth3<MODE>(dot3(P, Q[j - 1]) - P.w, alpha);
+    const Smooth3 sq = smooth3<MODE>(dot3(P, Q[j + 1]) - P.w, alpha);
+    const float4 M0 = s.M0[w], M1 = s.M1[w], M2 = s.M2[w];
+    const float in = smooth3<MODE>(dot3(M0, Q[j]) - M0.w, alpha).s *
+                     smooth3<MODE>(dot3(M1, Q[j]) - M1.w, alpha).s *
+                     smooth3<MODE>(dot3(M2, Q[j]) - M2.w, alpha).s;
+    V *= in * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+  }
+  if (__all_sync(0xffffffffu, V == 0.f || degenerate)) return 0.f;
+  // obstruction: every triangle against every leg, except the triangles in the plane
+  // of a triangle the leg's end points lie on (the leg meets that plane only there)
+  float vis[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) vis[j] = 1.f;
+  float4 Pr[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) Pr[j] = s.P[cd.w[j - 1]];
+  for (int w = 0; w < W; ++w) {
+    const float4 P = s.P[w], M0 = s.M0[w], M1 = s.M1[w], M2 = s.M2[w];
+    bool cop[K + 2];   // w in the plane of reflection j's triangle (warp-uniform)
+    cop[0] = cop[K + 1] = false;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const float nn = fmaf(P.x, Pr[j].x, fmaf(P.y, Pr[j].y, P.z * Pr[j].z));
+      cop[j] = fabsf(nn) >= 1.f - 1e-5f &&
+               fabsf(fmaf(-nn, Pr[j].w, P.w)) <= 1e-5f * (1.f + fabsf(P.w));
+    }
+    float d[K + 2], e0[K + 2], e1[K + 2], e2[K + 2];
+    Smooth3 sd[K + 2];
+#pragma unroll
+    for (int i = 0; i <= K + 1; ++i) {
+      d[i] = dot3(P, Q[i]) - P.w;
+      sd[i] = smooth3<MODE>(d[i], alpha);
+      e0[i] = dot3(M0, Q[i]) - M0.w;
+      e1[i] = dot3(M1, Q[i]) - M1.w;
+      e2[i] = dot3(M2, Q[i]) - M2.w;
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      if (cop[j] || cop[j + 1]) continue;
+      const float X = fmaf(sd[j].s, sd[j + 1].sb, sd[j].sb * sd[j + 1].s);
+      const float den = d[j] - d[j + 1];
+      const float t = __fdividef(d[j], den);
+      // the leg's line misses the plane (or meets it absurdly far): not blocked
+      if (!(fabsf(t) <= 1e8f)) continue;
+      const float in = smooth3<MODE>(fmaf(t, e0[j + 1] - e0[j], e0[j]), alpha).s *
+                       smooth3<MODE>(fmaf(t, e1[j + 1] - e1[j], e1[j]), alpha).s *
+                       smooth3<MODE>(fmaf(t, e2[j + 1] - e2[j], e2[j]), alpha).s;
+      vis[j] = fmaf(-X, in * vis[j], vis[j]);
+    }
+  }
+  float p = V * gk;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) p *= vis[j];
+  p = __fdividef(p, L * L);
+  return degenerate ? 0.f : p;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) forward3_kernel(const Fwd3Args a) {
+  extern __shared__ float4 smem[];
+  SmemTris s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
+  stage_tris(a.tris, a.W, s);
+  __syncthreads();
+  const float3 tx = make_float3(__ldg(a.tx), __ldg(a.tx + 1), __ldg(a.tx + 2));
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
+       u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    long long r = tile * 32 + lane;
+    const bool live = r < a.R;
+    if (!live) r = a.R - 1;
+    const float3 q = make_float3(__ldg(a.rx + 3 * r), __ldg(a.rx + 3 * r + 1),
+                                 __ldg(a.rx + 3 * r + 2));
+    const int c0 = (int)(chunk * a.chunk);
+    const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
+    float acc = 0.f;
+    Cand cd = decode_candidate(c0, a.W, a.K);
+    for (int i = 0; i < nc; ++i) {
+      if (i > 0) next_candidate(cd, a.W);
+      switch (cd.k) {
+        case 0: acc += path_power3<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0]); break;
+        case 1: acc += path_power3<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1]); break;
+        case 2: acc += path_power3<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2]); break;
+        default: acc += path_power3<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3]); break;
+      }
+    }
+    if (live) a.partial[chunk * a.R + r] = acc;
+  }
+}
+
+__global__ void reduce3_kernel(const float* __restrict__ partial, long long n_chunks, long long R,
+                               float* __restrict__ power) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (long long c = 0; c < n_chunks; ++c) acc += partial[c * R + r];
+    power[r] = acc;
+  }
+}
+
+}  // namespace
+
+size_t forward3_smem_bytes(int W) { return (size_t)4 * W * sizeof(float4); }
+
+cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st) {
+  const size_t smem = forward3_smem_bytes(a.W);
+  if (a.n_units > 0) {
+    switch (mode) {
+      case MODE_SIGMOID: forward3_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_HARD: forward3_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a); break;
+      default: forward3_kernel<MODE_STEP><<<ctas, threads, smem, st>>>(a); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.R > 0) {
+    const long long nb = (a.R + 255) / 256;
+    reduce3_kernel<<<(int)(nb < 4096 ? nb : 4096), 256, 0, st>>>(a.partial, a.n_chunks, a.R,
+                                                                 a.power);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = forward3_smem_bytes(W);
+  switch (mode) {
+    case MODE_SIGMOID:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward3_kernel<MODE_SIGMOID>,
+                                                           threads, smem);
+    case MODE_HARD:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward3_kernel<MODE_HARD>,
+                                                           threads, smem);
+    default:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward3_kernel<MODE_STEP>,
+                                                           threads, smem);
+  }
+}
+
+cudaError_t forward3_set_smem_limit(int W) {
+  const int smem = (int)forward3_smem_bytes(W);
+  cudaError_t e = cudaFuncSetAttribute(forward3_kernel<MODE_SIGMOID>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(forward3_kernel<MODE_HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(forward3_kernel<MODE_STEP>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace drt

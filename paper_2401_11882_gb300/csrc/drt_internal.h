@@ -64,6 +64,23 @@ struct FieldArgs {
   float* power;      // [R] or null
 };
 
+// 3D forward (drt_forward3d.cu): triangle walls, 3D receivers, one receiver per lane.
+struct Fwd3Args {
+  const float* tris;   // [W][9]
+  int W;
+  const float* rx;     // [R][3]
+  long long R;
+  const float* tx;     // [3]
+  int K;
+  float alpha;
+  float gk[DRT_MAX_ORDER + 1];
+  long long n_cand;
+  int chunk;
+  long long n_chunks, n_tiles, n_units;
+  float* partial;      // [n_chunks][R]
+  float* power;        // [R]
+};
+
 struct VjpArgs {
   const float4* walls;
   int W;
@@ -105,6 +122,11 @@ cudaError_t forward_set_smem_limit(int W);
 cudaError_t launch_loss(const float* power, int R, float* loss, int32_t* argmin, cudaStream_t st);
 cudaError_t launch_loss_backward(const int32_t* argmin, const float* grad_loss, int R,
                                  float* grad_power, cudaStream_t st);
+
+size_t forward3_smem_bytes(int W);
+cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t forward3_set_smem_limit(int W);
 
 cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t field_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);

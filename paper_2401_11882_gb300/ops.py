@@ -150,6 +150,31 @@ def field_vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavel
     return gtx, gw
 
 
+def forward3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+             refl_coef: float = 0.5, tile: TileConfig | None = None) -> torch.Tensor:
+    """Received power per receiver of a 3D scene of triangle walls (float32 [R]) on the
+    current stream: tris [W, 9] (corners A, B, C), tx [3], rx [R, 3] (drt3_forward)."""
+    tris = _as_f32(tris, 9, "tris", 4)
+    rx = _as_f32(rx, 3, "rx", 4)
+    tx = _as_f32(tx.reshape(1, 3), 3, "tx", 4)
+    if tris.device != rx.device or tris.device != tx.device:
+        raise ValueError("tris, tx and rx must be on the same device")
+    if smoothing not in _lib.SMOOTHING:
+        raise ValueError(f"unknown smoothing {smoothing!r}")
+    sc = _lib.Scene3(tris.data_ptr(), tris.shape[0], rx.data_ptr(), rx.shape[0], tx.data_ptr(),
+                     int(max_order), float(alpha), _lib.SMOOTHING[smoothing], float(refl_coef))
+    dev = tris.device
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt3_forward_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    _lib.call("drt3_forward", ctypes.byref(sc), tlp, _ptr(power), _ptr(ws),
+              ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return power
+
+
 def tune_forward_timings(walls, tx, rx, max_order: int, alpha: float, smoothing: str,
                          candidates, refl_coef: float = 0.5, reps: int = 3):
     """Times drt_forward with each TileConfig of ``candidates`` in the library

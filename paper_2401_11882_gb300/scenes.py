@@ -218,3 +218,77 @@ def scene_batch(n_scenes: int = 4096, seed: int = 0, walls_range=(8, 256), rx_ra
     return SceneBatch(np.concatenate(walls), np.asarray(w_off, np.int32), np.concatenate(rxs),
                       np.asarray(r_off, np.int32), np.asarray(ks, np.int32),
                       np.stack(txs).astype(np.float32), alpha, smoothing)
+
+
+# --------------------------------------------------------------------------- 3D scenes
+@dataclass
+class Scene3:
+    """One 3D scene: triangle walls, one TX, a set of RX, and the smoothing knobs."""
+
+    tris: np.ndarray           # float32 [W, 9]: corners A, B, C as x, y, z
+    tx: np.ndarray             # float32 [3]
+    rx: np.ndarray             # float32 [R, 3]
+    max_order: int = 1
+    alpha: float = 100.0
+    smoothing: str = "hard_sigmoid"
+    refl_coef: float = 0.5
+    name: str = ""
+
+    def __post_init__(self):
+        self.tris = np.ascontiguousarray(self.tris, dtype=np.float32).reshape(-1, 9)
+        self.tx = np.ascontiguousarray(self.tx, dtype=np.float32).reshape(3)
+        self.rx = np.ascontiguousarray(self.rx, dtype=np.float32).reshape(-1, 3)
+        if self.smoothing not in SMOOTHINGS:
+            raise ValueError(f"unknown smoothing {self.smoothing!r}")
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
+
+    @property
+    def n_rx(self) -> int:
+        return int(self.rx.shape[0])
+
+
+def extrude(walls: np.ndarray, z0: float, z1: float) -> np.ndarray:
+    """Vertical rectangles z in [z0, z1] over 2D walls [W, 4], two triangles each ([2W, 9])."""
+    out = []
+    for x0, y0, x1, y1 in np.asarray(walls, np.float64):
+        a, b = (x0, y0, z0), (x1, y1, z0)
+        c, d = (x1, y1, z1), (x0, y0, z1)
+        out.append(a + b + c)
+        out.append(a + c + d)
+    return np.array(out, dtype=np.float32).reshape(-1, 9)
+
+
+def room3d(grid: int = 128, alpha: float = 100.0, smoothing: str = "hard_sigmoid",
+           max_order: int = 2) -> Scene3:
+    """The 64-wall scene of ``large_scene`` as a room of height 1: its walls extruded over
+    z in [0, 1] (128 triangles) plus a floor and a ceiling (2 triangles each), 132
+    triangles; TX (0.5, 0.2, 0.5); a grid x grid receiver plane at z = 0.3."""
+    base = clutter_scene(60, 2, 0, alpha, smoothing, 2, True)
+    corners = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float64)
+    slabs = []
+    for z, order in ((0.0, (0, 1, 2, 3)), (1.0, (0, 3, 2, 1))):
+        p = [tuple(corners[i]) + (z,) for i in order]
+        slabs.append(p[0] + p[1] + p[2])
+        slabs.append(p[0] + p[2] + p[3])
+    tris = np.concatenate([extrude(base.walls, 0.0, 1.0),
+                           np.array(slabs, dtype=np.float32).reshape(-1, 9)])
+    rx2 = rx_grid(grid)
+    rx = np.concatenate([rx2, np.full((rx2.shape[0], 1), 0.3, np.float32)], 1)
+    return Scene3(tris, np.array([0.5, 0.2, 0.5], np.float32), rx, max_order=max_order,
+                  alpha=alpha, smoothing=smoothing, name="room3d")
+
+
+def random_scene3(rng: np.random.Generator, n_tris: int, n_rx: int, max_order: int, alpha: float,
+                  smoothing: str) -> Scene3:
+    """Random triangles (corners within 0.35 of a centre in [0.1, 0.9]^3), TX and RX in the
+    unit cube (triangles, then TX, then RX drawn in that order)."""
+    centre = rng.uniform(0.1, 0.9, (n_tris, 1, 3))
+    tris = (centre + rng.uniform(-0.35, 0.35, (n_tris, 3, 3))).reshape(n_tris, 9)
+    tx = rng.uniform(0.1, 0.9, 3)
+    rx = rng.uniform(0.05, 0.95, (n_rx, 3))
+    rx = rx[np.linalg.norm(rx - tx, axis=1) > 1e-2]
+    return Scene3(tris, tx, rx, max_order=max_order, alpha=alpha, smoothing=smoothing,
+                  name=f"random {n_tris} triangles")

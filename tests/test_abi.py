@@ -122,3 +122,23 @@ def test_field_vjp_rejects_bad_args_before_any_launch(lib, wavelength, eps_r, fi
                            None if gw_ptr is None else ctypes.c_void_p(gw_ptr),
                            ctypes.c_void_p(256), 1 << 20, None)
     assert st == 1 and len(lib.drt_last_error()) > 0
+
+
+def _scene3(**kw):
+    from paper_2401_11882_gb300 import _lib
+    d = dict(tris=16, n_tris=4, rx=64, n_rx=3, tx=128, max_order=1, alpha=10.0, smoothing=1,
+             refl_coef=0.5)
+    d.update(kw)
+    return _lib.Scene3(**d)
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("n_tris", 0, 1), ("n_tris", 5000, 2), ("max_order", 4, 2), ("alpha", -1.0, 1),
+    ("smoothing", 7, 1), ("tris", 0, 1), ("tris", 2, 1), ("rx", 6, 1), ("n_rx", -1, 1),
+    ("refl_coef", float("nan"), 1)])
+def test_forward3_rejects_bad_scene_before_any_launch(lib, field, value, status):
+    sc = _scene3(**{field: value})
+    out = ctypes.c_size_t()
+    assert lib.drt3_forward_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == status
+    assert lib.drt3_forward(ctypes.byref(sc), None, ctypes.c_void_p(256), None, 0, None) == status
+    assert len(lib.drt_last_error()) > 0

@@ -150,3 +150,24 @@ def test_alpha_zero_closed_form(oracle_mod):
                 tests = (k + 1) * W - 2 * k
                 ref += GAMMA ** k * 16.0 ** -k * (15.0 / 16.0) ** tests / L ** 2
         np.testing.assert_allclose(P, ref, rtol=1e-12)
+
+
+def test_two_triangles_of_one_mirror_reflect_once(oracle_mod):
+    # a square mirror made of two triangles: a path cannot reflect on it twice in a
+    # row (the leg between the two reflections has zero length), so K = 2 adds nothing
+    # to K = 1, even with the reflection point on the shared diagonal, where the
+    # smoothed on-object tests of both triangles are 1/2
+    sq = np.array([[-1.0, -1.0, 0.0, 1.0, -1.0, 0.0, 1.0, 1.0, 0.0],
+                   [-1.0, -1.0, 0.0, 1.0, 1.0, 0.0, -1.0, 1.0, 0.0]])
+    tx = np.array([0.3, 0.3, 1.0])
+    rx = np.array([[-0.3, -0.3, 1.0], [-0.2, -0.25, 0.7]])
+    for fn, alpha in (("hard_sigmoid", 10.0), ("sigmoid", 10.0)):
+        P1 = _P3(oracle_mod, sq, tx, rx, 1, alpha, fn)
+        P2 = _P3(oracle_mod, sq, tx, rx, 2, alpha, fn)
+        np.testing.assert_array_equal(P2, P1)
+    # on the diagonal the two halves' on-object tests add up to one (C4), and neither
+    # half blocks a leg that starts or ends on the other (same plane)
+    d1 = np.sum((rx[0] - np.array([0.3, 0.3, -1.0])) ** 2)
+    P = _P3(oracle_mod, sq, tx, rx[:1], 1, 10.0, "hard_sigmoid")[0]
+    d0 = np.sum((rx[0] - tx) ** 2)
+    assert P == pytest.approx(1.0 / d0 + GAMMA / d1, rel=1e-12)

@@ -79,6 +79,10 @@ MUTANTS = {
                               "const double cross_plane = smooth(x, al, kind) * smooth(y, al, kind) +"),
     "3d same-side term": ("smooth(-p, al, kind) * smooth(-q, al, kind);",
                           "smooth(-p, al, kind) * smooth(q, al, kind);"),
+    "3d coplanar pair kept": ("if (coplanar(tris[seq[j - 1]], tris[seq[j]])) return 0.0;",
+                              "if (false) return 0.0;"),
+    "3d coplanar triangles tested": ("if (j >= 1 && coplanar(t, tris[seq[j - 1]])) continue;",
+                                     "if (j >= 1 && &t == &tris[seq[j - 1]]) continue;"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
