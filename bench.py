@@ -366,6 +366,18 @@ def measure_extras(drt, dev, sc, w, t, r):
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
                                   tile=drt.TileConfig(single_rx=True)))
     out["hard_forward_one_rx_per_lane_evals_per_s"] = ev / s
+    # 3D: the 64-wall scene as a room of 132 triangles, 128 x 128 receivers, K <= 2
+    r3 = scenes.room3d(128)
+    w3, t3, x3 = (torch.tensor(a, device=dev) for a in (r3.tris, r3.tx, r3.rx))
+    n3 = r3.n_rx * workload.num_candidates(r3.n_tris, r3.max_order)
+    s3h = timed(lambda: drt.forward3(w3, t3, x3, 2, 100.0, "hard_sigmoid"), 3)
+    s3s = timed(lambda: drt.forward3(w3, t3, x3, 2, 100.0, "sigmoid"), 1)
+    out["room3d_forward"] = {
+        "workload": "64-wall scene as a room (walls extruded over z in [0, 1], floor, ceiling: "
+                    "132 triangles), 128x128 receivers at z = 0.3, K<=2 (17425 sequences), alpha=100",
+        "hard_ms": s3h * 1e3, "hard_evals_per_s": n3 / s3h,
+        "sigmoid_ms": s3s * 1e3, "sigmoid_evals_per_s": n3 / s3s,
+        "note": "warps whose paths all have validity exactly 0 skip their obstruction loop"}
     # coherent field (Eq. 7 with complex path fields, Fresnel TE, eps_r 5, wavelength 0.02)
     s = timed(lambda: drt.field(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid", 0.02, 5.0))
     out["coherent_field_hard_evals_per_s"] = ev / s
