@@ -195,6 +195,16 @@ drt_status drt3_forward_workspace_size(const drt3_scene* scene, const drt_tile* 
 drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* power,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* Transmitter gradient of drt3_forward: grad_tx = sum_r grad_power[r] dP_r / dTX
+   (reverse mode with the path recomputed, as drt_vjp; the gradient the antenna
+   placement of Sec. VII needs).  grad_power: [n_rx] device; grad_tx: [3] device,
+   overwritten; workspace: at least drt3_vjp_tx_workspace_size bytes (per-warp
+   partials, added in a fixed order: deterministic). */
+drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* tile,
+                                      size_t* bytes);
+drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
+                       float* grad_tx, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Autotuner probe for drt_forward (the work decomposition does not change the
    result beyond the order of the per-chunk sums): runs drt_forward on `scene`
    with each of the n_cand tiles of `cands` (host array), one untimed launch

@@ -22,6 +22,7 @@ Functions and the passages they follow:
 * ``field_jvp``, ``field_gradient``  its exact forward-mode derivative, and the gradient of
                         sum_r g_r |E_r|^2
 * ``power3``          Sec. VI's 3D extension for triangle walls (same steps, planes for lines)
+* ``power3_jvp``, ``gradient3_tx``  its exact forward-mode derivative; the TX gradient
 * ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
                         finders' convergence check compares with zero (``oracle/mpt.py``)
 
@@ -82,6 +83,7 @@ def _load():
         lib.drt_oracle_field.argtypes = [p, i, p, p, i, i, d, i, d, d, d, i, p, p, p]
         lib.drt_oracle_field_jvp.argtypes = [p, i, p, p, i, i, d, i, d, d, d, p, p, i, p, p]
         lib.drt_oracle_power3.argtypes = [p, i, p, p, i, i, d, i, d, i, p]
+        lib.drt_oracle_power3_jvp.argtypes = [p, i, p, p, i, i, d, i, d, p, p, i, p, p]
         _lib = lib
         return lib
 
@@ -287,6 +289,41 @@ def power3(tris, tx, rx, max_order: int, alpha: float, smoothing, refl_coef: flo
                                    float(refl_coef), _threads(threads), _ptr(out))
     if rc:
         raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def power3_jvp(tris, tx, rx, max_order, alpha, smoothing, dtris, dtx, refl_coef=0.5,
+               threads=None):
+    """(P, dP): the 3D power and its exact derivative along (dtris [W, 9], dtx [3])."""
+    tris = _f64(tris).reshape(-1, 9)
+    tx = _f64(tx).reshape(3)
+    rx = _f64(rx).reshape(-1, 3)
+    dtris, dtx = _f64(dtris).reshape(tris.shape), _f64(dtx).reshape(3)
+    P = np.zeros(rx.shape[0]); dP = np.zeros(rx.shape[0])
+    rc = _load().drt_oracle_power3_jvp(_ptr(tris), tris.shape[0], _ptr(tx), _ptr(rx),
+                                       rx.shape[0], int(max_order), float(alpha),
+                                       _kind(smoothing), float(refl_coef), _ptr(dtris),
+                                       _ptr(dtx), _threads(threads), _ptr(P), _ptr(dP))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return P, dP
+
+
+def gradient3_tx(tris, tx, rx, max_order, alpha, smoothing, g, refl_coef=0.5, threads=None):
+    """sum_r g_r dP_r / d(TX) [3] of a 3D scene."""
+    tris = _f64(tris).reshape(-1, 9)
+    rx = _f64(rx).reshape(-1, 3)
+    g = _f64(g).reshape(-1)
+    nz = np.nonzero(g)[0]
+    out = np.zeros(3)
+    if nz.size == 0:
+        return out
+    for a in range(3):
+        dtx = np.zeros(3)
+        dtx[a] = 1.0
+        _, dP = power3_jvp(tris, tx, rx[nz], max_order, alpha, smoothing, np.zeros_like(tris),
+                           dtx, refl_coef, threads)
+        out[a] = float(np.dot(g[nz], dP))
     return out
 
 

@@ -73,6 +73,8 @@ inline Dual operator/(double a, Dual b) { return Dual(a) / b; }
 inline Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
 inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, a.d * e); }
 inline Dual sqrt(Dual a) { double r = std::sqrt(a.v); return Dual(r, a.d / (2.0 * r)); }
+inline Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+inline Dual& operator*=(Dual& a, Dual b) { return a = a * b; }
 inline Dual cos(Dual a) { return Dual(std::cos(a.v), -a.d * std::sin(a.v)); }
 inline Dual sin(Dual a) { return Dual(std::sin(a.v), a.d * std::cos(a.v)); }
 
@@ -409,113 +411,157 @@ void set_threads(int nthreads) {
 //   path power Gamma^k V vis / L^2 as in 2D;
 //   two consecutive reflections on triangles of one plane (normals parallel and
 //   offsets equal to within 1e-5): a degenerate path (zero-length leg), power 0.
+template <class T>
 struct V3 {
-  double x, y, z;
+  T x, y, z;
 };
-V3 operator+(const V3& a, const V3& b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
-V3 operator-(const V3& a, const V3& b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
-V3 operator*(double s, const V3& a) { return V3{s * a.x, s * a.y, s * a.z}; }
-double dot(const V3& a, const V3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-V3 cross(const V3& a, const V3& b) {
-  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+template <class T>
+V3<T> operator+(const V3<T>& a, const V3<T>& b) { return V3<T>{a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T>
+V3<T> operator-(const V3<T>& a, const V3<T>& b) { return V3<T>{a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T, class S>
+V3<T> operator*(const S& s, const V3<T>& a) { return V3<T>{s * a.x, s * a.y, s * a.z}; }
+template <class T>
+T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T>
+V3<T> cross(const V3<T>& a, const V3<T>& b) {
+  return V3<T>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
-double norm(const V3& a) { return std::sqrt(dot(a, a)); }
+template <class T>
+T norm(const V3<T>& a) { return sqrt(dot(a, a)); }
 
+template <class T>
 struct Tri {
-  V3 v[3];   // corners A, B, C
-  V3 n;      // unit normal
-  double c;  // n . A
-  V3 m[3];   // in-plane unit normals of the edges, pointing inside
+  V3<T> v[3];   // corners A, B, C
+  V3<T> n;      // unit normal
+  T c;          // n . A
+  V3<T> m[3];   // in-plane unit normals of the edges, pointing inside
 };
 
-Tri make_tri(const double* p) {
-  Tri t;
-  for (int i = 0; i < 3; ++i) t.v[i] = V3{p[3 * i], p[3 * i + 1], p[3 * i + 2]};
-  V3 nn = cross(t.v[1] - t.v[0], t.v[2] - t.v[0]);
+template <class T>
+Tri<T> make_tri(const T* p) {
+  Tri<T> t;
+  for (int i = 0; i < 3; ++i) t.v[i] = V3<T>{p[3 * i], p[3 * i + 1], p[3 * i + 2]};
+  V3<T> nn = cross(t.v[1] - t.v[0], t.v[2] - t.v[0]);
   t.n = (1.0 / norm(nn)) * nn;
   t.c = dot(t.n, t.v[0]);
   for (int k = 0; k < 3; ++k) {
-    V3 e = t.v[(k + 1) % 3] - t.v[k];
+    V3<T> e = t.v[(k + 1) % 3] - t.v[k];
     t.m[k] = (1.0 / norm(e)) * cross(t.n, e);
   }
   return t;
 }
 
-double plane_dist(const Tri& t, const V3& p) { return dot(t.n, p) - t.c; }
-double edge_dist(const Tri& t, int k, const V3& p) { return dot(t.m[k], p - t.v[k]); }
+template <class T>
+T plane_dist(const Tri<T>& t, const V3<T>& p) { return dot(t.n, p) - t.c; }
+template <class T>
+T edge_dist(const Tri<T>& t, int k, const V3<T>& p) { return dot(t.m[k], p - t.v[k]); }
 
 // prod_k s(delta_k(p)): p (on the plane) inside the triangle
-double inside(const Tri& t, const V3& p, double alpha, int kind) {
-  double r = 1.0;
+template <class T>
+T inside(const Tri<T>& t, const V3<T>& p, double alpha, int kind) {
+  T r = T(1.0);
   for (int k = 0; k < 3; ++k) r *= smooth(edge_dist(t, k, p), alpha, kind);
   return r;
 }
 
 // Triangles a and b lie in one plane (normals parallel, offsets equal, to 1e-5).
-bool coplanar(const Tri& ta, const Tri& tb) {
-  const double nn = dot(ta.n, tb.n);
-  return std::fabs(nn) >= 1.0 - 1e-5 && std::fabs(ta.c - nn * tb.c) <= 1e-5 * (1.0 + std::fabs(ta.c));
+template <class T>
+bool coplanar(const Tri<T>& ta, const Tri<T>& tb) {
+  const double nn = re(dot(ta.n, tb.n));
+  return std::fabs(nn) >= 1.0 - 1e-5 && std::fabs(re(ta.c) - nn * re(tb.c)) <= 1e-5 * (1.0 + std::fabs(re(ta.c)));
 }
 
-double path_power3(const std::vector<Tri>& tris, const V3& tx, const V3& rx,
-                   const std::vector<int>& seq, const Params& P) {
+template <class T>
+T path_power3(const std::vector<Tri<T>>& tris, const V3<T>& tx, const V3<T>& rx,
+              const std::vector<int>& seq, const Params& P) {
   const int k = (int)seq.size();
   const int W = (int)tris.size();
-  std::vector<V3> img(k + 1);
+  std::vector<V3<T>> img(k + 1);
   img[0] = tx;
   for (int j = 1; j <= k; ++j) {
-    const Tri& t = tris[seq[j - 1]];
+    const Tri<T>& t = tris[seq[j - 1]];
     img[j] = img[j - 1] - (2.0 * plane_dist(t, img[j - 1])) * t.n;
   }
   // two consecutive reflections in one plane (two triangles of one flat face): the
   // leg between them has zero length, so the path is degenerate
   for (int j = 1; j < k; ++j)
-    if (coplanar(tris[seq[j - 1]], tris[seq[j]])) return 0.0;
-  std::vector<V3> Q(k + 2);
+    if (coplanar(tris[seq[j - 1]], tris[seq[j]])) return T(0.0);
+  std::vector<V3<T>> Q(k + 2);
   Q[0] = tx;
   Q[k + 1] = rx;
   for (int j = k; j >= 1; --j) {
-    const Tri& t = tris[seq[j - 1]];
-    const double a = plane_dist(t, img[j]);
-    const double b = plane_dist(t, Q[j + 1]);
-    if (b - a == 0.0) return 0.0;
+    const Tri<T>& t = tris[seq[j - 1]];
+    const T a = plane_dist(t, img[j]);
+    const T b = plane_dist(t, Q[j + 1]);
+    if (re(b) - re(a) == 0.0) return T(0.0);
     Q[j] = Q[j + 1] + (b / (b - a)) * (img[j] - Q[j + 1]);
   }
-  double L = 0.0;
+  T L = T(0.0);
   for (int j = 0; j <= k; ++j) {
-    const double l = norm(Q[j + 1] - Q[j]);
-    if (l == 0.0) return 0.0;
+    const T l = norm(Q[j + 1] - Q[j]);
+    if (re(l) == 0.0) return T(0.0);
     L += l;
   }
   const double al = P.alpha;
   const int kind = P.kind;
-  double validity = 1.0;
+  T validity = T(1.0);
   for (int j = 1; j <= k; ++j) {
-    const Tri& t = tris[seq[j - 1]];
-    const double p = plane_dist(t, Q[j - 1]), q = plane_dist(t, Q[j + 1]);
-    const double same_side = smooth(p, al, kind) * smooth(q, al, kind) +
-                             smooth(-p, al, kind) * smooth(-q, al, kind);
+    const Tri<T>& t = tris[seq[j - 1]];
+    const T p = plane_dist(t, Q[j - 1]), q = plane_dist(t, Q[j + 1]);
+    const T same_side = smooth(p, al, kind) * smooth(q, al, kind) +
+                        smooth(-p, al, kind) * smooth(-q, al, kind);
     validity *= inside(t, Q[j], al, kind) * same_side;
   }
   // a leg meets the plane of an end point's triangle only at that end point: it is
   // not tested against any triangle of that plane
-  double visibility = 1.0;
+  T visibility = T(1.0);
   for (int j = 0; j <= k; ++j) {
     for (int wi = 0; wi < W; ++wi) {
-      const Tri& t = tris[wi];
+      const Tri<T>& t = tris[wi];
       if (j >= 1 && coplanar(t, tris[seq[j - 1]])) continue;
       if (j + 1 <= k && coplanar(t, tris[seq[j]])) continue;
-      const double x = plane_dist(t, Q[j]), y = plane_dist(t, Q[j + 1]);
-      const double cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +
-                                 smooth(-x, al, kind) * smooth(y, al, kind);
-      if (x - y == 0.0) continue;   // the leg's line never meets the plane
-      const V3 hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);
+      const T x = plane_dist(t, Q[j]), y = plane_dist(t, Q[j + 1]);
+      const T cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +
+                            smooth(-x, al, kind) * smooth(y, al, kind);
+      if (re(x) - re(y) == 0.0) continue;   // the leg's line never meets the plane
+      const V3<T> hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);
       visibility *= 1.0 - cross_plane * inside(t, hit, al, kind);
     }
   }
   double gk = 1.0;
   for (int j = 0; j < k; ++j) gk *= P.gamma;
   return gk * validity * visibility / (L * L);
+}
+
+// an input value with its tangent (dropped for plain values)
+template <class T>
+T input(double v, double d);
+template <>
+double input<double>(double v, double) { return v; }
+template <>
+Dual input<Dual>(double v, double d) { return Dual(v, d); }
+
+template <class T>
+int power3_impl(const double* tris_xyz, const double* dtris, int W, const double* tx,
+                const double* dtx, const double* rx, int R, int K, double alpha, int kind,
+                double gamma, T* out) {
+  std::vector<T> xyz(9 * W);
+  for (int i = 0; i < 9 * W; ++i) xyz[i] = input<T>(tris_xyz[i], dtris ? dtris[i] : 0.0);
+  std::vector<Tri<T>> tris;
+  for (int i = 0; i < W; ++i) tris.push_back(make_tri<T>(&xyz[9 * i]));
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  const V3<T> t{input<T>(tx[0], dtx ? dtx[0] : 0.0), input<T>(tx[1], dtx ? dtx[1] : 0.0),
+                input<T>(tx[2], dtx ? dtx[2] : 0.0)};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < R; ++r) {
+    const V3<T> q{T(rx[3 * r]), T(rx[3 * r + 1]), T(rx[3 * r + 2])};
+    T sum = T(0.0);
+    for (const auto& seq : cands) sum += path_power3(tris, t, q, seq, prm);
+    out[r] = sum;
+  }
+  return 0;
 }
 
 }  // namespace
@@ -527,21 +573,25 @@ int drt_oracle_power3(const double* tris_xyz, int W, const double* tx, const dou
                       int K, double alpha, int kind, double gamma, int nthreads, double* Pw) {
   if (check_args(tris_xyz, W, tx, rx, R, K, alpha, kind)) return 1;
   set_threads(nthreads);
-  std::vector<Tri> tris;
-  for (int i = 0; i < W; ++i) tris.push_back(make_tri(tris_xyz + 9 * i));
-  auto cands = candidates(W, K);
-  Params prm{K, alpha, kind, gamma};
-  const V3 t{tx[0], tx[1], tx[2]};
-#pragma omp parallel for schedule(dynamic, 1)
-  for (int r = 0; r < R; ++r) {
-    const V3 q{rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]};
-    double sum = 0.0;
-    for (const auto& seq : cands) sum += path_power3(tris, t, q, seq, prm);
-    Pw[r] = sum;
-  }
-  return 0;
+  return power3_impl<double>(tris_xyz, nullptr, W, tx, nullptr, rx, R, K, alpha, kind, gamma, Pw);
 }
 
+// Forward-mode derivative of the 3D power along (dtris [W][9], dtx [3]).
+int drt_oracle_power3_jvp(const double* tris_xyz, int W, const double* tx, const double* rx,
+                          int R, int K, double alpha, int kind, double gamma,
+                          const double* dtris, const double* dtx, int nthreads, double* Pw,
+                          double* dP) {
+  if (check_args(tris_xyz, W, tx, rx, R, K, alpha, kind) || !dtris || !dtx) return 1;
+  set_threads(nthreads);
+  std::vector<Dual> out(R > 0 ? R : 1);
+  const int rc = power3_impl<Dual>(tris_xyz, dtris, W, tx, dtx, rx, R, K, alpha, kind, gamma,
+                                   out.data());
+  for (int r = 0; r < R; ++r) {
+    if (Pw) Pw[r] = out[r].v;
+    dP[r] = out[r].d;
+  }
+  return rc;
+}
 
 // Number of path candidates for W walls and maximum order K.
 long long drt_oracle_num_candidates(int W, int K) {

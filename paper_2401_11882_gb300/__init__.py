@@ -9,16 +9,16 @@ Public calls (PyTorch tensors on a CUDA device, float32):
 * ``field(...)``: the coherent reading of Eq. 7 (complex path fields, Fresnel
   reflection), field and power per receiver; ``field_power(...)`` is its power
   |E|^2, differentiable in ``walls`` and ``tx``; ``field_vjp`` the raw adjoint.
-* ``forward3(tris, tx, rx, ...)``: the 3D extension (triangle walls), power per receiver.
+* ``forward3(tris, tx, rx, ...)``: the 3D extension (triangle walls), power per receiver;
+  ``power3`` differentiable in ``tx``; ``vjp3_tx`` its raw transmitter adjoint.
 
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
 from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, loss, min_loss,
                   min_loss_backward, min_loss_vjp, num_candidates, objective, objective_host,
-                  power, vjp)
+                  power, power3, vjp, vjp3_tx)
 
 __all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "forward3", "loss",
-           "min_loss",
-           "min_loss_backward", "min_loss_vjp", "num_candidates", "objective", "objective_host",
-           "power", "vjp"]
+           "min_loss", "min_loss_backward", "min_loss_vjp", "num_candidates", "objective",
+           "objective_host", "power", "power3", "vjp", "vjp3_tx"]

@@ -82,6 +82,8 @@ SIGNATURES = {
     "drt_field": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     "drt3_forward_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt3_forward": (ctypes.c_int, [_P, _P, _P, _P, _SZ, _P]),
+    "drt3_vjp_tx_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt3_vjp_tx": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
     "drt_field_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_field_vjp": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P, _P,
                                      _SZ, _P]),

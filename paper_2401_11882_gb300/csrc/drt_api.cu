@@ -115,7 +115,7 @@ drt_status check_tile(const drt_tile* t) {
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
 
-enum Kernel { FWD, VJP, FIELD, FIELD_VJP, FWD3 };
+enum Kernel { FWD, VJP, FIELD, FIELD_VJP, FWD3, VJP3 };
 
 drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
   int sms = 0;
@@ -145,6 +145,7 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
                     : (kern == FIELD)     ? field_occupancy(mode, d->pairs, d->threads, W, &per_sm)
                     : (kern == FIELD_VJP) ? field_vjp_occupancy(mode, true, d->threads, W, &per_sm)
                     : (kern == FWD3)      ? forward3_occupancy(mode, d->threads, W, &per_sm)
+                    : (kern == VJP3)      ? vjp3_occupancy(mode, d->threads, W, &per_sm)
                                           : vjp_occupancy(mode, true, d->threads, W, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
@@ -384,6 +385,56 @@ drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* po
   cudaError_t e = launch_forward3(a, scene->smoothing, d.ctas, d.threads,
                                   static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "3D forward launch");
+  return DRT_OK;
+}
+
+drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* tile,
+                                      size_t* bytes) {
+  drt_scene flat;
+  drt_status st = check_scene3(scene, &flat);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(&flat, tile, VJP3, &d)) != DRT_OK) return st;
+  *bytes = (size_t)d.ctas * (d.threads / 32) * 3 * sizeof(float);
+  return DRT_OK;
+}
+
+drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
+                       float* grad_tx, void* workspace, size_t workspace_bytes, void* stream) {
+  drt_scene flat;
+  drt_status st = check_scene3(scene, &flat);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!grad_tx || (scene->n_rx > 0 && !grad_power))
+    return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  Decomp d;
+  if ((st = decompose(&flat, tile, VJP3, &d)) != DRT_OK) return st;
+  const size_t need = (size_t)d.ctas * (d.threads / 32) * 3 * sizeof(float);
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 4))
+    return fail(DRT_ERR_WORKSPACE, "3D vjp needs %zu workspace bytes, got %zu", need,
+                workspace_bytes);
+  Vjp3Args a;
+  a.tris = scene->tris;
+  a.W = scene->n_tris;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.grad_power = grad_power;
+  a.warp_tx = static_cast<float*>(workspace);
+  a.grad_tx = grad_tx;
+  cudaError_t e = launch_vjp3(a, scene->smoothing, d.ctas, d.threads,
+                              static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "3D vjp launch");
   return DRT_OK;
 }
 

@@ -223,6 +223,344 @@ __global__ void __launch_bounds__(256, 2) forward3_kernel(const Fwd3Args a) {
   }
 }
 
+// ------------------------------------------------------------ TX adjoint
+// Reverse mode of path_power3 for the transmitter only (the gradient the antenna
+// placement of Sec. VII needs): recompute the path, sweep the triangles once for
+// each leg's visibility as (product of the non-zero factors, number of zero
+// factors), then once more pushing each factor's adjoint into the path vertices;
+// the vertex adjoints flow back through the leg lengths, the validity, the
+// backtrace and the image chain to the transmitter.  A path with an exactly-zero
+// factor has an exactly-zero gradient (a saturated smoothing), as in 2D.
+struct LegTri {
+  float x, y, X, t, ins, f;
+  Smooth3 sx, sy, sd[3];
+  float e0[3], e1[3];
+};
+
+template <int MODE>
+__device__ __forceinline__ bool leg_tri(const float4& P, const float4* M, float3 a, float3 b,
+                                        float alpha, LegTri& r) {
+  r.x = dot3(P, a) - P.w;
+  r.y = dot3(P, b) - P.w;
+  r.sx = smooth3<MODE>(r.x, alpha);
+  r.sy = smooth3<MODE>(r.y, alpha);
+  r.X = fmaf(r.sx.s, r.sy.sb, r.sx.sb * r.sy.s);
+  r.t = __fdividef(r.x, r.x - r.y);
+  if (!(fabsf(r.t) <= 1e8f)) return false;
+  r.ins = 1.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.e0[k] = dot3(M[k], a) - M[k].w;
+    r.e1[k] = dot3(M[k], b) - M[k].w;
+    r.sd[k] = smooth3<MODE>(fmaf(r.t, r.e1[k] - r.e0[k], r.e0[k]), alpha);
+    r.ins *= r.sd[k].s;
+  }
+  r.f = fmaf(-r.X, r.ins, 1.f);
+  return true;
+}
+
+__device__ __forceinline__ void axpy3(float a, float4 v, float3& acc) {
+  acc.x = fmaf(a, v.x, acc.x);
+  acc.y = fmaf(a, v.y, acc.y);
+  acc.z = fmaf(a, v.z, acc.z);
+}
+
+template <int MODE, int K>
+__device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, float3 rx,
+                                          const Cand& cd, float alpha, float gk, float g,
+                                          float3& txb) {
+  bool degenerate = false;
+#pragma unroll
+  for (int j = 1; j < K; ++j) {
+    const float4 Pa = s.P[cd.w[j - 1]], Pb = s.P[cd.w[j]];
+    const float nn = fmaf(Pa.x, Pb.x, fmaf(Pa.y, Pb.y, Pa.z * Pb.z));
+    if (fabsf(nn) >= 1.f - 1e-5f && fabsf(fmaf(-nn, Pb.w, Pa.w)) <= 1e-5f * (1.f + fabsf(Pa.w)))
+      degenerate = true;
+  }
+  float3 I[K + 1];
+  I[0] = tx;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 P = s.P[cd.w[j - 1]];
+    const float d2 = 2.f * (dot3(P, I[j - 1]) - P.w);
+    I[j] = make_float3(fmaf(-d2, P.x, I[j - 1].x), fmaf(-d2, P.y, I[j - 1].y),
+                       fmaf(-d2, P.z, I[j - 1].z));
+  }
+  float3 Q[K + 2];
+  float ta[K + 1], tb[K + 1], tt[K + 1];
+  Q[0] = tx;
+  Q[K + 1] = rx;
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 P = s.P[cd.w[j - 1]];
+    ta[j] = dot3(P, I[j]) - P.w;
+    tb[j] = dot3(P, Q[j + 1]) - P.w;
+    float t = __fdiv_rn(tb[j], tb[j] - ta[j]);
+    if (!(fabsf(t) <= 1e8f)) {
+      degenerate = true;
+      t = 0.f;
+    }
+    tt[j] = t;
+    Q[j] = make_float3(fmaf(t, I[j].x - Q[j + 1].x, Q[j + 1].x),
+                       fmaf(t, I[j].y - Q[j + 1].y, Q[j + 1].y),
+                       fmaf(t, I[j].z - Q[j + 1].z, Q[j + 1].z));
+  }
+  float len[K + 1], L = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float dx = Q[j + 1].x - Q[j].x, dy = Q[j + 1].y - Q[j].y, dz = Q[j + 1].z - Q[j].z;
+    const float len2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    degenerate |= !(len2 > 0.f);
+    len[j] = __fsqrt_rn(len2);
+    L += len[j];
+  }
+  if (degenerate) {
+    g = 0.f;
+    L = 1.f;
+  }
+  float V[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 P = s.P[w];
+    const Smooth3 sp = smooth3<MODE>(dot3(P, Q[j - 1]) - P.w, alpha);
+    const Smooth3 sq = smooth3<MODE>(dot3(P, Q[j + 1]) - P.w, alpha);
+    const float4 M0 = s.M0[w], M1 = s.M1[w], M2 = s.M2[w];
+    const float in = smooth3<MODE>(dot3(M0, Q[j]) - M0.w, alpha).s *
+                     smooth3<MODE>(dot3(M1, Q[j]) - M1.w, alpha).s *
+                     smooth3<MODE>(dot3(M2, Q[j]) - M2.w, alpha).s;
+    V[j] = in * fmaf(sp.s, sq.s, sp.sb * sq.sb);
+  }
+  bool dead = degenerate || g == 0.f;
+#pragma unroll
+  for (int j = 1; j <= K; ++j) dead |= (V[j] == 0.f);
+  if (__all_sync(0xffffffffu, dead)) return;
+  float4 Pr[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) Pr[j] = s.P[cd.w[j - 1]];
+  // sweep 1: each leg's visibility as (product of non-zero factors, zero count)
+  float nz[K + 1];
+  int zc[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    nz[j] = 1.f;
+    zc[j] = 0;
+  }
+  for (int w = 0; w < W; ++w) {
+    const float4 P = s.P[w];
+    const float4 M[3] = {s.M0[w], s.M1[w], s.M2[w]};
+    bool cop[K + 2];
+    cop[0] = cop[K + 1] = false;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const float nn = fmaf(P.x, Pr[j].x, fmaf(P.y, Pr[j].y, P.z * Pr[j].z));
+      cop[j] = fabsf(nn) >= 1.f - 1e-5f &&
+               fabsf(fmaf(-nn, Pr[j].w, P.w)) <= 1e-5f * (1.f + fabsf(P.w));
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      if (cop[j] || cop[j + 1]) continue;
+      LegTri r;
+      if (!leg_tri<MODE>(P, M, Q[j], Q[j + 1], alpha, r)) continue;
+      if (r.f == 0.f) zc[j] += 1;
+      else nz[j] *= r.f;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j <= K; ++j) dead |= (zc[j] != 0);
+  if (__all_sync(0xffffffffu, dead)) return;
+  if (dead) g = 0.f;
+  // factor adjoints: p = C prod(F), C = Gamma^k / L^2, F = {V_1..V_K, vis_0..vis_K}
+  constexpr int NF = 2 * K + 1;
+  float F[NF];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) F[j - 1] = V[j];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) F[K + j] = zc[j] ? 0.f : nz[j];
+  float pre[NF + 1], suf[NF + 1];
+  pre[0] = 1.f;
+#pragma unroll
+  for (int i = 0; i < NF; ++i) pre[i + 1] = pre[i] * F[i];
+  suf[NF] = 1.f;
+#pragma unroll
+  for (int i = NF - 1; i >= 0; --i) suf[i] = suf[i + 1] * F[i];
+  const float C = __fdiv_rn(gk, L * L);
+  const float p = C * pre[NF];
+  const float gC = g * C;
+  float Vb[K + 1], visb[K + 1];
+#pragma unroll
+  for (int j = 1; j <= K; ++j) Vb[j] = gC * pre[j - 1] * suf[j];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) visb[j] = gC * pre[K + j] * suf[K + j + 1];
+  const float Lb = -2.f * g * __fdiv_rn(p, L);
+  float3 Qb[K + 2];
+#pragma unroll
+  for (int i = 0; i <= K + 1; ++i) Qb[i] = make_float3(0.f, 0.f, 0.f);
+  // sweep 2: each factor f = 1 - X ins pushes its adjoint into the leg's end points
+  for (int w = 0; w < W; ++w) {
+    const float4 P = s.P[w];
+    const float4 M[3] = {s.M0[w], s.M1[w], s.M2[w]};
+    bool cop[K + 2];
+    cop[0] = cop[K + 1] = false;
+#pragma unroll
+    for (int j = 1; j <= K; ++j) {
+      const float nn = fmaf(P.x, Pr[j].x, fmaf(P.y, Pr[j].y, P.z * Pr[j].z));
+      cop[j] = fabsf(nn) >= 1.f - 1e-5f &&
+               fabsf(fmaf(-nn, Pr[j].w, P.w)) <= 1e-5f * (1.f + fabsf(P.w));
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      if (cop[j] || cop[j + 1]) continue;
+      LegTri r;
+      if (!leg_tri<MODE>(P, M, Q[j], Q[j + 1], alpha, r)) continue;
+      float dvis;
+      if (zc[j] == 0) dvis = __fdiv_rn(nz[j], r.f);
+      else dvis = (zc[j] == 1 && r.f == 0.f) ? nz[j] : 0.f;
+      const float fb = visb[j] * dvis;
+      if (fb == 0.f) continue;
+      const float Xb = -fb * r.ins, inb = -fb * r.X;
+      float xb = Xb * r.sx.ds * (r.sy.sb - r.sy.s);
+      float yb = Xb * r.sy.ds * (r.sx.sb - r.sx.s);
+      float tbar = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float others = r.sd[(k + 1) % 3].s * r.sd[(k + 2) % 3].s;
+        const float db = inb * r.sd[k].ds * others;
+        axpy3(db * (1.f - r.t), M[k], Qb[j]);
+        axpy3(db * r.t, M[k], Qb[j + 1]);
+        tbar = fmaf(db, r.e1[k] - r.e0[k], tbar);
+      }
+      const float den = r.x - r.y;
+      const float id2 = __frcp_rn(den * den);
+      xb = fmaf(tbar * -r.y, id2, xb);
+      yb = fmaf(tbar * r.x, id2, yb);
+      axpy3(xb, P, Qb[j]);
+      axpy3(yb, P, Qb[j + 1]);
+    }
+  }
+  // legs: L = sum |Q_{j+1} - Q_j|
+#pragma unroll
+  for (int j = 0; j <= K; ++j) {
+    const float il = len[j] > 0.f ? __frcp_rn(len[j]) : 0.f;
+    const float4 u = make_float4((Q[j + 1].x - Q[j].x) * il, (Q[j + 1].y - Q[j].y) * il,
+                                 (Q[j + 1].z - Q[j].z) * il, 0.f);
+    axpy3(Lb, u, Qb[j + 1]);
+    axpy3(-Lb, u, Qb[j]);
+  }
+  // validity: on the triangle (three edge tests) and the same-side test
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const int w = cd.w[j - 1];
+    const float4 P = s.P[w];
+    const float4 M[3] = {s.M0[w], s.M1[w], s.M2[w]};
+    const Smooth3 sp = smooth3<MODE>(dot3(P, Q[j - 1]) - P.w, alpha);
+    const Smooth3 sq = smooth3<MODE>(dot3(P, Q[j + 1]) - P.w, alpha);
+    const float S = fmaf(sp.s, sq.s, sp.sb * sq.sb);
+    Smooth3 sdl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sdl[k] = smooth3<MODE>(dot3(M[k], Q[j]) - M[k].w, alpha);
+    const float ins = sdl[0].s * sdl[1].s * sdl[2].s;
+    const float insb = Vb[j] * S, Sb = Vb[j] * ins;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      axpy3(insb * sdl[k].ds * sdl[(k + 1) % 3].s * sdl[(k + 2) % 3].s, M[k], Qb[j]);
+    axpy3(Sb * sp.ds * (sq.s - sq.sb), P, Qb[j - 1]);
+    axpy3(Sb * sq.ds * (sp.s - sp.sb), P, Qb[j + 1]);
+  }
+  // backtrace, reversed: Q_j = Q_{j+1} + t (I_j - Q_{j+1}), t = b / (b - a)
+  float3 Ib[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) Ib[j] = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 1; j <= K; ++j) {
+    const float4 P = s.P[cd.w[j - 1]];
+    const float t = tt[j];
+    const float4 q = make_float4(Qb[j].x, Qb[j].y, Qb[j].z, 0.f);
+    axpy3(1.f - t, q, Qb[j + 1]);
+    axpy3(t, q, Ib[j]);
+    const float tbar = fmaf(Qb[j].x, I[j].x - Q[j + 1].x,
+                            fmaf(Qb[j].y, I[j].y - Q[j + 1].y, Qb[j].z * (I[j].z - Q[j + 1].z)));
+    const float den = tb[j] - ta[j];
+    const float id2 = (den != 0.f && !degenerate) ? __frcp_rn(den * den) : 0.f;
+    axpy3(tbar * tb[j] * id2, P, Ib[j]);
+    axpy3(-tbar * ta[j] * id2, P, Qb[j + 1]);
+  }
+  // image chain, reversed: I_j = I_{j-1} - 2 (n . I_{j-1} - c) n
+#pragma unroll
+  for (int j = K; j >= 1; --j) {
+    const float4 P = s.P[cd.w[j - 1]];
+    const float dbar = -2.f * fmaf(Ib[j].x, P.x, fmaf(Ib[j].y, P.y, Ib[j].z * P.z));
+    Ib[j - 1].x += fmaf(dbar, P.x, Ib[j].x);
+    Ib[j - 1].y += fmaf(dbar, P.y, Ib[j].y);
+    Ib[j - 1].z += fmaf(dbar, P.z, Ib[j].z);
+  }
+  txb.x += Qb[0].x + Ib[0].x;
+  txb.y += Qb[0].y + Ib[0].y;
+  txb.z += Qb[0].z + Ib[0].z;
+}
+
+__device__ __forceinline__ float warp_sum3(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// grad_tx += sum_r g_r dP_r / dTX: lanes are receivers, as in the forward
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) vjp3_kernel(const Vjp3Args a) {
+  extern __shared__ float4 smem[];
+  SmemTris s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
+  stage_tris(a.tris, a.W, s);
+  __syncthreads();
+  const float3 tx = make_float3(__ldg(a.tx), __ldg(a.tx + 1), __ldg(a.tx + 2));
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  float3 txb = make_float3(0.f, 0.f, 0.f);
+  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    long long r = tile * 32 + lane;
+    const bool live = r < a.R;
+    if (!live) r = a.R - 1;
+    const float g = live ? __ldg(a.grad_power + r) : 0.f;
+    if (__all_sync(0xffffffffu, g == 0.f)) continue;
+    const float3 q = make_float3(__ldg(a.rx + 3 * r), __ldg(a.rx + 3 * r + 1),
+                                 __ldg(a.rx + 3 * r + 2));
+    const long long c0 = chunk * a.chunk;
+    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+    for (long long c = c0; c < c1; ++c) {
+      const Cand cd = decode_candidate(c, a.W, a.K);
+      switch (cd.k) {
+        case 0: path_vjp3<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb); break;
+        case 1: path_vjp3<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb); break;
+        case 2: path_vjp3<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb); break;
+        default: path_vjp3<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb); break;
+      }
+    }
+  }
+  txb.x = warp_sum3(txb.x);
+  txb.y = warp_sum3(txb.y);
+  txb.z = warp_sum3(txb.z);
+  if (lane == 0) {
+    a.warp_tx[3 * gwarp] = txb.x;
+    a.warp_tx[3 * gwarp + 1] = txb.y;
+    a.warp_tx[3 * gwarp + 2] = txb.z;
+  }
+}
+
+// grad_tx = sum of the per-warp partials, in warp order (one thread per component)
+__global__ void vjp3_finalize_kernel(const float* __restrict__ warp_tx, long long n_warps,
+                                     float* __restrict__ grad_tx) {
+  const int c = threadIdx.x;
+  if (c < 3) {
+    float acc = 0.f;
+    for (long long w = 0; w < n_warps; ++w) acc += warp_tx[3 * w + c];
+    grad_tx[c] = acc;
+  }
+}
+
 __global__ void reduce3_kernel(const float* __restrict__ partial, long long n_chunks, long long R,
                                float* __restrict__ power) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
@@ -256,6 +594,39 @@ cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cudaStream_t st) {
+  const size_t smem = forward3_smem_bytes(a.W);
+  if (a.n_units > 0) {
+    switch (mode) {
+      case MODE_SIGMOID: vjp3_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_HARD: vjp3_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a); break;
+      default: vjp3_kernel<MODE_STEP><<<ctas, threads, smem, st>>>(a); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vjp3_finalize_kernel<<<1, 32, 0, st>>>(a.warp_tx, (long long)ctas * (threads / 32), a.grad_tx);
+  } else {
+    cudaError_t e = cudaMemsetAsync(a.grad_tx, 0, 3 * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t vjp3_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = forward3_smem_bytes(W);
+  switch (mode) {
+    case MODE_SIGMOID:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_SIGMOID>,
+                                                           threads, smem);
+    case MODE_HARD:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_HARD>,
+                                                           threads, smem);
+    default:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_STEP>,
+                                                           threads, smem);
+  }
+}
+
 cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
   const size_t smem = forward3_smem_bytes(W);
   switch (mode) {
@@ -279,8 +650,17 @@ cudaError_t forward3_set_smem_limit(int W) {
   e = cudaFuncSetAttribute(forward3_kernel<MODE_HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(forward3_kernel<MODE_STEP>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(forward3_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(vjp3_kernel<MODE_SIGMOID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(vjp3_kernel<MODE_HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(vjp3_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem);
 }
 
 }  // namespace drt

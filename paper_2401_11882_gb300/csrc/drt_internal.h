@@ -81,6 +81,24 @@ struct Fwd3Args {
   float* power;        // [R]
 };
 
+// 3D transmitter adjoint (drt_forward3d.cu): lanes are receivers; per-warp partials.
+struct Vjp3Args {
+  const float* tris;
+  int W;
+  const float* rx;
+  long long R;
+  const float* tx;
+  int K;
+  float alpha;
+  float gk[DRT_MAX_ORDER + 1];
+  long long n_cand;
+  int chunk;
+  long long n_chunks, n_tiles, n_units;
+  const float* grad_power;   // [R]
+  float* warp_tx;            // [ctas * warps_per_cta][3]
+  float* grad_tx;            // [3]
+};
+
 struct VjpArgs {
   const float4* walls;
   int W;
@@ -127,6 +145,8 @@ size_t forward3_smem_bytes(int W);
 cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
 cudaError_t forward3_set_smem_limit(int W);
+cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t vjp3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
 
 cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t field_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);

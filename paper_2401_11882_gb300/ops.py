@@ -150,10 +150,7 @@ def field_vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavel
     return gtx, gw
 
 
-def forward3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
-             refl_coef: float = 0.5, tile: TileConfig | None = None) -> torch.Tensor:
-    """Received power per receiver of a 3D scene of triangle walls (float32 [R]) on the
-    current stream: tris [W, 9] (corners A, B, C), tx [3], rx [R, 3] (drt3_forward)."""
+def _scene3(tris, tx, rx, max_order, alpha, smoothing, refl_coef):
     tris = _as_f32(tris, 9, "tris", 4)
     rx = _as_f32(rx, 3, "rx", 4)
     tx = _as_f32(tx.reshape(1, 3), 3, "tx", 4)
@@ -163,7 +160,15 @@ def forward3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
         raise ValueError(f"unknown smoothing {smoothing!r}")
     sc = _lib.Scene3(tris.data_ptr(), tris.shape[0], rx.data_ptr(), rx.shape[0], tx.data_ptr(),
                      int(max_order), float(alpha), _lib.SMOOTHING[smoothing], float(refl_coef))
-    dev = tris.device
+    return sc, (tris, tx, rx)
+
+
+def forward3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+             refl_coef: float = 0.5, tile: TileConfig | None = None) -> torch.Tensor:
+    """Received power per receiver of a 3D scene of triangle walls (float32 [R]) on the
+    current stream: tris [W, 9] (corners A, B, C), tx [3], rx [R, 3] (drt3_forward)."""
+    sc, keep = _scene3(tris, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
     tl = tile.as_c() if tile else None
     tlp = ctypes.byref(tl) if tl is not None else None
     nbytes = ctypes.c_size_t()
@@ -173,6 +178,54 @@ def forward3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
     _lib.call("drt3_forward", ctypes.byref(sc), tlp, _ptr(power), _ptr(ws),
               ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
     return power
+
+
+def vjp3_tx(tris, tx, rx, max_order: int, alpha: float, smoothing: str,
+            grad_power: torch.Tensor, refl_coef: float = 0.5,
+            tile: TileConfig | None = None) -> torch.Tensor:
+    """grad_power^T dP / dTX [3] of a 3D scene (drt3_vjp_tx)."""
+    sc, keep = _scene3(tris, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    gp = _as_f32(grad_power.reshape(-1, 1), 1, "grad_power", 4)
+    if gp.shape[0] != sc.n_rx:
+        raise ValueError("grad_power must have one entry per receiver")
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt3_vjp_tx_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    gtx = torch.empty(3, dtype=torch.float32, device=dev)
+    _lib.call("drt3_vjp_tx", ctypes.byref(sc), tlp, _ptr(gp), _ptr(gtx), _ptr(ws),
+              ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return gtx
+
+
+class Power3Function(torch.autograd.Function):
+    """3D received power, differentiable in the transmitter (drt3_vjp_tx backward)."""
+
+    @staticmethod
+    def forward(ctx, tris, tx, rx, max_order, alpha, smoothing, refl_coef, tile):
+        ctx.save_for_backward(tris, tx, rx)
+        ctx.args = (max_order, alpha, smoothing, refl_coef, tile)
+        return forward3(tris, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
+
+    @staticmethod
+    def backward(ctx, grad_power):
+        tris, tx, rx = ctx.saved_tensors
+        max_order, alpha, smoothing, refl_coef, tile = ctx.args
+        if ctx.needs_input_grad[0]:
+            raise NotImplementedError("the 3D power is differentiable in the transmitter only")
+        if not ctx.needs_input_grad[1]:
+            return (None,) * 8
+        gtx = vjp3_tx(tris, tx, rx, max_order, alpha, smoothing, grad_power.contiguous(),
+                      refl_coef, tile)
+        return None, gtx.reshape(tx.shape), None, None, None, None, None, None
+
+
+def power3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+           refl_coef: float = 0.5, tile: TileConfig | None = None) -> torch.Tensor:
+    """3D received power per receiver, differentiable in ``tx``."""
+    return Power3Function.apply(tris, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
 
 
 def tune_forward_timings(walls, tx, rx, max_order: int, alpha: float, smoothing: str,

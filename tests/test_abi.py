@@ -142,3 +142,13 @@ def test_forward3_rejects_bad_scene_before_any_launch(lib, field, value, status)
     assert lib.drt3_forward_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == status
     assert lib.drt3_forward(ctypes.byref(sc), None, ctypes.c_void_p(256), None, 0, None) == status
     assert len(lib.drt_last_error()) > 0
+
+
+def test_vjp3_tx_rejects_bad_args_before_any_launch(lib):
+    p = ctypes.c_void_p(256)
+    sc = _scene3()
+    assert lib.drt3_vjp_tx(ctypes.byref(sc), None, p, None, p, 1 << 20, None) == 1
+    assert lib.drt3_vjp_tx(ctypes.byref(sc), None, None, p, p, 1 << 20, None) == 1
+    bad = _scene3(n_tris=0)
+    out = ctypes.c_size_t()
+    assert lib.drt3_vjp_tx_workspace_size(ctypes.byref(bad), None, ctypes.byref(out)) == 1

@@ -3,7 +3,7 @@ against the 2D kernel on extruded scenes."""
 import numpy as np
 import pytest
 
-from parity import assert_power_close, fp32_sensitivity
+from parity import assert_grad_close, assert_power_close, fp32_sensitivity
 from paper_2401_11882_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -94,3 +94,62 @@ def test_tile_shapes_and_empty(drt, oracle_mod):
     assert _gpu3(drt, sc, rx=np.zeros((0, 3), np.float32)).shape == (0,)
     one = scenes.Scene3(sc.tris[:1], sc.tx, sc.rx, max_order=3, alpha=60.0)
     assert_power_close(_gpu3(drt, one), _ref3(oracle_mod, one), "one triangle")
+
+
+# --------------------------------------------------------------------------- TX adjoint
+def _vjp3(drt, sc, g, rx=None):
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.asarray(a, np.float32), device=dev)
+    out = drt.vjp3_tx(t(sc.tris), t(sc.tx), t(sc.rx if rx is None else rx), sc.max_order,
+                      sc.alpha, sc.smoothing, t(g), sc.refl_coef)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+VJP_CASES = [
+    (0, 4, 45, 1, 30.0, "sigmoid"),
+    (1, 6, 40, 2, 40.0, "hard_sigmoid"),
+    (2, 5, 33, 2, 1.0, "step"),
+    (3, 5, 36, 3, 15.0, "sigmoid"),
+    (4, 7, 50, 2, 100.0, "hard_sigmoid"),
+    (5, 6, 40, 2, 0.0, "sigmoid"),
+]
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha,smoothing", VJP_CASES)
+def test_tx_gradient_random_scenes(drt, oracle_mod, seed, W, R, K, alpha, smoothing):
+    sc = scenes.random_scene3(np.random.default_rng(seed), W, R, K, alpha, smoothing)
+    g = np.random.default_rng(seed + 50).normal(size=sc.n_rx).astype(np.float32)
+    got = _vjp3(drt, sc, g)
+    ref = oracle_mod.gradient3_tx(sc.tris, sc.tx, sc.rx, K, alpha, smoothing,
+                                  g.astype(np.float64), sc.refl_coef)
+    assert_grad_close(got, ref, "3D grad_tx")
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+def test_tx_gradient_room_sampled(drt, oracle_mod, smoothing):
+    sc = scenes.room3d(alpha=100.0, smoothing=smoothing)
+    rng = np.random.default_rng(7)
+    idx = rng.choice(sc.n_rx, 8, replace=False)
+    g = np.zeros(sc.n_rx, np.float32)
+    g[idx] = rng.normal(size=8)
+    got = _vjp3(drt, sc, g)
+    ref = oracle_mod.gradient3_tx(sc.tris, sc.tx, sc.rx[idx], 2, 100.0, smoothing,
+                                  g[idx].astype(np.float64), sc.refl_coef)
+    assert_grad_close(got, ref, "room grad_tx")
+
+
+def test_power3_autograd_and_determinism(drt, oracle_mod):
+    sc = scenes.random_scene3(np.random.default_rng(8), 5, 40, 2, 30.0, "hard_sigmoid")
+    dev = torch.device("cuda:0")
+    tris = torch.tensor(sc.tris, device=dev)
+    tx = torch.tensor(sc.tx, device=dev, requires_grad=True)
+    rx = torch.tensor(sc.rx, device=dev)
+    g = torch.tensor(np.random.default_rng(9).normal(size=sc.n_rx).astype(np.float32), device=dev)
+    (drt.power3(tris, tx, rx, 2, 30.0, "hard_sigmoid") * g).sum().backward()
+    ref = oracle_mod.gradient3_tx(sc.tris, sc.tx, sc.rx, 2, 30.0, "hard_sigmoid",
+                                  g.cpu().numpy().astype(np.float64), 0.5)
+    assert_grad_close(tx.grad.cpu().numpy(), ref, "autograd grad_tx")
+    a = _vjp3(drt, sc, g.cpu().numpy())
+    b = _vjp3(drt, sc, g.cpu().numpy())
+    np.testing.assert_array_equal(a, b)

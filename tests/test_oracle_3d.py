@@ -171,3 +171,37 @@ def test_two_triangles_of_one_mirror_reflect_once(oracle_mod):
     P = _P3(oracle_mod, sq, tx, rx[:1], 1, 10.0, "hard_sigmoid")[0]
     d0 = np.sum((rx[0] - tx) ** 2)
     assert P == pytest.approx(1.0 / d0 + GAMMA / d1, rel=1e-12)
+
+
+def test_3d_gradient_closed_form_ground_reflection(oracle_mod):
+    # d/dTX of 1/|RX - TX|^2 + Gamma/|RX - TX'|^2, TX' the image of TX in z = 0
+    ground = np.array([[-50.0, -50.0, 0.0, 50.0, -50.0, 0.0, 0.0, 50.0, 0.0]])
+    tx = np.array([0.2, -0.1, 1.0])
+    rx = np.array([[2.0, 0.5, 0.5], [1.0, -1.0, 2.0]])
+    g = np.array([0.7, -1.3])
+    got = oracle_mod.gradient3_tx(ground, tx, rx, 1, 1.0, "step", g, GAMMA)
+    ref = np.zeros(3)
+    for r, gr in zip(rx, g):
+        d = r - tx
+        ref += gr * 2.0 * d / np.dot(d, d) ** 2
+        img = tx * np.array([1.0, 1.0, -1.0])
+        e = r - img
+        ref += gr * GAMMA * 2.0 * e * np.array([1.0, 1.0, -1.0]) / np.dot(e, e) ** 2
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("fn,alpha", [("sigmoid", 25.0), ("hard_sigmoid", 40.0)])
+def test_3d_jvp_equals_central_differences(oracle_mod, fn, alpha):
+    rng = np.random.default_rng(6)
+    tris = _random_tris(rng, 4)
+    tx = rng.uniform(-1, 1, 3)
+    rx = rng.uniform(-1, 1, (4, 3))
+    for _ in range(3):
+        dw = rng.normal(size=tris.shape)
+        dtx = rng.normal(size=3)
+        _, dP = oracle_mod.power3_jvp(tris, tx, rx, 2, alpha, fn, dw, dtx, GAMMA)
+        h = 1e-6
+        Pp = _P3(oracle_mod, tris + h * dw, tx + h * dtx, rx, 2, alpha, fn)
+        Pm = _P3(oracle_mod, tris - h * dw, tx - h * dtx, rx, 2, alpha, fn)
+        np.testing.assert_allclose(dP, (Pp - Pm) / (2 * h), rtol=1e-5,
+                                   atol=1e-5 * np.abs(dP).max())

@@ -73,14 +73,14 @@ MUTANTS = {
                                   "for (int k = 0; k < 2; ++k) r *= smooth(edge_dist(t, k, p), alpha, kind);"),
     "3d edge normals outward": ("t.m[k] = (1.0 / norm(e)) * cross(t.n, e);",
                                 "t.m[k] = (1.0 / norm(e)) * cross(e, t.n);"),
-    "3d crossing point": ("const V3 hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);",
-                          "const V3 hit = Q[j] + (y / (x - y)) * (Q[j + 1] - Q[j]);"),
-    "3d crossing test sign": ("const double cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +",
-                              "const double cross_plane = smooth(x, al, kind) * smooth(y, al, kind) +"),
+    "3d crossing point": ("const V3<T> hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);",
+                          "const V3<T> hit = Q[j] + (y / (x - y)) * (Q[j + 1] - Q[j]);"),
+    "3d crossing test sign": ("const T cross_plane = smooth(x, al, kind) * smooth(-y, al, kind) +",
+                              "const T cross_plane = smooth(x, al, kind) * smooth(y, al, kind) +"),
     "3d same-side term": ("smooth(-p, al, kind) * smooth(-q, al, kind);",
                           "smooth(-p, al, kind) * smooth(q, al, kind);"),
-    "3d coplanar pair kept": ("if (coplanar(tris[seq[j - 1]], tris[seq[j]])) return 0.0;",
-                              "if (false) return 0.0;"),
+    "3d coplanar pair kept": ("if (coplanar(tris[seq[j - 1]], tris[seq[j]])) return T(0.0);",
+                              "if (false) return T(0.0);"),
     "3d coplanar triangles tested": ("if (j >= 1 && coplanar(t, tris[seq[j - 1]])) continue;",
                                      "if (j >= 1 && &t == &tris[seq[j - 1]]) continue;"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
