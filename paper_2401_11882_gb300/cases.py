@@ -7,6 +7,7 @@ a profiler can capture a chosen launch of it (e.g. ``ncu -k regex:vjp_kernel -s 
     field     drt.field (coherent field, Fresnel TE, --eps-r, --wavelength)
     field_vjp drt.field_vjp with dense g = 1/R (after one drt.field)
     forward3  drt.forward3 on the 3D room (``scenes.room3d``, --rx-grid receivers a side)
+    vjp3      drt.vjp3_tx (transmitter gradient) on the same room, dense g = 1/R
     mlp       the surrogate MLP's inference on --batch random points
 
 Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload)
@@ -25,7 +26,8 @@ from . import ops, scenes
 
 def main() -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["forward", "vjp", "mlp", "field", "field_vjp", "forward3"])
+    ap.add_argument("op", choices=["forward", "vjp", "mlp", "field", "field_vjp", "forward3",
+                                   "vjp3"])
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--scene", choices=["gradient", "large"], default="gradient")
     ap.add_argument("--smoothing", default="sigmoid", choices=["hard_sigmoid", "sigmoid", "step"])
@@ -52,21 +54,28 @@ def main() -> int:
         torch.cuda.synchronize(dev)
         print(json.dumps({"op": "mlp", "batch": args.batch, "ms": a.elapsed_time(b) / args.reps}))
         return 0
-    if args.op == "forward3":
+    if args.op in ("forward3", "vjp3"):
         sc3 = scenes.room3d(args.rx_grid, args.alpha, args.smoothing)
         w3, t3, r3 = (torch.tensor(x, device=dev) for x in (sc3.tris, sc3.tx, sc3.rx))
+        g3 = torch.full((sc3.n_rx,), 1.0 / sc3.n_rx, device=dev)
+
+        def run3():
+            if args.op == "vjp3":
+                return ops.vjp3_tx(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing, g3)
+            return ops.forward3(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing)
+
         for _ in range(2):
-            ops.forward3(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing)
+            run3()
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(args.reps):
-            ops.forward3(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing)
+            run3()
         b.record()
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / args.reps
         n = sc3.n_rx * ops.num_candidates(sc3.n_tris, sc3.max_order)
-        print(json.dumps({"op": "forward3", "scene": "room3d", "smoothing": args.smoothing,
+        print(json.dumps({"op": args.op, "scene": "room3d", "smoothing": args.smoothing,
                           "alpha": args.alpha, "n_tris": sc3.n_tris, "n_rx": sc3.n_rx, "ms": ms,
                           "evals_per_s": n / (ms / 1e3)}))
         return 0
