@@ -1,13 +1,15 @@
 """Pins of the oracle's 3D extension (Sec. VI: the method for triangle walls).
 
 Closed forms (free-space LOS, blocking, a ground reflection, alpha = 0), the 2D
-oracle reproduced exactly by extruded scenes in the hard limit, invariance under
-rigid motions, and reciprocity."""
+oracle reproduced exactly by extruded scenes in the hard limit, classical 3D ray
+tracing by brute force on arbitrary triangles (``classical_rt3``), invariance
+under rigid motions, and reciprocity."""
 import itertools
 
 import numpy as np
 import pytest
 
+from classical_rt3 import classical_power3
 from test_oracle_bruteforce import CASES, _scene
 
 GAMMA = 0.5
@@ -205,3 +207,20 @@ def test_3d_jvp_equals_central_differences(oracle_mod, fn, alpha):
         Pm = _P3(oracle_mod, tris - h * dw, tx - h * dtx, rx, 2, alpha, fn)
         np.testing.assert_allclose(dP, (Pp - Pm) / (2 * h), rtol=1e-5,
                                    atol=1e-5 * np.abs(dP).max())
+
+
+@pytest.mark.parametrize("seed,W,K", [(1, 4, 1), (2, 3, 2), (3, 4, 2), (4, 5, 1), (5, 3, 2)])
+def test_step_mode_equals_classical_3d_ray_tracing(oracle_mod, seed, W, K):
+    # arbitrary triangles: reflection points by Fermat minimisation over the planes,
+    # exact barycentric and segment-triangle predicates (no image method, no smoothing)
+    rng = np.random.default_rng(100 + seed)
+    tris = _random_tris(rng, W)
+    tx = rng.uniform(-1, 1, 3)
+    rx = rng.uniform(-1, 1, (4, 3))
+    P = _P3(oracle_mod, tris, tx, rx, K, 1.0, "step")
+    P0 = _P3(oracle_mod, tris, tx, rx, 0, 1.0, "step")
+    for r in range(rx.shape[0]):
+        ref, margin = classical_power3(tris, tx, rx[r], K, GAMMA)
+        assert margin > 1e-6, "a predicate sits on a tie; pick another seed"
+        assert P[r] == pytest.approx(ref, rel=1e-9, abs=1e-300)
+    assert np.any(P > P0)   # some reflection path is valid and unblocked
