@@ -260,8 +260,8 @@ def run_ours(args):
     evals = sc.n_rx * n_cand
     value = world * args.steps * evals / (total_ms / 1e3)
 
-    # end to end through the public API, from pinned host buffers (inputs H2D, loss,
-    # power and gradients D2H every step)
+    # end to end through the C ABI's host-array call (drt_objective_host), from pinned
+    # host buffers: inputs H2D, loss, argmin, power and gradients D2H every step
     hw = torch.tensor(sc.walls).pin_memory()
     ht = torch.tensor(sc.tx).pin_memory()
     hr = torch.tensor(sc.rx).pin_memory()
@@ -277,7 +277,8 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     h2d = hw.numel() * 4 + ht.numel() * 4 + hr.numel() * 4
-    d2h = sum(o.numel() * o.element_size() for o in out)
+    # loss, power, grad_tx, grad_walls and the 4-byte argmin drt_objective_host copies back
+    d2h = sum(o.numel() * o.element_size() for o in out) + 4
 
     # extras (not part of the timed step): sigmoid forward, dense adjoint on the
     # 128-wall gradient scene, forward with invalid-path culling
@@ -319,8 +320,8 @@ def run_ours(args):
                      "flops_per_launch": work["flops"], "ms_per_launch": fwd_avg_s * 1e3,
                      "note": "achieved counts the frozen convention's 40 FLOP per leg x wall "
                              "test; the kernel needs fewer FMA-pipe operations per test, so the "
-                             "hardware view is the ncu FMA-pipe utilisation in "
-                             "profiles/forward_large_scene.md (75% busy for the hard sigmoid)"},
+                             "hardware view is the FMA-pipe utilisation ncu reports for this "
+                             "kernel (about 75% busy for the hard sigmoid)"},
         "cpu_baseline": cpu,
         "e2e": {"value": world * args.steps * evals / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -1,6 +1,7 @@
 """Runs one named workload a few times and prints its CUDA-event timings, so that
-a profiler can capture a chosen launch of it (e.g. ``ncu -k regex:vjp_kernel -s 2
--c 1 python -m paper_2401_11882_gb300.cases vjp --rx-grid 32``).
+a profiler can capture a chosen launch of it (e.g. ``ncu --clock-control none -k
+regex:vjp_kernel -s 2 -c 1 python -m paper_2401_11882_gb300.cases vjp --rx-grid 32``;
+without ``--clock-control none`` ncu locks the GPU's clocks).
 
     forward   drt.forward on the scene
     vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
