@@ -24,6 +24,10 @@
  *    message (per host thread).  Device-side faults surface, as usual in
  *    CUDA, at the caller's next synchronisation.
  *  - No exception crosses the ABI.
+ *  - The first call on each device caches per-device settings (SM count,
+ *    the kernels' shared-memory limits); they are not re-applied after
+ *    cudaDeviceReset, so a device must not be used through this library
+ *    after it has been reset in the same process.
  */
 #ifndef DRT_H
 #define DRT_H
@@ -262,6 +266,32 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
                             const float* grad_loss, float* grad_tx, float* grad_walls,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/* The whole objective of Sec. III end to end, from HOST arrays to HOST arrays:
+   copies the scene's walls, tx and rx to the device (one cudaMemcpyAsync per
+   array), computes the received power (drt_forward), the loss -min_r power[r]
+   with its lowest-index argmin (drt_loss, Eq. 8) and the gradient of the loss
+   w.r.t. the TX and, when grad_walls is not NULL, the walls (drt_min_loss_vjp),
+   and copies the results back (one cudaMemcpyAsync per array), all enqueued on
+   `stream`.  For a caller that holds its scene in host memory and has no
+   device arrays of its own.
+   scene: host pointer whose walls [n_walls][4], tx [2] and rx [n_rx][2] are
+   HOST arrays (no alignment needed), n_rx >= 1; other fields as for drt_scene.
+   Outputs, all HOST pointers, overwritten: loss [1]; argmin [1] int32 or NULL;
+   power [n_rx] or NULL; grad_tx [2]; grad_walls [n_walls][4] or NULL.
+   workspace: DEVICE scratch of at least drt_objective_host_workspace_size
+   bytes, 256-byte aligned (it holds the device copies of the inputs, the
+   power, the loss and the gradients, and the forward's and adjoint's
+   workspaces; contents undefined on return).
+   The copies are asynchronous with respect to the host when the host arrays
+   are pinned (page-locked); the outputs are valid once the stream has been
+   synchronised.  Errors as for the calls it makes; a rejected call enqueues
+   nothing. */
+drt_status drt_objective_host_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                             size_t* bytes);
+drt_status drt_objective_host(const drt_scene* scene, const drt_tile* tile, float* loss,
+                              int32_t* argmin, float* power, float* grad_tx, float* grad_walls,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
    Batched gradient descent on the TX position (Sec. VII, antenna placement),
    for many scenes of uneven size, each with several starting positions.
@@ -409,17 +439,22 @@ drt_status drt_mlp_adam(float* params, float* m, float* v, const float* grad, in
    workspace.  This call instead uses a scratch array of
    DRT_NOALLOC_SCRATCH_BYTES compiled into the library's device image, which
    every GPU that loads the library keeps until the process exits, and calls no
-   allocator.  Same arguments and result as drt_forward with default tiling
-   (scene: host pointer; power: [n_rx] device, overwritten).
+   allocator.  Same arguments as drt_forward with default tiling (scene: host
+   pointer; power: [n_rx] device, overwritten); the result equals drt_forward's
+   within FP32 rounding: for large n_rx the candidate chunk is larger than the
+   default one, so the per-chunk partial sums are grouped differently.  Two
+   calls with the same arguments give the same bits.
    - Limit: one partial sum per (candidate chunk, receiver) must fit, so
      n_rx <= DRT_NOALLOC_SCRATCH_BYTES / 4; larger scenes get
-     DRT_ERR_UNSUPPORTED before anything is enqueued.
+     DRT_ERR_UNSUPPORTED before anything is enqueued.  Scenes that drt_forward
+     rejects are rejected with the same status.
    - All calls on a device share the array, and it keeps the last call's
      contents (every value a call reads was written by that same call).
      Calls that overlap on the GPU race on it: order them on one stream.
    - The first call on each device looks the array's device address up
      (cudaGetSymbolAddress) with that device current; make that first call
-     before any stream capture begins. */
+     before any stream capture begins.  The address is kept until the process
+     exits: do not call this entry point on a device after cudaDeviceReset. */
 drt_status drt_forward_noalloc(const drt_scene* scene, float* power, void* stream);
 
 #ifdef __cplusplus

@@ -20,7 +20,11 @@
 //    is only a stand-in symbol.  Its device address is looked up once per
 //    device, on the first call made with that device current
 //    (cudaGetSymbolAddress); that first call should therefore happen before
-//    any stream capture begins.
+//    any stream capture begins.  The address is kept for the life of the
+//    process: after cudaDeviceReset the device image is loaded anew, possibly
+//    elsewhere, so this entry point (like the rest of the library, whose
+//    per-device settings are lost too) must not be used on a device after it
+//    has been reset.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -76,7 +80,12 @@ extern "C" drt_status drt_forward_noalloc(const drt_scene* scene, float* power, 
     set_error_message("drt_forward_noalloc: scene is NULL");
     return DRT_ERR_INVALID_ARG;
   }
-  if (scene->n_rx <= 0) return drt_forward(scene, nullptr, power, nullptr, 0, stream);
+  // Validate the whole scene first (wall count, order, pointers), so that the
+  // candidate count below is only computed for supported sizes.
+  size_t default_need = 0;
+  drt_status st = drt_forward_workspace_size(scene, nullptr, &default_need);
+  if (st != DRT_OK) return st;
+  if (scene->n_rx == 0) return drt_forward(scene, nullptr, power, nullptr, 0, stream);
   // One partial sum per (candidate chunk, receiver): choose the chunk so that they fit.
   const long long max_chunks = (long long)(kScratchFloats / (size_t)scene->n_rx);
   if (max_chunks < 1) {
@@ -86,7 +95,7 @@ extern "C" drt_status drt_forward_noalloc(const drt_scene* scene, float* power, 
     return DRT_ERR_UNSUPPORTED;
   }
   int64_t n_cand = 0;
-  drt_status st = drt_num_candidates(scene->n_walls, scene->max_order, &n_cand);
+  st = drt_num_candidates(scene->n_walls, scene->max_order, &n_cand);
   if (st != DRT_OK) return st;
   long long chunk = (n_cand + max_chunks - 1) / max_chunks;
   if (chunk < 64) chunk = 64;

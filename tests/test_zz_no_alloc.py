@@ -69,3 +69,30 @@ def test_rejects_receiver_counts_beyond_the_scratch(lib):
     st = lib.drt_forward_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), None)
     assert st == 2                       # DRT_ERR_UNSUPPORTED, nothing enqueued
     assert b"scratch" in lib.drt_last_error()
+
+
+def test_accepts_the_largest_receiver_count(lib):
+    """n_rx exactly at capacity: one candidate chunk must hold every candidate,
+    and the result still matches drt_forward."""
+    dev = torch.device("cuda:0")
+    cap = (8 << 20) // 4
+    base = scenes.clutter_scene(4, 8, seed=5, alpha=100.0, smoothing="hard_sigmoid",
+                                max_order=2)
+    rng = np.random.default_rng(11)
+    # receivers above y = 0.3, well clear of the transmitter at (0.5, 0.2)
+    rx = np.stack([rng.uniform(0.05, 0.95, cap), rng.uniform(0.3, 0.95, cap)], 1)
+    sc = base.replace(rx=rx.astype(np.float32))
+    got = _noalloc(lib, sc, dev)
+    assert got.shape == (cap,) and np.all(np.isfinite(got))
+    ref = _existing(sc, dev)
+    assert_power_close(got, ref, "noalloc at n_rx = capacity")
+
+
+def test_rejects_an_oversized_wall_count_before_counting_candidates(lib):
+    """A wall count beyond DRT_MAX_WALLS is refused by the scene check (the
+    candidate count of such a scene would not fit in 64 bits)."""
+    from paper_2401_11882_gb300 import _lib
+    desc = _lib.Scene(256, 2**31 - 1, 256, 16, 256, 3, 10.0, 1, 0.5)
+    st = lib.drt_forward_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), None)
+    assert st == 2                       # DRT_ERR_UNSUPPORTED, nothing enqueued
+    assert b"n_walls" in lib.drt_last_error()
