@@ -93,6 +93,8 @@ SIGNATURES = {
     "drt_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_forward_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "drt_min_loss_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "drt_objective_host_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt_objective_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_batch_plan_create": (ctypes.c_int, [_P, _P, _P]),
     "drt_batch_workspace_size": (ctypes.c_int, [_P, _P]),
     "drt_batch_bind": (ctypes.c_int, [_P, _P, _P, _SZ, _P]),

@@ -692,3 +692,121 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ end to end
+// Layout of drt_objective_host's device workspace: the copied inputs, the
+// intermediate power, loss and argmin, the gradients, then the forward's and
+// the adjoint's own workspaces; every section starts on a 256-byte boundary.
+namespace {
+struct HostObjLayout {
+  size_t walls, tx, rx, power, loss, argmin, gtx, gw, fws, vws, total;
+  size_t fws_bytes, vws_bytes;
+};
+
+size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+drt_status host_obj_layout(const drt_scene* sc, const drt_tile* tile, HostObjLayout* L) {
+  Decomp df, dv;
+  drt_status st = decompose(sc, tile, FWD, &df);
+  if (st != DRT_OK) return st;
+  if ((st = decompose(sc, tile, VJP, &dv)) != DRT_OK) return st;
+  const size_t W = (size_t)sc->n_walls, R = (size_t)sc->n_rx;
+  L->fws_bytes = (size_t)df.n_chunks * R * sizeof(float);
+  L->vws_bytes = vjp_workspace(sc, dv);
+  size_t off = 0;
+  auto take = [&](size_t n) { const size_t o = off; off += round256(n); return o; };
+  L->walls = take(W * 4 * sizeof(float));
+  L->tx = take(2 * sizeof(float));
+  L->rx = take(R * 2 * sizeof(float));
+  L->power = take(R * sizeof(float));
+  L->loss = take(sizeof(float));
+  L->argmin = take(sizeof(int32_t));
+  L->gtx = take(2 * sizeof(float));
+  L->gw = take(W * 4 * sizeof(float));
+  L->fws = take(L->fws_bytes);
+  L->vws = take(L->vws_bytes);
+  L->total = off;
+  return DRT_OK;
+}
+
+// The scene with its arrays checked as host arrays (drt_objective_host): the
+// same rules as check_scene except alignment, which only device arrays need.
+drt_status check_host_scene(const drt_scene* sc) {
+  if (!sc) return fail(DRT_ERR_INVALID_ARG, "scene is NULL");
+  if (!sc->walls || !sc->tx || !sc->rx)
+    return fail(DRT_ERR_INVALID_ARG, "walls, tx and rx host pointers are required");
+  if (sc->n_rx < 1) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 1", sc->n_rx);
+  drt_scene probe = *sc;
+  // any 256-aligned non-null value passes the pointer checks of check_scene
+  probe.walls = probe.tx = probe.rx = reinterpret_cast<const float*>(256);
+  return check_scene(&probe);
+}
+}  // namespace
+
+extern "C" {
+
+drt_status drt_objective_host_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                             size_t* bytes) {
+  drt_status st = check_host_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  HostObjLayout L;
+  if ((st = host_obj_layout(scene, tile, &L)) != DRT_OK) return st;
+  *bytes = L.total;
+  return DRT_OK;
+}
+
+drt_status drt_objective_host(const drt_scene* scene, const drt_tile* tile, float* loss,
+                              int32_t* argmin, float* power, float* grad_tx, float* grad_walls,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  drt_status st = check_host_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!loss || !grad_tx) return fail(DRT_ERR_INVALID_ARG, "loss and grad_tx are required");
+  HostObjLayout L;
+  if ((st = host_obj_layout(scene, tile, &L)) != DRT_OK) return st;
+  if (!workspace || workspace_bytes < L.total || !aligned(workspace, 256))
+    return fail(DRT_ERR_WORKSPACE, "objective needs %zu 256-byte aligned workspace bytes, got %zu",
+                L.total, workspace_bytes);
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t strm = static_cast<cudaStream_t>(stream);
+  const size_t W = (size_t)scene->n_walls, R = (size_t)scene->n_rx;
+  drt_scene dev = *scene;
+  dev.walls = reinterpret_cast<const float*>(ws + L.walls);
+  dev.tx = reinterpret_cast<const float*>(ws + L.tx);
+  dev.rx = reinterpret_cast<const float*>(ws + L.rx);
+  float* d_power = reinterpret_cast<float*>(ws + L.power);
+  float* d_loss = reinterpret_cast<float*>(ws + L.loss);
+  int32_t* d_arg = reinterpret_cast<int32_t*>(ws + L.argmin);
+  float* d_gtx = reinterpret_cast<float*>(ws + L.gtx);
+  float* d_gw = grad_walls ? reinterpret_cast<float*>(ws + L.gw) : nullptr;
+  // inputs: one copy per array
+  cudaError_t e = cudaMemcpyAsync(const_cast<float*>(dev.walls), scene->walls, W * 16,
+                                  cudaMemcpyHostToDevice, strm);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<float*>(dev.tx), scene->tx, 8, cudaMemcpyHostToDevice, strm);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<float*>(dev.rx), scene->rx, R * 8, cudaMemcpyHostToDevice,
+                        strm);
+  if (e != cudaSuccess) return cuda_fail(e, "objective input copies");
+  // power, loss = -min power (lowest-index argmin), gradient of the loss
+  if ((st = drt_forward(&dev, tile, d_power, ws + L.fws, L.fws_bytes, stream)) != DRT_OK)
+    return st;
+  if ((st = drt_loss(d_power, scene->n_rx, d_loss, d_arg, stream)) != DRT_OK) return st;
+  if ((st = drt_min_loss_vjp(&dev, tile, d_arg, nullptr, d_gtx, d_gw, ws + L.vws, L.vws_bytes,
+                             stream)) != DRT_OK)
+    return st;
+  // outputs: one copy per array
+  e = cudaMemcpyAsync(loss, d_loss, 4, cudaMemcpyDeviceToHost, strm);
+  if (e == cudaSuccess && argmin) e = cudaMemcpyAsync(argmin, d_arg, 4, cudaMemcpyDeviceToHost, strm);
+  if (e == cudaSuccess && power)
+    e = cudaMemcpyAsync(power, d_power, R * 4, cudaMemcpyDeviceToHost, strm);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad_tx, d_gtx, 8, cudaMemcpyDeviceToHost, strm);
+  if (e == cudaSuccess && grad_walls)
+    e = cudaMemcpyAsync(grad_walls, d_gw, W * 16, cudaMemcpyDeviceToHost, strm);
+  if (e != cudaSuccess) return cuda_fail(e, "objective output copies");
+  return DRT_OK;
+}
+
+}  // extern "C"

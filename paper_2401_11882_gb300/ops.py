@@ -433,21 +433,44 @@ def objective(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", refl_co
     return ObjectiveFunction.apply(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
 
 
+def _host_f32(a, cols: int, name: str) -> torch.Tensor:
+    t = torch.as_tensor(a)
+    if t.is_cuda:
+        raise TypeError(f"{name} must be a host array")
+    t = t.detach().to(torch.float32).reshape(-1, cols)
+    return t.contiguous()
+
+
 def objective_host(walls, tx, rx, max_order, alpha, smoothing="hard_sigmoid", refl_coef=0.5,
                    device="cuda", grad_walls=False, tile=None):
-    """End-to-end call from host arrays: copy the inputs to the device, run power,
-    loss and its gradient, copy (loss, power, grad_tx[, grad_walls]) back to the host."""
+    """End-to-end call from host arrays (drt_objective_host): the library copies the
+    inputs to the device, runs power, loss and its gradient, and copies
+    (loss, power, grad_tx[, grad_walls]) back into host tensors.  Pinned host inputs
+    keep the copies asynchronous; the call returns after the stream has finished."""
     dev = torch.device(device)
-    w = torch.as_tensor(walls).to(dev, non_blocking=True)
-    t = torch.as_tensor(tx).to(dev, non_blocking=True)
-    r = torch.as_tensor(rx).to(dev, non_blocking=True)
-    p = forward(w, t, r, max_order, alpha, smoothing, refl_coef, tile)
-    l, arg = min_loss(p)
-    gtx, gw = min_loss_vjp(w, t, r, max_order, alpha, smoothing, arg, None, refl_coef,
-                           wall_grad=grad_walls, tile=tile)
-    out = [l.to("cpu", non_blocking=True), p.to("cpu", non_blocking=True),
-           gtx.to("cpu", non_blocking=True)]
-    if grad_walls:
-        out.append(gw.to("cpu", non_blocking=True))
+    w = _host_f32(walls, 4, "walls")
+    t = _host_f32(tx, 2, "tx")
+    r = _host_f32(rx, 2, "rx")
+    if smoothing not in _lib.SMOOTHING:
+        raise ValueError(f"unknown smoothing {smoothing!r}")
+    sc = _lib.Scene(w.data_ptr(), w.shape[0], r.data_ptr(), r.shape[0], t.data_ptr(),
+                    int(max_order), float(alpha), _lib.SMOOTHING[smoothing], float(refl_coef))
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_objective_host_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    pin = w.is_pinned()
+    loss_h = torch.empty(1, dtype=torch.float32, pin_memory=pin)
+    arg_h = torch.empty(1, dtype=torch.int32, pin_memory=pin)
+    p_h = torch.empty(r.shape[0], dtype=torch.float32, pin_memory=pin)
+    gtx_h = torch.empty(2, dtype=torch.float32, pin_memory=pin)
+    gw_h = torch.empty(w.shape[0], 4, dtype=torch.float32, pin_memory=pin) if grad_walls else None
+    _lib.call("drt_objective_host", ctypes.byref(sc), tlp, _ptr(loss_h), _ptr(arg_h), _ptr(p_h),
+              _ptr(gtx_h), None if gw_h is None else _ptr(gw_h), _ptr(ws),
+              ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
     torch.cuda.current_stream(dev).synchronize()
+    out = [loss_h, p_h, gtx_h]
+    if grad_walls:
+        out.append(gw_h)
     return tuple(out)

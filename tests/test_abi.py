@@ -152,3 +152,30 @@ def test_vjp3_tx_rejects_bad_args_before_any_launch(lib):
     bad = _scene3(n_tris=0)
     out = ctypes.c_size_t()
     assert lib.drt3_vjp_tx_workspace_size(ctypes.byref(bad), None, ctypes.byref(out)) == 1
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("n_walls", 0, 1), ("n_walls", 5000, 2), ("max_order", 4, 2), ("alpha", -1.0, 1),
+    ("smoothing", 7, 1), ("walls", 0, 1), ("tx", 0, 1), ("rx", 0, 1), ("n_rx", 0, 1),
+    ("refl_coef", float("nan"), 1)])
+def test_objective_host_rejects_bad_scene_before_any_copy(lib, field, value, status):
+    # host arrays need no alignment (walls = 8 is accepted below); everything else as
+    # for drt_forward, checked on the host before any CUDA call
+    sc = _scene(walls=8, **{field: value}) if field != "walls" else _scene(walls=value)
+    out = ctypes.c_size_t()
+    p = ctypes.c_void_p(256)
+    assert lib.drt_objective_host_workspace_size(ctypes.byref(sc), None,
+                                                 ctypes.byref(out)) == status
+    assert lib.drt_objective_host(ctypes.byref(sc), None, p, None, None, p, None, p, 1 << 20,
+                                  None) == status
+    assert len(lib.drt_last_error()) > 0
+
+
+def test_objective_host_requires_loss_and_grad_tx(lib):
+    sc = _scene(walls=8)
+    p = ctypes.c_void_p(256)
+    assert lib.drt_objective_host(ctypes.byref(sc), None, None, None, None, p, None, p, 1 << 20,
+                                  None) == 1
+    assert lib.drt_objective_host(ctypes.byref(sc), None, p, None, None, None, None, p, 1 << 20,
+                                  None) == 1
+    assert lib.drt_objective_host(None, None, p, None, None, p, None, p, 1 << 20, None) == 1
