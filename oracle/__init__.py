@@ -25,6 +25,9 @@ Functions and the passages they follow:
 * ``power3_jvp``, ``gradient3_tx``  its exact forward-mode derivative; the TX gradient
 * ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
                         finders' convergence check compares with zero (``oracle/mpt.py``)
+* ``power_mpt``, ``mpt_paths``  Sec. V-B, "Continuous Path Finding": reflection points found
+                        iteratively (Min-Path-Tracing: Gauss-Newton on the reflection law from the
+                        walls' midpoints) with the smoothed convergence check s(eps - C)
 
 Readings of the paper that the oracle fixes (the paper leaves them open):
 incoherent scalar power p = Gamma^k V / L^2 with Gamma = 0.5; smoothing
@@ -84,6 +87,8 @@ def _load():
         lib.drt_oracle_field_jvp.argtypes = [p, i, p, p, i, i, d, i, d, d, d, p, p, i, p, p]
         lib.drt_oracle_power3.argtypes = [p, i, p, p, i, i, d, i, d, i, p]
         lib.drt_oracle_power3_jvp.argtypes = [p, i, p, p, i, i, d, i, d, p, p, i, p, p]
+        lib.drt_oracle_power_mpt.argtypes = [p, i, p, p, i, i, d, i, d, i, d, i, p]
+        lib.drt_oracle_mpt_paths.argtypes = [p, i, p, p, i, d, i, d, i, d, p, p, p, p, p]
         _lib = lib
         return lib
 
@@ -351,3 +356,44 @@ def paths(walls, tx, rx1, max_order, alpha, smoothing, refl_coef=0.5) -> dict:
     return dict(seq=seq, order=order, degenerate=deg, verts=verts, validity=val, vis=vis,
                 length=length, power=pw)
 
+
+
+
+def power_mpt(walls, tx, rx, max_order, alpha, smoothing, n_iter=10, eps=0.05, refl_coef=0.5,
+              threads=None) -> np.ndarray:
+    """Received power (float64 [R]) with the reflection points found by ``n_iter``
+    Min-Path-Tracing steps from the walls' midpoints (Sec. V-B) and each path's
+    validity taken as its on-segment tests times the convergence check
+    s(eps - C), C the MPT cost (drt_oracle.cpp, path finder)."""
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    out = np.zeros(rx.shape[0])
+    rc = _load().drt_oracle_power_mpt(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx),
+                                      rx.shape[0], int(max_order), float(alpha),
+                                      _kind(smoothing), float(refl_coef), int(n_iter),
+                                      float(eps), _threads(threads), _ptr(out))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def mpt_paths(walls, tx, rx1, max_order, alpha, smoothing, n_iter=10, eps=0.05,
+              refl_coef=0.5) -> dict:
+    """Per candidate of one receiver ``rx1``: the MPT finder's along-wall coordinates
+    ``tau`` [n, K] (NaN past the path's order), the MPT ``cost`` and the convergence
+    check ``kappa`` at the final points, the path ``power`` and a ``degenerate``
+    flag, with the candidate table's ``seq`` and ``order``."""
+    walls, tx, rx1 = _scene_args(walls, tx, rx1)
+    W, K = walls.shape[0], int(max_order)
+    n = num_candidates(W, K)
+    tau = np.zeros((n, max(K, 1)))
+    cost = np.zeros(n); kappa = np.zeros(n); pw = np.zeros(n)
+    deg = np.zeros(n, np.int32)
+    rc = _load().drt_oracle_mpt_paths(_ptr(walls), W, _ptr(tx), _ptr(rx1), K, float(alpha),
+                                      _kind(smoothing), float(refl_coef), int(n_iter),
+                                      float(eps), _ptr(tau), _ptr(cost), _ptr(kappa), _ptr(pw),
+                                      _ptr(deg))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    seq, order = candidates(W, K)
+    return dict(seq=seq, order=order, tau=tau[:, :K], cost=cost, kappa=kappa, power=pw,
+                degenerate=deg)

@@ -41,6 +41,7 @@
 // double (values), a forward-mode dual number, or std::complex<double>
 // (complex-step differentiation, comparisons taken on the real part).
 
+#include <cfloat>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -197,6 +198,43 @@ struct PathRecord {
   double power;          // p
 };
 
+// Visibility of every leg of the path Q_0..Q_{k+1} (its unit normals in
+// leg_normal): each leg Q_j -> Q_{j+1} is tested against every wall other than
+// the walls its two end points lie on; returns the product over the legs.
+template <class T>
+T obstruction(const std::vector<Wall<T>>& walls, const std::vector<Vec<T>>& Q,
+              const std::vector<Vec<T>>& leg_normal, const std::vector<int>& seq,
+              const Params& P, PathRecord* rec) {
+  const int k = (int)seq.size();
+  const int W = (int)walls.size();
+  const double a = P.alpha;
+  const int kind = P.kind;
+  T visibility = T(1.0);
+  for (int j = 0; j <= k; ++j) {
+    const int skip_a = (j >= 1) ? seq[j - 1] : -1;     // wall holding Q_j
+    const int skip_b = (j + 1 <= k) ? seq[j] : -1;     // wall holding Q_{j+1}
+    T vis = T(1.0);
+    for (int wi = 0; wi < W; ++wi) {
+      if (wi == skip_a || wi == skip_b) continue;
+      const Wall<T>& w = walls[wi];
+      // the leg's end points on opposite sides of the wall's line ...
+      T x1 = dist_line(w, Q[j]);
+      T y1 = dist_line(w, Q[j + 1]);
+      T cross1 = smooth(x1, a, kind) * smooth(T(-y1), a, kind) +
+                 smooth(T(-x1), a, kind) * smooth(y1, a, kind);
+      // ... and the wall's end points on opposite sides of the leg's line
+      T x2 = dot(leg_normal[j], sub(w.a, Q[j]));
+      T y2 = dot(leg_normal[j], sub(w.b, Q[j]));
+      T cross2 = smooth(x2, a, kind) * smooth(T(-y2), a, kind) +
+                 smooth(T(-x2), a, kind) * smooth(y2, a, kind);
+      vis = vis * (1.0 - cross1 * cross2);
+    }
+    if (rec && j < 7) rec->vis[j] = re(vis);
+    visibility = visibility * vis;
+  }
+  return visibility;
+}
+
 // Geometry, validity and visibility of one path candidate `seq` (k = seq.size()).
 template <class T>
 struct PathTerms {
@@ -270,29 +308,7 @@ PathTerms<T> path_terms(const std::vector<Wall<T>>& walls, const Vec<T>& tx, con
     validity = validity * on_seg * same_side;
   }
   // obstruction of each leg
-  T visibility = T(1.0);
-  for (int j = 0; j <= k; ++j) {
-    const int skip_a = (j >= 1) ? seq[j - 1] : -1;     // wall holding Q_j
-    const int skip_b = (j + 1 <= k) ? seq[j] : -1;     // wall holding Q_{j+1}
-    T vis = T(1.0);
-    for (int wi = 0; wi < W; ++wi) {
-      if (wi == skip_a || wi == skip_b) continue;
-      const Wall<T>& w = walls[wi];
-      // the leg's end points on opposite sides of the wall's line ...
-      T x1 = dist_line(w, Q[j]);
-      T y1 = dist_line(w, Q[j + 1]);
-      T cross1 = smooth(x1, a, kind) * smooth(T(-y1), a, kind) +
-                 smooth(T(-x1), a, kind) * smooth(y1, a, kind);
-      // ... and the wall's end points on opposite sides of the leg's line
-      T x2 = dot(leg_normal[j], sub(w.a, Q[j]));
-      T y2 = dot(leg_normal[j], sub(w.b, Q[j]));
-      T cross2 = smooth(x2, a, kind) * smooth(T(-y2), a, kind) +
-                 smooth(T(-x2), a, kind) * smooth(y2, a, kind);
-      vis = vis * (1.0 - cross1 * cross2);
-    }
-    if (rec && j < 7) rec->vis[j] = re(vis);
-    visibility = visibility * vis;
-  }
+  T visibility = obstruction(walls, Q, leg_normal, seq, P, rec);
   T L = T(0.0);
   for (int j = 0; j <= k; ++j) L = L + leg_len[j];
   // incidence at each reflection: the incoming leg j-1 is Q_{j-1} -> Q_j, whose unit
@@ -360,6 +376,211 @@ Vec<T> path_field(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec
   const T amp = coef * t.validity * t.visibility / t.L;
   const T phase = (2.0 * M_PI / wavelength) * t.L;
   return Vec<T>{amp * cos(phase), -(amp * sin(phase))};
+}
+
+// ---------------------------------------------------------------- path finder
+// Sec. V-B, "Continuous Path Finding": besides the image method, the framework
+// finds the reflection points iteratively and checks convergence with the
+// Min-Path-Tracing (MPT) cost, whose comparison with zero is smoothed by s.  The
+// paper defers the formulation to the MPT paper; the reading here, for
+// reflections on the walls' infinite lines, is:
+//   unknowns   tau_j, the coordinate of reflection point X_j = A_j + tau_j u_j
+//              along wall w_j (j = 1..k); X_0 = TX, X_{k+1} = RX;
+//   legs       d_j = X_{j+1} - X_j, l_j = |d_j|, unit direction h_j = d_j / l_j;
+//   residuals  r_j = h_j - R_j h_{j-1}, R_j v = v - 2 (n_j . v) n_j (the mirror of
+//              wall j): zero iff the reflection law holds at X_j; the MPT cost is
+//              C = sum_j |r_j|^2;
+//   start      tau_j = len_j / 2 (every wall's midpoint);
+//   each step  a Gauss-Newton step on the residuals, (J^T J + mu) delta = -J^T r with
+//              dh_j / dX_{j+1} = -dh_j / dX_j = (I - h_j h_j^T) / l_j and mu = 1e-6
+//              times the diagonal (a Levenberg term that keeps a grazing leg's
+//              singular system solvable); every delta_j clamped to [-len_j, len_j]
+//              (a valid point lies within len_j / 2 of the start); then
+//              backtracking: the largest fraction 2^-m (m < 12) of delta that lowers
+//              C by 1e-4 of its slope along delta, up to 8 units of rounding of C,
+//              and no step if none does;
+//   check      kappa = s(eps - C) with C at the final points;
+//   validity   prod_j s(tau_j) s(len_j - tau_j) * kappa: the convergence check takes
+//              the place of the image method's same-side test (a converged
+//              reflection has its neighbours on one side);
+//   degenerate a leg of zero length at any step: the path contributes 0.
+// (Fermat path tracing, Newton steps on the path length, is not used: the length
+// is not differentiable where a leg vanishes, and for two walls meeting at a
+// corner the iteration runs into the corner and stalls there.)
+struct FinderLegs {
+  std::vector<Vec<double>> X, h;   // vertices X_0..X_{k+1}; unit leg directions h_0..h_k
+  std::vector<double> l;           // leg lengths
+  bool degenerate;
+};
+
+FinderLegs finder_legs(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
+                       const Vec<double>& rx, const std::vector<int>& seq,
+                       const std::vector<double>& tau) {
+  const int k = (int)seq.size();
+  FinderLegs f;
+  f.X.resize(k + 2);
+  f.h.resize(k + 1);
+  f.l.resize(k + 1);
+  f.degenerate = false;
+  f.X[0] = tx;
+  f.X[k + 1] = rx;
+  for (int j = 1; j <= k; ++j) {
+    const Wall<double>& w = walls[seq[j - 1]];
+    f.X[j] = Vec<double>{w.a.x + tau[j - 1] * w.u.x, w.a.y + tau[j - 1] * w.u.y};
+  }
+  for (int j = 0; j <= k; ++j) {
+    const Vec<double> d = sub(f.X[j + 1], f.X[j]);
+    f.l[j] = std::sqrt(dot(d, d));
+    if (f.l[j] == 0.0) {
+      f.degenerate = true;
+      return f;
+    }
+    f.h[j] = Vec<double>{d.x / f.l[j], d.y / f.l[j]};
+  }
+  return f;
+}
+
+constexpr int FINDER_HALVINGS = 12;
+
+// reflection law residual r_j = h_j - R_j h_{j-1} at point j (1..k)
+Vec<double> mpt_residual(const Wall<double>& w, const Vec<double>& hin, const Vec<double>& hout) {
+  const double in = dot(w.n, hin);
+  return Vec<double>{hout.x - (hin.x - 2.0 * in * w.n.x), hout.y - (hin.y - 2.0 * in * w.n.y)};
+}
+
+double mpt_cost(const std::vector<Wall<double>>& walls, const std::vector<int>& seq,
+                const FinderLegs& f) {
+  double C = 0.0;
+  for (int j = 1; j <= (int)seq.size(); ++j) {
+    const Vec<double> r = mpt_residual(walls[seq[j - 1]], f.h[j - 1], f.h[j]);
+    C += dot(r, r);
+  }
+  return C;
+}
+
+// Solves the k x k symmetric positive definite system A x = b (Cholesky, in place).
+void spd_solve(std::vector<double>& A, std::vector<double>& b, int k) {
+  for (int c = 0; c < k; ++c) {
+    double d = A[c * k + c];
+    for (int p = 0; p < c; ++p) d -= A[c * k + p] * A[c * k + p];
+    d = std::sqrt(d > 0.0 ? d : 0.0);
+    A[c * k + c] = d;
+    for (int r = c + 1; r < k; ++r) {
+      double v = A[r * k + c];
+      for (int p = 0; p < c; ++p) v -= A[r * k + p] * A[c * k + p];
+      A[r * k + c] = d > 0.0 ? v / d : 0.0;
+    }
+  }
+  for (int r = 0; r < k; ++r) {   // L y = b
+    double v = b[r];
+    for (int p = 0; p < r; ++p) v -= A[r * k + p] * b[p];
+    b[r] = A[r * k + r] > 0.0 ? v / A[r * k + r] : 0.0;
+  }
+  for (int r = k - 1; r >= 0; --r) {   // L^T x = y
+    double v = b[r];
+    for (int p = r + 1; p < k; ++p) v -= A[p * k + r] * b[p];
+    b[r] = A[r * k + r] > 0.0 ? v / A[r * k + r] : 0.0;
+  }
+}
+
+// Reflection points of `seq` after n_iter MPT steps; returns false if the path is
+// degenerate.
+bool mpt_points(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
+                const Vec<double>& rx, const std::vector<int>& seq, int n_iter,
+                std::vector<double>& tau) {
+  const int k = (int)seq.size();
+  tau.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) tau[j] = 0.5 * walls[seq[j]].len;
+  if (k == 0) return !finder_legs(walls, tx, rx, seq, tau).degenerate;
+  auto proj = [](const FinderLegs& f, int leg, const Vec<double>& v) {   // (I - h h^T) v / l
+    const double c = dot(f.h[leg], v);
+    return Vec<double>{(v.x - c * f.h[leg].x) / f.l[leg], (v.y - c * f.h[leg].y) / f.l[leg]};
+  };
+  auto mirror_dir = [](const Wall<double>& w, const Vec<double>& v) {
+    const double c = dot(w.n, v);
+    return Vec<double>{v.x - 2.0 * c * w.n.x, v.y - 2.0 * c * w.n.y};
+  };
+  for (int it = 0; it < n_iter; ++it) {
+    const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
+    if (f.degenerate) return false;
+    // J: entry (j, i) = dr_j / dtau_i (a 2-vector), nonzero for |i - j| <= 1
+    std::vector<Vec<double>> J(k * k, Vec<double>{0.0, 0.0});
+    std::vector<Vec<double>> r(k);
+    for (int j = 1; j <= k; ++j) {
+      const Wall<double>& w = walls[seq[j - 1]];
+      r[j - 1] = mpt_residual(w, f.h[j - 1], f.h[j]);
+      // tau_j moves the end of leg j - 1 and the start of leg j
+      const Vec<double> a = proj(f, j, w.u), c = mirror_dir(w, proj(f, j - 1, w.u));
+      J[(j - 1) * k + (j - 1)] = Vec<double>{-a.x - c.x, -a.y - c.y};
+      if (j < k) J[(j - 1) * k + j] = proj(f, j, walls[seq[j]].u);   // the end of leg j
+      if (j > 1)                                                     // the start of leg j - 1
+        J[(j - 1) * k + (j - 2)] = mirror_dir(w, proj(f, j - 1, walls[seq[j - 2]].u));
+    }
+    std::vector<double> A(k * k, 0.0), b(k, 0.0);
+    for (int a = 0; a < k; ++a) {
+      for (int c = 0; c < k; ++c) {
+        double v = 0.0;
+        for (int j = 0; j < k; ++j) v += dot(J[j * k + a], J[j * k + c]);
+        A[a * k + c] = v;
+      }
+      double v = 0.0;
+      for (int j = 0; j < k; ++j) v += dot(J[j * k + a], r[j]);
+      b[a] = -v;
+    }
+    // slope of C along the step: grad C = 2 J^T r = -2 b
+    std::vector<double> g0(b);
+    for (int j = 0; j < k; ++j) A[j * k + j] *= 1.0 + 1e-6;
+    spd_solve(A, b, k);
+    double slope = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double lim = walls[seq[j]].len;
+      b[j] = b[j] < -lim ? -lim : (b[j] > lim ? lim : b[j]);
+      slope -= 2.0 * g0[j] * b[j];
+    }
+    const double C0 = mpt_cost(walls, seq, f);
+    const double tol = 8.0 * DBL_EPSILON * C0;
+    double t = 1.0;
+    for (int m = 0; m < FINDER_HALVINGS; ++m, t *= 0.5) {
+      std::vector<double> trial(tau);
+      for (int j = 0; j < k; ++j) trial[j] += t * b[j];
+      const FinderLegs ft = finder_legs(walls, tx, rx, seq, trial);
+      if (ft.degenerate) continue;
+      if (mpt_cost(walls, seq, ft) <= C0 + 1e-4 * t * slope + tol) {
+        tau.swap(trial);
+        break;
+      }
+    }
+  }
+  return !finder_legs(walls, tx, rx, seq, tau).degenerate;
+}
+
+// Power of one path candidate whose reflection points come from the MPT path
+// finder, with the smoothed convergence check; fills tau [k], C and kappa.
+double mpt_path_power(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
+                      const Vec<double>& rx, const std::vector<int>& seq, const Params& P,
+                      int n_iter, double eps, std::vector<double>& tau, double* cost,
+                      double* kappa) {
+  const int k = (int)seq.size();
+  *cost = 0.0;
+  *kappa = 0.0;
+  if (!mpt_points(walls, tx, rx, seq, n_iter, tau)) return 0.0;
+  const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
+  *cost = mpt_cost(walls, seq, f);
+  *kappa = smooth(eps - *cost, P.alpha, P.kind);
+  double validity = *kappa;
+  for (int j = 1; j <= k; ++j) {
+    const Wall<double>& w = walls[seq[j - 1]];
+    validity = validity * smooth(tau[j - 1], P.alpha, P.kind) *
+               smooth(w.len - tau[j - 1], P.alpha, P.kind);
+  }
+  std::vector<Vec<double>> normal(k + 1);
+  for (int j = 0; j <= k; ++j) normal[j] = Vec<double>{-f.h[j].y, f.h[j].x};
+  const double visibility = obstruction(walls, f.X, normal, seq, P, nullptr);
+  double L = 0.0;
+  for (int j = 0; j <= k; ++j) L += f.l[j];
+  double gk = 1.0;
+  for (int j = 0; j < k; ++j) gk *= P.gamma;
+  return gk * validity * visibility / (L * L);
 }
 
 template <class T>
@@ -781,6 +1002,55 @@ int drt_oracle_paths(const double* walls_xy, int W, const double* tx, const doub
     validity[i] = rec.validity;
     length[i] = rec.length;
     power[i] = rec.power;
+  }
+  return 0;
+}
+
+
+// Path-finder variant of drt_oracle_power (MPT points, convergence check): power [R].
+int drt_oracle_power_mpt(const double* walls_xy, int W, const double* tx, const double* rx,
+                         int R, int K, double alpha, int kind, double gamma, int n_iter,
+                         double eps, int nthreads, double* out) {
+  if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind) || n_iter < 0) return 1;
+  std::vector<double> xy(walls_xy, walls_xy + 4 * W);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<double> t{tx[0], tx[1]};
+  set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+  for (int r = 0; r < R; ++r) {
+    Vec<double> q{rx[2 * r], rx[2 * r + 1]};
+    double sum = 0.0;
+    std::vector<double> tau;
+    double C, kap;
+    for (const auto& seq : cands)
+      sum += mpt_path_power(walls, t, q, seq, prm, n_iter, eps, tau, &C, &kap);
+    out[r] = sum;
+  }
+  return 0;
+}
+
+// Per path of one receiver: the MPT finder's along-wall coordinates tau [n_cand][K]
+// (NaN past the path's order and for a degenerate path), cost C [n_cand], kappa
+// [n_cand], power [n_cand], degenerate flag [n_cand].
+int drt_oracle_mpt_paths(const double* walls_xy, int W, const double* tx, const double* rx1,
+                         int K, double alpha, int kind, double gamma, int n_iter, double eps,
+                         double* tau_out, double* cost, double* kappa, double* power,
+                         int* degenerate) {
+  if (check_args(walls_xy, W, tx, rx1, 1, K, alpha, kind) || n_iter < 0) return 1;
+  std::vector<double> xy(walls_xy, walls_xy + 4 * W);
+  auto walls = make_walls(xy, W);
+  auto cands = candidates(W, K);
+  Params prm{K, alpha, kind, gamma};
+  Vec<double> t{tx[0], tx[1]};
+  Vec<double> q{rx1[0], rx1[1]};
+  for (size_t i = 0; i < cands.size(); ++i) {
+    std::vector<double> tau;
+    const int k = (int)cands[i].size();
+    power[i] = mpt_path_power(walls, t, q, cands[i], prm, n_iter, eps, tau, &cost[i], &kappa[i]);
+    degenerate[i] = mpt_points(walls, t, q, cands[i], n_iter, tau) ? 0 : 1;
+    for (int j = 0; j < K; ++j) tau_out[i * K + j] = (j < k && !degenerate[i]) ? tau[j] : NAN;
   }
   return 0;
 }

@@ -18,7 +18,7 @@ SRC = os.path.join(ROOT, "oracle", "drt_oracle.cpp")
 PIN_FILES = ["tests/test_oracle_smoothing.py", "tests/test_oracle_candidates.py",
              "tests/test_oracle_geometry.py", "tests/test_oracle_bruteforce.py",
              "tests/test_oracle_gradients.py", "tests/test_oracle_field.py",
-             "tests/test_oracle_3d.py"]
+             "tests/test_oracle_3d.py", "tests/test_oracle_mpt_finder.py"]
 
 MUTANTS = {
     "mirror sign": ("return Vec<T>{p.x - 2.0 * d * w.n.x", "return Vec<T>{p.x + 2.0 * d * w.n.x"),
@@ -83,6 +83,18 @@ MUTANTS = {
                               "if (false) return T(0.0);"),
     "3d coplanar triangles tested": ("if (j >= 1 && coplanar(t, tris[seq[j - 1]])) continue;",
                                      "if (j >= 1 && &t == &tris[seq[j - 1]]) continue;"),
+    "mpt residual mirror sign": ("hout.x - (hin.x - 2.0 * in * w.n.x)",
+                                 "hout.x - (hin.x + 2.0 * in * w.n.x)"),
+    "mpt jacobian drops the incoming leg": (
+        "J[(j - 1) * k + (j - 1)] = Vec<double>{-a.x - c.x, -a.y - c.y};",
+        "J[(j - 1) * k + (j - 1)] = Vec<double>{-a.x, -a.y};"),
+    "mpt check compares the wrong way": ("*kappa = smooth(eps - *cost, P.alpha, P.kind);",
+                                          "*kappa = smooth(*cost - eps, P.alpha, P.kind);"),
+    "mpt on-segment far end": ("smooth(w.len - tau[j - 1], P.alpha, P.kind);",
+                               "smooth(tau[j - 1] - w.len, P.alpha, P.kind);"),
+    "mpt line search takes increases": (
+        "if (mpt_cost(walls, seq, ft) <= C0 + 1e-4 * t * slope + tol) {",
+        "if (mpt_cost(walls, seq, ft) >= C0 + 1e-4 * t * slope + tol) {"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
