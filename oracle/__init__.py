@@ -22,7 +22,8 @@ Functions and the passages they follow:
 * ``field_jvp``, ``field_gradient``  its exact forward-mode derivative, and the gradient of
                         sum_r g_r |E_r|^2
 * ``power3``          Sec. VI's 3D extension for triangle walls (same steps, planes for lines)
-* ``power3_jvp``, ``gradient3_tx``  its exact forward-mode derivative; the TX gradient
+* ``power3_jvp``, ``gradient3_tx``, ``gradient3``  its exact forward-mode derivative; the TX
+                        gradient; the gradient w.r.t. the TX and every triangle corner
 * ``mpt.cost``          Sec. V-B: the Min-Path-Tracing cost that the iterative path
                         finders' convergence check compares with zero (``oracle/mpt.py``)
 * ``power_mpt``, ``mpt_paths``  Sec. V-B, "Continuous Path Finding": reflection points found
@@ -53,13 +54,18 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (g++ -O2, no fast-math, OpenMP) if it is missing or stale."""
+    """Compile liboracle.so (g++ -O2, no fast-math, no FMA contraction, OpenMP) if it is
+    missing or stale."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
+    # -ffp-contract=off: every a * b + c is a rounded product and a rounded sum on
+    # every host (gcc fuses them into one FMA by default on Arm), so the oracle's
+    # results do not depend on the machine it is built on
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o",
+           tmp, _SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -330,6 +336,32 @@ def gradient3_tx(tris, tx, rx, max_order, alpha, smoothing, g, refl_coef=0.5, th
                            dtx, refl_coef, threads)
         out[a] = float(np.dot(g[nz], dP))
     return out
+
+
+def gradient3(tris, tx, rx, max_order, alpha, smoothing, g, refl_coef=0.5, threads=None):
+    """(sum_r g_r dP_r / dTX [3], sum_r g_r dP_r / dtris [W, 9]) of a 3D scene, one
+    forward-mode pass per parameter over the receivers with g_r != 0."""
+    tris = _f64(tris).reshape(-1, 9)
+    rx = _f64(rx).reshape(-1, 3)
+    g = _f64(g).reshape(-1)
+    nz = np.nonzero(g)[0]
+    gtx, gtris = np.zeros(3), np.zeros(tris.shape)
+    if nz.size == 0:
+        return gtx, gtris
+    for a in range(3 + tris.size):
+        dtx, dtr = np.zeros(3), np.zeros(tris.size)
+        if a < 3:
+            dtx[a] = 1.0
+        else:
+            dtr[a - 3] = 1.0
+        _, dP = power3_jvp(tris, tx, rx[nz], max_order, alpha, smoothing, dtr.reshape(tris.shape),
+                           dtx, refl_coef, threads)
+        v = float(np.dot(g[nz], dP))
+        if a < 3:
+            gtx[a] = v
+        else:
+            gtris.flat[a - 3] = v
+    return gtx, gtris
 
 
 def loss(P) -> tuple[float, int]:

@@ -403,7 +403,12 @@ Vec<T> path_field(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec
 //   validity   prod_j s(tau_j) s(len_j - tau_j) * kappa: the convergence check takes
 //              the place of the image method's same-side test (a converged
 //              reflection has its neighbours on one side);
-//   degenerate a leg of zero length at any step: the path contributes 0.
+//   degenerate a leg of zero length at any step, or a leg shorter than 1e-3 (in the
+//              scene's length unit) at the final points: the path contributes 0
+//              (iterations that run into the corner where two walls meet shrink the
+//              leg between them towards zero without converging; at 1e-3 such a
+//              leg is still long enough that single and double precision runs of
+//              the finder agree on which side of the limit it ends);
 // (Fermat path tracing, Newton steps on the path length, is not used: the length
 // is not differentiable where a leg vanishes, and for two walls meeting at a
 // corner the iteration runs into the corner and stalls there.)
@@ -441,6 +446,7 @@ FinderLegs finder_legs(const std::vector<Wall<double>>& walls, const Vec<double>
 }
 
 constexpr int FINDER_HALVINGS = 12;
+constexpr double MPT_MIN_LEG = 1e-3;
 
 // reflection law residual r_j = h_j - R_j h_{j-1} at point j (1..k)
 Vec<double> mpt_residual(const Wall<double>& w, const Vec<double>& hin, const Vec<double>& hout) {
@@ -491,7 +497,10 @@ bool mpt_points(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
   const int k = (int)seq.size();
   tau.assign(k, 0.0);
   for (int j = 0; j < k; ++j) tau[j] = 0.5 * walls[seq[j]].len;
-  if (k == 0) return !finder_legs(walls, tx, rx, seq, tau).degenerate;
+  if (k == 0) {
+    const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
+    return !f.degenerate && f.l[0] >= MPT_MIN_LEG;
+  }
   auto proj = [](const FinderLegs& f, int leg, const Vec<double>& v) {   // (I - h h^T) v / l
     const double c = dot(f.h[leg], v);
     return Vec<double>{(v.x - c * f.h[leg].x) / f.l[leg], (v.y - c * f.h[leg].y) / f.l[leg]};
@@ -551,7 +560,11 @@ bool mpt_points(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
       }
     }
   }
-  return !finder_legs(walls, tx, rx, seq, tau).degenerate;
+  const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
+  if (f.degenerate) return false;
+  for (double l : f.l)
+    if (l < MPT_MIN_LEG) return false;
+  return true;
 }
 
 // Power of one path candidate whose reflection points come from the MPT path

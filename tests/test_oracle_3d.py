@@ -192,6 +192,26 @@ def test_3d_gradient_closed_form_ground_reflection(oracle_mod):
     np.testing.assert_allclose(got, ref, rtol=1e-12)
 
 
+def test_3d_corner_derivative_closed_form_ground_height(oracle_mod):
+    # raising the ground plane z = h (all corners of its triangle) moves TX's image
+    # (tx, ty, 2h - tz): d/dh Gamma / |RX - I|^2 = 4 Gamma (rz - Iz) / |RX - I|^4, and the
+    # line of sight does not move; per corner the derivatives must add up to it
+    h = 0.15
+    ground = np.array([[-50.0, -50.0, h, 50.0, -50.0, h, 0.0, 50.0, h]])
+    tx = np.array([0.2, -0.1, 1.0])
+    rx = np.array([[2.0, 0.5, 0.5], [1.0, -1.0, 2.0]])
+    g = np.array([0.7, -1.3])
+    gtx, gtris = oracle_mod.gradient3(ground, tx, rx, 1, 1.0, "step", g, GAMMA)
+    img = np.array([tx[0], tx[1], 2 * h - tx[2]])
+    ref = sum(gr * 4 * GAMMA * (r[2] - img[2]) / np.dot(r - img, r - img) ** 2
+              for r, gr in zip(rx, g))
+    assert gtris[0, [2, 5, 8]].sum() == pytest.approx(ref, rel=1e-12)
+    # in-plane moves of the corners change nothing while the reflection point stays inside
+    np.testing.assert_allclose(gtris[0, [0, 1, 3, 4, 6, 7]], 0.0, atol=1e-12)
+    np.testing.assert_allclose(gtx, oracle_mod.gradient3_tx(ground, tx, rx, 1, 1.0, "step", g,
+                                                            GAMMA), rtol=1e-14)
+
+
 @pytest.mark.parametrize("fn,alpha", [("sigmoid", 25.0), ("hard_sigmoid", 40.0)])
 def test_3d_jvp_equals_central_differences(oracle_mod, fn, alpha):
     rng = np.random.default_rng(6)

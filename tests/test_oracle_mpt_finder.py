@@ -108,14 +108,18 @@ def test_converges_to_the_image_method_points_on_valid_paths():
                     continue
                 seq = tuple(int(w) for w in im["seq"][c][:k])
                 tau_im = mpt.tau_of(walls, seq, im["verts"][c][1:k + 1])
-                if f["cost"][c] < 1e-20:
+                if not f["degenerate"][c] and f["cost"][c] < 1e-20:
                     np.testing.assert_allclose(f["tau"][c][:k], tau_im, atol=1e-8)
                 lens = np.hypot(walls[list(seq), 2] - walls[list(seq), 0],
                                 walls[list(seq), 3] - walls[list(seq), 1])
+                legs = np.hypot(*np.diff(im["verts"][c][:k + 2], axis=0).T)
                 if (mpt.cost(walls, seq, tau_im, tx, rx) < 1e-20 and
                         np.all((tau_im > 0) & (tau_im < lens))):
                     n_valid += 1
-                    assert not f["degenerate"][c]
+                    # a leg shorter than 1e-4 makes the path degenerate by definition
+                    assert bool(f["degenerate"][c]) == bool(legs.min() < 1e-4)
+                    if f["degenerate"][c]:
+                        continue
                     if np.abs(f["tau"][c][:k] - tau_im).max() <= 1e-10:
                         n_conv += 1
                         assert f["cost"][c] < 1e-18 and f["kappa"][c] == 1.0
@@ -153,3 +157,18 @@ def test_check_replaces_the_same_side_test():
         np.testing.assert_allclose(f["power"][ok], im["power"][ok], rtol=1e-9)
         assert np.all(f["power"][f["kappa"] == 0.0] == 0.0)
     assert n > 40
+
+
+def test_a_leg_shorter_than_the_limit_makes_the_path_degenerate():
+    # a receiver h = 2e-4 above the mirror: the converged reflection point lies 4e-4 to
+    # its left, so the last leg (sqrt(5) h) is shorter than 1e-3 and the path contributes
+    # nothing; 2e-3 above the mirror it is an ordinary path
+    tx = np.array([0.1, 0.4])
+    for h, deg in ((2e-4, 1), (2e-3, 0)):
+        rx = np.array([0.9, h])
+        d = oracle.mpt_paths(X_AXIS, tx, rx, 1, 100.0, "hard_sigmoid", n_iter=12)
+        assert d["degenerate"][1] == deg
+        if deg:
+            assert d["power"][1] == 0.0 and d["kappa"][1] == 0.0 and np.isnan(d["tau"][1, 0])
+        else:
+            assert d["tau"][1, 0] == pytest.approx(0.1 + 0.8 * 0.4 / (0.4 + h), abs=1e-10)

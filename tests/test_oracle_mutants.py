@@ -95,6 +95,7 @@ MUTANTS = {
     "mpt line search takes increases": (
         "if (mpt_cost(walls, seq, ft) <= C0 + 1e-4 * t * slope + tol) {",
         "if (mpt_cost(walls, seq, ft) >= C0 + 1e-4 * t * slope + tol) {"),
+    "mpt keeps paths with a vanishing leg": ("if (l < MPT_MIN_LEG) return false;", ""),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
