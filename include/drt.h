@@ -40,7 +40,13 @@ extern "C" {
 #endif
 
 #define DRT_MAX_ORDER 3    /* largest supported K */
-#define DRT_MAX_WALLS 1024 /* largest supported W per scene */
+#define DRT_MAX_WALLS 1024 /* largest supported W per scene (see DRT_MAX_WALLS_STREAMED) */
+/* Largest W of drt_forward (and its workspace query and tuner): above
+   DRT_MAX_WALLS it reads the walls' records from a staging area in its workspace
+   instead of shared memory.  Every other entry point takes at most DRT_MAX_WALLS.
+   Every entry point also needs fewer than 2^31 path candidates (N_K below);
+   larger (n_walls, max_order) pairs get DRT_ERR_UNSUPPORTED. */
+#define DRT_MAX_WALLS_STREAMED 65536
 
 typedef enum {
   DRT_OK = 0,
@@ -110,11 +116,55 @@ drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* ti
    with V_j the smoothed validity of reflection j (on-segment and same-side
    tests, Sec. V-A), vis_j the smoothed visibility of leg j (every wall except
    the ones the leg's end points lie on), L the path length.
-   scene: host pointer to the descriptor; power: [n_rx], overwritten;
-   workspace: device scratch of at least drt_forward_workspace_size bytes
-   (contents undefined on return); tile: host pointer or NULL for defaults. */
+   scene: host pointer to the descriptor (n_walls up to DRT_MAX_WALLS_STREAMED);
+   power: [n_rx], overwritten; workspace: device scratch of at least
+   drt_forward_workspace_size bytes (contents undefined on return; 16-byte aligned
+   when n_walls > DRT_MAX_WALLS: it then also holds the walls' records, which the
+   kernels read through the caches instead of shared memory); tile: host pointer
+   or NULL for defaults. */
 drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+   Iterative path finder with the smoothed convergence check (Sec. V-B,
+   "Continuous Path Finding": the path finders check convergence with the
+   Min-Path-Tracing cost, which is zero on a valid path, the comparison with
+   zero smoothed by s).  For every candidate (w_1..w_k) the reflection points
+   X_j = A_j + tau_j u_j on the walls' lines are found by Min-Path-Tracing
+   steps instead of the image method:
+     residuals  r_j = h_j - R_j h_{j-1}, h_j the unit direction of leg j, R_j the
+                mirror of wall j (zero iff the reflection law holds at X_j);
+     cost       C = sum_j |r_j|^2;
+     start      tau_j = |B_j - A_j| / 2 (the walls' midpoints);
+     each step  a Gauss-Newton step (J^T J + 1e-6 diag) delta = -J^T r, every
+                delta_j clamped to [-len_j, len_j], then the largest fraction
+                2^-m (m < 12) of delta that lowers C by 1e-4 of its slope (up to
+                8 units of FP32 rounding of C), or no step;
+     validity   prod_j s(tau_j) s(len_j - tau_j) * kappa with the convergence
+                check kappa = s(check_eps - C); the same-side test of drt_forward
+                is not applied (a converged reflection has its neighbours on one
+                side);
+   obstruction, Gamma^k and 1 / L^2 as in drt_forward.  A path with a leg of
+   zero length at any step, or shorter than 1e-3 (scene units) at the final
+   points, contributes 0.  n_iter: 0..DRT_MPT_MAX_ITER steps.
+   check_eps: finite, in the units of C (which is dimensionless, 0 to 4 per
+   reflection).  With the hard sigmoid, check_eps >= 3 / alpha makes kappa = 1 on
+   converged paths.  One receiver per lane; tile as for drt_forward (the flags
+   are ignored). */
+#define DRT_MPT_MAX_ITER 64
+drt_status drt_forward_mpt_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                          size_t* bytes);
+drt_status drt_forward_mpt(const drt_scene* scene, const drt_tile* tile, int32_t n_iter,
+                           float check_eps, float* power, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
+/* Per path record of the path finder for every (receiver, candidate):
+   paths [n_rx][N_K][K + 2] device floats, overwritten: tau_1..tau_K (NaN past the
+   path's order and for a degenerate path), C, kappa (0 for a degenerate path).
+   For inspection and tests of small scenes: the output holds n_rx * N_K * (K + 2)
+   floats.  Needs no workspace.  Enqueued on `stream`. */
+drt_status drt_mpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
+                         void* stream);
 
 /* Coherent field per receiver: Eq. 7 read as a sum of complex path fields (the
    field normal to the scene plane, free-space spreading 1/L of the unfolded path):
@@ -208,6 +258,23 @@ drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* t
                                       size_t* bytes);
 drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
                        float* grad_tx, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Vector-Jacobian product of drt3_forward with respect to the transmitter and,
+   when grad_tris is not NULL, every triangle corner (Sec. III: the gradient of
+   the loss w.r.t. the scene parameters, in 3D):
+     grad_tx[i]      = sum_r grad_power[r] dP_r / dTX[i],
+     grad_tris[w][c] = sum_r grad_power[r] dP_r / dtris[w][c].
+   Reverse mode with the path recomputed, as drt3_vjp_tx; the adjoints of each
+   triangle's plane (n, c = n . A) and in-plane edge records (m_k, m_k . start)
+   are summed per CTA (warp reductions, shared-memory atomics: the order of those
+   additions varies between runs) and chained back to the corners in a fixed
+   order by a last kernel.  grad_power: [n_rx]; grad_tx: [3], overwritten;
+   grad_tris: [n_tris][9] (4-byte aligned), overwritten, or NULL; workspace: at
+   least drt3_vjp_workspace_size bytes (either variant). */
+drt_status drt3_vjp_workspace_size(const drt3_scene* scene, const drt_tile* tile, size_t* bytes);
+drt_status drt3_vjp(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
+                    float* grad_tx, float* grad_tris, void* workspace, size_t workspace_bytes,
+                    void* stream);
 
 /* Autotuner probe for drt_forward (the work decomposition does not change the
    result beyond the order of the per-chunk sums): runs drt_forward on `scene`
@@ -407,10 +474,14 @@ drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const floa
                              float* grad, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Selects the tensor-core path of the MLP's dense layers for this process:
-   1 (default) = tcgen05.mma with the accumulator in tensor memory, for tiles
-   whose batch is a multiple of 128 (other shapes use the next path);
-   0 = mma.sync (warp-level MMA).  Both give the same function up to FP32
-   summation order. */
+   1 (default) = inference (drt_mlp_forward) by the fused tcgen05.mma kernel
+   (accumulators in tensor memory), the training GEMMs of drt_mlp_loss_grad by
+   mma.sync (warp-level MMA), which is the faster of the two for them (batch
+   8192: 0.35 against 0.47 ms);
+   2 = tcgen05.mma for inference and for the training GEMMs whose batch is a
+   multiple of 128 (other shapes use mma.sync);
+   0 = mma.sync everywhere.
+   All give the same function up to FP32 summation order. */
 drt_status drt_mlp_set_tensor_core_path(int32_t use_tcgen05);
 
 /* Synchronous: *timed_out = 1 if a tcgen05 kernel gave up waiting for its

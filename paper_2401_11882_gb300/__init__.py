@@ -10,15 +10,21 @@ Public calls (PyTorch tensors on a CUDA device, float32):
   reflection), field and power per receiver; ``field_power(...)`` is its power
   |E|^2, differentiable in ``walls`` and ``tx``; ``field_vjp`` the raw adjoint.
 * ``forward3(tris, tx, rx, ...)``: the 3D extension (triangle walls), power per receiver;
-  ``power3`` differentiable in ``tx``; ``vjp3_tx`` its raw transmitter adjoint.
+  ``power3`` differentiable in ``tris`` and ``tx``; ``vjp3`` its raw adjoint (``vjp3_tx``
+  for the transmitter only).
+* ``forward_mpt(...)``: power with the reflection points found iteratively
+  (Min-Path-Tracing) and the smoothed convergence check; ``mpt_paths`` its per-path
+  record.
+* ``objective_host(...)``: the objective end to end from host arrays.
 
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
-from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, loss, min_loss,
-                  min_loss_backward, min_loss_vjp, num_candidates, objective, objective_host,
-                  power, power3, vjp, vjp3_tx)
+from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, forward_mpt,
+                  loss, min_loss, min_loss_backward, min_loss_vjp, mpt_paths, num_candidates,
+                  objective, objective_host, power, power3, vjp, vjp3, vjp3_tx)
 
-__all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "forward3", "loss",
-           "min_loss", "min_loss_backward", "min_loss_vjp", "num_candidates", "objective",
-           "objective_host", "power", "power3", "vjp", "vjp3_tx"]
+__all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "forward3",
+           "forward_mpt", "loss", "min_loss", "min_loss_backward", "min_loss_vjp", "mpt_paths",
+           "num_candidates", "objective", "objective_host", "power", "power3", "vjp", "vjp3",
+           "vjp3_tx"]

@@ -84,6 +84,8 @@ SIGNATURES = {
     "drt3_forward": (ctypes.c_int, [_P, _P, _P, _P, _SZ, _P]),
     "drt3_vjp_tx_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt3_vjp_tx": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
+    "drt3_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt3_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_field_vjp_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_field_vjp": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P, _P,
                                      _SZ, _P]),
@@ -94,6 +96,9 @@ SIGNATURES = {
     "drt_forward_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "drt_min_loss_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_objective_host_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt_forward_mpt_workspace_size": (ctypes.c_int, [_P, _P, _P]),
+    "drt_forward_mpt": (ctypes.c_int, [_P, _P, _I32, ctypes.c_float, _P, _P, _SZ, _P]),
+    "drt_mpt_paths": (ctypes.c_int, [_P, _I32, ctypes.c_float, _P, _P]),
     "drt_objective_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_batch_plan_create": (ctypes.c_int, [_P, _P, _P]),
     "drt_batch_workspace_size": (ctypes.c_int, [_P, _P]),

@@ -7,13 +7,15 @@ without ``--clock-control none`` ncu locks the GPU's clocks).
     vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
     field     drt.field (coherent field, Fresnel TE, --eps-r, --wavelength)
     field_vjp drt.field_vjp with dense g = 1/R (after one drt.field)
+    forward_mpt drt.forward_mpt (the iterative path finder, --n-iter steps, --check-eps)
     forward3  drt.forward3 on the 3D room (``scenes.room3d``, --rx-grid receivers a side)
     vjp3      drt.vjp3_tx (transmitter gradient) on the same room, dense g = 1/R
     mlp       the surrogate MLP's inference on --batch random points
 
-Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload)
-and ``large`` (square + 60 segments, K <= 2, the benchmark workload), each on an
-n x n receiver grid.
+Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload),
+``large`` (square + 60 segments, K <= 2, the benchmark workload) and ``clutter``
+(square + --segments random segments, K <= --order; more than 1020 segments
+exceed what shared memory holds), each on an n x n receiver grid.
 """
 from __future__ import annotations
 
@@ -28,9 +30,13 @@ from . import ops, scenes
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("op", choices=["forward", "vjp", "mlp", "field", "field_vjp", "forward3",
-                                   "vjp3"])
+                                   "vjp3", "forward_mpt"])
     ap.add_argument("--batch", type=int, default=65536)
-    ap.add_argument("--scene", choices=["gradient", "large"], default="gradient")
+    ap.add_argument("--scene", choices=["gradient", "large", "clutter"], default="gradient")
+    ap.add_argument("--segments", type=int, default=4092)
+    ap.add_argument("--order", type=int, default=1)
+    ap.add_argument("--n-iter", type=int, default=10)
+    ap.add_argument("--check-eps", type=float, default=0.05)
     ap.add_argument("--smoothing", default="sigmoid", choices=["hard_sigmoid", "sigmoid", "step"])
     ap.add_argument("--alpha", type=float, default=100.0)
     ap.add_argument("--rx-grid", type=int, default=32)
@@ -80,8 +86,12 @@ def main() -> int:
                           "alpha": args.alpha, "n_tris": sc3.n_tris, "n_rx": sc3.n_rx, "ms": ms,
                           "evals_per_s": n / (ms / 1e3)}))
         return 0
-    sc = (scenes.gradient_scene if args.scene == "gradient" else scenes.large_scene)(
-        alpha=args.alpha, smoothing=args.smoothing)
+    if args.scene == "clutter":
+        sc = scenes.clutter_scene(args.segments, 1, seed=1, alpha=args.alpha,
+                                  smoothing=args.smoothing, max_order=args.order)
+    else:
+        sc = (scenes.gradient_scene if args.scene == "gradient" else scenes.large_scene)(
+            alpha=args.alpha, smoothing=args.smoothing)
     rx = scenes.rx_grid(args.rx_grid)
     w, t, r = (torch.tensor(x, device=dev) for x in (sc.walls, sc.tx, rx))
     g = torch.full((r.shape[0],), 1.0 / r.shape[0], device=dev)
@@ -94,13 +104,16 @@ def main() -> int:
         tile = ops.TileConfig(single_rx=True) if args.single_rx else None
         if args.op == "forward":
             return ops.forward(w, t, r, sc.max_order, args.alpha, args.smoothing, tile=tile)
+        if args.op == "forward_mpt":
+            return ops.forward_mpt(w, t, r, sc.max_order, args.alpha, args.smoothing,
+                                   args.n_iter, args.check_eps, tile=tile)
         if args.op == "field":
             return ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
                              args.eps_r, tile=tile)
         if args.op == "field_vjp":
             return ops.field_vjp(w, t, r, sc.max_order, args.alpha, args.smoothing,
                                  args.wavelength, args.eps_r, E, g)
-        return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g)
+        return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g, tile=tile)
 
     for _ in range(2):
         run()

@@ -22,6 +22,7 @@
 #include "drt_common.cuh"
 #include "drt_internal.h"
 #include "drt_path_vjp.cuh"
+#include "drt_path_vjp_pair.cuh"
 
 namespace drt {
 
@@ -65,6 +66,82 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
         case 1: path_vjp<MODE, 1, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y); break;
         case 2: path_vjp<MODE, 2, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y); break;
         default: path_vjp<MODE, 3, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y); break;
+      }
+    }
+  }
+  txb_x = warp_sum(txb_x);
+  txb_y = warp_sum(txb_y);
+  if (lane == 0) {
+    a.warp_tx[2 * gwarp] = txb_x;
+    a.warp_tx[2 * gwarp + 1] = txb_y;
+  }
+  if (WG) {
+    __syncthreads();
+    float* out = a.cta_walls + (size_t)blockIdx.x * a.W * VJP_SLOTS;
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) out[i] = s.acc[i];
+  }
+}
+
+// Sigmoid with the wall gradient, two receivers per lane: units are (64
+// receivers) x (a chunk of candidates); lane l holds receivers l and l + 32 of
+// its tile.  The paired wall
+// records follow the four single-receiver arrays, the per-CTA wall table follows
+// those.
+// Resident CTAs per SM the paired kernel is compiled for (registers per thread
+// follow: 65536 / (256 threads x this)).  Two CTAs (128 registers, a few hundred
+// bytes of spills) measured faster than one (227 registers, no spills, 8 warps
+// per SM: dependency stalls dominate).
+#ifndef DRT_VJP_PAIR_MIN_CTAS
+#define DRT_VJP_PAIR_MIN_CTAS 2
+#endif
+#ifndef DRT_VJP_PAIR_MAX_THREADS
+#define DRT_VJP_PAIR_MAX_THREADS 256
+#endif
+
+template <bool WG>
+__global__ void __launch_bounds__(DRT_VJP_PAIR_MAX_THREADS, DRT_VJP_PAIR_MIN_CTAS)
+    vjp_pair_kernel(const VjpArgs a) {
+  extern __shared__ float4 smem[];
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  VSmem s;
+  s.G = smem;
+  s.E = smem + a.W;
+  s.T = smem + 2 * a.W;
+  s.H = smem + 3 * a.W;
+  const SmemPairsVjp pr{smem + 4 * a.W, smem + 5 * a.W, smem + 6 * a.W, smem + 7 * a.W,
+                        smem + 8 * a.W};
+  s.acc = reinterpret_cast<float*>(smem + 9 * a.W);
+  stage_walls<MODE_SIGMOID>(a.walls, a.W, tx, a.alpha, SmemWalls{s.G, s.E, s.T, s.H});
+  if (WG)
+    for (int i = threadIdx.x; i < a.W * VJP_SLOTS; i += blockDim.x) s.acc[i] = 0.f;
+  __syncthreads();
+  stage_pairs_vjp(s, a.W, pr);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const long long warps_per_cta = blockDim.x >> 5;
+  const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * warps_per_cta;
+  float txb_x = 0.f, txb_y = 0.f;
+  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+    const long long tile = u % a.n_tiles;
+    const long long chunk = u / a.n_tiles;
+    const long long r0 = tile * 64 + lane, r1 = r0 + 32;
+    const bool live0 = r0 < a.R, live1 = r1 < a.R;
+    const float g0 = live0 ? __ldg(a.grad_power + r0) : 0.f;
+    const float g1 = live1 ? __ldg(a.grad_power + r1) : 0.f;
+    if (__all_sync(FULL, g0 == 0.f && g1 == 0.f)) continue;
+    const float2 q0 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live0 ? r0 : a.R - 1));
+    const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live1 ? r1 : a.R - 1));
+    const long long c0 = chunk * a.chunk;
+    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+    for (long long c = c0; c < c1; ++c) {
+      const Cand cd = decode_candidate(c, a.W, a.K);
+      switch (cd.k) {
+        case 0: path_vjp_pair<0, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], g0, g1, txb_x, txb_y); break;
+        case 1: path_vjp_pair<1, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], g0, g1, txb_x, txb_y); break;
+        case 2: path_vjp_pair<2, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], g0, g1, txb_x, txb_y); break;
+        default: path_vjp_pair<3, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], g0, g1, txb_x, txb_y); break;
       }
     }
   }
@@ -293,13 +370,21 @@ void launch_vjp_t(const VjpArgs& a, int ctas, int threads, size_t smem, cudaStre
 
 }  // namespace
 
-size_t vjp_smem_bytes(int W, bool wall_grad) {
-  return (size_t)4 * W * sizeof(float4) + (wall_grad ? (size_t)W * VJP_SLOTS * sizeof(float) : 0);
+size_t vjp_smem_bytes(int W, bool wall_grad, bool pairs) {
+  return (size_t)(pairs ? 9 : 4) * W * sizeof(float4) +
+         (wall_grad ? (size_t)W * VJP_SLOTS * sizeof(float) : 0);
+}
+
+bool vjp_uses_pairs(int mode, int flags) {
+  return mode == MODE_SIGMOID && !(flags & DRT_TILE_SINGLE_RX);
 }
 
 cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   const bool wg = a.grad_walls != nullptr;
-  const size_t smem = vjp_smem_bytes(a.W, wg);
+  const size_t smem = vjp_smem_bytes(a.W, wg, a.pairs && !a.rx_index && wg);
+  if (a.pairs && !a.rx_index && mode == MODE_SIGMOID && wg) {
+    vjp_pair_kernel<true><<<ctas, threads, smem, st>>>(a);
+  } else
   switch (mode * 2 + (wg ? 1 : 0)) {
     case MODE_SIGMOID * 2: launch_vjp_t<MODE_SIGMOID, false>(a, ctas, threads, smem, st); break;
     case MODE_SIGMOID * 2 + 1: launch_vjp_t<MODE_SIGMOID, true>(a, ctas, threads, smem, st); break;
@@ -318,7 +403,7 @@ cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaSt
 
 cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   const bool wg = a.grad_walls != nullptr;
-  const size_t smem = vjp_smem_bytes(a.W, wg);
+  const size_t smem = vjp_smem_bytes(a.W, wg, false);
   switch (mode * 2 + (wg ? 1 : 0)) {
     case MODE_SIGMOID * 2: field_vjp_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a); break;
     case MODE_SIGMOID * 2 + 1: field_vjp_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a); break;
@@ -336,7 +421,7 @@ cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, 
 }
 
 cudaError_t field_vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas_per_sm) {
-  const size_t smem = vjp_smem_bytes(W, wg);
+  const size_t smem = vjp_smem_bytes(W, wg, false);
   switch (mode * 2 + (wg ? 1 : 0)) {
     case MODE_SIGMOID * 2:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, field_vjp_kernel<MODE_SIGMOID, false>, threads, smem);
@@ -353,8 +438,11 @@ cudaError_t field_vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas
   }
 }
 
-cudaError_t vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas_per_sm) {
-  const size_t smem = vjp_smem_bytes(W, wg);
+cudaError_t vjp_occupancy(int mode, bool wg, bool pairs, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = vjp_smem_bytes(W, wg, pairs);
+  if (pairs && mode == MODE_SIGMOID && wg)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_pair_kernel<true>,
+                                                         threads, smem);
   switch (mode * 2 + (wg ? 1 : 0)) {
     case MODE_SIGMOID * 2:
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp_kernel<MODE_SIGMOID, false>, threads, smem);
@@ -372,8 +460,11 @@ cudaError_t vjp_occupancy(int mode, bool wg, int threads, int W, int* ctas_per_s
 }
 
 cudaError_t vjp_set_smem_limit(int W) {
-  const int s0 = (int)vjp_smem_bytes(W, false), s1 = (int)vjp_smem_bytes(W, true);
+  const int s0 = (int)vjp_smem_bytes(W, false, false), s1 = (int)vjp_smem_bytes(W, true, false);
   cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(vjp_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)vjp_smem_bytes(W, true, true));
+  if (e != cudaSuccess) return e;
 #define DRT_SET(M, B, S)                                                                    \
   e = cudaFuncSetAttribute(vjp_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \
   if (e != cudaSuccess) return e;                                                           \

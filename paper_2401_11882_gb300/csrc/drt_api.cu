@@ -65,6 +65,8 @@ drt_status device_info(int* sms) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(field)");
     e = forward3_set_smem_limit(DRT_MAX_WALLS);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(forward3)");
+    e = forward_mpt_set_smem_limit(DRT_MAX_WALLS);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(forward_mpt)");
     d.smem_set = true;
   }
   *sms = d.sms;
@@ -80,15 +82,21 @@ long long num_candidates(int W, int K) {
   return n;
 }
 
-drt_status check_scene(const drt_scene* sc) {
+// max_walls: DRT_MAX_WALLS for the kernels that hold every wall in shared memory,
+// DRT_MAX_WALLS_STREAMED for drt_forward (global staging above DRT_MAX_WALLS)
+drt_status check_scene(const drt_scene* sc, int max_walls = DRT_MAX_WALLS) {
   if (!sc) return fail(DRT_ERR_INVALID_ARG, "scene is NULL");
-  if (sc->n_walls < 1 || sc->n_walls > DRT_MAX_WALLS)
-    return fail(sc->n_walls > DRT_MAX_WALLS ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
-                "n_walls = %d outside 1..%d", sc->n_walls, DRT_MAX_WALLS);
+  if (sc->n_walls < 1 || sc->n_walls > max_walls)
+    return fail(sc->n_walls > max_walls ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
+                "n_walls = %d outside 1..%d", sc->n_walls, max_walls);
   if (sc->n_rx < 0) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 0", sc->n_rx);
   if (sc->max_order < 0 || sc->max_order > DRT_MAX_ORDER)
     return fail(sc->max_order > DRT_MAX_ORDER ? DRT_ERR_UNSUPPORTED : DRT_ERR_INVALID_ARG,
                 "max_order = %d outside 0..%d", sc->max_order, DRT_MAX_ORDER);
+  // the kernels index the candidates with 32-bit integers
+  if (num_candidates(sc->n_walls, sc->max_order) > 0x7fffffffLL)
+    return fail(DRT_ERR_UNSUPPORTED, "%d walls with max_order %d: more than 2^31 - 1 candidates",
+                sc->n_walls, sc->max_order);
   if (!(sc->alpha >= 0.f) || !std::isfinite(sc->alpha))
     return fail(DRT_ERR_INVALID_ARG, "alpha must be finite and >= 0");
   if (!std::isfinite(sc->refl_coef)) return fail(DRT_ERR_INVALID_ARG, "refl_coef must be finite");
@@ -115,7 +123,10 @@ drt_status check_tile(const drt_tile* t) {
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
 
-enum Kernel { FWD, VJP, FIELD, FIELD_VJP, FWD3, VJP3 };
+// VJP_RX: the min-loss adjoint's one-receiver kernel (lanes = candidates)
+// VJP_TX: drt_vjp without the wall gradient (one receiver per lane)
+// VJP3_TX: drt3_vjp without the triangle gradient
+enum Kernel { FWD, VJP, VJP_TX, VJP_RX, FIELD, FIELD_VJP, FWD3, VJP3, VJP3_TX, FWD_MPT };
 
 drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
   int sms = 0;
@@ -127,15 +138,16 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   d->threads = warps * 32;
   d->n_cand = num_candidates(W, K);
   long long chunk = (t && t->cands_per_unit) ? t->cands_per_unit : 64;
-  if ((kern == FWD || kern == FIELD || kern == FWD3) && R > 0) {
+  if ((kern == FWD || kern == FIELD || kern == FWD3 || kern == FWD_MPT) && R > 0) {
     const long long max_chunks = std::max(1LL, MAX_PARTIALS / R);
     chunk = std::max(chunk, (d->n_cand + max_chunks - 1) / max_chunks);
   }
   if (chunk > (1LL << 30)) chunk = 1LL << 30;
   d->chunk = (int)chunk;
   d->n_chunks = (d->n_cand + chunk - 1) / chunk;
-  d->pairs = (kern == FWD || kern == FIELD) &&
-             forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0);
+  d->pairs = ((kern == FWD || kern == FIELD) &&
+              forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0)) ||
+             (kern == VJP && vjp_uses_pairs(sc->smoothing, t ? t->flags : 0));
   d->n_tiles = d->pairs ? (R + 63) / 64 : (R + 31) / 32;
   d->n_units = d->n_tiles * d->n_chunks;
   int per_sm = (t && t->ctas_per_sm) ? t->ctas_per_sm : 0;
@@ -145,14 +157,18 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
                     : (kern == FIELD)     ? field_occupancy(mode, d->pairs, d->threads, W, &per_sm)
                     : (kern == FIELD_VJP) ? field_vjp_occupancy(mode, true, d->threads, W, &per_sm)
                     : (kern == FWD3)      ? forward3_occupancy(mode, d->threads, W, &per_sm)
-                    : (kern == VJP3)      ? vjp3_occupancy(mode, d->threads, W, &per_sm)
-                                          : vjp_occupancy(mode, true, d->threads, W, &per_sm);
+                    : (kern == VJP3)      ? vjp3_occupancy(mode, true, d->threads, W, &per_sm)
+                    : (kern == VJP3_TX)   ? vjp3_occupancy(mode, false, d->threads, W, &per_sm)
+                    : (kern == FWD_MPT)   ? forward_mpt_occupancy(mode, d->threads, W, &per_sm)
+                                          : vjp_occupancy(mode, true, d->pairs, d->threads, W,
+                                                          &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) return fail(DRT_ERR_UNSUPPORTED, "kernel does not fit on an SM");
   }
   long long ctas = (long long)sms * per_sm;
   const long long needed = (d->n_units + warps - 1) / warps;
-  if (kern == FWD || kern == FIELD || kern == FWD3) ctas = std::min(ctas, std::max(1LL, needed));
+  if (kern == FWD || kern == FIELD || kern == FWD3 || kern == FWD_MPT)
+    ctas = std::min(ctas, std::max(1LL, needed));
   d->ctas = (int)std::max(1LL, ctas);
   return DRT_OK;
 }
@@ -199,28 +215,40 @@ drt_status drt_num_candidates(int32_t n_walls, int32_t max_order, int64_t* count
   return DRT_OK;
 }
 
+// drt_forward's workspace: the per-chunk partial sums, then (more walls than
+// shared memory holds) the staged wall records, 16-byte aligned
+size_t forward_partials_bytes(const drt_scene* sc, const Decomp& d) {
+  return ((size_t)d.n_chunks * (size_t)sc->n_rx * sizeof(float) + 15) & ~(size_t)15;
+}
+size_t forward_workspace(const drt_scene* sc, const Decomp& d) {
+  const size_t staged =
+      forward_streams_walls(sc->n_walls) ? (d.pairs ? 8 : 4) * (size_t)sc->n_walls * 16 : 0;
+  return forward_partials_bytes(sc, d) + staged;
+}
+
 drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes) {
-  drt_status st = check_scene(scene);
+  drt_status st = check_scene(scene, DRT_MAX_WALLS_STREAMED);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
   if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
   Decomp d;
   if ((st = decompose(scene, tile, FWD, &d)) != DRT_OK) return st;
-  *bytes = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  *bytes = forward_workspace(scene, d);
   return DRT_OK;
 }
 
 drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
                        void* workspace, size_t workspace_bytes, void* stream) {
-  drt_status st = check_scene(scene);
+  drt_status st = check_scene(scene, DRT_MAX_WALLS_STREAMED);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
   if (scene->n_rx > 0 && !power) return fail(DRT_ERR_INVALID_ARG, "power is NULL");
   if (scene->n_rx == 0) return DRT_OK;
   Decomp d;
   if ((st = decompose(scene, tile, FWD, &d)) != DRT_OK) return st;
-  const size_t need = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
-  if (!workspace || workspace_bytes < need)
+  const size_t need = forward_workspace(scene, d);
+  const bool streamed = forward_streams_walls(scene->n_walls);
+  if (!workspace || workspace_bytes < need || (streamed && !aligned(workspace, 16)))
     return fail(DRT_ERR_WORKSPACE, "forward needs %zu workspace bytes, got %zu", need,
                 workspace_bytes);
   FwdArgs a;
@@ -241,9 +269,107 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
   a.pairs = d.pairs;
   a.partial = static_cast<float*>(workspace);
   a.power = power;
+  a.staged = streamed ? reinterpret_cast<float4*>(static_cast<char*>(workspace) +
+                                                  forward_partials_bytes(scene, d))
+                      : nullptr;
   cudaError_t e = launch_forward(a, scene->smoothing, d.ctas, d.threads,
                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return DRT_OK;
+}
+
+namespace {
+drt_status check_mpt_args(int32_t n_iter, float check_eps) {
+  if (n_iter < 0 || n_iter > DRT_MPT_MAX_ITER)
+    return fail(DRT_ERR_INVALID_ARG, "n_iter = %d outside 0..%d", n_iter, DRT_MPT_MAX_ITER);
+  if (!std::isfinite(check_eps)) return fail(DRT_ERR_INVALID_ARG, "check_eps must be finite");
+  return DRT_OK;
+}
+
+MptArgs mpt_args(const drt_scene* scene, const drt_tile* tile, const Decomp& d, int32_t n_iter,
+                 float check_eps) {
+  MptArgs m{};
+  FwdArgs& a = m.f;
+  a.walls = reinterpret_cast<const float4*>(scene->walls);
+  a.W = scene->n_walls;
+  a.rx = scene->rx;
+  a.R = scene->n_rx;
+  a.tx = scene->tx;
+  a.K = scene->max_order;
+  a.alpha = scene->alpha;
+  gamma_powers(scene->refl_coef, a.gk);
+  a.n_cand = d.n_cand;
+  a.chunk = d.chunk;
+  a.n_chunks = d.n_chunks;
+  a.n_tiles = d.n_tiles;
+  a.n_units = d.n_units;
+  a.cull = 0;
+  a.pairs = false;
+  (void)tile;
+  m.n_iter = n_iter;
+  m.check_eps = check_eps;
+  return m;
+}
+}  // namespace
+
+drt_status drt_forward_mpt_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                          size_t* bytes) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(scene, tile, FWD_MPT, &d)) != DRT_OK) return st;
+  *bytes = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  return DRT_OK;
+}
+
+drt_status drt_forward_mpt(const drt_scene* scene, const drt_tile* tile, int32_t n_iter,
+                           float check_eps, float* power, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if ((st = check_mpt_args(n_iter, check_eps)) != DRT_OK) return st;
+  if (scene->n_rx > 0 && !power) return fail(DRT_ERR_INVALID_ARG, "power is NULL");
+  if (scene->n_rx == 0) return DRT_OK;
+  Decomp d;
+  if ((st = decompose(scene, tile, FWD_MPT, &d)) != DRT_OK) return st;
+  const size_t need = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
+  if (!workspace || workspace_bytes < need)
+    return fail(DRT_ERR_WORKSPACE, "MPT forward needs %zu workspace bytes, got %zu", need,
+                workspace_bytes);
+  MptArgs m = mpt_args(scene, tile, d, n_iter, check_eps);
+  m.f.partial = static_cast<float*>(workspace);
+  m.f.power = power;
+  m.paths = nullptr;
+  cudaError_t e = launch_forward_mpt(m, scene->smoothing, d.ctas, d.threads,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "MPT forward launch");
+  return DRT_OK;
+}
+
+drt_status drt_mpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
+                         void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_mpt_args(n_iter, check_eps)) != DRT_OK) return st;
+  if (scene->n_rx > 0 && (!paths || !aligned(paths, 4)))
+    return fail(DRT_ERR_INVALID_ARG, "paths must be a 4-byte aligned device pointer");
+  if (scene->n_rx == 0) return DRT_OK;
+  const long long n_cand = num_candidates(scene->n_walls, scene->max_order);
+  if ((long long)scene->n_rx * n_cand * (scene->max_order + 2) > (1LL << 40))
+    return fail(DRT_ERR_UNSUPPORTED, "paths output of %lld records is too large",
+                (long long)scene->n_rx * n_cand);
+  Decomp d;
+  if ((st = decompose(scene, nullptr, FWD_MPT, &d)) != DRT_OK) return st;
+  MptArgs m = mpt_args(scene, nullptr, d, n_iter, check_eps);
+  m.f.partial = nullptr;
+  m.f.power = nullptr;
+  m.paths = paths;
+  cudaError_t e = launch_mpt_paths(m, scene->smoothing, d.ctas, d.threads,
+                                   static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "MPT paths launch");
   return DRT_OK;
 }
 
@@ -388,34 +514,42 @@ drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* po
   return DRT_OK;
 }
 
-drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* tile,
-                                      size_t* bytes) {
+drt_status drt3_vjp_workspace_size(const drt3_scene* scene, const drt_tile* tile, size_t* bytes) {
   drt_scene flat;
   drt_status st = check_scene3(scene, &flat);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
   if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
-  Decomp d;
+  // enough for either variant (with or without the triangle gradient)
+  Decomp d, dt;
   if ((st = decompose(&flat, tile, VJP3, &d)) != DRT_OK) return st;
-  *bytes = (size_t)d.ctas * (d.threads / 32) * 3 * sizeof(float);
+  if ((st = decompose(&flat, tile, VJP3_TX, &dt)) != DRT_OK) return st;
+  *bytes = std::max(vjp3_workspace_floats(scene->n_tris, d.ctas, d.ctas * (d.threads / 32), true),
+                    vjp3_workspace_floats(scene->n_tris, dt.ctas, dt.ctas * (dt.threads / 32),
+                                          false)) * sizeof(float);
   return DRT_OK;
 }
 
-drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
-                       float* grad_tx, void* workspace, size_t workspace_bytes, void* stream) {
+drt_status drt3_vjp(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
+                    float* grad_tx, float* grad_tris, void* workspace, size_t workspace_bytes,
+                    void* stream) {
   drt_scene flat;
   drt_status st = check_scene3(scene, &flat);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
   if (!grad_tx || (scene->n_rx > 0 && !grad_power))
     return fail(DRT_ERR_INVALID_ARG, "NULL pointer");
+  if (grad_tris && !aligned(grad_tris, 4))
+    return fail(DRT_ERR_INVALID_ARG, "grad_tris must be 4-byte aligned");
   Decomp d;
-  if ((st = decompose(&flat, tile, VJP3, &d)) != DRT_OK) return st;
-  const size_t need = (size_t)d.ctas * (d.threads / 32) * 3 * sizeof(float);
+  if ((st = decompose(&flat, tile, grad_tris ? VJP3 : VJP3_TX, &d)) != DRT_OK) return st;
+  const int warps = d.ctas * (d.threads / 32);
+  const size_t need =
+      vjp3_workspace_floats(scene->n_tris, d.ctas, warps, grad_tris != nullptr) * sizeof(float);
   if (!workspace || workspace_bytes < need || !aligned(workspace, 4))
     return fail(DRT_ERR_WORKSPACE, "3D vjp needs %zu workspace bytes, got %zu", need,
                 workspace_bytes);
-  Vjp3Args a;
+  Vjp3Args a{};
   a.tris = scene->tris;
   a.W = scene->n_tris;
   a.rx = scene->rx;
@@ -430,18 +564,40 @@ drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const floa
   a.n_tiles = d.n_tiles;
   a.n_units = d.n_units;
   a.grad_power = grad_power;
-  a.warp_tx = static_cast<float*>(workspace);
+  float* ws = static_cast<float*>(workspace);
+  a.warp_tx = ws;
+  a.cta_tris = grad_tris ? ws + (size_t)warps * 3 : nullptr;
   a.grad_tx = grad_tx;
+  a.grad_tris = grad_tris;
   cudaError_t e = launch_vjp3(a, scene->smoothing, d.ctas, d.threads,
                               static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "3D vjp launch");
   return DRT_OK;
 }
 
+drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* tile,
+                                      size_t* bytes) {
+  drt_scene flat;
+  drt_status st = check_scene3(scene, &flat);
+  if (st != DRT_OK) return st;
+  if ((st = check_tile(tile)) != DRT_OK) return st;
+  if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
+  Decomp d;
+  if ((st = decompose(&flat, tile, VJP3_TX, &d)) != DRT_OK) return st;
+  *bytes = vjp3_workspace_floats(scene->n_tris, d.ctas, d.ctas * (d.threads / 32), false) *
+           sizeof(float);
+  return DRT_OK;
+}
+
+drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
+                       float* grad_tx, void* workspace, size_t workspace_bytes, void* stream) {
+  return drt3_vjp(scene, tile, grad_power, grad_tx, nullptr, workspace, workspace_bytes, stream);
+}
+
 drt_status drt_tune_forward(const drt_scene* scene, const drt_tile* cands, int32_t n_cand,
                             int32_t reps, float* power, void* workspace, size_t workspace_bytes,
                             drt_tile* best, float* ms_out, void* stream) {
-  drt_status st = check_scene(scene);
+  drt_status st = check_scene(scene, DRT_MAX_WALLS_STREAMED);
   if (st != DRT_OK) return st;
   if (!cands || n_cand < 1 || !best || !power)
     return fail(DRT_ERR_INVALID_ARG, "cands, n_cand >= 1, best and power are required");
@@ -521,9 +677,11 @@ drt_status drt_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile, 
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
   if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
-  Decomp d;
+  // enough for either mapping (with or without the wall gradient)
+  Decomp d, dt;
   if ((st = decompose(scene, tile, VJP, &d)) != DRT_OK) return st;
-  *bytes = vjp_workspace(scene, d);
+  if ((st = decompose(scene, tile, VJP_TX, &dt)) != DRT_OK) return st;
+  *bytes = std::max(vjp_workspace(scene, d), vjp_workspace(scene, dt));
   return DRT_OK;
 }
 
@@ -538,7 +696,7 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
   if (grad_walls && !aligned(grad_walls, 16))
     return fail(DRT_ERR_INVALID_ARG, "grad_walls must be 16-byte aligned");
   Decomp d;
-  if ((st = decompose(scene, tile, VJP, &d)) != DRT_OK) return st;
+  if ((st = decompose(scene, tile, grad_walls ? VJP : VJP_TX, &d)) != DRT_OK) return st;
   const size_t need = vjp_workspace(scene, d);
   if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
     return fail(DRT_ERR_WORKSPACE, "vjp needs %zu aligned workspace bytes, got %zu", need,
@@ -559,6 +717,7 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
   a.n_chunks = d.n_chunks;
   a.n_tiles = d.n_tiles;
   a.n_units = d.n_units;
+  a.pairs = d.pairs;
   a.grad_power = grad_power;
   float* ws = static_cast<float*>(workspace);
   a.cta_walls = ws;
@@ -653,8 +812,9 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
   if (scene->n_rx < 1) return fail(DRT_ERR_INVALID_ARG, "n_rx = %d < 1", scene->n_rx);
   if (grad_walls && !aligned(grad_walls, 16))
     return fail(DRT_ERR_INVALID_ARG, "grad_walls must be 16-byte aligned");
-  Decomp d;
+  Decomp d, drx;
   if ((st = decompose(scene, tile, VJP, &d)) != DRT_OK) return st;
+  if ((st = decompose(scene, tile, VJP_RX, &drx)) != DRT_OK) return st;
   const size_t need = vjp_workspace(scene, d);
   if (!workspace || workspace_bytes < need || !aligned(workspace, 16))
     return fail(DRT_ERR_WORKSPACE, "min-loss vjp needs %zu aligned workspace bytes, got %zu",
@@ -683,8 +843,10 @@ drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const 
   a.grad_walls = grad_walls;
   // one receiver: only ceil(N_K / 32) warps have work, so launch no more CTAs than
   // that (fewer per-CTA tables for the final reduction to add up)
+  // (and no more than the receiver-tile decomposition the workspace is sized for)
   const long long busy = (a.n_units + d.threads / 32 - 1) / (d.threads / 32);
-  const int ctas = (int)std::max(1LL, std::min((long long)d.ctas, busy));
+  const int ctas = (int)std::max(
+      1LL, std::min({(long long)d.ctas, (long long)drx.ctas, busy}));
   cudaError_t e = launch_vjp(a, scene->smoothing, ctas, d.threads,
                              static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "min-loss vjp launch");
@@ -711,7 +873,7 @@ drt_status host_obj_layout(const drt_scene* sc, const drt_tile* tile, HostObjLay
   if (st != DRT_OK) return st;
   if ((st = decompose(sc, tile, VJP, &dv)) != DRT_OK) return st;
   const size_t W = (size_t)sc->n_walls, R = (size_t)sc->n_rx;
-  L->fws_bytes = (size_t)df.n_chunks * R * sizeof(float);
+  L->fws_bytes = forward_workspace(sc, df);
   L->vws_bytes = vjp_workspace(sc, dv);
   size_t off = 0;
   auto take = [&](size_t n) { const size_t o = off; off += round256(n); return o; };

@@ -24,12 +24,16 @@ namespace drt {
 
 namespace {
 
-template <int MODE>
+// GLOBAL: the wall records were written to a.staged by stage_global_kernel (scenes
+// with more walls than shared memory holds) and are read through the L1 / L2
+// caches instead of shared memory.
+template <int MODE, bool GLOBAL = false>
 __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_kernel(const FwdArgs a) {
   extern __shared__ float4 smem[];
-  SmemWalls s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
+  float4* base = GLOBAL ? a.staged : smem;
+  SmemWalls s{base, base + a.W, base + 2 * a.W, base + 3 * a.W};
   const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
-  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
+  if (!GLOBAL) stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -76,16 +80,19 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
 // Hard sigmoid and sigmoid, two receivers per lane (tiles of 64 receivers:
 // lane l holds receivers l and l + 32 of its tile); the walls' paired records
 // follow the four single-receiver arrays in shared memory.
-template <int MODE>
+template <int MODE, bool GLOBAL = false>
 __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
   extern __shared__ float4 smem[];
-  SmemWalls s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
-  SmemPairs pr{smem + 4 * a.W, smem + 5 * a.W, smem + 6 * a.W, smem + 7 * a.W};
+  float4* base = GLOBAL ? a.staged : smem;
+  SmemWalls s{base, base + a.W, base + 2 * a.W, base + 3 * a.W};
+  SmemPairs pr{base + 4 * a.W, base + 5 * a.W, base + 6 * a.W, base + 7 * a.W};
   const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
-  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
-  __syncthreads();
-  stage_pairs<MODE>(s, a.W, pr);
-  __syncthreads();
+  if (!GLOBAL) {
+    stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
+    __syncthreads();
+    stage_pairs<MODE>(s, a.W, pr);
+    __syncthreads();
+  }
 
   const int lane = threadIdx.x & 31;
   const long long warps_per_cta = blockDim.x >> 5;
@@ -116,6 +123,23 @@ __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
     }
     if (live0) a.partial[chunk * a.R + r0] = acc0;
     if (live1) a.partial[chunk * a.R + r1] = acc1;
+  }
+}
+
+// Writes the wall records of forward_kernel / forward_pair_kernel (4 or 8
+// float4 per wall, the shared-memory layout) to a global buffer, for scenes with
+// more walls than shared memory holds.  One CTA: the records are a few float4 per
+// wall, written once per launch.
+template <int MODE>
+__global__ void __launch_bounds__(1024) stage_global_kernel(const FwdArgs a) {
+  float4* base = a.staged;
+  SmemWalls s{base, base + a.W, base + 2 * a.W, base + 3 * a.W};
+  const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
+  stage_walls<MODE>(a.walls, a.W, tx, a.alpha, s);
+  if (a.pairs) {
+    __syncthreads();   // the block's own global writes are visible to it after the barrier
+    stage_pairs<MODE>(s, a.W, SmemPairs{base + 4 * a.W, base + 5 * a.W, base + 6 * a.W,
+                                        base + 7 * a.W});
   }
 }
 
@@ -194,12 +218,40 @@ __global__ void loss_backward_kernel(const int32_t* __restrict__ argmin,
 
 size_t forward_smem_bytes(int W, bool pairs) { return (size_t)(pairs ? 8 : 4) * W * sizeof(float4); }
 
+bool forward_streams_walls(int W) { return W > DRT_MAX_WALLS; }
+
 bool forward_uses_pairs(int mode, float alpha, int flags) {
   return (mode == MODE_HARD || mode == MODE_SIGMOID) && !(alpha > FAST_SKIP_MAX_ALPHA) &&
          !(flags & DRT_TILE_SINGLE_RX);
 }
 
 cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
+  if (forward_streams_walls(a.W)) {
+    if (a.n_units > 0) {
+      switch (mode) {
+        case MODE_SIGMOID: stage_global_kernel<MODE_SIGMOID><<<1, 1024, 0, st>>>(a); break;
+        case MODE_HARD: stage_global_kernel<MODE_HARD><<<1, 1024, 0, st>>>(a); break;
+        default: stage_global_kernel<MODE_STEP><<<1, 1024, 0, st>>>(a); break;
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      if (a.pairs) {
+        if (mode == MODE_SIGMOID)
+          forward_pair_kernel<MODE_SIGMOID, true><<<ctas, threads, 0, st>>>(a);
+        else
+          forward_pair_kernel<MODE_HARD, true><<<ctas, threads, 0, st>>>(a);
+      } else {
+        switch (mode) {
+          case MODE_SIGMOID: forward_kernel<MODE_SIGMOID, true><<<ctas, threads, 0, st>>>(a); break;
+          case MODE_HARD: forward_kernel<MODE_HARD, true><<<ctas, threads, 0, st>>>(a); break;
+          default: forward_kernel<MODE_STEP, true><<<ctas, threads, 0, st>>>(a); break;
+        }
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return launch_reduce_chunks(a.partial, a.n_chunks, a.R, a.power, st);
+  }
   const size_t smem = forward_smem_bytes(a.W, a.pairs);
   if (a.n_units > 0 && a.pairs) {
     if (mode == MODE_SIGMOID)
@@ -232,6 +284,25 @@ cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cu
 }
 
 cudaError_t forward_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm) {
+  if (forward_streams_walls(W)) {
+    if (pairs)
+      return mode == MODE_SIGMOID
+                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       ctas_per_sm, forward_pair_kernel<MODE_SIGMOID, true>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       ctas_per_sm, forward_pair_kernel<MODE_HARD, true>, threads, 0);
+    switch (mode) {
+      case MODE_SIGMOID:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            ctas_per_sm, forward_kernel<MODE_SIGMOID, true>, threads, 0);
+      case MODE_HARD:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            ctas_per_sm, forward_kernel<MODE_HARD, true>, threads, 0);
+      default:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            ctas_per_sm, forward_kernel<MODE_STEP, true>, threads, 0);
+    }
+  }
   const size_t smem = forward_smem_bytes(W, pairs);
   if (pairs)
     return mode == MODE_SIGMOID
@@ -270,6 +341,15 @@ cudaError_t forward_set_smem_limit(int W) {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(forward_kernel<MODE_STEP>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_reduce_chunks(const float* partial, long long n_chunks, long long R,
+                                 float* power, cudaStream_t st) {
+  if (R <= 0) return cudaSuccess;
+  const long long nb = (R + 255) / 256;
+  const int rb = (int)(nb < 4096 ? nb : 4096);
+  reduce_chunks_kernel<<<rb, 256, 0, st>>>(partial, n_chunks, R, power);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_loss(const float* power, int R, float* loss, int32_t* argmin,

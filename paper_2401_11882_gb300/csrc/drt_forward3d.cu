@@ -259,16 +259,51 @@ __device__ __forceinline__ bool leg_tri(const float4& P, const float4* M, float3
   return true;
 }
 
+// Per-triangle adjoint slots of the wall gradient (the four records' values):
+// P = {n, c} in 0..3, M_k = {m_k, o_k} in 4 + 4k .. 7 + 4k.
+constexpr int TRI_SLOTS = 16;
+
+// Sums v[0..15] over the warp by recursive halving: lane l ends with the warp
+// total of v[(l >> 1) & 15] (each total held by 2 lanes); 16 shuffles.
+__device__ __forceinline__ float warp_reduce_scatter16(const float* v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float a[8], b[4], c[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    a[k] = (b4 ? v[k + 8] : v[k]) + __shfl_xor_sync(full, b4 ? v[k] : v[k + 8], 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    b[k] = (b3 ? a[k + 4] : a[k]) + __shfl_xor_sync(full, b3 ? a[k] : a[k + 4], 8);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    c[k] = (b2 ? b[k + 2] : b[k]) + __shfl_xor_sync(full, b2 ? b[k] : b[k + 2], 4);
+  float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(full, b1 ? c[0] : c[1], 2);
+  return d + __shfl_xor_sync(full, d, 1);
+}
+
+// Adds the warp's 16 adjoint slots of triangle w into the CTA table (the
+// triangle is the same in every lane).
+__device__ __forceinline__ void add_tri_adjoint(float* acc, int w, const float* v) {
+  const float t = warp_reduce_scatter16(v);
+  const int lane = threadIdx.x & 31;
+  if ((lane & 1) == 0) atomicAdd(&acc[w * TRI_SLOTS + ((lane >> 1) & 15)], t);
+}
+
 __device__ __forceinline__ void axpy3(float a, float4 v, float3& acc) {
   acc.x = fmaf(a, v.x, acc.x);
   acc.y = fmaf(a, v.y, acc.y);
   acc.z = fmaf(a, v.z, acc.z);
 }
 
-template <int MODE, int K>
+// WG: also the adjoints of every triangle's records (plane {n, c}, edges
+// {m_k, o_k}) into the CTA table acc [W][TRI_SLOTS], summed over the warp (the
+// candidate is the same in all lanes).
+template <int MODE, int K, bool WG>
 __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, float3 rx,
                                           const Cand& cd, float alpha, float gk, float g,
-                                          float3& txb) {
+                                          float3& txb, float* acc) {
   bool degenerate = false;
 #pragma unroll
   for (int j = 1; j < K; ++j) {
@@ -278,11 +313,14 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
       degenerate = true;
   }
   float3 I[K + 1];
+  float dimg[K + 1];   // d = n . I_{j-1} - c of each image step
   I[0] = tx;
+  dimg[0] = 0.f;
 #pragma unroll
   for (int j = 1; j <= K; ++j) {
     const float4 P = s.P[cd.w[j - 1]];
-    const float d2 = 2.f * (dot3(P, I[j - 1]) - P.w);
+    dimg[j] = dot3(P, I[j - 1]) - P.w;
+    const float d2 = 2.f * dimg[j];
     I[j] = make_float3(fmaf(-d2, P.x, I[j - 1].x), fmaf(-d2, P.y, I[j - 1].y),
                        fmaf(-d2, P.z, I[j - 1].z));
   }
@@ -397,6 +435,8 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
 #pragma unroll
   for (int i = 0; i <= K + 1; ++i) Qb[i] = make_float3(0.f, 0.f, 0.f);
   // sweep 2: each factor f = 1 - X ins pushes its adjoint into the leg's end points
+  // (and, WG, into the triangle's records: x = n . Q_j - c, y = n . Q_{j+1} - c,
+  // delta_k = (1 - t) e0_k + t e1_k with e_k = m_k . Q - o_k)
   for (int w = 0; w < W; ++w) {
     const float4 P = s.P[w];
     const float4 M[3] = {s.M0[w], s.M1[w], s.M2[w]};
@@ -407,6 +447,12 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
       const float nn = fmaf(P.x, Pr[j].x, fmaf(P.y, Pr[j].y, P.z * Pr[j].z));
       cop[j] = fabsf(nn) >= 1.f - 1e-5f &&
                fabsf(fmaf(-nn, Pr[j].w, P.w)) <= 1e-5f * (1.f + fabsf(P.w));
+    }
+    float wa[TRI_SLOTS];
+    bool any = false;
+    if (WG) {
+#pragma unroll
+      for (int i = 0; i < TRI_SLOTS; ++i) wa[i] = 0.f;
     }
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
@@ -429,6 +475,14 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
         axpy3(db * (1.f - r.t), M[k], Qb[j]);
         axpy3(db * r.t, M[k], Qb[j + 1]);
         tbar = fmaf(db, r.e1[k] - r.e0[k], tbar);
+        if (WG) {
+          const float b0 = db * (1.f - r.t), b1 = db * r.t;
+          float* m = wa + 4 + 4 * k;
+          m[0] = fmaf(b0, Q[j].x, fmaf(b1, Q[j + 1].x, m[0]));
+          m[1] = fmaf(b0, Q[j].y, fmaf(b1, Q[j + 1].y, m[1]));
+          m[2] = fmaf(b0, Q[j].z, fmaf(b1, Q[j + 1].z, m[2]));
+          m[3] -= b0 + b1;
+        }
       }
       const float den = r.x - r.y;
       const float id2 = __frcp_rn(den * den);
@@ -436,7 +490,15 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
       yb = fmaf(tbar * r.x, id2, yb);
       axpy3(xb, P, Qb[j]);
       axpy3(yb, P, Qb[j + 1]);
+      if (WG) {
+        wa[0] = fmaf(xb, Q[j].x, fmaf(yb, Q[j + 1].x, wa[0]));
+        wa[1] = fmaf(xb, Q[j].y, fmaf(yb, Q[j + 1].y, wa[1]));
+        wa[2] = fmaf(xb, Q[j].z, fmaf(yb, Q[j + 1].z, wa[2]));
+        wa[3] -= xb + yb;
+        any = true;
+      }
     }
+    if (WG && __any_sync(0xffffffffu, any)) add_tri_adjoint(acc, w, wa);
   }
   // legs: L = sum |Q_{j+1} - Q_j|
 #pragma unroll
@@ -461,11 +523,26 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
     for (int k = 0; k < 3; ++k) sdl[k] = smooth3<MODE>(dot3(M[k], Q[j]) - M[k].w, alpha);
     const float ins = sdl[0].s * sdl[1].s * sdl[2].s;
     const float insb = Vb[j] * S, Sb = Vb[j] * ins;
+    float wa[TRI_SLOTS];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      axpy3(insb * sdl[k].ds * sdl[(k + 1) % 3].s * sdl[(k + 2) % 3].s, M[k], Qb[j]);
-    axpy3(Sb * sp.ds * (sq.s - sq.sb), P, Qb[j - 1]);
-    axpy3(Sb * sq.ds * (sp.s - sp.sb), P, Qb[j + 1]);
+    for (int k = 0; k < 3; ++k) {
+      const float dk = insb * sdl[k].ds * sdl[(k + 1) % 3].s * sdl[(k + 2) % 3].s;
+      axpy3(dk, M[k], Qb[j]);
+      wa[4 + 4 * k] = dk * Q[j].x;   // delta_k = m_k . Q_j - o_k
+      wa[5 + 4 * k] = dk * Q[j].y;
+      wa[6 + 4 * k] = dk * Q[j].z;
+      wa[7 + 4 * k] = -dk;
+    }
+    const float pb = Sb * sp.ds * (sq.s - sq.sb), qb = Sb * sq.ds * (sp.s - sp.sb);
+    axpy3(pb, P, Qb[j - 1]);
+    axpy3(qb, P, Qb[j + 1]);
+    if (WG) {   // p = n . Q_{j-1} - c, q = n . Q_{j+1} - c
+      wa[0] = fmaf(pb, Q[j - 1].x, qb * Q[j + 1].x);
+      wa[1] = fmaf(pb, Q[j - 1].y, qb * Q[j + 1].y);
+      wa[2] = fmaf(pb, Q[j - 1].z, qb * Q[j + 1].z);
+      wa[3] = -(pb + qb);
+      add_tri_adjoint(acc, w, wa);
+    }
   }
   // backtrace, reversed: Q_j = Q_{j+1} + t (I_j - Q_{j+1}), t = b / (b - a)
   float3 Ib[K + 1];
@@ -482,14 +559,35 @@ __device__ __forceinline__ void path_vjp3(const SmemTris& s, int W, float3 tx, f
                             fmaf(Qb[j].y, I[j].y - Q[j + 1].y, Qb[j].z * (I[j].z - Q[j + 1].z)));
     const float den = tb[j] - ta[j];
     const float id2 = (den != 0.f && !degenerate) ? __frcp_rn(den * den) : 0.f;
-    axpy3(tbar * tb[j] * id2, P, Ib[j]);
-    axpy3(-tbar * ta[j] * id2, P, Qb[j + 1]);
+    const float abar = tbar * tb[j] * id2, bbar = -tbar * ta[j] * id2;
+    axpy3(abar, P, Ib[j]);
+    axpy3(bbar, P, Qb[j + 1]);
+    if (WG) {   // a = n . I_j - c, b = n . Q_{j+1} - c
+      float wa[TRI_SLOTS];
+#pragma unroll
+      for (int i = 4; i < TRI_SLOTS; ++i) wa[i] = 0.f;
+      wa[0] = fmaf(abar, I[j].x, bbar * Q[j + 1].x);
+      wa[1] = fmaf(abar, I[j].y, bbar * Q[j + 1].y);
+      wa[2] = fmaf(abar, I[j].z, bbar * Q[j + 1].z);
+      wa[3] = -(abar + bbar);
+      add_tri_adjoint(acc, cd.w[j - 1], wa);
+    }
   }
-  // image chain, reversed: I_j = I_{j-1} - 2 (n . I_{j-1} - c) n
+  // image chain, reversed: I_j = I_{j-1} - 2 d n, d = n . I_{j-1} - c
 #pragma unroll
   for (int j = K; j >= 1; --j) {
     const float4 P = s.P[cd.w[j - 1]];
     const float dbar = -2.f * fmaf(Ib[j].x, P.x, fmaf(Ib[j].y, P.y, Ib[j].z * P.z));
+    if (WG) {   // n_bar = -2 d I_bar_j + d_bar I_{j-1}, c_bar = -d_bar
+      float wa[TRI_SLOTS];
+#pragma unroll
+      for (int i = 4; i < TRI_SLOTS; ++i) wa[i] = 0.f;
+      wa[0] = fmaf(-2.f * dimg[j], Ib[j].x, dbar * I[j - 1].x);
+      wa[1] = fmaf(-2.f * dimg[j], Ib[j].y, dbar * I[j - 1].y);
+      wa[2] = fmaf(-2.f * dimg[j], Ib[j].z, dbar * I[j - 1].z);
+      wa[3] = -dbar;
+      add_tri_adjoint(acc, cd.w[j - 1], wa);
+    }
     Ib[j - 1].x += fmaf(dbar, P.x, Ib[j].x);
     Ib[j - 1].y += fmaf(dbar, P.y, Ib[j].y);
     Ib[j - 1].z += fmaf(dbar, P.z, Ib[j].z);
@@ -505,12 +603,16 @@ __device__ __forceinline__ float warp_sum3(float v) {
   return v;
 }
 
-// grad_tx += sum_r g_r dP_r / dTX: lanes are receivers, as in the forward
-template <int MODE>
+// grad_tx += sum_r g_r dP_r / dTX (and, WG, the per-CTA table of the triangles'
+// record adjoints): lanes are receivers, as in the forward
+template <int MODE, bool WG>
 __global__ void __launch_bounds__(256, 1) vjp3_kernel(const Vjp3Args a) {
   extern __shared__ float4 smem[];
   SmemTris s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
+  float* acc = reinterpret_cast<float*>(smem + 4 * a.W);
   stage_tris(a.tris, a.W, s);
+  if (WG)
+    for (int i = threadIdx.x; i < a.W * TRI_SLOTS; i += blockDim.x) acc[i] = 0.f;
   __syncthreads();
   const float3 tx = make_float3(__ldg(a.tx), __ldg(a.tx + 1), __ldg(a.tx + 2));
   const int lane = threadIdx.x & 31;
@@ -533,10 +635,10 @@ __global__ void __launch_bounds__(256, 1) vjp3_kernel(const Vjp3Args a) {
     for (long long c = c0; c < c1; ++c) {
       const Cand cd = decode_candidate(c, a.W, a.K);
       switch (cd.k) {
-        case 0: path_vjp3<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb); break;
-        case 1: path_vjp3<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb); break;
-        case 2: path_vjp3<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb); break;
-        default: path_vjp3<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb); break;
+        case 0: path_vjp3<MODE, 0, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb, acc); break;
+        case 1: path_vjp3<MODE, 1, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb, acc); break;
+        case 2: path_vjp3<MODE, 2, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb, acc); break;
+        default: path_vjp3<MODE, 3, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb, acc); break;
       }
     }
   }
@@ -547,6 +649,95 @@ __global__ void __launch_bounds__(256, 1) vjp3_kernel(const Vjp3Args a) {
     a.warp_tx[3 * gwarp] = txb.x;
     a.warp_tx[3 * gwarp + 1] = txb.y;
     a.warp_tx[3 * gwarp + 2] = txb.z;
+  }
+  if (WG) {
+    __syncthreads();
+    float* out = a.cta_tris + (size_t)blockIdx.x * a.W * TRI_SLOTS;
+    for (int i = threadIdx.x; i < a.W * TRI_SLOTS; i += blockDim.x) out[i] = acc[i];
+  }
+}
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
+  return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z),
+                     fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float dot3f(float3 a, float3 b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+__device__ __forceinline__ float3 axpy3f(float a, float3 x, float3 y) {
+  return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
+}
+// adjoint of u = v / |v| (|v| = len): (u_bar - (u_bar . u) u) / len
+__device__ __forceinline__ float3 unit_adjoint(float3 ub, float3 u, float len) {
+  const float il = __frcp_rn(len);
+  const float c = dot3f(ub, u);
+  return make_float3(fmaf(-c, u.x, ub.x) * il, fmaf(-c, u.y, ub.y) * il, fmaf(-c, u.z, ub.z) * il);
+}
+
+// Per triangle: adds the per-CTA tables of the records' adjoints in a fixed order
+// and chains them back to the corners A, B, C (the records of stage_tris):
+//   N = (B - A) x (C - A), n = N / |N|, c = n . A;
+//   edge k from p to q: M_k = n x (q - p), m_k = M_k / |M_k|, o_k = m_k . p.
+__global__ void __launch_bounds__(256) vjp3_tris_finalize_kernel(const Vjp3Args a, int n_ctas) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < a.W; w += gridDim.x * blockDim.x) {
+    float v[TRI_SLOTS];
+#pragma unroll
+    for (int i = 0; i < TRI_SLOTS; ++i) v[i] = 0.f;
+    for (int c = 0; c < n_ctas; ++c) {
+      const float* src = a.cta_tris + ((size_t)c * a.W + w) * TRI_SLOTS;
+#pragma unroll
+      for (int i = 0; i < TRI_SLOTS; ++i) v[i] += src[i];
+    }
+    const float* t = a.tris + 9 * (size_t)w;
+    const float3 P3[3] = {make_float3(t[0], t[1], t[2]), make_float3(t[3], t[4], t[5]),
+                          make_float3(t[6], t[7], t[8])};
+    const float3 e1 = sub3(P3[1], P3[0]), e2 = sub3(P3[2], P3[0]);
+    const float3 N = cross3(e1, e2);
+    const float nl = __fsqrt_rn(dot3f(N, N));
+    const float3 n = make_float3(__fdiv_rn(N.x, nl), __fdiv_rn(N.y, nl), __fdiv_rn(N.z, nl));
+    float3 cb[3] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
+                    make_float3(0.f, 0.f, 0.f)};
+    float3 nb = make_float3(v[0], v[1], v[2]);
+    // c = n . A
+    nb = axpy3f(v[3], P3[0], nb);
+    cb[0] = axpy3f(v[3], n, cb[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float3 p = P3[k], q = P3[(k + 1) % 3];
+      const float3 e = sub3(q, p);
+      const float3 Mv = cross3(n, e);
+      const float ml = __fsqrt_rn(dot3f(Mv, Mv));
+      const float3 m = make_float3(__fdiv_rn(Mv.x, ml), __fdiv_rn(Mv.y, ml), __fdiv_rn(Mv.z, ml));
+      float3 mb = make_float3(v[4 + 4 * k], v[5 + 4 * k], v[6 + 4 * k]);
+      const float ob = v[7 + 4 * k];
+      // o = m . p
+      mb = axpy3f(ob, p, mb);
+      cb[k] = axpy3f(ob, m, cb[k]);
+      // m = M / |M|, M = n x e: n_bar += e x M_bar, e_bar = M_bar x n
+      const float3 Mb = unit_adjoint(mb, m, ml);
+      nb = make_float3(nb.x + cross3(e, Mb).x, nb.y + cross3(e, Mb).y, nb.z + cross3(e, Mb).z);
+      const float3 eb = cross3(Mb, n);
+      cb[(k + 1) % 3] = make_float3(cb[(k + 1) % 3].x + eb.x, cb[(k + 1) % 3].y + eb.y,
+                                    cb[(k + 1) % 3].z + eb.z);
+      cb[k] = make_float3(cb[k].x - eb.x, cb[k].y - eb.y, cb[k].z - eb.z);
+    }
+    // n = N / |N|, N = e1 x e2: e1_bar = e2 x N_bar, e2_bar = N_bar x e1
+    const float3 Nb = unit_adjoint(nb, n, nl);
+    const float3 e1b = cross3(e2, Nb), e2b = cross3(Nb, e1);
+    cb[1] = make_float3(cb[1].x + e1b.x, cb[1].y + e1b.y, cb[1].z + e1b.z);
+    cb[2] = make_float3(cb[2].x + e2b.x, cb[2].y + e2b.y, cb[2].z + e2b.z);
+    cb[0] = make_float3(cb[0].x - e1b.x - e2b.x, cb[0].y - e1b.y - e2b.y,
+                        cb[0].z - e1b.z - e2b.z);
+    float* out = a.grad_tris + 9 * (size_t)w;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      out[3 * k] = cb[k].x;
+      out[3 * k + 1] = cb[k].y;
+      out[3 * k + 2] = cb[k].z;
+    }
   }
 }
 
@@ -575,6 +766,14 @@ __global__ void reduce3_kernel(const float* __restrict__ partial, long long n_ch
 
 size_t forward3_smem_bytes(int W) { return (size_t)4 * W * sizeof(float4); }
 
+size_t vjp3_smem_bytes(int W, bool tri_grad) {
+  return forward3_smem_bytes(W) + (tri_grad ? (size_t)W * TRI_SLOTS * sizeof(float) : 0);
+}
+
+size_t vjp3_workspace_floats(int W, int ctas, int warps, bool tri_grad) {
+  return (size_t)warps * 3 + (tri_grad ? (size_t)ctas * W * TRI_SLOTS : 0);
+}
+
 cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st) {
   const size_t smem = forward3_smem_bytes(a.W);
   if (a.n_units > 0) {
@@ -595,35 +794,47 @@ cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, 
 }
 
 cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cudaStream_t st) {
-  const size_t smem = forward3_smem_bytes(a.W);
+  const bool wg = a.grad_tris != nullptr;
+  const size_t smem = vjp3_smem_bytes(a.W, wg);
   if (a.n_units > 0) {
-    switch (mode) {
-      case MODE_SIGMOID: vjp3_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a); break;
-      case MODE_HARD: vjp3_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a); break;
-      default: vjp3_kernel<MODE_STEP><<<ctas, threads, smem, st>>>(a); break;
+    switch (mode * 2 + (wg ? 1 : 0)) {
+      case MODE_SIGMOID * 2: vjp3_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_SIGMOID * 2 + 1: vjp3_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_HARD * 2: vjp3_kernel<MODE_HARD, false><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_HARD * 2 + 1: vjp3_kernel<MODE_HARD, true><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_STEP * 2: vjp3_kernel<MODE_STEP, false><<<ctas, threads, smem, st>>>(a); break;
+      default: vjp3_kernel<MODE_STEP, true><<<ctas, threads, smem, st>>>(a); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     vjp3_finalize_kernel<<<1, 32, 0, st>>>(a.warp_tx, (long long)ctas * (threads / 32), a.grad_tx);
+    if (wg) {
+      vjp3_tris_finalize_kernel<<<(a.W + 255) / 256, 256, 0, st>>>(a, ctas);
+    }
   } else {
     cudaError_t e = cudaMemsetAsync(a.grad_tx, 0, 3 * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    if (wg) e = cudaMemsetAsync(a.grad_tris, 0, (size_t)a.W * 9 * sizeof(float), st);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
 
-cudaError_t vjp3_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
-  const size_t smem = forward3_smem_bytes(W);
-  switch (mode) {
-    case MODE_SIGMOID:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_SIGMOID>,
-                                                           threads, smem);
-    case MODE_HARD:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_HARD>,
-                                                           threads, smem);
+cudaError_t vjp3_occupancy(int mode, bool tri_grad, int threads, int W, int* ctas_per_sm) {
+  const size_t smem = vjp3_smem_bytes(W, tri_grad);
+  switch (mode * 2 + (tri_grad ? 1 : 0)) {
+    case MODE_SIGMOID * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_SIGMOID, false>, threads, smem);
+    case MODE_SIGMOID * 2 + 1:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_SIGMOID, true>, threads, smem);
+    case MODE_HARD * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_HARD, false>, threads, smem);
+    case MODE_HARD * 2 + 1:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_HARD, true>, threads, smem);
+    case MODE_STEP * 2:
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_STEP, false>, threads, smem);
     default:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_STEP>,
-                                                           threads, smem);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, vjp3_kernel<MODE_STEP, true>, threads, smem);
   }
 }
 
@@ -653,14 +864,17 @@ cudaError_t forward3_set_smem_limit(int W) {
   e = cudaFuncSetAttribute(forward3_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(vjp3_kernel<MODE_SIGMOID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem);
+  const int s1 = (int)vjp3_smem_bytes(W, true);
+#define DRT_SET3(M)                                                                           \
+  e = cudaFuncSetAttribute(vjp3_kernel<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+  if (e != cudaSuccess) return e;                                                             \
+  e = cudaFuncSetAttribute(vjp3_kernel<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1); \
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(vjp3_kernel<MODE_HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(vjp3_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem);
+  DRT_SET3(MODE_SIGMOID)
+  DRT_SET3(MODE_HARD)
+  DRT_SET3(MODE_STEP)
+#undef DRT_SET3
+  return e;
 }
 
 }  // namespace drt

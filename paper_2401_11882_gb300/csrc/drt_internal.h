@@ -38,6 +38,7 @@ struct FwdArgs {
   bool pairs;       // two receivers per lane (n_tiles counts 64-receiver tiles)
   float* partial;   // [n_chunks][R]
   float* power;     // [R]
+  float4* staged;   // [8 or 4][W] wall records in global memory (W > DRT_MAX_WALLS), or null
 };
 
 // Coherent field (drt_field.cu): the forward's decomposition (one or two
@@ -97,6 +98,8 @@ struct Vjp3Args {
   const float* grad_power;   // [R]
   float* warp_tx;            // [ctas * warps_per_cta][3]
   float* grad_tx;            // [3]
+  float* cta_tris;           // [ctas][W][16] per-CTA record adjoints (triangle gradient only)
+  float* grad_tris;          // [W][9] or null
 };
 
 struct VjpArgs {
@@ -111,6 +114,7 @@ struct VjpArgs {
   long long n_cand;
   int chunk;
   long long n_chunks, n_tiles, n_units;
+  bool pairs;                // sigmoid receiver-tile kernel: two receivers per lane (64-receiver tiles)
   const float* grad_power;   // [R] (receiver-tile kernel)
   const int32_t* rx_index;   // [1]: one-receiver kernel (min-loss adjoint) when non-null
   const float* grad_loss;    // [1] or null (one-receiver kernel)
@@ -132,29 +136,52 @@ constexpr int VJP_SLOTS = 9;
 void set_error_message(const char* msg);
 
 size_t forward_smem_bytes(int W, bool pairs);
+// whether the forward reads its wall records from a global staging buffer (more
+// walls than its shared memory holds)
+bool forward_streams_walls(int W);
 // whether the forward runs two receivers per lane for this smoothing, alpha and tile flags
 bool forward_uses_pairs(int mode, float alpha, int flags);
 cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t forward_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);
 cudaError_t forward_set_smem_limit(int W);
+// power[r] = sum over chunks of partial[chunk][r], in chunk order
+cudaError_t launch_reduce_chunks(const float* partial, long long n_chunks, long long R,
+                                 float* power, cudaStream_t st);
 cudaError_t launch_loss(const float* power, int R, float* loss, int32_t* argmin, cudaStream_t st);
 cudaError_t launch_loss_backward(const int32_t* argmin, const float* grad_loss, int R,
                                  float* grad_power, cudaStream_t st);
+
+// Path-finder forward (drt_mpt.cu): the forward's decomposition (one receiver per
+// lane) with the reflection points found by Min-Path-Tracing steps.
+struct MptArgs {
+  FwdArgs f;          // scene, decomposition, partial sums and power (pairs = false)
+  int n_iter;         // MPT steps from the walls' midpoints
+  float check_eps;    // the convergence check is s(check_eps - C)
+  float* paths;       // drt_mpt_paths: [R][n_cand][K + 2] (tau_1..tau_K, C, kappa) or null
+};
+cudaError_t launch_forward_mpt(const MptArgs& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t launch_mpt_paths(const MptArgs& a, int mode, int ctas, int threads, cudaStream_t st);
+cudaError_t forward_mpt_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t forward_mpt_set_smem_limit(int W);
 
 size_t forward3_smem_bytes(int W);
 cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
 cudaError_t forward3_set_smem_limit(int W);
 cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cudaStream_t st);
-cudaError_t vjp3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t vjp3_occupancy(int mode, bool tri_grad, int threads, int W, int* ctas_per_sm);
+size_t vjp3_workspace_floats(int W, int ctas, int warps, bool tri_grad);
 
 cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t field_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);
 cudaError_t field_set_smem_limit(int W);
 
-size_t vjp_smem_bytes(int W, bool wall_grad);
+size_t vjp_smem_bytes(int W, bool wall_grad, bool pairs);
+// whether drt_vjp's receiver-tile kernel holds two receivers per lane for this smoothing and flags
+bool vjp_uses_pairs(int mode, int flags);
 cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st);
-cudaError_t vjp_occupancy(int mode, bool wall_grad, int threads, int W, int* ctas_per_sm);
+cudaError_t vjp_occupancy(int mode, bool wall_grad, bool pairs, int threads, int W,
+                          int* ctas_per_sm);
 cudaError_t vjp_set_smem_limit(int W);
 cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t field_vjp_occupancy(int mode, bool wall_grad, int threads, int W, int* ctas_per_sm);

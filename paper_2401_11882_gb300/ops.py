@@ -102,6 +102,39 @@ def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
     return power
 
 
+def forward_mpt(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+                n_iter: int = 10, check_eps: float = 0.05, refl_coef: float = 0.5,
+                tile: TileConfig | None = None) -> torch.Tensor:
+    """Received power per receiver (float32 [R]) with the reflection points found by
+    ``n_iter`` Min-Path-Tracing steps and the smoothed convergence check
+    s(check_eps - C) (drt_forward_mpt, Sec. V-B)."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_forward_mpt_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    _lib.call("drt_forward_mpt", ctypes.byref(sc), tlp, int(n_iter), ctypes.c_float(check_eps),
+              _ptr(power), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return power
+
+
+def mpt_paths(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+              n_iter: int = 10, check_eps: float = 0.05, refl_coef: float = 0.5) -> torch.Tensor:
+    """Path finder record per (receiver, candidate): float32 [R, N_K, K + 2] holding
+    tau_1..tau_K (NaN past the path's order or for a degenerate path), the MPT cost
+    C and the check kappa (drt_mpt_paths)."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    n = num_candidates(sc.n_walls, int(max_order))
+    out = torch.empty(sc.n_rx, n, int(max_order) + 2, dtype=torch.float32, device=dev)
+    _lib.call("drt_mpt_paths", ctypes.byref(sc), int(n_iter), ctypes.c_float(check_eps),
+              _ptr(out), _stream_ptr(dev))
+    return out
+
+
 def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
           eps_r: float, refl_coef: float = 0.5, tile: TileConfig | None = None):
     """Coherent field and power per receiver on the current stream:
@@ -200,8 +233,32 @@ def vjp3_tx(tris, tx, rx, max_order: int, alpha: float, smoothing: str,
     return gtx
 
 
+def vjp3(tris, tx, rx, max_order: int, alpha: float, smoothing: str,
+         grad_power: torch.Tensor, refl_coef: float = 0.5, tri_grad: bool = True,
+         tile: TileConfig | None = None):
+    """(grad_tx [3], grad_tris [W, 9] or None) = grad_power^T dP / d(tx, tris) of a 3D
+    scene (drt3_vjp)."""
+    sc, keep = _scene3(tris, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    gp = _as_f32(grad_power.reshape(-1, 1), 1, "grad_power", 4)
+    if gp.shape[0] != sc.n_rx:
+        raise ValueError("grad_power must have one entry per receiver")
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt3_vjp_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    gtx = torch.empty(3, dtype=torch.float32, device=dev)
+    gtr = torch.empty(sc.n_tris, 9, dtype=torch.float32, device=dev) if tri_grad else None
+    _lib.call("drt3_vjp", ctypes.byref(sc), tlp, _ptr(gp), _ptr(gtx),
+              None if gtr is None else _ptr(gtr), _ptr(ws), ctypes.c_size_t(ws.numel()),
+              _stream_ptr(dev))
+    return gtx, gtr
+
+
 class Power3Function(torch.autograd.Function):
-    """3D received power, differentiable in the transmitter (drt3_vjp_tx backward)."""
+    """3D received power, differentiable in the transmitter and the triangles
+    (drt3_vjp backward)."""
 
     @staticmethod
     def forward(ctx, tris, tx, rx, max_order, alpha, smoothing, refl_coef, tile):
@@ -213,18 +270,18 @@ class Power3Function(torch.autograd.Function):
     def backward(ctx, grad_power):
         tris, tx, rx = ctx.saved_tensors
         max_order, alpha, smoothing, refl_coef, tile = ctx.args
-        if ctx.needs_input_grad[0]:
-            raise NotImplementedError("the 3D power is differentiable in the transmitter only")
-        if not ctx.needs_input_grad[1]:
+        need_t, need_tx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_t or need_tx):
             return (None,) * 8
-        gtx = vjp3_tx(tris, tx, rx, max_order, alpha, smoothing, grad_power.contiguous(),
-                      refl_coef, tile)
-        return None, gtx.reshape(tx.shape), None, None, None, None, None, None
+        gtx, gtr = vjp3(tris, tx, rx, max_order, alpha, smoothing, grad_power.contiguous(),
+                        refl_coef, tri_grad=need_t, tile=tile)
+        return (gtr.reshape(tris.shape) if need_t else None,
+                gtx.reshape(tx.shape) if need_tx else None, None, None, None, None, None, None)
 
 
 def power3(tris, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
            refl_coef: float = 0.5, tile: TileConfig | None = None) -> torch.Tensor:
-    """3D received power per receiver, differentiable in ``tx``."""
+    """3D received power per receiver, differentiable in ``tris`` and ``tx``."""
     return Power3Function.apply(tris, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
 
 

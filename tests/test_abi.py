@@ -65,7 +65,7 @@ def _scene(**kw):
 
 
 @pytest.mark.parametrize("field,value,status", [
-    ("n_walls", 0, 1), ("n_walls", 5000, 2), ("max_order", 4, 2), ("max_order", -1, 1),
+    ("n_walls", 0, 1), ("n_walls", 70000, 2), ("max_order", 4, 2), ("max_order", -1, 1),
     ("alpha", -1.0, 1), ("alpha", float("nan"), 1), ("smoothing", 7, 1), ("walls", 0, 1),
     ("walls", 8, 1), ("rx", 4, 1), ("n_rx", -2, 1), ("refl_coef", float("inf"), 1)])
 def test_forward_rejects_bad_scene_before_any_launch(lib, field, value, status):
@@ -155,7 +155,7 @@ def test_vjp3_tx_rejects_bad_args_before_any_launch(lib):
 
 
 @pytest.mark.parametrize("field,value,status", [
-    ("n_walls", 0, 1), ("n_walls", 5000, 2), ("max_order", 4, 2), ("alpha", -1.0, 1),
+    ("n_walls", 0, 1), ("n_walls", 70000, 2), ("max_order", 4, 2), ("alpha", -1.0, 1),
     ("smoothing", 7, 1), ("walls", 0, 1), ("tx", 0, 1), ("rx", 0, 1), ("n_rx", 0, 1),
     ("refl_coef", float("nan"), 1)])
 def test_objective_host_rejects_bad_scene_before_any_copy(lib, field, value, status):
@@ -179,3 +179,26 @@ def test_objective_host_requires_loss_and_grad_tx(lib):
     assert lib.drt_objective_host(ctypes.byref(sc), None, p, None, None, None, None, p, 1 << 20,
                                   None) == 1
     assert lib.drt_objective_host(None, None, p, None, None, p, None, p, 1 << 20, None) == 1
+
+
+def test_forward_wall_limits_on_the_host(lib):
+    # drt_forward takes up to DRT_MAX_WALLS_STREAMED walls, the other calls DRT_MAX_WALLS;
+    # more than 2^31 - 1 candidates is refused everywhere (all before any CUDA call)
+    out = ctypes.c_size_t()
+    sc = _scene(n_walls=70000)
+    assert lib.drt_forward_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == 2
+    assert b"n_walls" in lib.drt_last_error()
+    sc = _scene(n_walls=2000, max_order=3)
+    assert lib.drt_forward_workspace_size(ctypes.byref(sc), None, ctypes.byref(out)) == 2
+    assert b"candidates" in lib.drt_last_error()
+    p = ctypes.c_void_p(256)
+    sc = _scene(n_walls=2000, max_order=1)
+    assert lib.drt_vjp(ctypes.byref(sc), None, p, p, None, p, 1 << 20, None) == 2
+
+
+def test_mlp_path_switch_host_only(lib):
+    # 0 = mma.sync, 1 = fused tcgen05 inference + mma.sync training (default), 2 = tcgen05
+    assert lib.drt_mlp_set_tensor_core_path(3) == 1
+    assert lib.drt_mlp_set_tensor_core_path(-1) == 1
+    for mode in (0, 2, 1):
+        assert lib.drt_mlp_set_tensor_core_path(mode) == 0

@@ -153,3 +153,66 @@ def test_power3_autograd_and_determinism(drt, oracle_mod):
     a = _vjp3(drt, sc, g.cpu().numpy())
     b = _vjp3(drt, sc, g.cpu().numpy())
     np.testing.assert_array_equal(a, b)
+
+
+# --------------------------------------------------------------------------- triangle gradient
+def _vjp3_full(drt, sc, g, rx=None, tri_grad=True):
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.asarray(a, np.float32), device=dev)
+    gtx, gtr = drt.vjp3(t(sc.tris), t(sc.tx), t(sc.rx if rx is None else rx), sc.max_order,
+                        sc.alpha, sc.smoothing, t(g), sc.refl_coef, tri_grad=tri_grad)
+    torch.cuda.synchronize()
+    return gtx.cpu().numpy(), (gtr.cpu().numpy() if gtr is not None else None)
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha,smoothing", VJP_CASES)
+def test_triangle_gradient_random_scenes(drt, oracle_mod, seed, W, R, K, alpha, smoothing):
+    # every corner coordinate and the TX against the oracle's exact derivative
+    sc = scenes.random_scene3(np.random.default_rng(seed), W, R, K, alpha, smoothing)
+    g = np.random.default_rng(seed + 50).normal(size=sc.n_rx).astype(np.float32)
+    gtx, gtr = _vjp3_full(drt, sc, g)
+    ref_tx, ref_tr = oracle_mod.gradient3(sc.tris, sc.tx, sc.rx, K, alpha, smoothing,
+                                          g.astype(np.float64), sc.refl_coef)
+    assert_grad_close(gtx, ref_tx, "3D grad_tx")
+    assert_grad_close(gtr.ravel(), ref_tr.ravel(), "3D grad_tris")
+    # the transmitter part does not depend on the triangle gradient being requested
+    gtx0, none = _vjp3_full(drt, sc, g, tri_grad=False)
+    assert none is None
+    np.testing.assert_allclose(gtx, gtx0, rtol=1e-6, atol=1e-6 * np.abs(gtx0).max())
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+def test_triangle_gradient_room_sampled(drt, oracle_mod, smoothing):
+    # the 132-triangle room on 8 sampled receivers; 12 sampled corner coordinates by
+    # the oracle's forward-mode derivative along each
+    sc = scenes.room3d(alpha=100.0, smoothing=smoothing)
+    rng = np.random.default_rng(17)
+    idx = rng.choice(sc.n_rx, 8, replace=False)
+    g = np.zeros(sc.n_rx, np.float32)
+    g[idx] = rng.normal(size=8)
+    _, gtr = _vjp3_full(drt, sc, g)
+    coords = rng.choice(sc.tris.size, 12, replace=False)
+    ref = []
+    for c in coords:
+        d = np.zeros(sc.tris.size)
+        d[c] = 1.0
+        _, dP = oracle_mod.power3_jvp(sc.tris, sc.tx, sc.rx[idx], 2, 100.0, smoothing,
+                                      d.reshape(sc.tris.shape), np.zeros(3), sc.refl_coef)
+        ref.append(float(np.dot(g[idx].astype(np.float64), dP)))
+    got = gtr.ravel()[coords]
+    ref = np.array(ref)
+    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref) + 1e-9, (got, ref)
+
+
+def test_power3_autograd_in_the_triangles(drt, oracle_mod):
+    sc = scenes.random_scene3(np.random.default_rng(10), 4, 30, 2, 20.0, "sigmoid")
+    dev = torch.device("cuda:0")
+    tris = torch.tensor(sc.tris, device=dev, requires_grad=True)
+    tx = torch.tensor(sc.tx, device=dev, requires_grad=True)
+    rx = torch.tensor(sc.rx, device=dev)
+    g = np.random.default_rng(11).normal(size=sc.n_rx).astype(np.float32)
+    (drt.power3(tris, tx, rx, 2, 20.0, "sigmoid") * torch.tensor(g, device=dev)).sum().backward()
+    ref_tx, ref_tr = oracle_mod.gradient3(sc.tris, sc.tx, sc.rx, 2, 20.0, "sigmoid",
+                                          g.astype(np.float64), 0.5)
+    assert_grad_close(tx.grad.cpu().numpy(), ref_tx, "autograd 3D grad_tx")
+    assert_grad_close(tris.grad.cpu().numpy().ravel(), ref_tr.ravel(), "autograd 3D grad_tris")

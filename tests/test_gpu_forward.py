@@ -1,9 +1,11 @@
 """CUDA forward pass (received power, Eq. 7) and loss (Eq. 8) against the FP64 oracle."""
+import ctypes
+
 import numpy as np
 import pytest
 
 from parity import assert_power_close, fp32_sensitivity
-from paper_2401_11882_gb300 import scenes
+from paper_2401_11882_gb300 import _lib, ops, scenes
 
 pytestmark = pytest.mark.gpu
 
@@ -291,34 +293,73 @@ def _shadow_receivers(alpha):
             float(rows[0][4]))
 
 
-@pytest.mark.parametrize("alpha,min_strict", [(10.0, 1.0), (100.0, 0.85), (1000.0, 0.8)])
-def test_large_scene_deep_shadow_receivers(drt, oracle_mod, alpha, min_strict):
+@pytest.mark.parametrize("alpha", [10.0, 100.0, 1000.0])
+def test_large_scene_deep_shadow_receivers(drt, oracle_mod, alpha):
     """The oracle's lowest-power receivers of the benchmark scene (the loss's own
     receiver first), stored by tests/golden/make_shadow_receivers.py from a full
-    oracle pass, many decades below the brightest: each is held to 1e-4 relative
-    with no floor scaled by the scene's largest power, or to its FP32 input
-    sensitivity where that is larger.  Deep in shadow the power is a sum of nearly
-    blocked paths, and moving the inputs by two FP32 roundings moves the FP64 power
-    of these receivers by 1e-4 to 4e-3 relative at alpha = 100 (the loss's own
-    receiver: 9.5e-4), so no FP32 evaluation meets the plain bound on all of them;
-    min_strict of them must."""
+    oracle pass, many decades below the brightest.  Those in full hard-sigmoid
+    shadow (power exactly 0) must be exactly 0.  Each other one is held to 1e-4
+    relative, with no floor scaled by the scene's largest power, or to twice its
+    FP32 input sensitivity where that is larger: deep in shadow the power is a sum
+    of nearly blocked paths, and moving the inputs by two FP32 roundings moves the
+    FP64 power of these receivers by 4e-5 to 4e-3 relative at alpha = 100 (the
+    loss's own receiver: 9.5e-4) and by 7e-4 to 2.6 at alpha = 1000 (the hard
+    sigmoid's slope alpha / 6 on distances rounded to FP32), so no FP32 evaluation
+    can meet the plain bound there."""
     idx, stored, p_max = _shadow_receivers(alpha)
     sc = scenes.large_scene(alpha=alpha, smoothing="hard_sigmoid")
-    # the stored values are the oracle's own (recomputed here for the receivers kept)
+    # the stored values are the oracle's own (recomputed here for the receivers kept;
+    # the host's sqrt and libm may differ in the last bit between machines, which
+    # these ill-conditioned receivers amplify to ~1e-10)
     ref = _ref(oracle_mod, sc, sc.rx[idx])
-    np.testing.assert_allclose(ref, stored, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(ref, stored, rtol=1e-9, atol=0)
     assert stored.max() < 1e-3 * p_max          # deep shadow: far below the scene's scale
     P = _run(drt, sc)
-    err = np.abs(P[idx].astype(np.float64) - ref)
+    got = P[idx].astype(np.float64)
+    zero = ref == 0
+    assert np.all(got[zero] == 0.0)
+    err = np.abs(got - ref)
     plain = 1e-4 * np.abs(ref)
     sens = fp32_sensitivity(lambda w, t, r: oracle_mod.power(w, t, r, 2, alpha, "hard_sigmoid"),
                             sc.walls, sc.tx, sc.rx[idx])
     wide = np.maximum(plain, 2.0 * sens)
-    frac = float(np.mean(err <= plain))
-    assert frac >= min_strict, f"only {frac:.2f} within 1e-4 relative: {err / ref}"
-    assert np.all(err <= wide), f"worst relative error {np.max(err / ref):.3e}"
+    bad = np.nonzero(~(err <= wide))[0]
+    assert bad.size == 0, [(int(idx[i]), err[i] / ref[i], sens[i] / ref[i]) for i in bad]
+    # the well-conditioned ones (sensitivity within the plain bound) meet 1e-4 relative
+    well = ~zero & (2.0 * sens <= plain)
+    if alpha <= 100.0:
+        assert well.sum() >= 2
     # the loss (Eq. 8) and its receiver
     loss, am = drt.min_loss(torch.tensor(P, device="cuda:0"))
     assert abs(float(loss) + ref[0]) <= max(1e-4 * ref[0], 2.0 * sens[0])
     if stored[1] - stored[0] > 2e-4 * stored[0]:
         assert int(am) == idx[0]
+
+
+@pytest.mark.parametrize("n_seg,K,alpha,smoothing,n_rx", [
+    (4092, 1, 100.0, "hard_sigmoid", 8),   # 4096 walls: two receivers per lane, records in L2
+    (4092, 1, 50.0, "sigmoid", 6),
+    (1021, 1, 2e4, "hard_sigmoid", 8),     # 1025 walls, one receiver per lane (large alpha)
+    (2044, 1, 1.0, "step", 8),
+    (19996, 0, 100.0, "hard_sigmoid", 40),  # 20000 walls, line of sight only
+])
+def test_more_walls_than_shared_memory_holds(drt, oracle_mod, n_seg, K, alpha, smoothing, n_rx):
+    """Above DRT_MAX_WALLS (1024) the forward reads the walls' records from a staging
+    area in its workspace (every (leg, wall) pair is still tested, Sec. V): parity
+    with the oracle on a few receivers of a clutter scene (square + n_seg segments)."""
+    rng = np.random.default_rng(n_seg)
+    rx = rng.uniform(0.05, 0.95, (n_rx, 2)).astype(np.float32)
+    sc = scenes.clutter_scene(n_seg, 1, seed=n_seg, alpha=alpha, smoothing=smoothing,
+                              max_order=K, boundary=True, rx=rx)
+    assert sc.n_walls > 1024
+    ref = _ref(oracle_mod, sc)
+    sens = (fp32_sensitivity(lambda w, t, r: oracle_mod.power(w, t, r, K, alpha, smoothing),
+                             sc.walls, sc.tx, sc.rx) if alpha >= 1000 else None)
+    assert_power_close(_run(drt, sc), ref, sens=sens, min_strict=0.85 if sens is not None else 1.0)
+    # the workspace holds the staged records (4 float4 per wall, 8 with two receivers
+    # per lane) after the partial sums
+    w, t, r = (torch.tensor(x, device="cuda:0") for x in (sc.walls, sc.tx, sc.rx))
+    desc, _keep = ops.make_scene(w, t, r, K, alpha, smoothing)
+    n = ctypes.c_size_t()
+    _lib.call("drt_forward_workspace_size", ctypes.byref(desc), None, ctypes.byref(n))
+    assert n.value >= 4 * 16 * sc.n_walls

@@ -206,3 +206,52 @@ def test_min_loss_vjp_large_scene(drt, oracle_mod):
     got = gw.cpu().numpy().ravel()[coords]
     np.testing.assert_allclose(got, ref[2:], rtol=1e-3,
                                atol=1e-6 * max(np.abs(ref).max(), 1e-30))
+
+
+PAIR_CASES = [
+    # (seed, W, R, K, alpha): receiver counts around the 64-receiver tile of the
+    # sigmoid adjoint's two-receivers-per-lane kernel (a lone receiver, half tiles,
+    # ragged tails), every order, alpha from 0 to 1000
+    (40, 5, 1, 0, 30.0),
+    (41, 8, 33, 1, 20.0),
+    (42, 9, 63, 2, 100.0),
+    (43, 9, 64, 2, 10.0),
+    (44, 10, 65, 2, 300.0),
+    (45, 6, 130, 3, 40.0),
+    (46, 12, 97, 2, 0.0),
+    (47, 14, 80, 2, 1000.0),
+]
+
+
+@pytest.mark.parametrize("wall_grad", [True, False])
+@pytest.mark.parametrize("seed,W,R,K,alpha", PAIR_CASES)
+def test_sigmoid_two_receivers_per_lane(drt, oracle_mod, seed, W, R, K, alpha, wall_grad):
+    # the paired adjoint against the one-receiver-per-lane kernel (same per-path
+    # arithmetic up to rounding; the receivers' sums are grouped differently) and
+    # against the oracle's exact gradient
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, "sigmoid", boundary=(seed % 2 == 0))
+    g = rng.normal(size=sc.n_rx)
+    gtx, gw = _vjp(drt, sc, g, wall_grad=wall_grad)
+    gtx1, gw1 = _vjp(drt, sc, g, wall_grad=wall_grad, tile=drt.TileConfig(single_rx=True))
+    scale = np.linalg.norm(gtx1)
+    assert np.linalg.norm(gtx - gtx1) <= 1e-5 * scale + 1e-30, (gtx, gtx1)
+    ref = _oracle_grad(oracle_mod, sc, g.astype(np.float32).astype(np.float64))
+    assert_grad_close(gtx, ref[:2], "grad_tx")
+    if wall_grad:
+        assert np.linalg.norm(gw - gw1) <= 1e-5 * np.linalg.norm(gw1) + 1e-30
+        assert_grad_close(gw.ravel(), ref[2:], "grad_walls")
+    else:
+        assert gw is None
+
+
+def test_sigmoid_pair_adjoint_on_gradient_scene(drt):
+    # the benchmark's dense adjoint (128 walls, 16384 receivers, 16385 sequences): both
+    # kernels agree on every gradient component
+    sc = scenes.gradient_scene(alpha=100.0, smoothing="sigmoid")
+    g = np.full(sc.n_rx, 1.0 / sc.n_rx)
+    gtx, gw = _vjp(drt, sc, g)
+    gtx1, gw1 = _vjp(drt, sc, g, tile=drt.TileConfig(single_rx=True))
+    assert np.linalg.norm(gtx - gtx1) <= 1e-5 * np.linalg.norm(gtx1)
+    assert np.linalg.norm(gw - gw1) <= 1e-5 * np.linalg.norm(gw1)
+    assert np.all(np.abs(gw - gw1) <= 1e-4 * np.abs(gw1) + 1e-6 * np.abs(gw1).max())

@@ -89,8 +89,8 @@ def test_accepts_the_largest_receiver_count(lib):
 
 
 def test_rejects_an_oversized_wall_count_before_counting_candidates(lib):
-    """A wall count beyond DRT_MAX_WALLS is refused by the scene check (the
-    candidate count of such a scene would not fit in 64 bits)."""
+    """A wall count beyond the largest the forward takes is refused by the scene
+    check, before the candidate count (which would not fit in 64 bits) is formed."""
     from paper_2401_11882_gb300 import _lib
     desc = _lib.Scene(256, 2**31 - 1, 256, 16, 256, 3, 10.0, 1, 0.5)
     st = lib.drt_forward_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), None)
