@@ -117,8 +117,11 @@ def tune_forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "
 
 
 def tune_batch(batch, n_scenes: int | None = None, candidates=None, steps: int = 1,
-               timer=None, **descent_kw) -> TileConfig:
-    """Best tile for the batched descent, timed on (the first n_scenes of) the batch."""
+               timer=None, return_timings: bool = False, **descent_kw):
+    """Best tile for the batched descent, timed on (the first n_scenes of) the batch:
+    each candidate builds its own plan and runs ``steps`` descent steps once to warm
+    up and once timed.  Returns the tile, or (tile, [(tile, ms), ...]) with
+    ``return_timings``."""
     from .batched import BatchedDescent
     from . import scenes
     sub = batch
@@ -135,4 +138,5 @@ def tune_batch(batch, n_scenes: int | None = None, candidates=None, steps: int =
         ms = timer(lambda: bd.run(steps), 1)
         bd.close()
         timings.append((cfg, ms))
-    return pick_best(timings)
+    best = pick_best(timings)
+    return (best, timings) if return_timings else best

@@ -27,6 +27,12 @@ The batched-descent study (4096 uneven scenes x 4 starts: full-batch step time;
 200 Adam steps on the first 256 scenes):
 
     python -m paper_2401_11882_gb300.experiments --study batch
+
+The batch tiles (the autotuner's choice on the first 64 scenes, then full-batch
+steps with the default tile, the tuned tile, and the tuned tile with the exact
+invalid-path skip):
+
+    python -m paper_2401_11882_gb300.experiments --study batch_tiles --timed-steps 1
 """
 from __future__ import annotations
 
@@ -201,9 +207,9 @@ def batch_study(n_scenes=4096, timed_steps=3, conv_scenes=256, conv_steps=200, s
     return out
 
 
-def _time_full_batch(full, timed_steps, fl, evals, dev):
+def _time_full_batch(full, timed_steps, fl, evals, dev, tile=None):
     from .batched import BatchedDescent
-    bd = BatchedDescent(full, device=dev)
+    bd = BatchedDescent(full, device=dev, tile=tile)
     bd.run(1)
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -217,6 +223,41 @@ def _time_full_batch(full, timed_steps, fl, evals, dev):
            "evals_per_s": evals / s_step, "info": bd.info()}
     bd.close()
     return res
+
+
+def batch_tile_study(n_scenes=4096, tune_scenes=64, timed_steps=1, seed=0, device="cuda",
+                     smoothing="hard_sigmoid") -> dict:
+    """The batch autotuner on the 4096-scene batch: autotune.tune_batch times every
+    candidate tile (warps per CTA x CTAs per SM) on the first tune_scenes scenes; the
+    full batch is then timed with the library's default tile, with the tuned tile,
+    and with the tuned tile plus the exact invalid-path skip (DRT_TILE_CULL_INVALID:
+    warps whose paths all have hard-sigmoid validity exactly 0 skip the obstruction
+    loop; the losses are unchanged bit for bit, but the step no longer does the
+    literal work the FLOP convention counts, so its rate is reported apart)."""
+    from dataclasses import asdict, replace
+    from . import autotune, workload
+    full = scenes.scene_batch(n_scenes, seed, smoothing=smoothing)
+    dev = torch.device(device)
+    T = full.tx0.shape[1]
+    fl = sum(T * workload.forward_work(int(full.wall_off[i + 1] - full.wall_off[i]),
+                                       int(full.max_order[i]),
+                                       int(full.rx_off[i + 1] - full.rx_off[i]))["flops"]
+             for i in range(full.n_scenes))
+    evals = sum(T * int(full.rx_off[i + 1] - full.rx_off[i]) *
+                int(workload.num_candidates(int(full.wall_off[i + 1] - full.wall_off[i]),
+                                            int(full.max_order[i])))
+                for i in range(n_scenes))
+    best, timings = autotune.tune_batch(full, n_scenes=tune_scenes, steps=1, return_timings=True)
+    out = {"tuned_on_first_scenes": tune_scenes,
+           "candidates_ms_per_step": [[asdict(c), ms] for c, ms in timings],
+           "best": asdict(best)}
+    out["default_tile"] = _time_full_batch(full, timed_steps, fl, evals, dev)
+    out["tuned_tile"] = _time_full_batch(full, timed_steps, fl, evals, dev, tile=best)
+    skip = _time_full_batch(full, timed_steps, fl, evals, dev,
+                            tile=replace(best, cull_invalid=True))
+    skip.pop("tflops_by_convention")   # the skipped paths are not computed
+    out["tuned_tile_exact_skip"] = skip
+    return out
 
 
 def _convergence_run(full, n, conv_steps, dev):
@@ -266,7 +307,8 @@ def main():
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--starts", type=int, default=64)
-    ap.add_argument("--study", choices=["surrogate", "annealing", "batch"], default="surrogate")
+    ap.add_argument("--study", choices=["surrogate", "annealing", "batch", "batch_tiles"],
+                    default="surrogate")
     ap.add_argument("--scenes", type=int, default=256)
     ap.add_argument("--timed-steps", type=int, default=3, help="batch study: full-batch steps timed")
     ap.add_argument("--conv-steps", type=int, default=200, help="batch study: convergence steps")
@@ -275,6 +317,9 @@ def main():
     args = ap.parse_args()
     if args.study == "annealing":
         print(json.dumps(annealing_study(n_scenes=args.scenes)), flush=True)
+        return
+    if args.study == "batch_tiles":
+        print(json.dumps(batch_tile_study(timed_steps=args.timed_steps)), flush=True)
         return
     if args.study == "batch":
         print(json.dumps(batch_study(timed_steps=args.timed_steps, conv_scenes=args.scenes,

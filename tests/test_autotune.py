@@ -35,3 +35,34 @@ def test_pick_best_prefers_fastest_then_earliest():
 def test_candidate_sets_are_valid():
     for t in autotune.FORWARD_CANDIDATES + autotune.BATCH_CANDIDATES:
         assert 1 <= t.warps_per_cta <= 8 and t.ctas_per_sm >= 0 and t.cands_per_unit >= 0
+
+
+def test_tune_batch_times_every_candidate_and_returns_the_fastest(monkeypatch):
+    # the plan is replaced by a stand-in: no GPU; each candidate's time comes from a table
+    import paper_2401_11882_gb300.batched as batched
+    built = []
+
+    class FakeDescent:
+        def __init__(self, batch, tile=None, **kw):
+            built.append(tile)
+            self.tile = tile
+
+        def run(self, n):
+            pass
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(batched, "BatchedDescent", FakeDescent)
+    cands = [TileConfig(4, 0, 0), TileConfig(8, 0, 1), TileConfig(8, 0, 2)]
+    ms = {cands[0]: 5.0, cands[1]: 2.0, cands[2]: 3.0}
+
+    def timer(fn, reps):
+        fn()
+        return ms[built[-1]]
+
+    best, timings = autotune.tune_batch(object(), candidates=cands, timer=timer,
+                                        return_timings=True)
+    assert best == cands[1] and built == cands
+    assert [t for _, t in timings] == [5.0, 2.0, 3.0]
+    assert autotune.tune_batch(object(), candidates=cands, timer=timer) == cands[1]

@@ -191,3 +191,43 @@ def test_tx_stays_in_box(drt):
     assert tx[:, 0].min() >= 0.1 and tx[:, 0].max() <= 0.8
     assert tx[:, 1].min() >= 0.2 and tx[:, 1].max() <= 0.9
     bd.close()
+
+
+def test_autotuned_tile_runs_the_same_descent(drt):
+    """autotune.tune_batch times every batch candidate (warps per CTA x CTAs per SM)
+    on the device and returns the fastest; the tile moves work between CTAs but not
+    the candidates' order within a receiver's sum, so the descent is the same bit for
+    bit as with the library's default tile."""
+    from paper_2401_11882_gb300 import autotune
+    from paper_2401_11882_gb300.batched import BatchedDescent
+    batch = _small_batch(5, n=8)
+    best, timings = autotune.tune_batch(batch, steps=2, return_timings=True)
+    assert best in autotune.BATCH_CANDIDATES
+    assert len(timings) == len(autotune.BATCH_CANDIDATES)
+    assert all(ms > 0 for _, ms in timings)
+    assert dict(timings)[best] == min(ms for _, ms in timings)
+    a = BatchedDescent(batch, history=3)
+    b = BatchedDescent(batch, history=3, tile=best)
+    a.run(3)
+    b.run(3)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.history.cpu().numpy(), b.history.cpu().numpy())
+    np.testing.assert_array_equal(a.tx.cpu().numpy(), b.tx.cpu().numpy())
+    a.close()
+    b.close()
+
+
+def test_exact_skip_gives_the_same_descent(drt):
+    # DRT_TILE_CULL_INVALID skips the obstruction loop of paths whose hard-sigmoid
+    # validity is exactly 0 in every lane of the warp: such a path adds exactly 0
+    from paper_2401_11882_gb300.batched import BatchedDescent
+    batch = _small_batch(6, n=8)
+    a = BatchedDescent(batch, history=3)
+    b = BatchedDescent(batch, history=3, tile=drt.TileConfig(cull_invalid=True))
+    a.run(3)
+    b.run(3)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.history.cpu().numpy(), b.history.cpu().numpy())
+    np.testing.assert_array_equal(a.tx.cpu().numpy(), b.tx.cpu().numpy())
+    a.close()
+    b.close()
