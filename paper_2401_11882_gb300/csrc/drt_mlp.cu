@@ -453,7 +453,8 @@ int* tc_status_ptr() {
 template <int EPI>
 cudaError_t gemm(const mlp::GemmArgs& g, cudaStream_t st) {
   const bool tc_shape = (g.M % mlp::TC_BM == 0) && (g.K % mlp::TC_BK == 0) && (g.N % 64 == 0);
-  int* status = (g_tc_mode.load() && tc_shape) ? tc_status_ptr() : nullptr;
+  // the training GEMMs take tcgen05 only in mode 2 (mode 1: the fused inference kernel)
+  int* status = (g_tc_mode.load() == 2 && tc_shape) ? tc_status_ptr() : nullptr;
   if (status) {
     const int z = (EPI == mlp::EPI_DW && g.k_splits > 1) ? g.k_splits : 1;
     if (g.N % 128 == 0) {
@@ -547,7 +548,7 @@ drt_status drt_mlp_forward(const float* params, const void* shadow, const float*
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mlp::Layout L = mlp::layout();
   const mlp::bf16* sh = static_cast<const mlp::bf16*>(shadow);
-  int* status = g_tc_mode.load() ? tc_status_ptr() : nullptr;
+  int* status = g_tc_mode.load() != 0 ? tc_status_ptr() : nullptr;
   if (status) {
     // tcgen05 path: the whole network in one kernel, activations on chip
     mlp::FusedArgs fa{};
@@ -652,7 +653,7 @@ drt_status drt_mlp_loss_grad(const float* params, const void* shadow, const floa
 }
 
 drt_status drt_mlp_set_tensor_core_path(int32_t use_tcgen05) {
-  if (use_tcgen05 != 0 && use_tcgen05 != 1) return mlp_fail(DRT_ERR_INVALID_ARG, "use_tcgen05 must be 0 or 1");
+  if (use_tcgen05 < 0 || use_tcgen05 > 2) return mlp_fail(DRT_ERR_INVALID_ARG, "use_tcgen05 must be 0, 1 or 2");
   g_tc_mode.store(use_tcgen05);
   return DRT_OK;
 }

@@ -1,6 +1,6 @@
 """The tcgen05 (TMEM-accumulator) tensor-core path of the MLP (the fused
-inference kernel and the training GEMMs) against the mma.sync path and the
-FP64 oracle."""
+inference kernel and the training GEMMs, path 2) against the mma.sync path
+(path 0), the default mix (path 1) and the FP64 oracle."""
 import ctypes
 
 import numpy as np
@@ -36,7 +36,7 @@ def test_forward_and_gradient_agree_across_paths(env, batch):
     x = torch.from_numpy(rng.uniform(0, 1, (batch, 2)).astype(np.float32)).cuda()
     t = torch.from_numpy(rng.normal(size=batch).astype(np.float32)).cuda()
     out = {}
-    for path in (1, 0):
+    for path in (2, 1, 0):
         _lib.call("drt_mlp_set_tensor_core_path", path)
         m = sur.SurrogateMLP("cuda", seed=3, batch=batch)
         m.set_params(theta)
@@ -45,7 +45,11 @@ def test_forward_and_gradient_agree_across_paths(env, batch):
         torch.cuda.synchronize()
         out[path] = (y, float(loss), g.cpu().numpy().copy(), m.freqs.cpu().numpy())
     assert _status(_lib) == 0
-    y1, l1, g1, freqs = out[1]
+    # the default (1) runs inference like 2 (fused tcgen05) and training like 0 (mma.sync)
+    np.testing.assert_array_equal(out[1][0], out[2][0])
+    np.testing.assert_array_equal(out[1][2], out[0][2])
+    assert out[1][1] == out[0][1]
+    y1, l1, g1, freqs = out[2]
     y0, l0, g0, _ = out[0]
     np.testing.assert_allclose(y1, y0, rtol=2e-3, atol=2e-3 * np.abs(y0).max())
     assert l1 == pytest.approx(l0, rel=2e-3)
