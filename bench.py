@@ -373,12 +373,36 @@ def measure_extras(drt, dev, sc, w, t, r):
     n3 = r3.n_rx * workload.num_candidates(r3.n_tris, r3.max_order)
     s3h = timed(lambda: drt.forward3(w3, t3, x3, 2, 100.0, "hard_sigmoid"), 3)
     s3s = timed(lambda: drt.forward3(w3, t3, x3, 2, 100.0, "sigmoid"), 1)
+    g3 = torch.full((r3.n_rx,), 1.0 / r3.n_rx, device=dev)
+    v3h = timed(lambda: drt.vjp3(w3, t3, x3, 2, 100.0, "hard_sigmoid", g3), 2)
+    v3s = timed(lambda: drt.vjp3(w3, t3, x3, 2, 100.0, "sigmoid", g3), 1)
     out["room3d_forward"] = {
         "workload": "64-wall scene as a room (walls extruded over z in [0, 1], floor, ceiling: "
                     "132 triangles), 128x128 receivers at z = 0.3, K<=2 (17425 sequences), alpha=100",
         "hard_ms": s3h * 1e3, "hard_evals_per_s": n3 / s3h,
         "sigmoid_ms": s3s * 1e3, "sigmoid_evals_per_s": n3 / s3s,
-        "note": "warps whose paths all have validity exactly 0 skip their obstruction loop"}
+        "hard_vjp_ms": v3h * 1e3, "sigmoid_vjp_ms": v3s * 1e3,
+        "note": "warps whose paths all have validity exactly 0 skip their obstruction loop; "
+                "vjp = dense g = 1/R, gradient w.r.t. the TX and all 1188 corner coordinates"}
+    # reflection points by the iterative path finder (10 Gauss-Newton steps on the MPT
+    # cost, smoothed convergence check eps = 0.05) on the benchmark workload
+    sm_h = timed(lambda: drt.forward_mpt(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid", 10,
+                                         0.05), 2)
+    sm_s = timed(lambda: drt.forward_mpt(w, t, r, sc.max_order, sc.alpha, "sigmoid", 10, 0.05), 1)
+    out["mpt_forward"] = {"workload": "benchmark workload, reflection points from 10 MPT steps",
+                          "hard_ms": sm_h * 1e3, "hard_evals_per_s": ev / sm_h,
+                          "sigmoid_ms": sm_s * 1e3, "sigmoid_evals_per_s": ev / sm_s}
+    # more walls than shared memory holds: square + 4092 segments, K <= 1, 64x64 receivers
+    cs = scenes.clutter_scene(4092, 64, seed=1, alpha=100.0, smoothing="hard_sigmoid",
+                              max_order=1)
+    cw, ct, cr = (torch.tensor(a, device=dev) for a in (cs.walls, cs.tx, cs.rx))
+    sc_h = timed(lambda: drt.forward(cw, ct, cr, 1, 100.0, "hard_sigmoid"), 1)
+    n_tests = cs.n_rx * (1 + 2 * cs.n_walls) * cs.n_walls   # leg x wall tests per launch
+    out["streamed_walls_4096"] = {
+        "workload": "square + 4092 random segments (4096 walls, records in L2), 64x64 receivers, "
+                    "K<=1 (4097 sequences), alpha=100, hard sigmoid",
+        "ms": sc_h * 1e3, "evals_per_s": cs.n_rx * (1 + cs.n_walls) / sc_h,
+        "tests_per_s": n_tests / sc_h}
     # coherent field (Eq. 7 with complex path fields, Fresnel TE, eps_r 5, wavelength 0.02)
     s = timed(lambda: drt.field(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid", 0.02, 5.0))
     out["coherent_field_hard_evals_per_s"] = ev / s

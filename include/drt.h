@@ -516,9 +516,11 @@ drt_status drt_mlp_adam(float* params, float* m, float* v, const float* grad, in
    default one, so the per-chunk partial sums are grouped differently.  Two
    calls with the same arguments give the same bits.
    - Limit: one partial sum per (candidate chunk, receiver) must fit, so
-     n_rx <= DRT_NOALLOC_SCRATCH_BYTES / 4; larger scenes get
-     DRT_ERR_UNSUPPORTED before anything is enqueued.  Scenes that drt_forward
-     rejects are rejected with the same status.
+     n_rx <= DRT_NOALLOC_SCRATCH_BYTES / 4; above DRT_MAX_WALLS walls the
+     staged wall records (128 bytes per wall) share the array and lower that
+     bound accordingly.  Larger scenes get DRT_ERR_UNSUPPORTED before anything
+     is enqueued.  Scenes that drt_forward rejects are rejected with the same
+     status.
    - All calls on a device share the array, and it keeps the last call's
      contents (every value a call reads was written by that same call).
      Calls that overlap on the GPU race on it: order them on one stream.

@@ -9,7 +9,8 @@ without ``--clock-control none`` ncu locks the GPU's clocks).
     field_vjp drt.field_vjp with dense g = 1/R (after one drt.field)
     forward_mpt drt.forward_mpt (the iterative path finder, --n-iter steps, --check-eps)
     forward3  drt.forward3 on the 3D room (``scenes.room3d``, --rx-grid receivers a side)
-    vjp3      drt.vjp3_tx (transmitter gradient) on the same room, dense g = 1/R
+    vjp3      drt.vjp3 (transmitter and triangle gradients; --tx-only: drt.vjp3_tx) on
+              the same room, dense g = 1/R
     mlp       the surrogate MLP's inference on --batch random points
 
 Scenes: ``gradient`` (128 random segments, K <= 2, the dense-adjoint workload),
@@ -44,6 +45,7 @@ def main() -> int:
     ap.add_argument("--wavelength", type=float, default=0.02)
     ap.add_argument("--eps-r", type=float, default=5.0)
     ap.add_argument("--single-rx", action="store_true", help="one receiver per lane")
+    ap.add_argument("--tx-only", action="store_true", help="vjp3: transmitter gradient only")
     args = ap.parse_args()
     dev = torch.device("cuda:0")
     if args.op == "mlp":
@@ -67,8 +69,10 @@ def main() -> int:
         g3 = torch.full((sc3.n_rx,), 1.0 / sc3.n_rx, device=dev)
 
         def run3():
-            if args.op == "vjp3":
+            if args.op == "vjp3" and args.tx_only:
                 return ops.vjp3_tx(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing, g3)
+            if args.op == "vjp3":
+                return ops.vjp3(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing, g3)
             return ops.forward3(w3, t3, r3, sc3.max_order, args.alpha, args.smoothing)
 
         for _ in range(2):

@@ -217,8 +217,10 @@ drt_status drt_num_candidates(int32_t n_walls, int32_t max_order, int64_t* count
 
 // drt_forward's workspace: the per-chunk partial sums, then (more walls than
 // shared memory holds) the staged wall records, 16-byte aligned
+// The partial sums; rounded up to 16 bytes when the staged wall records follow them.
 size_t forward_partials_bytes(const drt_scene* sc, const Decomp& d) {
-  return ((size_t)d.n_chunks * (size_t)sc->n_rx * sizeof(float) + 15) & ~(size_t)15;
+  const size_t b = (size_t)d.n_chunks * (size_t)sc->n_rx * sizeof(float);
+  return forward_streams_walls(sc->n_walls) ? (b + 15) & ~(size_t)15 : b;
 }
 size_t forward_workspace(const drt_scene* sc, const Decomp& d) {
   const size_t staged =

@@ -86,8 +86,15 @@ extern "C" drt_status drt_forward_noalloc(const drt_scene* scene, float* power, 
   drt_status st = drt_forward_workspace_size(scene, nullptr, &default_need);
   if (st != DRT_OK) return st;
   if (scene->n_rx == 0) return drt_forward(scene, nullptr, power, nullptr, 0, stream);
-  // One partial sum per (candidate chunk, receiver): choose the chunk so that they fit.
-  const long long max_chunks = (long long)(kScratchFloats / (size_t)scene->n_rx);
+  // One partial sum per (candidate chunk, receiver): choose the chunk so that they
+  // fit beside the staged wall records of a scene with more walls than shared
+  // memory holds (at most 8 float4 per wall, after the partial sums rounded up to 16
+  // bytes).
+  const size_t staged = scene->n_walls > DRT_MAX_WALLS ? (size_t)scene->n_walls * 128 + 16 : 0;
+  const size_t room = DRT_NOALLOC_SCRATCH_BYTES > staged
+                          ? (DRT_NOALLOC_SCRATCH_BYTES - staged) / sizeof(float)
+                          : 0;
+  const long long max_chunks = (long long)(room / (size_t)scene->n_rx);
   if (max_chunks < 1) {
     set_error_message(("drt_forward_noalloc: n_rx = " + std::to_string(scene->n_rx) +
                        " exceeds the static scratch capacity of " +
@@ -108,7 +115,8 @@ extern "C" drt_status drt_forward_noalloc(const drt_scene* scene, float* power, 
   st = drt_forward_workspace_size(scene, &tile, &need);
   if (st != DRT_OK) return st;
   if (need > DRT_NOALLOC_SCRATCH_BYTES) {
-    set_error_message("drt_forward_noalloc: partial sums exceed the static scratch capacity");
+    set_error_message("drt_forward_noalloc: partial sums and wall records exceed the static "
+                      "scratch capacity");
     return DRT_ERR_UNSUPPORTED;
   }
   void* scratch = nullptr;

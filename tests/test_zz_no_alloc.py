@@ -96,3 +96,17 @@ def test_rejects_an_oversized_wall_count_before_counting_candidates(lib):
     st = lib.drt_forward_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), None)
     assert st == 2                       # DRT_ERR_UNSUPPORTED, nothing enqueued
     assert b"n_walls" in lib.drt_last_error()
+
+
+def test_more_walls_than_shared_memory_holds(lib):
+    """Above 1024 walls the forward stages the wall records in its workspace: here
+    the static array holds them beside the partial sums."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(2)
+    rx = rng.uniform(0.05, 0.95, (300, 2)).astype(np.float32)
+    sc = scenes.clutter_scene(2044, 1, seed=4, alpha=100.0, smoothing="hard_sigmoid",
+                              max_order=1, rx=rx)
+    assert sc.n_walls == 2048
+    got = _noalloc(lib, sc, dev)
+    assert np.all(np.isfinite(got))
+    assert_power_close(got, _existing(sc, dev), "noalloc vs drt_forward, 2048 walls")
