@@ -35,6 +35,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// Whether two scaled signed distances lie on the same side of a line, for the
+// smoothed straddle pair X(x, y): their product is positive.  A product that
+// underflows to 0 counts as opposite sides; one distance is then below 2^-74 of
+// alpha's scale, its e = 2^-|z| rounds to 1, and the pair's two forms (e_x + e_y
+// and 1 + e_x e_y) agree.  (A side known only through a tiny signed e, as the
+// transmitter's in the wall records, is passed as +-1.)  One multiply on the FMA
+// pipe and one compare.
+__device__ __forceinline__ bool same_side(float a, float b) { return a * b > 0.f; }
+
 // ------------------------------------------------------------ smoothing
 // s(x; alpha) = s(alpha x) (Eq. 3) for the three functions of Sec. IV:
 // the value s(x), the complement s(-x) (by C4 equal to 1 - s(x), but

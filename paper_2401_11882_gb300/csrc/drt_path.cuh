@@ -105,7 +105,7 @@ __device__ __forceinline__ void sigmoid_pair_factor(const float4& h, const float
                                                     const float* mc, float& num, float& den) {
   float ze0, ee0, ze1, ee1;
   if (j == 0) {
-    ze0 = h.w;
+    ze0 = copysignf(1.f, h.w);   // the TX side: only the sign is used
     ee0 = fabsf(h.w);
   } else {
     ze0 = fmaf(h.x, Qx[j], fmaf(h.y, Qy[j], h.z));
@@ -118,10 +118,10 @@ __device__ __forceinline__ void sigmoid_pair_factor(const float4& h, const float
   const float ea = ex2_approx(-fabsf(za));
   const float eb = ex2_approx(-fabsf(zb));
   const float ns1 = ee0 + ee1, no1 = fmaf(ee0, ee1, 1.f);
-  const bool same1 = (__float_as_int(ze0) ^ __float_as_int(ze1)) >= 0;
+  const bool same1 = same_side(ze0, ze1);
   const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
   const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
-  const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+  const bool same2 = same_side(za, zb);
   const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
   den = (ns1 + no1) * (ns2 + no2);
   num = fmaf(xb1, ns2 + no2, x1 * xb2);
@@ -229,7 +229,7 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
         const float4 h = s.H[w];
         const float4 e = s.E[w];
         float ze[K + 2], ee[K + 2];
-        ze[0] = h.w;
+        ze[0] = copysignf(1.f, h.w);   // the TX side: only the sign is used
         ee[0] = fabsf(h.w);
 #pragma unroll
         for (int i = 1; i <= K + 1; ++i) {
@@ -245,12 +245,12 @@ __device__ __forceinline__ float leg_visibility(const SmemWalls& s, int W, const
           // pair 1: the leg's end points w.r.t. the wall's line
           const float ns1 = ee[j] + ee[j + 1];
           const float no1 = fmaf(ee[j], ee[j + 1], 1.f);
-          const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+          const bool same1 = same_side(ze[j], ze[j + 1]);
           const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
           // pair 2: the wall's end points w.r.t. the leg's line
           const float ns2 = ea + eb;
           const float no2 = fmaf(ea, eb, 1.f);
-          const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+          const bool same2 = same_side(za, zb);
           const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
           const float den = (ns1 + no1) * (ns2 + no2);
           float num = fmaf(xb1, ns2 + no2, x1 * xb2);

@@ -47,8 +47,11 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 ex2_pair(float2 z) {
   return f2(ex2_approx(-fabsf(z.x)), ex2_approx(-fabsf(z.y)));
 }
-__device__ __forceinline__ bool same_sign(float a, float b) {
-  return (__float_as_int(a) ^ __float_as_int(b)) >= 0;
+// same_side for both receivers: one packed multiply, two compares
+__device__ __forceinline__ void same_side2(float2 a, float2 b, bool& sx, bool& sy) {
+  const float2 p = __fmul2_rn(a, b);
+  sx = p.x > 0.f;
+  sy = p.y > 0.f;
 }
 
 // Hard sigmoid: visibility of each leg of both receivers' paths, every wall
@@ -104,7 +107,9 @@ __device__ __forceinline__ void sigmoid_visibility_pair(const SmemWalls& s, cons
   // one wall's factors for every leg, folded into vn, vd
   auto wall = [&](int w) {
     const float4 A = p.A[w], B = p.B[w], C = p.C[w], D = p.D[w];
-    const float zt = s.H[w].w;   // signed TX-side value: only its sign is used
+    // the TX side: only the sign of H.w is used (as +-1, so that the same-side
+    // product cannot underflow)
+    const float zt = copysignf(1.f, s.H[w].w);
     const float2 hx = f2(A.x, A.y), hy = f2(A.z, A.w), hz = f2(B.x, B.y);
     const float2 ax = f2(C.x, C.y), ay = f2(C.z, C.w), bx = f2(D.x, D.y), by = f2(D.z, D.w);
     float2 ze[K + 2], ee[K + 2];
@@ -122,12 +127,14 @@ __device__ __forceinline__ void sigmoid_visibility_pair(const SmemWalls& s, cons
       const float2 ea = ex2_pair(za), eb = ex2_pair(zb);
       const float2 ns1 = add2(ee[j], ee[j + 1]);
       const float2 no1 = fma2(ee[j], ee[j + 1], one);
-      const bool s1x = same_sign(ze[j].x, ze[j + 1].x), s1y = same_sign(ze[j].y, ze[j + 1].y);
+      bool s1x, s1y;
+      same_side2(ze[j], ze[j + 1], s1x, s1y);
       const float2 x1 = f2(s1x ? ns1.x : no1.x, s1y ? ns1.y : no1.y);
       const float2 xb1 = f2(s1x ? no1.x : ns1.x, s1y ? no1.y : ns1.y);
       const float2 ns2 = add2(ea, eb);
       const float2 no2 = fma2(ea, eb, one);
-      const bool s2x = same_sign(za.x, zb.x), s2y = same_sign(za.y, zb.y);
+      bool s2x, s2y;
+      same_side2(za, zb, s2x, s2y);
       const float2 x2 = f2(s2x ? ns2.x : no2.x, s2y ? ns2.y : no2.y);
       const float2 xb2 = f2(s2x ? no2.x : ns2.x, s2y ? no2.y : ns2.y);
       const float2 d2 = add2(ns2, no2);

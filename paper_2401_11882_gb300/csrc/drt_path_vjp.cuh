@@ -89,7 +89,7 @@ __device__ __forceinline__ void sigmoid_vis_sweep(const VSmem& s, int W, const C
     const float4 h = s.H[w];
     const float4 e = s.E[w];
     float ze[K + 2], ee[K + 2];
-    ze[0] = h.w;
+    ze[0] = copysignf(1.f, h.w);   // the TX side: only the sign is used
     ee[0] = fabsf(h.w);
 #pragma unroll
     for (int i = 1; i <= K + 1; ++i) {
@@ -104,10 +104,10 @@ __device__ __forceinline__ void sigmoid_vis_sweep(const VSmem& s, int W, const C
       const float zb = fmaf(mxk[j], e.z, fmaf(myk[j], e.w, mck[j]));
       const float ea = ex2_approx(-fabsf(za)), eb = ex2_approx(-fabsf(zb));
       const float ns1 = ee[j] + ee[j + 1], no1 = fmaf(ee[j], ee[j + 1], 1.f);
-      const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+      const bool same1 = same_side(ze[j], ze[j + 1]);
       const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
       const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
-      const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+      const bool same2 = same_side(za, zb);
       const float xb2 = same2 ? no2 : ns2;
       const float d2 = ns2 + no2;
       vn[j] *= fmaf(xb1, d2, x1 * xb2);
@@ -611,7 +611,7 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
       const float4 E = s.E[w];
       const float4 h = s.H[w];
       float ze[K + 2], ev[K + 2], sF[K + 2], vb[K + 2];
-      ze[0] = h.w;
+      ze[0] = copysignf(1.f, h.w);   // the TX side: only the sign is used
       ev[0] = fabsf(h.w);
 #pragma unroll
       for (int i = 1; i <= K + 1; ++i) {
@@ -632,10 +632,10 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
         const float zb = fmaf(mxk[j], E.z, fmaf(myk[j], E.w, mck[j]));
         const float ea = ex2_approx(-fabsf(za)), eb = ex2_approx(-fabsf(zb));
         const float ns1 = ev[j] + ev[j + 1], no1 = fmaf(ev[j], ev[j + 1], 1.f);
-        const bool same1 = (__float_as_int(ze[j]) ^ __float_as_int(ze[j + 1])) >= 0;
+        const bool same1 = same_side(ze[j], ze[j + 1]);
         const float x1 = same1 ? ns1 : no1, xb1 = same1 ? no1 : ns1;
         const float ns2 = ea + eb, no2 = fmaf(ea, eb, 1.f);
-        const bool same2 = (__float_as_int(za) ^ __float_as_int(zb)) >= 0;
+        const bool same2 = same_side(za, zb);
         const float x2 = same2 ? ns2 : no2, xb2 = same2 ? no2 : ns2;
         const float D1 = ns1 + no1, D2 = ns2 + no2;
         const float num = fmaf(xb1, D2, x1 * xb2);

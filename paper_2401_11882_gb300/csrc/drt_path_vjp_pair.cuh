@@ -56,11 +56,13 @@ __device__ __forceinline__ PairTerms pair_terms(float2 e0, float2 e1, float2 z0,
   const float2 one = f2(1.f, 1.f);
   PairTerms t;
   const float2 ns1 = add2(e0, e1), no1 = fma2(e0, e1, one);
-  const bool s1x = same_sign(z0.x, z1.x), s1y = same_sign(z0.y, z1.y);
+  bool s1x, s1y;
+  same_side2(z0, z1, s1x, s1y);
   t.x1 = f2(s1x ? ns1.x : no1.x, s1y ? ns1.y : no1.y);
   t.xb1 = f2(s1x ? no1.x : ns1.x, s1y ? no1.y : ns1.y);
   const float2 ns2 = add2(ea, eb), no2 = fma2(ea, eb, one);
-  const bool s2x = same_sign(za.x, zb.x), s2y = same_sign(za.y, zb.y);
+  bool s2x, s2y;
+  same_side2(za, zb, s2x, s2y);
   t.x2 = f2(s2x ? ns2.x : no2.x, s2y ? ns2.y : no2.y);
   t.xb2 = f2(s2x ? no2.x : ns2.x, s2y ? no2.y : ns2.y);
   t.D1 = add2(ns1, no1);
@@ -82,7 +84,7 @@ __device__ __forceinline__ void sigmoid_vis_sweep_pair(const VSmem& s, const Sme
   for (int j = 0; j <= K; ++j) vis[j] = vn[j] = vd[j] = one;
   auto wall = [&](int w) {
     const float4 A = p.A[w], B = p.B[w], C = p.C[w], D = p.D[w];
-    const float zt = s.H[w].w;   // signed TX-side value: only its sign is used
+    const float zt = copysignf(1.f, s.H[w].w);   // the TX side: only the sign is used
     const float2 hx = f2(A.x, A.y), hy = f2(A.z, A.w), hz = f2(B.x, B.y);
     const float2 ax = f2(C.x, C.y), ay = f2(C.z, C.w), bx = f2(D.x, D.y), by = f2(D.z, D.w);
     float2 ze[K + 2], ee[K + 2];
@@ -138,7 +140,7 @@ __device__ __forceinline__ void sigmoid_adjoint_sweep_pair(
   const float2 tiny = f2(SIGMOID_VJP_TINY, SIGMOID_VJP_TINY);
   for (int w = 0; w < W; ++w) {
     const float4 A = p.A[w], B = p.B[w], C = p.C[w], D = p.D[w], N = p.N[w];
-    const float zt = s.H[w].w;
+    const float zt = copysignf(1.f, s.H[w].w);
     const float2 hx = f2(A.x, A.y), hy = f2(A.z, A.w), hz = f2(B.x, B.y);
     const float2 ax = f2(C.x, C.y), ay = f2(C.z, C.w), bx = f2(D.x, D.y), by = f2(D.z, D.w);
     const float2 nx = f2(N.x, N.y), ny = f2(N.z, N.w);

@@ -114,6 +114,10 @@ def _gpu_path_points(sc, seq, tau):
 
 
 def _path_agreement(oracle_mod, sc, gpu):
+    return _path_agreement_n(oracle_mod, sc, gpu, N_ITER)
+
+
+def _path_agreement_n(oracle_mod, sc, gpu, n_iter):
     """Per receiver: (agree, slack).  agree is True when every path's record agrees
     with the oracle's where it matters for the power: the same check factor (kappa,
     0 for a degenerate path) within 1e-3 relative (or 1e-6 absolute), and where
@@ -129,7 +133,7 @@ def _path_agreement(oracle_mod, sc, gpu):
     ok = np.ones(sc.n_rx, bool)
     slack = np.zeros(sc.n_rx)
     for r, rx in enumerate(sc.rx):
-        ref = oracle_mod.mpt_paths(sc.walls, sc.tx, rx, K, sc.alpha, sc.smoothing, N_ITER, EPS,
+        ref = oracle_mod.mpt_paths(sc.walls, sc.tx, rx, K, sc.alpha, sc.smoothing, n_iter, EPS,
                                    sc.refl_coef)
         g = gpu[r]
         refl = ref["order"] > 0
@@ -251,3 +255,39 @@ def test_rejects_bad_arguments(drt):
         drt.mpt_paths(w, t, r, 1, 100.0, "hard_sigmoid", n_iter=-1)
     empty = sc.replace(rx=np.zeros((0, 2), np.float32))
     assert _gpu_power(drt, empty).shape == (0,)
+
+
+@pytest.mark.parametrize("n_iter", [0, 1, 64])
+def test_iteration_count_edges(drt, oracle_mod, n_iter):
+    """No step (the points stay at the walls' midpoints), one step, and the largest
+    count DRT_MPT_MAX_ITER: converged paths and the power as in the oracle."""
+    rng = np.random.default_rng(30 + n_iter)
+    sc = scenes.random_small_scene(rng, 6, 40, 2, 50.0, "hard_sigmoid", boundary=True)
+    w, t, r = _t(sc)
+    gpu = drt.mpt_paths(w, t, r, 2, 50.0, "hard_sigmoid", n_iter, EPS, sc.refl_coef)
+    torch.cuda.synchronize()
+    gpu = gpu.cpu().numpy().astype(np.float64)
+    walls = sc.walls.astype(np.float64)
+    lens = np.hypot(walls[:, 2] - walls[:, 0], walls[:, 3] - walls[:, 1])
+    for rr, rx in enumerate(sc.rx[:8]):
+        ref = oracle_mod.mpt_paths(sc.walls, sc.tx, rx, 2, 50.0, "hard_sigmoid", n_iter, EPS,
+                                   sc.refl_coef)
+        for c in np.nonzero((ref["order"] > 0) & ~ref["degenerate"].astype(bool))[0]:
+            k = int(ref["order"][c])
+            if n_iter == 0:   # the start: every point at its wall's midpoint
+                seq = [int(x) for x in ref["seq"][c][:k]]
+                np.testing.assert_allclose(ref["tau"][c][:k], 0.5 * lens[seq], rtol=1e-12)
+                if not np.isnan(gpu[rr, c, 0]):
+                    np.testing.assert_allclose(gpu[rr, c, :k], 0.5 * lens[seq], rtol=1e-6)
+            elif ref["cost"][c] < 1e-10 and not np.isnan(gpu[rr, c, 0]):
+                np.testing.assert_allclose(gpu[rr, c, :k], ref["tau"][c][:k], atol=1e-4)
+    P = drt.forward_mpt(w, t, r, 2, 50.0, "hard_sigmoid", n_iter, EPS, sc.refl_coef)
+    ref = oracle_mod.power_mpt(sc.walls, sc.tx, sc.rx, 2, 50.0, "hard_sigmoid", n_iter, EPS,
+                               sc.refl_coef)
+    agree, slack = _path_agreement_n(oracle_mod, sc, gpu, n_iter)
+    err = np.abs(P.cpu().numpy().astype(np.float64) - ref)
+    sens = fp32_sensitivity(lambda a, b, c: oracle_mod.power_mpt(a, b, c, 2, 50.0, "hard_sigmoid",
+                                                                  n_iter, EPS), sc.walls, sc.tx,
+                            sc.rx)
+    tol = np.maximum(1e-4 * np.abs(ref), 2.0 * sens) + slack
+    assert agree.mean() >= 0.75 and np.all(err <= tol)
