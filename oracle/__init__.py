@@ -29,6 +29,8 @@ Functions and the passages they follow:
 * ``power_mpt``, ``mpt_paths``  Sec. V-B, "Continuous Path Finding": reflection points found
                         iteratively (Min-Path-Tracing: Gauss-Newton on the reflection law from the
                         walls' midpoints) with the smoothed convergence check s(eps - C)
+* ``power_fpt``, ``fpt_paths``  the same with Fermat path tracing (Newton on the total path
+                        length) as the finder, and the same MPT check
 
 Readings of the paper that the oracle fixes (the paper leaves them open):
 incoherent scalar power p = Gamma^k V / L^2 with Gamma = 0.5; smoothing
@@ -93,8 +95,8 @@ def _load():
         lib.drt_oracle_field_jvp.argtypes = [p, i, p, p, i, i, d, i, d, d, d, p, p, i, p, p]
         lib.drt_oracle_power3.argtypes = [p, i, p, p, i, i, d, i, d, i, p]
         lib.drt_oracle_power3_jvp.argtypes = [p, i, p, p, i, i, d, i, d, p, p, i, p, p]
-        lib.drt_oracle_power_mpt.argtypes = [p, i, p, p, i, i, d, i, d, i, d, i, p]
-        lib.drt_oracle_mpt_paths.argtypes = [p, i, p, p, i, d, i, d, i, d, p, p, p, p, p]
+        lib.drt_oracle_power_finder.argtypes = [p, i, p, p, i, i, d, i, d, i, i, d, i, p]
+        lib.drt_oracle_finder_paths.argtypes = [p, i, p, p, i, d, i, d, i, i, d, p, p, p, p, p]
         _lib = lib
         return lib
 
@@ -391,21 +393,48 @@ def paths(walls, tx, rx1, max_order, alpha, smoothing, refl_coef=0.5) -> dict:
 
 
 
+_FINDERS = {"mpt": 0, "fpt": 1}
+
+
+def _power_finder(finder, walls, tx, rx, max_order, alpha, smoothing, n_iter, eps, refl_coef,
+                  threads):
+    walls, tx, rx = _scene_args(walls, tx, rx)
+    out = np.zeros(rx.shape[0])
+    rc = _load().drt_oracle_power_finder(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx),
+                                         rx.shape[0], int(max_order), float(alpha),
+                                         _kind(smoothing), float(refl_coef), _FINDERS[finder],
+                                         int(n_iter), float(eps), _threads(threads), _ptr(out))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def _finder_paths(finder, walls, tx, rx1, max_order, alpha, smoothing, n_iter, eps, refl_coef):
+    walls, tx, rx1 = _scene_args(walls, tx, rx1)
+    W, K = walls.shape[0], int(max_order)
+    n = num_candidates(W, K)
+    tau = np.zeros((n, max(K, 1)))
+    cost = np.zeros(n); kappa = np.zeros(n); pw = np.zeros(n)
+    deg = np.zeros(n, np.int32)
+    rc = _load().drt_oracle_finder_paths(_ptr(walls), W, _ptr(tx), _ptr(rx1), K, float(alpha),
+                                         _kind(smoothing), float(refl_coef), _FINDERS[finder],
+                                         int(n_iter), float(eps), _ptr(tau), _ptr(cost),
+                                         _ptr(kappa), _ptr(pw), _ptr(deg))
+    if rc:
+        raise ValueError("oracle rejected the arguments")
+    seq, order = candidates(W, K)
+    return dict(seq=seq, order=order, tau=tau[:, :K], cost=cost, kappa=kappa, power=pw,
+                degenerate=deg)
+
+
 def power_mpt(walls, tx, rx, max_order, alpha, smoothing, n_iter=10, eps=0.05, refl_coef=0.5,
               threads=None) -> np.ndarray:
     """Received power (float64 [R]) with the reflection points found by ``n_iter``
     Min-Path-Tracing steps from the walls' midpoints (Sec. V-B) and each path's
     validity taken as its on-segment tests times the convergence check
     s(eps - C), C the MPT cost (drt_oracle.cpp, path finder)."""
-    walls, tx, rx = _scene_args(walls, tx, rx)
-    out = np.zeros(rx.shape[0])
-    rc = _load().drt_oracle_power_mpt(_ptr(walls), walls.shape[0], _ptr(tx), _ptr(rx),
-                                      rx.shape[0], int(max_order), float(alpha),
-                                      _kind(smoothing), float(refl_coef), int(n_iter),
-                                      float(eps), _threads(threads), _ptr(out))
-    if rc:
-        raise ValueError("oracle rejected the arguments")
-    return out
+    return _power_finder("mpt", walls, tx, rx, max_order, alpha, smoothing, n_iter, eps,
+                         refl_coef, threads)
 
 
 def mpt_paths(walls, tx, rx1, max_order, alpha, smoothing, n_iter=10, eps=0.05,
@@ -414,18 +443,21 @@ def mpt_paths(walls, tx, rx1, max_order, alpha, smoothing, n_iter=10, eps=0.05,
     ``tau`` [n, K] (NaN past the path's order), the MPT ``cost`` and the convergence
     check ``kappa`` at the final points, the path ``power`` and a ``degenerate``
     flag, with the candidate table's ``seq`` and ``order``."""
-    walls, tx, rx1 = _scene_args(walls, tx, rx1)
-    W, K = walls.shape[0], int(max_order)
-    n = num_candidates(W, K)
-    tau = np.zeros((n, max(K, 1)))
-    cost = np.zeros(n); kappa = np.zeros(n); pw = np.zeros(n)
-    deg = np.zeros(n, np.int32)
-    rc = _load().drt_oracle_mpt_paths(_ptr(walls), W, _ptr(tx), _ptr(rx1), K, float(alpha),
-                                      _kind(smoothing), float(refl_coef), int(n_iter),
-                                      float(eps), _ptr(tau), _ptr(cost), _ptr(kappa), _ptr(pw),
-                                      _ptr(deg))
-    if rc:
-        raise ValueError("oracle rejected the arguments")
-    seq, order = candidates(W, K)
-    return dict(seq=seq, order=order, tau=tau[:, :K], cost=cost, kappa=kappa, power=pw,
-                degenerate=deg)
+    return _finder_paths("mpt", walls, tx, rx1, max_order, alpha, smoothing, n_iter, eps,
+                         refl_coef)
+
+
+def power_fpt(walls, tx, rx, max_order, alpha, smoothing, n_iter=10, eps=0.05, refl_coef=0.5,
+              threads=None) -> np.ndarray:
+    """power_mpt with Fermat path tracing as the finder: ``n_iter`` Newton steps on the
+    total path length from the walls' midpoints (Sec. V-B), the same MPT check."""
+    return _power_finder("fpt", walls, tx, rx, max_order, alpha, smoothing, n_iter, eps,
+                         refl_coef, threads)
+
+
+def fpt_paths(walls, tx, rx1, max_order, alpha, smoothing, n_iter=10, eps=0.05,
+              refl_coef=0.5) -> dict:
+    """mpt_paths with Fermat path tracing as the finder (``cost`` is still the MPT cost
+    at the final points)."""
+    return _finder_paths("fpt", walls, tx, rx1, max_order, alpha, smoothing, n_iter, eps,
+                         refl_coef)

@@ -409,9 +409,18 @@ Vec<T> path_field(const std::vector<Wall<T>>& walls, const Vec<T>& tx, const Vec
 //              leg between them towards zero without converging; at 1e-3 such a
 //              leg is still long enough that single and double precision runs of
 //              the finder agree on which side of the limit it ends);
-// (Fermat path tracing, Newton steps on the path length, is not used: the length
-// is not differentiable where a leg vanishes, and for two walls meeting at a
-// corner the iteration runs into the corner and stalls there.)
+// Fermat path tracing (FPT) takes the same unknowns, start, clamp, check, validity
+// and degenerate rule, with the total path length as the objective:
+//   L = sum_j l_j, dL/dtau_j = u_j . (h_{j-1} - h_j),
+//   d2L/dtau_j^2 = u_j^T (I - h_{j-1} h_{j-1}^T) u_j / l_{j-1} + u_j^T (I - h_j h_j^T) u_j / l_j,
+//   d2L/dtau_j dtau_{j+1} = -u_j^T (I - h_j h_j^T) u_{j+1} / l_j;
+//   each step  a Newton step (H + mu) delta = -grad L (L is convex in tau: a sum of
+//              norms of affine functions), clamped, with the same backtracking on L;
+//   check      the MPT cost C at the final points, as for MPT (the paper checks the
+//              convergence of every finder with the MPT loss).  Where the wall's
+//              line separates the path's neighbours, the length's minimum is the
+//              straight line through the crossing point, whose C is 4 (i . n)^2:
+//              the check rejects it.
 struct FinderLegs {
   std::vector<Vec<double>> X, h;   // vertices X_0..X_{k+1}; unit leg directions h_0..h_k
   std::vector<double> l;           // leg lengths
@@ -567,16 +576,86 @@ bool mpt_points(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
   return true;
 }
 
-// Power of one path candidate whose reflection points come from the MPT path
-// finder, with the smoothed convergence check; fills tau [k], C and kappa.
-double mpt_path_power(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
-                      const Vec<double>& rx, const std::vector<int>& seq, const Params& P,
-                      int n_iter, double eps, std::vector<double>& tau, double* cost,
-                      double* kappa) {
+// Reflection points of `seq` after n_iter Fermat (Newton) steps on the path length;
+// returns false if the path is degenerate.
+bool fpt_points(const std::vector<Wall<double>>& walls, const Vec<double>& tx,
+                const Vec<double>& rx, const std::vector<int>& seq, int n_iter,
+                std::vector<double>& tau) {
+  const int k = (int)seq.size();
+  tau.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) tau[j] = 0.5 * walls[seq[j]].len;
+  auto length = [](const FinderLegs& f) {
+    double L = 0.0;
+    for (double l : f.l) L += l;
+    return L;
+  };
+  // u^T (I - h h^T) v / l for leg `leg`
+  auto pquad = [](const FinderLegs& f, int leg, const Vec<double>& u, const Vec<double>& v) {
+    return (dot(u, v) - dot(f.h[leg], u) * dot(f.h[leg], v)) / f.l[leg];
+  };
+  for (int it = 0; it < n_iter && k > 0; ++it) {
+    const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
+    if (f.degenerate) return false;
+    std::vector<double> H(k * k, 0.0), b(k, 0.0);
+    for (int j = 1; j <= k; ++j) {
+      const Vec<double>& u = walls[seq[j - 1]].u;
+      b[j - 1] = -(dot(u, f.h[j - 1]) - dot(u, f.h[j]));   // -dL/dtau_j
+      H[(j - 1) * k + (j - 1)] = pquad(f, j - 1, u, u) + pquad(f, j, u, u);
+      if (j < k) {
+        const double c = -pquad(f, j, u, walls[seq[j]].u);
+        H[(j - 1) * k + j] = c;
+        H[j * k + (j - 1)] = c;
+      }
+    }
+    std::vector<double> g0(b);   // -grad L
+    for (int j = 0; j < k; ++j) H[j * k + j] *= 1.0 + 1e-6;
+    spd_solve(H, b, k);
+    double slope = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double lim = walls[seq[j]].len;
+      b[j] = b[j] < -lim ? -lim : (b[j] > lim ? lim : b[j]);
+      slope -= g0[j] * b[j];
+    }
+    const double L0 = length(f);
+    const double tol = 8.0 * DBL_EPSILON * L0;
+    double t = 1.0;
+    for (int m = 0; m < FINDER_HALVINGS; ++m, t *= 0.5) {
+      std::vector<double> trial(tau);
+      for (int j = 0; j < k; ++j) trial[j] += t * b[j];
+      const FinderLegs ft = finder_legs(walls, tx, rx, seq, trial);
+      if (ft.degenerate) continue;
+      if (length(ft) <= L0 + 1e-4 * t * slope + tol) {
+        tau.swap(trial);
+        break;
+      }
+    }
+  }
+  const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
+  if (f.degenerate) return false;
+  for (double l : f.l)
+    if (l < MPT_MIN_LEG) return false;
+  return true;
+}
+
+enum Finder { FINDER_MPT = 0, FINDER_FPT = 1 };
+
+bool finder_points(int finder, const std::vector<Wall<double>>& walls, const Vec<double>& tx,
+                   const Vec<double>& rx, const std::vector<int>& seq, int n_iter,
+                   std::vector<double>& tau) {
+  return finder == FINDER_FPT ? fpt_points(walls, tx, rx, seq, n_iter, tau)
+                              : mpt_points(walls, tx, rx, seq, n_iter, tau);
+}
+
+// Power of one path candidate whose reflection points come from a path finder
+// (MPT or FPT), with the smoothed convergence check; fills tau [k], C and kappa.
+double finder_path_power(int finder, const std::vector<Wall<double>>& walls,
+                         const Vec<double>& tx, const Vec<double>& rx,
+                         const std::vector<int>& seq, const Params& P, int n_iter, double eps,
+                         std::vector<double>& tau, double* cost, double* kappa) {
   const int k = (int)seq.size();
   *cost = 0.0;
   *kappa = 0.0;
-  if (!mpt_points(walls, tx, rx, seq, n_iter, tau)) return 0.0;
+  if (!finder_points(finder, walls, tx, rx, seq, n_iter, tau)) return 0.0;
   const FinderLegs f = finder_legs(walls, tx, rx, seq, tau);
   *cost = mpt_cost(walls, seq, f);
   *kappa = smooth(eps - *cost, P.alpha, P.kind);
@@ -1021,10 +1100,11 @@ int drt_oracle_paths(const double* walls_xy, int W, const double* tx, const doub
 
 
 // Path-finder variant of drt_oracle_power (MPT points, convergence check): power [R].
-int drt_oracle_power_mpt(const double* walls_xy, int W, const double* tx, const double* rx,
-                         int R, int K, double alpha, int kind, double gamma, int n_iter,
-                         double eps, int nthreads, double* out) {
+int drt_oracle_power_finder(const double* walls_xy, int W, const double* tx, const double* rx,
+                            int R, int K, double alpha, int kind, double gamma, int finder,
+                            int n_iter, double eps, int nthreads, double* out) {
   if (check_args(walls_xy, W, tx, rx, R, K, alpha, kind) || n_iter < 0) return 1;
+  if (finder != FINDER_MPT && finder != FINDER_FPT) return 1;
   std::vector<double> xy(walls_xy, walls_xy + 4 * W);
   auto walls = make_walls(xy, W);
   auto cands = candidates(W, K);
@@ -1038,20 +1118,21 @@ int drt_oracle_power_mpt(const double* walls_xy, int W, const double* tx, const 
     std::vector<double> tau;
     double C, kap;
     for (const auto& seq : cands)
-      sum += mpt_path_power(walls, t, q, seq, prm, n_iter, eps, tau, &C, &kap);
+      sum += finder_path_power(finder, walls, t, q, seq, prm, n_iter, eps, tau, &C, &kap);
     out[r] = sum;
   }
   return 0;
 }
 
-// Per path of one receiver: the MPT finder's along-wall coordinates tau [n_cand][K]
-// (NaN past the path's order and for a degenerate path), cost C [n_cand], kappa
-// [n_cand], power [n_cand], degenerate flag [n_cand].
-int drt_oracle_mpt_paths(const double* walls_xy, int W, const double* tx, const double* rx1,
-                         int K, double alpha, int kind, double gamma, int n_iter, double eps,
-                         double* tau_out, double* cost, double* kappa, double* power,
-                         int* degenerate) {
+// Per path of one receiver: the finder's (0 MPT, 1 FPT) along-wall coordinates tau
+// [n_cand][K] (NaN past the path's order and for a degenerate path), MPT cost C
+// [n_cand], kappa [n_cand], power [n_cand], degenerate flag [n_cand].
+int drt_oracle_finder_paths(const double* walls_xy, int W, const double* tx, const double* rx1,
+                            int K, double alpha, int kind, double gamma, int finder, int n_iter,
+                            double eps, double* tau_out, double* cost, double* kappa,
+                            double* power, int* degenerate) {
   if (check_args(walls_xy, W, tx, rx1, 1, K, alpha, kind) || n_iter < 0) return 1;
+  if (finder != FINDER_MPT && finder != FINDER_FPT) return 1;
   std::vector<double> xy(walls_xy, walls_xy + 4 * W);
   auto walls = make_walls(xy, W);
   auto cands = candidates(W, K);
@@ -1061,8 +1142,9 @@ int drt_oracle_mpt_paths(const double* walls_xy, int W, const double* tx, const 
   for (size_t i = 0; i < cands.size(); ++i) {
     std::vector<double> tau;
     const int k = (int)cands[i].size();
-    power[i] = mpt_path_power(walls, t, q, cands[i], prm, n_iter, eps, tau, &cost[i], &kappa[i]);
-    degenerate[i] = mpt_points(walls, t, q, cands[i], n_iter, tau) ? 0 : 1;
+    power[i] = finder_path_power(finder, walls, t, q, cands[i], prm, n_iter, eps, tau, &cost[i],
+                                 &kappa[i]);
+    degenerate[i] = finder_points(finder, walls, t, q, cands[i], n_iter, tau) ? 0 : 1;
     for (int j = 0; j < K; ++j) tau_out[i * K + j] = (j < k && !degenerate[i]) ? tau[j] : NAN;
   }
   return 0;

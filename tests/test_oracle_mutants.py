@@ -18,7 +18,8 @@ SRC = os.path.join(ROOT, "oracle", "drt_oracle.cpp")
 PIN_FILES = ["tests/test_oracle_smoothing.py", "tests/test_oracle_candidates.py",
              "tests/test_oracle_geometry.py", "tests/test_oracle_bruteforce.py",
              "tests/test_oracle_gradients.py", "tests/test_oracle_field.py",
-             "tests/test_oracle_3d.py", "tests/test_oracle_mpt_finder.py"]
+             "tests/test_oracle_3d.py", "tests/test_oracle_mpt_finder.py",
+             "tests/test_oracle_fpt_finder.py"]
 
 MUTANTS = {
     "mirror sign": ("return Vec<T>{p.x - 2.0 * d * w.n.x", "return Vec<T>{p.x + 2.0 * d * w.n.x"),
@@ -95,6 +96,14 @@ MUTANTS = {
     "mpt line search takes increases": (
         "if (mpt_cost(walls, seq, ft) <= C0 + 1e-4 * t * slope + tol) {",
         "if (mpt_cost(walls, seq, ft) >= C0 + 1e-4 * t * slope + tol) {"),
+    "fpt gradient sign": ("b[j - 1] = -(dot(u, f.h[j - 1]) - dot(u, f.h[j]));",
+                          "b[j - 1] = (dot(u, f.h[j - 1]) - dot(u, f.h[j]));"),
+    "fpt hessian coupling sign": ("const double c = -pquad(f, j, u, walls[seq[j]].u);",
+                                  "const double c = pquad(f, j, u, walls[seq[j]].u);"),
+    "fpt hessian drops the outgoing leg": ("pquad(f, j - 1, u, u) + pquad(f, j, u, u)",
+                                           "pquad(f, j - 1, u, u)"),
+    "fpt line search takes increases": ("if (length(ft) <= L0 + 1e-4 * t * slope + tol)",
+                                        "if (length(ft) >= L0 + 1e-4 * t * slope + tol)"),
     "mpt keeps paths with a vanishing leg": ("if (l < MPT_MIN_LEG) return false;", ""),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
