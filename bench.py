@@ -389,9 +389,13 @@ def measure_extras(drt, dev, sc, w, t, r):
     sm_h = timed(lambda: drt.forward_mpt(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid", 10,
                                          0.05), 2)
     sm_s = timed(lambda: drt.forward_mpt(w, t, r, sc.max_order, sc.alpha, "sigmoid", 10, 0.05), 1)
-    out["mpt_forward"] = {"workload": "benchmark workload, reflection points from 10 MPT steps",
+    sf_h = timed(lambda: drt.forward_fpt(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid", 10,
+                                         0.05), 2)
+    out["mpt_forward"] = {"workload": "benchmark workload, reflection points from 10 MPT steps "
+                                      "(fermat_*: 10 Fermat path-tracing steps)",
                           "hard_ms": sm_h * 1e3, "hard_evals_per_s": ev / sm_h,
-                          "sigmoid_ms": sm_s * 1e3, "sigmoid_evals_per_s": ev / sm_s}
+                          "sigmoid_ms": sm_s * 1e3, "sigmoid_evals_per_s": ev / sm_s,
+                          "fermat_hard_ms": sf_h * 1e3, "fermat_hard_evals_per_s": ev / sf_h}
     # more walls than shared memory holds: square + 4092 segments, K <= 1, 64x64 receivers
     cs = scenes.clutter_scene(4092, 64, seed=1, alpha=100.0, smoothing="hard_sigmoid",
                               max_order=1)

@@ -166,6 +166,30 @@ drt_status drt_forward_mpt(const drt_scene* scene, const drt_tile* tile, int32_t
 drt_status drt_mpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
                          void* stream);
 
+/* The same three calls with Fermat path tracing (Sec. V-B) as the finder: from the
+   walls' midpoints, n_iter Newton steps on the total path length L = sum_j l_j
+   along the walls' lines, (H + 1e-6 diag H) delta = -grad L with
+     dL/dtau_j = u_j . (h_{j-1} - h_j),
+     H_jj = (1 - (h_{j-1} . u_j)^2) / l_{j-1} + (1 - (h_j . u_j)^2) / l_j,
+     H_{j,j+1} = -(u_j . u_{j+1} - (h_j . u_j)(h_j . u_{j+1})) / l_j
+   (u_j the wall's unit direction, h_j and l_j leg j's unit direction and length),
+   the same clamp, backtracking (on L), convergence check s(check_eps - C) with the
+   MPT cost C at the final points, validity and degenerate rule as the MPT finder.
+   L is convex in tau, so every accepted step shortens the path; where a wall's line
+   separates a path's neighbours the minimum is the straight crossing, whose C is
+   4 (i . n)^2 and which the check rejects.  Where two walls meet in a corner the
+   iteration can run into it (the leg between them vanishing, L losing its
+   derivative) and end degenerate where the MPT finder converges.  Arguments,
+   layouts and errors as for drt_forward_mpt / drt_mpt_paths; the paths record's C
+   is the MPT cost. */
+drt_status drt_forward_fpt_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                          size_t* bytes);
+drt_status drt_forward_fpt(const drt_scene* scene, const drt_tile* tile, int32_t n_iter,
+                           float check_eps, float* power, void* workspace,
+                           size_t workspace_bytes, void* stream);
+drt_status drt_fpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
+                         void* stream);
+
 /* Coherent field per receiver: Eq. 7 read as a sum of complex path fields (the
    field normal to the scene plane, free-space spreading 1/L of the unfolded path):
      E_r = sum over the candidates of  prod_j C_j * V * vis * exp(-2 pi i L / wavelength) / L

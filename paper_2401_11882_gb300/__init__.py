@@ -14,17 +14,18 @@ Public calls (PyTorch tensors on a CUDA device, float32):
   for the transmitter only).
 * ``forward_mpt(...)``: power with the reflection points found iteratively
   (Min-Path-Tracing) and the smoothed convergence check; ``mpt_paths`` its per-path
-  record.
+  record; ``forward_fpt`` / ``fpt_paths`` the same with Fermat path tracing.
 * ``objective_host(...)``: the objective end to end from host arrays.
 
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
-from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, forward_mpt,
-                  loss, min_loss, min_loss_backward, min_loss_vjp, mpt_paths, num_candidates,
-                  objective, objective_host, power, power3, vjp, vjp3, vjp3_tx)
+from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, forward_fpt,
+                  forward_mpt, fpt_paths, loss, min_loss, min_loss_backward, min_loss_vjp,
+                  mpt_paths, num_candidates, objective, objective_host, power, power3, vjp, vjp3,
+                  vjp3_tx)
 
 __all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "forward3",
-           "forward_mpt", "loss", "min_loss", "min_loss_backward", "min_loss_vjp", "mpt_paths",
-           "num_candidates", "objective", "objective_host", "power", "power3", "vjp", "vjp3",
-           "vjp3_tx"]
+           "forward_fpt", "forward_mpt", "fpt_paths", "loss", "min_loss", "min_loss_backward",
+           "min_loss_vjp", "mpt_paths", "num_candidates", "objective", "objective_host", "power",
+           "power3", "vjp", "vjp3", "vjp3_tx"]

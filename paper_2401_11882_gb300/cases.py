@@ -8,6 +8,7 @@ without ``--clock-control none`` ncu locks the GPU's clocks).
     field     drt.field (coherent field, Fresnel TE, --eps-r, --wavelength)
     field_vjp drt.field_vjp with dense g = 1/R (after one drt.field)
     forward_mpt drt.forward_mpt (the iterative path finder, --n-iter steps, --check-eps)
+    forward_fpt drt.forward_fpt (the same with Fermat path tracing)
     forward3  drt.forward3 on the 3D room (``scenes.room3d``, --rx-grid receivers a side)
     vjp3      drt.vjp3 (transmitter and triangle gradients; --tx-only: drt.vjp3_tx) on
               the same room, dense g = 1/R
@@ -31,7 +32,7 @@ from . import ops, scenes
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("op", choices=["forward", "vjp", "mlp", "field", "field_vjp", "forward3",
-                                   "vjp3", "forward_mpt"])
+                                   "vjp3", "forward_mpt", "forward_fpt"])
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--scene", choices=["gradient", "large", "clutter"], default="gradient")
     ap.add_argument("--segments", type=int, default=4092)
@@ -108,9 +109,10 @@ def main() -> int:
         tile = ops.TileConfig(single_rx=True) if args.single_rx else None
         if args.op == "forward":
             return ops.forward(w, t, r, sc.max_order, args.alpha, args.smoothing, tile=tile)
-        if args.op == "forward_mpt":
-            return ops.forward_mpt(w, t, r, sc.max_order, args.alpha, args.smoothing,
-                                   args.n_iter, args.check_eps, tile=tile)
+        if args.op in ("forward_mpt", "forward_fpt"):
+            fn = ops.forward_mpt if args.op == "forward_mpt" else ops.forward_fpt
+            return fn(w, t, r, sc.max_order, args.alpha, args.smoothing, args.n_iter,
+                      args.check_eps, tile=tile)
         if args.op == "field":
             return ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
                              args.eps_r, tile=tile)

@@ -126,7 +126,7 @@ constexpr long long MAX_PARTIALS = 1LL << 26;
 // VJP_RX: the min-loss adjoint's one-receiver kernel (lanes = candidates)
 // VJP_TX: drt_vjp without the wall gradient (one receiver per lane)
 // VJP3_TX: drt3_vjp without the triangle gradient
-enum Kernel { FWD, VJP, VJP_TX, VJP_RX, FIELD, FIELD_VJP, FWD3, VJP3, VJP3_TX, FWD_MPT };
+enum Kernel { FWD, VJP, VJP_TX, VJP_RX, FIELD, FIELD_VJP, FWD3, VJP3, VJP3_TX, FWD_MPT, FWD_FPT };
 
 drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp* d) {
   int sms = 0;
@@ -138,7 +138,8 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   d->threads = warps * 32;
   d->n_cand = num_candidates(W, K);
   long long chunk = (t && t->cands_per_unit) ? t->cands_per_unit : 64;
-  if ((kern == FWD || kern == FIELD || kern == FWD3 || kern == FWD_MPT) && R > 0) {
+  const bool finder = kern == FWD_MPT || kern == FWD_FPT;
+  if ((kern == FWD || kern == FIELD || kern == FWD3 || finder) && R > 0) {
     const long long max_chunks = std::max(1LL, MAX_PARTIALS / R);
     chunk = std::max(chunk, (d->n_cand + max_chunks - 1) / max_chunks);
   }
@@ -159,7 +160,9 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
                     : (kern == FWD3)      ? forward3_occupancy(mode, d->threads, W, &per_sm)
                     : (kern == VJP3)      ? vjp3_occupancy(mode, true, d->threads, W, &per_sm)
                     : (kern == VJP3_TX)   ? vjp3_occupancy(mode, false, d->threads, W, &per_sm)
-                    : (kern == FWD_MPT)   ? forward_mpt_occupancy(mode, d->threads, W, &per_sm)
+                    : finder              ? forward_mpt_occupancy(
+                                                mode, kern == FWD_FPT ? FINDER_FPT : FINDER_MPT,
+                                                d->threads, W, &per_sm)
                                           : vjp_occupancy(mode, true, d->pairs, d->threads, W,
                                                           &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -167,7 +170,7 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
   }
   long long ctas = (long long)sms * per_sm;
   const long long needed = (d->n_units + warps - 1) / warps;
-  if (kern == FWD || kern == FIELD || kern == FWD3 || kern == FWD_MPT)
+  if (kern == FWD || kern == FIELD || kern == FWD3 || finder)
     ctas = std::min(ctas, std::max(1LL, needed));
   d->ctas = (int)std::max(1LL, ctas);
   return DRT_OK;
@@ -314,21 +317,23 @@ MptArgs mpt_args(const drt_scene* scene, const drt_tile* tile, const Decomp& d, 
 }
 }  // namespace
 
-drt_status drt_forward_mpt_workspace_size(const drt_scene* scene, const drt_tile* tile,
-                                          size_t* bytes) {
+namespace {
+drt_status finder_workspace_size(int finder, const drt_scene* scene, const drt_tile* tile,
+                                  size_t* bytes) {
   drt_status st = check_scene(scene);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
   if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
   Decomp d;
-  if ((st = decompose(scene, tile, FWD_MPT, &d)) != DRT_OK) return st;
+  if ((st = decompose(scene, tile, finder == FINDER_FPT ? FWD_FPT : FWD_MPT, &d)) != DRT_OK)
+    return st;
   *bytes = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
   return DRT_OK;
 }
 
-drt_status drt_forward_mpt(const drt_scene* scene, const drt_tile* tile, int32_t n_iter,
-                           float check_eps, float* power, void* workspace,
-                           size_t workspace_bytes, void* stream) {
+drt_status finder_forward(int finder, const drt_scene* scene, const drt_tile* tile,
+                          int32_t n_iter, float check_eps, float* power, void* workspace,
+                          size_t workspace_bytes, void* stream) {
   drt_status st = check_scene(scene);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
@@ -336,23 +341,25 @@ drt_status drt_forward_mpt(const drt_scene* scene, const drt_tile* tile, int32_t
   if (scene->n_rx > 0 && !power) return fail(DRT_ERR_INVALID_ARG, "power is NULL");
   if (scene->n_rx == 0) return DRT_OK;
   Decomp d;
-  if ((st = decompose(scene, tile, FWD_MPT, &d)) != DRT_OK) return st;
+  if ((st = decompose(scene, tile, finder == FINDER_FPT ? FWD_FPT : FWD_MPT, &d)) != DRT_OK)
+    return st;
   const size_t need = (size_t)d.n_chunks * (size_t)scene->n_rx * sizeof(float);
   if (!workspace || workspace_bytes < need)
-    return fail(DRT_ERR_WORKSPACE, "MPT forward needs %zu workspace bytes, got %zu", need,
-                workspace_bytes);
+    return fail(DRT_ERR_WORKSPACE, "path-finder forward needs %zu workspace bytes, got %zu",
+                need, workspace_bytes);
   MptArgs m = mpt_args(scene, tile, d, n_iter, check_eps);
+  m.finder = finder;
   m.f.partial = static_cast<float*>(workspace);
   m.f.power = power;
   m.paths = nullptr;
   cudaError_t e = launch_forward_mpt(m, scene->smoothing, d.ctas, d.threads,
                                      static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "MPT forward launch");
+  if (e != cudaSuccess) return cuda_fail(e, "path-finder forward launch");
   return DRT_OK;
 }
 
-drt_status drt_mpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
-                         void* stream) {
+drt_status finder_paths(int finder, const drt_scene* scene, int32_t n_iter, float check_eps,
+                        float* paths, void* stream) {
   drt_status st = check_scene(scene);
   if (st != DRT_OK) return st;
   if ((st = check_mpt_args(n_iter, check_eps)) != DRT_OK) return st;
@@ -364,15 +371,52 @@ drt_status drt_mpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps
     return fail(DRT_ERR_UNSUPPORTED, "paths output of %lld records is too large",
                 (long long)scene->n_rx * n_cand);
   Decomp d;
-  if ((st = decompose(scene, nullptr, FWD_MPT, &d)) != DRT_OK) return st;
+  if ((st = decompose(scene, nullptr, finder == FINDER_FPT ? FWD_FPT : FWD_MPT, &d)) != DRT_OK)
+    return st;
   MptArgs m = mpt_args(scene, nullptr, d, n_iter, check_eps);
+  m.finder = finder;
   m.f.partial = nullptr;
   m.f.power = nullptr;
   m.paths = paths;
   cudaError_t e = launch_mpt_paths(m, scene->smoothing, d.ctas, d.threads,
                                    static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "MPT paths launch");
+  if (e != cudaSuccess) return cuda_fail(e, "path-finder paths launch");
   return DRT_OK;
+}
+}  // namespace
+
+drt_status drt_forward_mpt_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                          size_t* bytes) {
+  return finder_workspace_size(FINDER_MPT, scene, tile, bytes);
+}
+
+drt_status drt_forward_mpt(const drt_scene* scene, const drt_tile* tile, int32_t n_iter,
+                           float check_eps, float* power, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  return finder_forward(FINDER_MPT, scene, tile, n_iter, check_eps, power, workspace,
+                        workspace_bytes, stream);
+}
+
+drt_status drt_mpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
+                         void* stream) {
+  return finder_paths(FINDER_MPT, scene, n_iter, check_eps, paths, stream);
+}
+
+drt_status drt_forward_fpt_workspace_size(const drt_scene* scene, const drt_tile* tile,
+                                          size_t* bytes) {
+  return finder_workspace_size(FINDER_FPT, scene, tile, bytes);
+}
+
+drt_status drt_forward_fpt(const drt_scene* scene, const drt_tile* tile, int32_t n_iter,
+                           float check_eps, float* power, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+  return finder_forward(FINDER_FPT, scene, tile, n_iter, check_eps, power, workspace,
+                        workspace_bytes, stream);
+}
+
+drt_status drt_fpt_paths(const drt_scene* scene, int32_t n_iter, float check_eps, float* paths,
+                         void* stream) {
+  return finder_paths(FINDER_FPT, scene, n_iter, check_eps, paths, stream);
 }
 
 drt_status drt_field_workspace_size(const drt_scene* scene, const drt_tile* tile, size_t* bytes) {

@@ -153,15 +153,17 @@ cudaError_t launch_loss_backward(const int32_t* argmin, const float* grad_loss, 
 
 // Path-finder forward (drt_mpt.cu): the forward's decomposition (one receiver per
 // lane) with the reflection points found by Min-Path-Tracing steps.
+enum : int { FINDER_MPT = 0, FINDER_FPT = 1 };   // the path finder (Sec. V-B)
 struct MptArgs {
   FwdArgs f;          // scene, decomposition, partial sums and power (pairs = false)
-  int n_iter;         // MPT steps from the walls' midpoints
+  int n_iter;         // finder steps from the walls' midpoints
+  int finder;         // FINDER_MPT or FINDER_FPT
   float check_eps;    // the convergence check is s(check_eps - C)
   float* paths;       // drt_mpt_paths: [R][n_cand][K + 2] (tau_1..tau_K, C, kappa) or null
 };
 cudaError_t launch_forward_mpt(const MptArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t launch_mpt_paths(const MptArgs& a, int mode, int ctas, int threads, cudaStream_t st);
-cudaError_t forward_mpt_occupancy(int mode, int threads, int W, int* ctas_per_sm);
+cudaError_t forward_mpt_occupancy(int mode, int finder, int threads, int W, int* ctas_per_sm);
 cudaError_t forward_mpt_set_smem_limit(int W);
 
 size_t forward3_smem_bytes(int W);

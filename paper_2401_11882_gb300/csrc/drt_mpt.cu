@@ -18,6 +18,12 @@
 // (an iteration running into the corner where two walls meet), makes the path
 // degenerate: it contributes 0.
 //
+// Fermat path tracing (FPT) runs the same loop with the total length L = sum_j l_j
+// as the objective: Newton steps (H + mu) delta = -grad L with
+// dL/dtau_j = u_j . (h_{j-1} - h_j) and H's entries (1 - (h . u)^2) / l on the
+// diagonal, -(u_j . u_{j+1} - (h_j . u_j)(h_j . u_{j+1})) / l_j beside it, the
+// backtracking on L; the check is still s(eps - C) with the MPT cost C.
+//
 // Mapping: the forward's (one receiver per lane, a warp-uniform candidate,
 // units of 32 receivers x a chunk of candidates, chunk sums added in order).
 // The iterations diverge only where lanes take different numbers of
@@ -106,6 +112,22 @@ __device__ __forceinline__ float2 mpt_mirror(const float4& G, float2 v) {
   return make_float2(fmaf(-2.f * c, G.x, v.x), fmaf(-2.f * c, G.y, v.y));
 }
 
+template <int K>
+__device__ __forceinline__ float fpt_length(const MptLegs<K>& f) {
+  float L = 0.f;
+#pragma unroll
+  for (int j = 0; j <= K; ++j) L += f.l[j];
+  return L;
+}
+
+// The finder's objective: the MPT cost C, or the path length L for FPT.
+template <int FINDER, int K>
+__device__ __forceinline__ float finder_objective(const SmemWalls& s, const Cand& cd,
+                                                  const MptLegs<K>& f) {
+  if (FINDER == FINDER_FPT) return fpt_length<K>(f);
+  return mpt_cost<K>(s, cd, f);
+}
+
 // Result of the path finder for one path: tau, the final cost, degeneracy.
 template <int K>
 struct MptResult {
@@ -114,9 +136,9 @@ struct MptResult {
   bool degenerate;
 };
 
-template <int K>
-__device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, float2 tx,
-                                           float2 rx, int n_iter, MptResult<K>& res) {
+template <int FINDER, int K>
+__device__ __forceinline__ void finder_points(const SmemWalls& s, const Cand& cd, float2 tx,
+                                              float2 rx, int n_iter, MptResult<K>& res) {
   float tau[K > 0 ? K : 1];
 #pragma unroll
   for (int j = 0; j < K; ++j) tau[j] = 0.5f * s.G[cd.w[j]].w;
@@ -124,6 +146,37 @@ __device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, f
   mpt_legs<K>(s, cd, tx, rx, tau, f);
   bool dead = f.degenerate;
   for (int it = 0; it < n_iter && K > 0 && !dead; ++it) {
+    float A[K + 1][K + 1], b[K + 1], g0[K + 1];
+    if (FINDER == FINDER_FPT) {
+      // b = -grad L, A = the Hessian of L (tridiagonal)
+#pragma unroll
+      for (int j = 1; j <= K; ++j) {
+        const float4 G = s.G[cd.w[j - 1]];
+        const float ux = G.y, uy = -G.x;   // the wall's unit direction
+        const float gin = fmaf(ux, f.hx[j - 1], uy * f.hy[j - 1]);
+        const float gout = fmaf(ux, f.hx[j], uy * f.hy[j]);
+        b[j] = gout - gin;
+#pragma unroll
+        for (int q = 1; q <= K; ++q) A[j][q] = 0.f;
+        A[j][j] = fmaf(-gin, gin, 1.f) * __frcp_rn(f.l[j - 1]) +
+                  fmaf(-gout, gout, 1.f) * __frcp_rn(f.l[j]);
+      }
+#pragma unroll
+      for (int j = 1; j < K; ++j) {
+        const float4 G = s.G[cd.w[j - 1]], Gn = s.G[cd.w[j]];
+        const float ux = G.y, uy = -G.x, vx = Gn.y, vy = -Gn.x;
+        const float hu = fmaf(ux, f.hx[j], uy * f.hy[j]);
+        const float hv = fmaf(vx, f.hx[j], vy * f.hy[j]);
+        const float c = -fmaf(-hu, hv, fmaf(ux, vx, uy * vy)) * __frcp_rn(f.l[j]);
+        A[j][j + 1] = c;
+        A[j + 1][j] = c;
+      }
+#pragma unroll
+      for (int p = 1; p <= K; ++p) {
+        g0[p] = b[p];
+        A[p][p] *= 1.f + MPT_MU;
+      }
+    } else {
     // Jacobian: J[j][i] = dr_j / dtau_i (2-vectors), nonzero for |i - j| <= 1
     float2 J[K + 1][K + 1];
     float2 r[K + 1];
@@ -147,7 +200,6 @@ __device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, f
       }
     }
     // normal equations (J^T J + mu) delta = -J^T r
-    float A[K + 1][K + 1], b[K + 1], g0[K + 1];
 #pragma unroll
     for (int p = 1; p <= K; ++p) {
 #pragma unroll
@@ -163,6 +215,7 @@ __device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, f
       b[p] = -v;
       g0[p] = b[p];
       A[p][p] *= 1.f + MPT_MU;
+    }
     }
     // Cholesky: A = L L^T (lower triangle in place), then L y = b, L^T x = y
 #pragma unroll
@@ -195,15 +248,16 @@ __device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, f
       for (int p = q + 1; p <= K; ++p) v = fmaf(-A[p][q], b[p], v);
       b[q] = A[q][q] > 0.f ? v * __frcp_rn(A[q][q]) : 0.f;
     }
-    // clamp, slope of C along the step (grad C = 2 J^T r = -2 g0)
+    // clamp, slope of the objective along the step (grad C = 2 J^T r = -2 g0 for
+    // MPT, grad L = -g0 for FPT)
     float slope = 0.f;
 #pragma unroll
     for (int q = 1; q <= K; ++q) {
       const float lim = s.G[cd.w[q - 1]].w;
       b[q] = fminf(fmaxf(b[q], -lim), lim);
-      slope = fmaf(-2.f * g0[q], b[q], slope);
+      slope = fmaf((FINDER == FINDER_FPT ? -1.f : -2.f) * g0[q], b[q], slope);
     }
-    const float C0 = mpt_cost<K>(s, cd, f);
+    const float C0 = finder_objective<FINDER, K>(s, cd, f);
     const float tol = MPT_ROUNDING * C0;
     float t = 1.f;
     for (int m = 0; m < MPT_HALVINGS; ++m, t *= 0.5f) {
@@ -213,7 +267,7 @@ __device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, f
       MptLegs<K> ft;
       mpt_legs<K>(s, cd, tx, rx, trial, ft);
       if (ft.degenerate) continue;
-      if (mpt_cost<K>(s, cd, ft) <= fmaf(1e-4f * t, slope, C0) + tol) {
+      if (finder_objective<FINDER, K>(s, cd, ft) <= fmaf(1e-4f * t, slope, C0) + tol) {
 #pragma unroll
         for (int q = 0; q < K; ++q) tau[q] = trial[q];
         f = ft;
@@ -232,12 +286,12 @@ __device__ __forceinline__ void mpt_points(const SmemWalls& s, const Cand& cd, f
 // Power of one candidate of order K with MPT reflection points.  When `out` is
 // not null it receives the per-path record of a scene of maximum order KS:
 // tau_1..tau_KS (NaN past K, or for a degenerate path), C, kappa.
-template <int MODE, int K>
+template <int MODE, int FINDER, int K>
 __device__ __forceinline__ float path_power_mpt(const SmemWalls& s, int W, float2 tx, float2 rx,
                                                 const Cand& cd, float alpha, float gk, int n_iter,
                                                 float eps, float* out, int KS) {
   MptResult<K> m;
-  mpt_points<K>(s, cd, tx, rx, n_iter, m);
+  finder_points<FINDER, K>(s, cd, tx, rx, n_iter, m);
   const float kappa = m.degenerate ? 0.f : smooth3<MODE>(eps - m.C, alpha).s;
   if (out) {
     const float nan = __int_as_float(0x7fc00000);
@@ -297,7 +351,7 @@ __device__ __forceinline__ float path_power_mpt(const SmemWalls& s, int W, float
   return path_power_of<MODE, K>(g, vis, gk);
 }
 
-template <int MODE>
+template <int MODE, int FINDER>
 __global__ void __launch_bounds__(256, 2) forward_mpt_kernel(const MptArgs m) {
   const FwdArgs& a = m.f;
   extern __shared__ float4 smem[];
@@ -328,10 +382,10 @@ __global__ void __launch_bounds__(256, 2) forward_mpt_kernel(const MptArgs m) {
                                      : nullptr;
       float p;
       switch (cd.k) {
-        case 0: p = path_power_mpt<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], m.n_iter, m.check_eps, out, a.K); break;
-        case 1: p = path_power_mpt<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], m.n_iter, m.check_eps, out, a.K); break;
-        case 2: p = path_power_mpt<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], m.n_iter, m.check_eps, out, a.K); break;
-        default: p = path_power_mpt<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], m.n_iter, m.check_eps, out, a.K); break;
+        case 0: p = path_power_mpt<MODE, FINDER, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], m.n_iter, m.check_eps, out, a.K); break;
+        case 1: p = path_power_mpt<MODE, FINDER, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], m.n_iter, m.check_eps, out, a.K); break;
+        case 2: p = path_power_mpt<MODE, FINDER, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], m.n_iter, m.check_eps, out, a.K); break;
+        default: p = path_power_mpt<MODE, FINDER, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], m.n_iter, m.check_eps, out, a.K); break;
       }
       acc += p;
     }
@@ -351,10 +405,18 @@ cudaError_t launch_mpt_t(F kern, const MptArgs& a, int ctas, int threads, cudaSt
 cudaError_t launch_forward_mpt(const MptArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (a.f.n_units > 0) {
-    switch (mode) {
-      case MODE_SIGMOID: e = launch_mpt_t(forward_mpt_kernel<MODE_SIGMOID>, a, ctas, threads, st); break;
-      case MODE_HARD: e = launch_mpt_t(forward_mpt_kernel<MODE_HARD>, a, ctas, threads, st); break;
-      default: e = launch_mpt_t(forward_mpt_kernel<MODE_STEP>, a, ctas, threads, st); break;
+    if (a.finder == FINDER_FPT) {
+      switch (mode) {
+        case MODE_SIGMOID: e = launch_mpt_t(forward_mpt_kernel<MODE_SIGMOID, FINDER_FPT>, a, ctas, threads, st); break;
+        case MODE_HARD: e = launch_mpt_t(forward_mpt_kernel<MODE_HARD, FINDER_FPT>, a, ctas, threads, st); break;
+        default: e = launch_mpt_t(forward_mpt_kernel<MODE_STEP, FINDER_FPT>, a, ctas, threads, st); break;
+      }
+    } else {
+      switch (mode) {
+        case MODE_SIGMOID: e = launch_mpt_t(forward_mpt_kernel<MODE_SIGMOID, FINDER_MPT>, a, ctas, threads, st); break;
+        case MODE_HARD: e = launch_mpt_t(forward_mpt_kernel<MODE_HARD, FINDER_MPT>, a, ctas, threads, st); break;
+        default: e = launch_mpt_t(forward_mpt_kernel<MODE_STEP, FINDER_MPT>, a, ctas, threads, st); break;
+      }
     }
     if (e != cudaSuccess) return e;
   }
@@ -366,28 +428,43 @@ cudaError_t launch_mpt_paths(const MptArgs& a, int mode, int ctas, int threads, 
   return launch_forward_mpt(a, mode, ctas, threads, st);
 }
 
-cudaError_t forward_mpt_occupancy(int mode, int threads, int W, int* ctas_per_sm) {
+cudaError_t forward_mpt_occupancy(int mode, int finder, int threads, int W, int* ctas_per_sm) {
   const size_t smem = forward_smem_bytes(W, false);
+  if (finder == FINDER_FPT) {
+    switch (mode) {
+      case MODE_SIGMOID:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_SIGMOID, FINDER_FPT>, threads, smem);
+      case MODE_HARD:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_HARD, FINDER_FPT>, threads, smem);
+      default:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_STEP, FINDER_FPT>, threads, smem);
+    }
+  }
   switch (mode) {
     case MODE_SIGMOID:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_SIGMOID>, threads, smem);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_SIGMOID, FINDER_MPT>, threads, smem);
     case MODE_HARD:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_HARD>, threads, smem);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_HARD, FINDER_MPT>, threads, smem);
     default:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_STEP>, threads, smem);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, forward_mpt_kernel<MODE_STEP, FINDER_MPT>, threads, smem);
   }
 }
 
 cudaError_t forward_mpt_set_smem_limit(int W) {
   const int smem = (int)forward_smem_bytes(W, false);
-  cudaError_t e = cudaFuncSetAttribute(forward_mpt_kernel<MODE_SIGMOID>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(forward_mpt_kernel<MODE_HARD>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(forward_mpt_kernel<MODE_STEP>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const void* kernels[] = {
+      (const void*)forward_mpt_kernel<MODE_SIGMOID, FINDER_MPT>,
+      (const void*)forward_mpt_kernel<MODE_HARD, FINDER_MPT>,
+      (const void*)forward_mpt_kernel<MODE_STEP, FINDER_MPT>,
+      (const void*)forward_mpt_kernel<MODE_SIGMOID, FINDER_FPT>,
+      (const void*)forward_mpt_kernel<MODE_HARD, FINDER_FPT>,
+      (const void*)forward_mpt_kernel<MODE_STEP, FINDER_FPT>};
+  for (const void* k : kernels) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace drt

@@ -102,23 +102,41 @@ def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
     return power
 
 
+def _finder_forward(name: str, walls, tx, rx, max_order, alpha, smoothing, n_iter, check_eps,
+                    refl_coef, tile) -> torch.Tensor:
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call(f"drt_forward_{name}_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    _lib.call(f"drt_forward_{name}", ctypes.byref(sc), tlp, int(n_iter),
+              ctypes.c_float(check_eps), _ptr(power), _ptr(ws), ctypes.c_size_t(ws.numel()),
+              _stream_ptr(dev))
+    return power
+
+
+def _finder_paths(name: str, walls, tx, rx, max_order, alpha, smoothing, n_iter, check_eps,
+                  refl_coef) -> torch.Tensor:
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    n = num_candidates(sc.n_walls, int(max_order))
+    out = torch.empty(sc.n_rx, n, int(max_order) + 2, dtype=torch.float32, device=dev)
+    _lib.call(f"drt_{name}_paths", ctypes.byref(sc), int(n_iter), ctypes.c_float(check_eps),
+              _ptr(out), _stream_ptr(dev))
+    return out
+
+
 def forward_mpt(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
                 n_iter: int = 10, check_eps: float = 0.05, refl_coef: float = 0.5,
                 tile: TileConfig | None = None) -> torch.Tensor:
     """Received power per receiver (float32 [R]) with the reflection points found by
     ``n_iter`` Min-Path-Tracing steps and the smoothed convergence check
     s(check_eps - C) (drt_forward_mpt, Sec. V-B)."""
-    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
-    dev = keep[0].device
-    tl = tile.as_c() if tile else None
-    tlp = ctypes.byref(tl) if tl is not None else None
-    nbytes = ctypes.c_size_t()
-    _lib.call("drt_forward_mpt_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
-    ws = _workspace(dev, nbytes.value)
-    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
-    _lib.call("drt_forward_mpt", ctypes.byref(sc), tlp, int(n_iter), ctypes.c_float(check_eps),
-              _ptr(power), _ptr(ws), ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
-    return power
+    return _finder_forward("mpt", walls, tx, rx, max_order, alpha, smoothing, n_iter,
+                           check_eps, refl_coef, tile)
 
 
 def mpt_paths(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
@@ -126,13 +144,24 @@ def mpt_paths(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "har
     """Path finder record per (receiver, candidate): float32 [R, N_K, K + 2] holding
     tau_1..tau_K (NaN past the path's order or for a degenerate path), the MPT cost
     C and the check kappa (drt_mpt_paths)."""
-    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
-    dev = keep[0].device
-    n = num_candidates(sc.n_walls, int(max_order))
-    out = torch.empty(sc.n_rx, n, int(max_order) + 2, dtype=torch.float32, device=dev)
-    _lib.call("drt_mpt_paths", ctypes.byref(sc), int(n_iter), ctypes.c_float(check_eps),
-              _ptr(out), _stream_ptr(dev))
-    return out
+    return _finder_paths("mpt", walls, tx, rx, max_order, alpha, smoothing, n_iter, check_eps,
+                         refl_coef)
+
+
+def forward_fpt(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+                n_iter: int = 10, check_eps: float = 0.05, refl_coef: float = 0.5,
+                tile: TileConfig | None = None) -> torch.Tensor:
+    """forward_mpt with Fermat path tracing (Newton steps on the path length) as the
+    finder and the same MPT convergence check (drt_forward_fpt)."""
+    return _finder_forward("fpt", walls, tx, rx, max_order, alpha, smoothing, n_iter,
+                           check_eps, refl_coef, tile)
+
+
+def fpt_paths(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_sigmoid",
+              n_iter: int = 10, check_eps: float = 0.05, refl_coef: float = 0.5) -> torch.Tensor:
+    """mpt_paths with Fermat path tracing as the finder (drt_fpt_paths)."""
+    return _finder_paths("fpt", walls, tx, rx, max_order, alpha, smoothing, n_iter, check_eps,
+                         refl_coef)
 
 
 def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
