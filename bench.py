@@ -442,6 +442,22 @@ def measure_extras(drt, dev, sc, w, t, r):
                     "each, alpha=100, hard sigmoid; one step = forward + argmin + adjoint + Adam",
         "ms_per_step": bs * 1e3, "steps_per_s": 1.0 / bs,
         "forward_tflops_by_convention": bflops / bs / 1e12}
+    # batched descent on 3D rooms (Sec. VI): 64 rooms of 16-72 triangles, R 16-512,
+    # K 0-2, 4 starts each, alpha 100, hard sigmoid
+    full3 = scenes.scene_batch3(64, 0)
+    bd3 = BatchedDescent(full3, history=0, box=(0.02, 0.02, 0.02, 0.98, 0.98, 0.98))
+    bd3.run(1)
+    torch.cuda.synchronize(dev)
+    bs3 = timed(lambda: bd3.run(1), 3)
+    ev3 = sum(full3.tx0.shape[1] * int(full3.rx_off[i + 1] - full3.rx_off[i]) *
+              workload.num_candidates(int(full3.wall_off[i + 1] - full3.wall_off[i]),
+                                      int(full3.max_order[i])) for i in range(full3.n_scenes))
+    out["batched_descent_3d_64_rooms"] = {
+        "workload": "64 rooms (square + 2-30 segments extruded, floor, ceiling: 16-72 "
+                    "triangles), R 16-512, K 0-2, 4 starts each, alpha=100, hard sigmoid; one "
+                    "step = forward + argmin + adjoint + Adam",
+        "ms_per_step": bs3 * 1e3, "steps_per_s": 1.0 / bs3, "evals_per_s": ev3 / bs3}
+    bd3.close()
     bd.close()
     # surrogate MLP (tcgen05 path), batch 8192
     from paper_2401_11882_gb300.surrogate import SurrogateMLP

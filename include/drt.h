@@ -393,11 +393,15 @@ drt_status drt_objective_host(const drt_scene* scene, const drt_tile* tile, floa
    replayed.  Usage: drt_batch_plan_create -> drt_batch_workspace_size ->
    drt_batch_bind -> drt_batch_run (any number of times) ->
    drt_batch_plan_destroy.  Results are deterministic (fixed summation order).
+   With dim = 3 the scenes are 3D (Sec. VI: triangle walls as in drt3_scene,
+   receivers and TX in 3D), and the same calls run the same five phases with
+   one receiver per lane.
    ------------------------------------------------------------------------ */
 typedef struct {
-  const float* walls;            /* device [sum_s W_s][4], 16-byte aligned, scene after scene */
+  const float* walls;            /* device [sum_s W_s][4], 16-byte aligned, scene after scene
+                                    (dim 3: triangles [sum_s W_s][9], 4-byte aligned) */
   const int32_t* wall_off;       /* device [n_scenes + 1]: scene s owns walls wall_off[s] .. wall_off[s+1]-1 */
-  const float* rx;               /* device [sum_s R_s][2], 8-byte aligned */
+  const float* rx;               /* device [sum_s R_s][2], 8-byte aligned (dim 3: [sum_s R_s][3]) */
   const int32_t* rx_off;         /* device [n_scenes + 1] */
   const int32_t* max_order;      /* device [n_scenes]: K of each scene, 0..DRT_MAX_ORDER */
   const int32_t* wall_off_host;  /* host copies of the three arrays above, used to plan the work */
@@ -407,12 +411,13 @@ typedef struct {
   int32_t n_tx;                  /* T >= 1 starting positions per scene */
   int32_t smoothing;             /* drt_smoothing */
   float refl_coef;               /* Gamma */
+  int32_t dim;                   /* 2 (or 0) for 2D scenes, 3 for 3D scenes */
 } drt_batch;
 
 typedef struct {
-  float* tx;                     /* device [S][T][2], in/out: TX positions */
-  float* adam_m;                 /* device [S][T][2], in/out: Adam first moments (start at 0) */
-  float* adam_v;                 /* device [S][T][2], in/out: Adam second moments (start at 0) */
+  float* tx;                     /* device [S][T][2] ([S][T][3] for 3D), in/out: TX positions */
+  float* adam_m;                 /* device, as tx, in/out: Adam first moments (start at 0) */
+  float* adam_v;                 /* device, as tx, in/out: Adam second moments (start at 0) */
   int32_t* step;                 /* device [1], in/out: steps taken so far (Adam's t - 1) */
   float* loss;                   /* device [S][T], out: loss of the latest step, before its update */
   float* loss_history;           /* device [history_len][S][T] or NULL: row i = loss of step i */
@@ -422,6 +427,7 @@ typedef struct {
   float lr, beta1, beta2, eps;   /* Adam; the learning rate of step i is lr * lr_decay^i */
   float lo_x, lo_y, hi_x, hi_y;  /* the TX is clamped to this box after every update */
   float lr_decay;                /* per-step factor of the learning rate, in (0, 1] */
+  float lo_z, hi_z;              /* 3D: the box's z range */
 } drt_descent_state;
 
 typedef struct drt_batch_plan drt_batch_plan;

@@ -50,7 +50,7 @@ class Batch(ctypes.Structure):
                 ("wall_off_host", ctypes.c_void_p), ("rx_off_host", ctypes.c_void_p),
                 ("max_order_host", ctypes.c_void_p), ("n_scenes", ctypes.c_int32),
                 ("n_tx", ctypes.c_int32), ("smoothing", ctypes.c_int32),
-                ("refl_coef", ctypes.c_float)]
+                ("refl_coef", ctypes.c_float), ("dim", ctypes.c_int32)]
 
 
 class DescentState(ctypes.Structure):
@@ -60,7 +60,8 @@ class DescentState(ctypes.Structure):
                 ("alpha_schedule", ctypes.c_void_p), ("n_alpha", ctypes.c_int32),
                 ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("lo_x", ctypes.c_float), ("lo_y", ctypes.c_float),
-                ("hi_x", ctypes.c_float), ("hi_y", ctypes.c_float), ("lr_decay", ctypes.c_float)]
+                ("hi_x", ctypes.c_float), ("hi_y", ctypes.c_float), ("lr_decay", ctypes.c_float),
+                ("lo_z", ctypes.c_float), ("hi_z", ctypes.c_float)]
 
 
 class DrtError(RuntimeError):

@@ -20,32 +20,42 @@ from .ops import TileConfig
 class BatchedDescent:
     """Adam on the TX of every (scene, start) problem of a batch.
 
+    ``batch`` is a ``scenes.SceneBatch`` (2D walls) or a ``scenes.SceneBatch3``
+    (triangle walls, 3D receivers and TX; Sec. VI).
     ``alpha`` is a float or a per-step schedule (the last value repeats);
-    ``box`` = (lo_x, lo_y, hi_x, hi_y) clamps the TX after every step;
+    ``box`` = (lo_x, lo_y, hi_x, hi_y) clamps the TX after every step, with
+    (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z) for a 3D batch (default the unit cube);
     the learning rate of step i is ``lr * lr_decay**i``;
     ``history`` rows of per-step losses are kept on the device.
     """
 
     def __init__(self, batch, lr=1e-2, betas=(0.9, 0.999), eps=1e-8, alpha=100.0,
-                 box=(0.0, 0.0, 1.0, 1.0), history=0, device="cuda",
+                 box=None, history=0, device="cuda",
                  tile: TileConfig | None = None, tx0=None, lr_decay: float = 1.0):
         self.device = torch.device(device)
         dev = self.device
         self.batch = batch
+        self.dim = 3 if hasattr(batch, "tris") else 2
+        d = self.dim
+        if box is None:
+            box = (0.0,) * d + (1.0,) * d
+        if len(box) != 2 * d:
+            raise ValueError(f"box must have {2 * d} values")
+        lo, hi = list(box[:d]) + [0.0] * (3 - d), list(box[d:]) + [0.0] * (3 - d)
         self.S, self.T = batch.n_scenes, batch.tx0.shape[1]
         self.P = self.S * self.T
         self._wall_off_h = np.ascontiguousarray(batch.wall_off, np.int32)
         self._rx_off_h = np.ascontiguousarray(batch.rx_off, np.int32)
         self._order_h = np.ascontiguousarray(batch.max_order, np.int32)
-        self.walls = torch.tensor(batch.walls, device=dev)
+        self.walls = torch.tensor(batch.tris if d == 3 else batch.walls, device=dev)
         self.rx = torch.tensor(batch.rx, device=dev)
         self.wall_off = torch.tensor(self._wall_off_h, device=dev)
         self.rx_off = torch.tensor(self._rx_off_h, device=dev)
         self.order = torch.tensor(self._order_h, device=dev)
         start = batch.tx0 if tx0 is None else tx0
-        self.tx = torch.tensor(np.asarray(start, np.float32).reshape(self.P, 2), device=dev)
-        self.m = torch.zeros(self.P, 2, device=dev)
-        self.v = torch.zeros(self.P, 2, device=dev)
+        self.tx = torch.tensor(np.asarray(start, np.float32).reshape(self.P, d), device=dev)
+        self.m = torch.zeros(self.P, d, device=dev)
+        self.v = torch.zeros(self.P, d, device=dev)
         self.step = torch.zeros(1, dtype=torch.int32, device=dev)
         self.loss = torch.zeros(self.P, device=dev)
         self.history = torch.full((history, self.P), float("nan"), device=dev) if history else None
@@ -55,7 +65,7 @@ class BatchedDescent:
                                 self.rx_off.data_ptr(), self.order.data_ptr(),
                                 self._wall_off_h.ctypes.data, self._rx_off_h.ctypes.data,
                                 self._order_h.ctypes.data, self.S, self.T,
-                                _lib.SMOOTHING[batch.smoothing], float(batch.refl_coef))
+                                _lib.SMOOTHING[batch.smoothing], float(batch.refl_coef), d)
         self._tile = tile.as_c() if tile else None
         plan = ctypes.c_void_p()
         _lib.call("drt_batch_plan_create", ctypes.byref(self._desc),
@@ -68,8 +78,8 @@ class BatchedDescent:
             self.tx.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.step.data_ptr(),
             self.loss.data_ptr(), self.history.data_ptr() if self.history is not None else None,
             history, self.alpha.data_ptr(), len(sched), float(lr), float(betas[0]),
-            float(betas[1]), float(eps), float(box[0]), float(box[1]), float(box[2]),
-            float(box[3]), float(lr_decay))
+            float(betas[1]), float(eps), float(lo[0]), float(lo[1]), float(hi[0]),
+            float(hi[1]), float(lr_decay), float(lo[2]), float(hi[2]))
         _lib.call("drt_batch_bind", self._plan, ctypes.byref(self._state),
                   ctypes.c_void_p(self.workspace.data_ptr()), ctypes.c_size_t(self.workspace.numel()),
                   ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))

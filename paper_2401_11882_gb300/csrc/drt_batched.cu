@@ -19,7 +19,8 @@
 //   5. batch_step_end_kernel: advances the device-side step counter, which
 //      also selects the step's alpha from a schedule.
 // Kernel boundaries order the phases, so no kernel waits on another CTA.
-// The host captures one step into a CUDA graph once and replays it.
+// The host captures one step into a CUDA graph once and replays it.  A batch of
+// 3D scenes (dim 3) takes the same plan with the 3D phases of drt_forward3d.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -358,6 +359,7 @@ cudaError_t occupancy(F kern, int threads, size_t smem, int* n) {
 
 // ------------------------------------------------------------------ host side
 struct BatchPlan {
+  int dim = 2;   // 2D segments or 3D triangles
   int S = 0, T = 0, P = 0, mode = 0, Wmax = 0, threads = 256, warps = 8;
   float gamma = 0.5f;
   const float* walls = nullptr;
@@ -375,6 +377,7 @@ struct BatchPlan {
          off_power = 0, off_argmin = 0, off_partial = 0, ws_bytes = 0;
   bool bound = false;
   BatchArgs args{};
+  Batch3Args args3{};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -438,6 +441,9 @@ void launch_batch_forward(BatchPlan* pl, size_t sf, cudaStream_t st) {
 }
 
 cudaError_t launch_evaluate(BatchPlan* pl, cudaStream_t st) {
+  if (pl->dim == 3)
+    return launch_batch3(pl->args3, pl->mode, pl->ctas_fwd, pl->ctas_adj, pl->threads, pl->Wmax,
+                         false, st);
   BatchArgs& a = pl->args;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
@@ -450,6 +456,9 @@ cudaError_t launch_evaluate(BatchPlan* pl, cudaStream_t st) {
 }
 
 cudaError_t launch_step(BatchPlan* pl, cudaStream_t st) {
+  if (pl->dim == 3)
+    return launch_batch3(pl->args3, pl->mode, pl->ctas_fwd, pl->ctas_adj, pl->threads, pl->Wmax,
+                         true, st);
   BatchArgs& a = pl->args;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
@@ -476,7 +485,12 @@ cudaError_t launch_step(BatchPlan* pl, cudaStream_t st) {
 
 drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan** out,
                              std::string* err) {
+  if (b->dim != 0 && b->dim != 2 && b->dim != 3) {
+    *err = "dim must be 2 or 3";
+    return DRT_ERR_INVALID_ARG;
+  }
   BatchPlan* pl = new BatchPlan();
+  pl->dim = b->dim == 3 ? 3 : 2;
   pl->S = b->n_scenes;
   pl->T = b->n_tx;
   pl->P = pl->S * pl->T;
@@ -491,7 +505,7 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
   pl->threads = pl->warps * 32;
   pl->per_sm_req = tile ? tile->ctas_per_sm : 0;
   pl->cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
-  pl->pairs = (pl->mode == MODE_HARD || pl->mode == MODE_SIGMOID) &&
+  pl->pairs = pl->dim == 2 && (pl->mode == MODE_HARD || pl->mode == MODE_SIGMOID) &&
               !(tile && (tile->flags & DRT_TILE_SINGLE_RX));
   std::vector<double> cost(pl->P);
   std::vector<long long> tiles(pl->P), adj_units(pl->P);
@@ -548,7 +562,8 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
   pl->off_pwoff = off; off = align_up(off + (size_t)pl->P * sizeof(long long));
   pl->off_power = off; off = align_up(off + (size_t)pl->n_power * sizeof(float));
   pl->off_argmin = off; off = align_up(off + (size_t)pl->P * sizeof(int32_t));
-  pl->off_partial = off; off = align_up(off + (size_t)pl->n_adj_units * 2 * sizeof(float));
+  pl->off_partial = off;
+  off = align_up(off + (size_t)pl->n_adj_units * pl->dim * sizeof(float));
   pl->ws_bytes = off;
   *out = pl;
   return DRT_OK;
@@ -560,7 +575,7 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
     *err = "workspace must be 256-byte aligned and >= " + std::to_string(pl->ws_bytes) + " bytes";
     return DRT_ERR_WORKSPACE;
   }
-  cudaError_t e = set_smem_limits(pl->Wmax);
+  cudaError_t e = pl->dim == 3 ? batch3_set_smem_limits(pl->Wmax) : set_smem_limits(pl->Wmax);
   if (e != cudaSuccess) { *err = cudaGetErrorString(e); return DRT_ERR_CUDA; }
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -570,7 +585,8 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
   }
   int occ_f = 0, occ_a = 0;
   const size_t sf = batch_fwd_smem(pl->Wmax, pl->pairs), sa = batch_adj_smem(pl->Wmax);
-  switch (pl->mode) {
+  if (pl->dim == 3) e = batch3_occupancy(pl->mode, pl->threads, pl->Wmax, &occ_f, &occ_a);
+  else switch (pl->mode) {
     case MODE_SIGMOID:
       e = pl->pairs ? occupancy(batch_forward_kernel<MODE_SIGMOID, true>, pl->threads, sf, &occ_f)
                     : occupancy(batch_forward_kernel<MODE_SIGMOID, false>, pl->threads, sf, &occ_f);
@@ -610,6 +626,49 @@ drt_status batch_bind(BatchPlan* pl, const drt_descent_state* d, void* ws, size_
                            cudaMemcpyHostToDevice, st)) != cudaSuccess) {
     *err = cudaGetErrorString(e);
     return DRT_ERR_CUDA;
+  }
+  if (pl->dim == 3) {
+    Batch3Args& b3 = pl->args3;
+    b3.tris = pl->walls;
+    b3.tri_off = pl->wall_off;
+    b3.rx = pl->rx;
+    b3.rx_off = pl->rx_off;
+    b3.order = pl->order;
+    b3.S = pl->S;
+    b3.T = pl->T;
+    b3.gk[0] = 1.f;
+    for (int k = 1; k <= DRT_MAX_ORDER; ++k) b3.gk[k] = b3.gk[k - 1] * pl->gamma;
+    b3.alpha_sched = d->alpha_schedule;
+    b3.n_alpha = d->n_alpha;
+    b3.step = d->step;
+    b3.tx = d->tx;
+    b3.m = d->adam_m;
+    b3.v = d->adam_v;
+    b3.loss = d->loss;
+    b3.loss_hist = d->loss_history;
+    b3.hist_len = d->history_len;
+    b3.lr = d->lr;
+    b3.b1 = d->beta1;
+    b3.b2 = d->beta2;
+    b3.eps = d->eps;
+    b3.lr_decay = d->lr_decay;
+    b3.lo[0] = d->lo_x;
+    b3.lo[1] = d->lo_y;
+    b3.lo[2] = d->lo_z;
+    b3.hi[0] = d->hi_x;
+    b3.hi[1] = d->hi_y;
+    b3.hi[2] = d->hi_z;
+    b3.counter = reinterpret_cast<unsigned long long*>(base + pl->off_counter);
+    b3.fwd_prob = reinterpret_cast<const int32_t*>(base + pl->off_prob);
+    b3.fwd_prefix = reinterpret_cast<const long long*>(base + pl->off_fprefix);
+    b3.fwd_unit = reinterpret_cast<const int32_t*>(base + pl->off_funit);
+    b3.n_fwd_units = pl->n_fwd_units;
+    b3.adj_prefix = reinterpret_cast<const long long*>(base + pl->off_aprefix);
+    b3.n_adj_units = pl->n_adj_units;
+    b3.pw_off = reinterpret_cast<const long long*>(base + pl->off_pwoff);
+    b3.power = reinterpret_cast<float*>(base + pl->off_power);
+    b3.argmin = reinterpret_cast<int32_t*>(base + pl->off_argmin);
+    b3.adj_partial = reinterpret_cast<float*>(base + pl->off_partial);
   }
   BatchArgs& a = pl->args;
   a.walls = reinterpret_cast<const float4*>(pl->walls);
@@ -756,9 +815,11 @@ drt_status drt_batch_plan_create(const drt_batch* b, const drt_tile* tile, drt_b
   if (b->n_scenes < 1 || b->n_tx < 1) return bad(DRT_ERR_INVALID_ARG, "n_scenes and n_tx must be >= 1");
   if (b->smoothing < 0 || b->smoothing > 2) return bad(DRT_ERR_INVALID_ARG, "unknown smoothing");
   if (!std::isfinite(b->refl_coef)) return bad(DRT_ERR_INVALID_ARG, "refl_coef must be finite");
-  if (!al(b->walls, 16) || !al(b->rx, 8) || !al(b->wall_off, 4) || !al(b->rx_off, 4) ||
-      !al(b->max_order, 4))
-    return bad(DRT_ERR_INVALID_ARG, "device arrays must be non-NULL and aligned (walls 16, rx 8)");
+  const bool d3 = b->dim == 3;
+  if (!al(b->walls, d3 ? 4 : 16) || !al(b->rx, d3 ? 4 : 8) || !al(b->wall_off, 4) ||
+      !al(b->rx_off, 4) || !al(b->max_order, 4))
+    return bad(DRT_ERR_INVALID_ARG,
+               "device arrays must be non-NULL and aligned (2D: walls 16, rx 8; 3D: 4)");
   if (!b->wall_off_host || !b->rx_off_host || !b->max_order_host)
     return bad(DRT_ERR_INVALID_ARG, "host copies of the offsets are required");
   if ((long long)b->n_scenes * b->n_tx > (1LL << 30)) return bad(DRT_ERR_UNSUPPORTED, "too many problems");
@@ -784,9 +845,12 @@ drt_status drt_batch_workspace_size(const drt_batch_plan* plan, size_t* bytes) {
 drt_status drt_batch_bind(drt_batch_plan* plan, const drt_descent_state* d, void* workspace,
                           size_t workspace_bytes, void* stream) {
   if (!plan || !d) return bad(DRT_ERR_INVALID_ARG, "NULL argument");
-  if (!al(d->tx, 8) || !al(d->adam_m, 8) || !al(d->adam_v, 8) || !al(d->step, 4) ||
+  const bool d3 = plan->impl.dim == 3;
+  const size_t ta = d3 ? 4 : 8;
+  if (!al(d->tx, ta) || !al(d->adam_m, ta) || !al(d->adam_v, ta) || !al(d->step, 4) ||
       !al(d->loss, 4) || !al(d->alpha_schedule, 4))
-    return bad(DRT_ERR_INVALID_ARG, "state arrays must be non-NULL and aligned (tx, m, v: 8)");
+    return bad(DRT_ERR_INVALID_ARG, "state arrays must be non-NULL and aligned (tx, m, v: 8 in 2D)");
+  if (d3 && !(d->lo_z <= d->hi_z)) return bad(DRT_ERR_INVALID_ARG, "clamp box: lo_z > hi_z");
   if (d->n_alpha < 1) return bad(DRT_ERR_INVALID_ARG, "n_alpha must be >= 1");
   if (d->loss_history && d->history_len < 0) return bad(DRT_ERR_INVALID_ARG, "history_len < 0");
   if (!(d->lr >= 0.f) || !std::isfinite(d->lr) || !(d->beta1 >= 0.f && d->beta1 < 1.f) ||

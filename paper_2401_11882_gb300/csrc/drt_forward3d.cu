@@ -762,7 +762,315 @@ __global__ void reduce3_kernel(const float* __restrict__ partial, long long n_ch
   }
 }
 
+// ------------------------------------------------------- batched descent (3D)
+// The 2D batched descent's phases for triangle scenes (Sec. VI with Sec. VII's
+// antenna placement): a problem is (scene, start); a forward unit is (problem,
+// 32-receiver tile) with the scene's candidates split over the CTA's warps,
+// taken from a global counter longest first; an adjoint unit is (problem, a block
+// of warps x 32 candidates) of the argmin receiver, lanes holding candidates.
+constexpr int BATCH3_MAX_WARPS = 8;
+
+__device__ __forceinline__ long long batch3_n_candidates(int W, int K) {
+  long long n = 1, level = 1;
+  for (int k = 1; k <= K; ++k) {
+    level = (k == 1) ? W : level * (W - 1);
+    n += level;
+  }
+  return n;
+}
+
+__device__ __forceinline__ float batch3_alpha(const Batch3Args& a) {
+  int st = *a.step;
+  st = st < 0 ? 0 : (st >= a.n_alpha ? a.n_alpha - 1 : st);
+  return a.alpha_sched[st];
+}
+
+__device__ __forceinline__ float3 batch3_tx(const Batch3Args& a, int p) {
+  return make_float3(a.tx[3 * p], a.tx[3 * p + 1], a.tx[3 * p + 2]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) batch3_forward_kernel(const Batch3Args a) {
+  extern __shared__ float4 smem[];
+  __shared__ long long s_unit;
+  __shared__ int s_info[2];   // problem, sorted index
+  __shared__ float s_part[BATCH3_MAX_WARPS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float alpha = batch3_alpha(a);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long u = (long long)atomicAdd(a.counter, 1ULL);
+      s_unit = u;
+      if (u < a.n_fwd_units) {
+        const int i = a.fwd_unit[u];
+        s_info[0] = a.fwd_prob[i];
+        s_info[1] = i;
+      }
+    }
+    __syncthreads();
+    const long long u = s_unit;
+    if (u >= a.n_fwd_units) break;
+    const int p = s_info[0];
+    const long long tile = u - a.fwd_prefix[s_info[1]];
+    const int s = p / a.T;
+    const int woff = a.tri_off[s], W = a.tri_off[s + 1] - woff;
+    const int roff = a.rx_off[s], R = a.rx_off[s + 1] - roff;
+    const int K = a.order[s];
+    const float3 tx = batch3_tx(a, p);
+    SmemTris st{smem, smem + W, smem + 2 * W, smem + 3 * W};
+    stage_tris(a.tris + 9 * (size_t)woff, W, st);
+    __syncthreads();
+    const int r = (int)(tile * 32) + lane;
+    const bool live = r < R;
+    const size_t ri = 3 * (size_t)(roff + (live ? r : R - 1));
+    const float3 q = make_float3(__ldg(a.rx + ri), __ldg(a.rx + ri + 1), __ldg(a.rx + ri + 2));
+    const long long nc = batch3_n_candidates(W, K);
+    float acc = 0.f;
+    // each warp takes a contiguous block of candidates and steps through it
+    const long long cb = nc * warp / nwarps, ce = nc * (warp + 1) / nwarps;
+    Cand cd;
+    if (cb < ce) cd = decode_candidate(cb, W, K);
+    for (long long c = cb; c < ce; ++c) {
+      if (c > cb) next_candidate(cd, W);
+      switch (cd.k) {
+        case 0: acc += path_power3<MODE, 0>(st, W, tx, q, cd, alpha, a.gk[0]); break;
+        case 1: acc += path_power3<MODE, 1>(st, W, tx, q, cd, alpha, a.gk[1]); break;
+        case 2: acc += path_power3<MODE, 2>(st, W, tx, q, cd, alpha, a.gk[2]); break;
+        default: acc += path_power3<MODE, 3>(st, W, tx, q, cd, alpha, a.gk[3]); break;
+      }
+    }
+    s_part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      float sum = 0.f;
+      for (int w2 = 0; w2 < nwarps; ++w2) sum += s_part[w2][lane];
+      if (live) a.power[a.pw_off[p] + r] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// loss = -min_r P_r and its argmin (lowest index among ties) per problem
+__global__ void batch3_argmin_kernel(const Batch3Args a) {
+  const int lane = threadIdx.x & 31;
+  const int P = a.S * a.T;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int step = *a.step;
+  for (long long p = gw; p < P; p += nw) {
+    const int s = (int)(p / a.T);
+    const int R = a.rx_off[s + 1] - a.rx_off[s];
+    const float* pw = a.power + a.pw_off[p];
+    float best = INFINITY;
+    int bi = 0x7fffffff;
+    for (int r = lane; r < R; r += 32) {
+      const float val = pw[r];
+      if (val < best || (val == best && r < bi)) {
+        best = val;
+        bi = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov < best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      a.loss[p] = -best;
+      a.argmin[p] = (bi < R) ? bi : 0;
+      if (a.loss_hist && step >= 0 && step < a.hist_len) a.loss_hist[(long long)step * P + p] = -best;
+    }
+  }
+}
+
+// largest i with prefix[i] <= u (prefix[0] = 0, prefix[n] > u)
+__device__ __forceinline__ int batch3_find(const long long* prefix, int n, long long u) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) batch3_adjoint_kernel(const Batch3Args a) {
+  extern __shared__ float4 smem[];
+  __shared__ long long s_unit;
+  __shared__ int s_prob;
+  __shared__ float s_part[BATCH3_MAX_WARPS][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float alpha = batch3_alpha(a);
+  const int P = a.S * a.T;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long u = (long long)atomicAdd(a.counter + 1, 1ULL);
+      s_unit = u;
+      if (u < a.n_adj_units) s_prob = batch3_find(a.adj_prefix, P, u);
+    }
+    __syncthreads();
+    const long long u = s_unit;
+    if (u >= a.n_adj_units) break;
+    const int p = s_prob;
+    const long long chunk = u - a.adj_prefix[p];
+    const int s = p / a.T;
+    const int woff = a.tri_off[s], W = a.tri_off[s + 1] - woff;
+    const int roff = a.rx_off[s];
+    const int K = a.order[s];
+    const float3 tx = batch3_tx(a, p);
+    SmemTris st{smem, smem + W, smem + 2 * W, smem + 3 * W};
+    stage_tris(a.tris + 9 * (size_t)woff, W, st);
+    __syncthreads();
+    const size_t ri = 3 * (size_t)(roff + a.argmin[p]);
+    const float3 q = make_float3(__ldg(a.rx + ri), __ldg(a.rx + ri + 1), __ldg(a.rx + ri + 2));
+    const long long nc = batch3_n_candidates(W, K);
+    const long long base = chunk * nwarps * 32 + (long long)warp * 32;
+    float3 txb = make_float3(0.f, 0.f, 0.f);
+    if (base < nc) {
+      const long long c = base + lane;
+      const bool livec = c < nc;
+      const Cand mine = decode_candidate(livec ? c : nc - 1, W, K);
+      const int k_lo = decode_candidate(base, W, K).k;
+      const int k_hi = decode_candidate(min(base + 31, nc - 1), W, K).k;
+      // candidates are ordered by reflection count: the warp runs each order present,
+      // the lanes of other orders with weight 0 on a placeholder sequence
+      for (int k = k_lo; k <= k_hi; ++k) {
+        const bool use = livec && mine.k == k;
+        Cand cd = mine;
+        if (!use) {
+          cd.k = k;
+#pragma unroll
+          for (int j = 0; j < KMAX; ++j) cd.w[j] = (j & 1) ? (W > 1 ? 1 : 0) : 0;
+        }
+        const float g = use ? -1.f : 0.f;   // loss = -P[argmin]
+        switch (k) {
+          case 0: path_vjp3<MODE, 0, false>(st, W, tx, q, cd, alpha, a.gk[0], g, txb, nullptr); break;
+          case 1: path_vjp3<MODE, 1, false>(st, W, tx, q, cd, alpha, a.gk[1], g, txb, nullptr); break;
+          case 2: path_vjp3<MODE, 2, false>(st, W, tx, q, cd, alpha, a.gk[2], g, txb, nullptr); break;
+          default: path_vjp3<MODE, 3, false>(st, W, tx, q, cd, alpha, a.gk[3], g, txb, nullptr); break;
+        }
+      }
+      txb.x = warp_sum3(txb.x);
+      txb.y = warp_sum3(txb.y);
+      txb.z = warp_sum3(txb.z);
+    }
+    if (lane == 0) {
+      s_part[warp][0] = txb.x;
+      s_part[warp][1] = txb.y;
+      s_part[warp][2] = txb.z;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float g3[3] = {0.f, 0.f, 0.f};
+      for (int w2 = 0; w2 < nwarps; ++w2)
+        for (int i = 0; i < 3; ++i) g3[i] += s_part[w2][i];
+      for (int i = 0; i < 3; ++i) a.adj_partial[3 * u + i] = g3[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Adam on the TX (three coordinates), the problem's adjoint partials added in unit order
+__global__ void batch3_adam_kernel(const Batch3Args a) {
+  const int P = a.S * a.T;
+  const int t = *a.step + 1;   // Adam's 1-based step
+  const float c1 = 1.f - powf(a.b1, (float)t), c2 = 1.f - powf(a.b2, (float)t);
+  const float lr = a.lr * powf(a.lr_decay, (float)(t - 1));
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float g[3] = {0.f, 0.f, 0.f};
+    for (long long u = a.adj_prefix[p]; u < a.adj_prefix[p + 1]; ++u)
+      for (int i = 0; i < 3; ++i) g[i] += a.adj_partial[3 * u + i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float m = fmaf(a.b1, a.m[3 * p + i], (1.f - a.b1) * g[i]);
+      const float v = fmaf(a.b2, a.v[3 * p + i], (1.f - a.b2) * g[i] * g[i]);
+      a.m[3 * p + i] = m;
+      a.v[3 * p + i] = v;
+      const float mh = m / c1, vh = v / c2;
+      float x = a.tx[3 * p + i] - lr * mh / (sqrtf(vh) + a.eps);
+      x = fminf(fmaxf(x, a.lo[i]), a.hi[i]);
+      a.tx[3 * p + i] = x;
+    }
+  }
+}
+
+__global__ void batch3_step_end_kernel(int32_t* step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
+}
+
 }  // namespace
+
+size_t batch3_smem_bytes(int Wmax) { return (size_t)4 * (Wmax > 1 ? Wmax : 1) * sizeof(float4); }
+
+cudaError_t batch3_set_smem_limits(int Wmax) {
+  const int smem = (int)batch3_smem_bytes(Wmax);
+  const void* kernels[] = {(const void*)batch3_forward_kernel<MODE_SIGMOID>,
+                           (const void*)batch3_forward_kernel<MODE_HARD>,
+                           (const void*)batch3_forward_kernel<MODE_STEP>,
+                           (const void*)batch3_adjoint_kernel<MODE_SIGMOID>,
+                           (const void*)batch3_adjoint_kernel<MODE_HARD>,
+                           (const void*)batch3_adjoint_kernel<MODE_STEP>};
+  for (const void* k : kernels) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batch3_occupancy(int mode, int threads, int Wmax, int* fwd_per_sm, int* adj_per_sm) {
+  const size_t smem = batch3_smem_bytes(Wmax);
+  cudaError_t e;
+  switch (mode) {
+    case MODE_SIGMOID:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd_per_sm, batch3_forward_kernel<MODE_SIGMOID>, threads, smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(adj_per_sm, batch3_adjoint_kernel<MODE_SIGMOID>, threads, smem);
+      return e;
+    case MODE_HARD:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd_per_sm, batch3_forward_kernel<MODE_HARD>, threads, smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(adj_per_sm, batch3_adjoint_kernel<MODE_HARD>, threads, smem);
+      return e;
+    default:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd_per_sm, batch3_forward_kernel<MODE_STEP>, threads, smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(adj_per_sm, batch3_adjoint_kernel<MODE_STEP>, threads, smem);
+      return e;
+  }
+}
+
+cudaError_t launch_batch3(const Batch3Args& a, int mode, int ctas_fwd, int ctas_adj, int threads,
+                          int Wmax, bool full_step, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = batch3_smem_bytes(Wmax);
+  switch (mode) {
+    case MODE_SIGMOID: batch3_forward_kernel<MODE_SIGMOID><<<ctas_fwd, threads, smem, st>>>(a); break;
+    case MODE_HARD: batch3_forward_kernel<MODE_HARD><<<ctas_fwd, threads, smem, st>>>(a); break;
+    default: batch3_forward_kernel<MODE_STEP><<<ctas_fwd, threads, smem, st>>>(a); break;
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int P = a.S * a.T;
+  const long long nb = ((long long)P * 32 + 255) / 256;
+  batch3_argmin_kernel<<<(int)(nb < 1 ? 1 : (nb > 4096 ? 4096 : nb)), 256, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess || !full_step) return e;
+  switch (mode) {
+    case MODE_SIGMOID: batch3_adjoint_kernel<MODE_SIGMOID><<<ctas_adj, threads, smem, st>>>(a); break;
+    case MODE_HARD: batch3_adjoint_kernel<MODE_HARD><<<ctas_adj, threads, smem, st>>>(a); break;
+    default: batch3_adjoint_kernel<MODE_STEP><<<ctas_adj, threads, smem, st>>>(a); break;
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int pb = (P + 255) / 256;
+  batch3_adam_kernel<<<pb < 1 ? 1 : (pb > 4096 ? 4096 : pb), 256, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  batch3_step_end_kernel<<<1, 32, 0, st>>>(a.step);
+  return cudaGetLastError();
+}
 
 size_t forward3_smem_bytes(int W) { return (size_t)4 * W * sizeof(float4); }
 

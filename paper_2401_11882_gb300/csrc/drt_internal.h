@@ -167,6 +167,47 @@ cudaError_t forward_mpt_occupancy(int mode, int finder, int threads, int W, int*
 cudaError_t forward_mpt_set_smem_limit(int W);
 
 size_t forward3_smem_bytes(int W);
+// Batched descent on 3D scenes (drt_forward3d.cu; the host plan is drt_batched.cu's):
+// the 2D batched descent's five phases for triangle walls, one receiver per lane.
+struct Batch3Args {
+  const float* tris;          // [sum_s W_s][9]
+  const int32_t* tri_off;     // [S + 1]
+  const float* rx;            // [sum_s R_s][3]
+  const int32_t* rx_off;      // [S + 1]
+  const int32_t* order;       // K per scene
+  int S, T;
+  float gk[DRT_MAX_ORDER + 1];
+  const float* alpha_sched;
+  int n_alpha;
+  int32_t* step;
+  float* tx;                  // [S*T][3]
+  float* m;                   // [S*T][3]
+  float* v;                   // [S*T][3]
+  float* loss;                // [S*T]
+  float* loss_hist;           // [hist_len][S*T] or null
+  int hist_len;
+  float lr, b1, b2, eps, lr_decay;
+  float lo[3], hi[3];         // the box the TX is clamped to
+  unsigned long long* counter;   // [2]
+  const int32_t* fwd_prob;
+  const long long* fwd_prefix;
+  const int32_t* fwd_unit;
+  long long n_fwd_units;
+  const long long* adj_prefix;
+  long long n_adj_units;
+  const long long* pw_off;
+  float* power;
+  int32_t* argmin;
+  float* adj_partial;         // [n_adj_units][3]
+};
+size_t batch3_smem_bytes(int Wmax);
+cudaError_t batch3_set_smem_limits(int Wmax);
+cudaError_t batch3_occupancy(int mode, int threads, int Wmax, int* fwd_per_sm, int* adj_per_sm);
+// the whole step (forward, argmin, adjoint, Adam, step counter), or the forward
+// and argmin alone (evaluate)
+cudaError_t launch_batch3(const Batch3Args& a, int mode, int ctas_fwd, int ctas_adj, int threads,
+                          int Wmax, bool full_step, cudaStream_t st);
+
 cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
 cudaError_t forward3_set_smem_limit(int W);

@@ -292,3 +292,66 @@ def random_scene3(rng: np.random.Generator, n_tris: int, n_rx: int, max_order: i
     rx = rx[np.linalg.norm(rx - tx, axis=1) > 1e-2]
     return Scene3(tris, tx, rx, max_order=max_order, alpha=alpha, smoothing=smoothing,
                   name=f"random {n_tris} triangles")
+
+
+@dataclass
+class SceneBatch3:
+    """Many 3D scenes of uneven size, concatenated (CSR offsets)."""
+
+    tris: np.ndarray         # float32 [sum W, 9]
+    wall_off: np.ndarray     # int32 [S + 1]
+    rx: np.ndarray           # float32 [sum R, 3]
+    rx_off: np.ndarray       # int32 [S + 1]
+    max_order: np.ndarray    # int32 [S]
+    tx0: np.ndarray          # float32 [S, T, 3] initial TX positions
+    alpha: float = 100.0
+    smoothing: str = "hard_sigmoid"
+    refl_coef: float = 0.5
+
+    @property
+    def n_scenes(self) -> int:
+        return int(self.max_order.shape[0])
+
+    def scene(self, s: int, t: int = 0) -> Scene3:
+        w = self.tris[self.wall_off[s]:self.wall_off[s + 1]]
+        r = self.rx[self.rx_off[s]:self.rx_off[s + 1]]
+        return Scene3(w, self.tx0[s, t], r, max_order=int(self.max_order[s]), alpha=self.alpha,
+                      smoothing=self.smoothing, refl_coef=self.refl_coef)
+
+
+def scene_batch3(n_scenes: int = 64, seed: int = 0, segments_range=(2, 30), rx_range=(16, 512),
+                 orders=(0, 1, 2), n_tx: int = 4, alpha: float = 100.0,
+                 smoothing: str = "hard_sigmoid") -> SceneBatch3:
+    """Uneven batch of rooms: per scene n ~ U{segments_range} random segments
+    (``random_segments``) inside the unit square, extruded with the square's four
+    walls over z in [0, 1] and closed by a floor and a ceiling (2 (n + 4) + 4
+    triangles); R ~ U{rx_range} receivers uniform in [0.05, 0.95]^2 x [0.1, 0.9];
+    K ~ U{orders}; n_tx TX starts drawn the same way.  Draw order per scene: n, R,
+    K, segments, RX, TX starts."""
+    rng = np.random.default_rng(seed)
+    corners = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float64)
+    slabs = []
+    for z, order in ((0.0, (0, 1, 2, 3)), (1.0, (0, 3, 2, 1))):
+        p = [tuple(corners[i]) + (z,) for i in order]
+        slabs.append(p[0] + p[1] + p[2])
+        slabs.append(p[0] + p[2] + p[3])
+    slabs = np.array(slabs, dtype=np.float32).reshape(-1, 9)
+
+    def points(n):
+        return np.concatenate([rx_uniform(rng, n), rng.uniform(0.1, 0.9, (n, 1))],
+                              1).astype(np.float32)
+
+    tris, rxs, w_off, r_off, ks, txs = [], [], [0], [0], [], []
+    for _ in range(n_scenes):
+        n = int(rng.integers(segments_range[0], segments_range[1] + 1))
+        R = int(rng.integers(rx_range[0], rx_range[1] + 1))
+        K = int(rng.choice(orders))
+        walls2 = np.concatenate([unit_square_walls(), random_segments(rng, n)])
+        t3 = np.concatenate([extrude(walls2, 0.0, 1.0), slabs])
+        r = points(R)
+        t = points(n_tx)
+        tris.append(t3); rxs.append(r); ks.append(K); txs.append(t)
+        w_off.append(w_off[-1] + t3.shape[0]); r_off.append(r_off[-1] + R)
+    return SceneBatch3(np.concatenate(tris), np.asarray(w_off, np.int32), np.concatenate(rxs),
+                       np.asarray(r_off, np.int32), np.asarray(ks, np.int32),
+                       np.stack(txs).astype(np.float32), alpha, smoothing)

@@ -202,3 +202,26 @@ def test_mlp_path_switch_host_only(lib):
     assert lib.drt_mlp_set_tensor_core_path(-1) == 1
     for mode in (0, 2, 1):
         assert lib.drt_mlp_set_tensor_core_path(mode) == 0
+
+
+def test_batch_plan_dimension_checks(lib):
+    # host-only: the plan is built from host copies; nothing is enqueued
+    from paper_2401_11882_gb300 import _lib
+    off = (ctypes.c_int32 * 2)(0, 20)
+    roff = (ctypes.c_int32 * 2)(0, 40)
+    order = (ctypes.c_int32 * 1)(1)
+    plan = ctypes.c_void_p()
+    b = _lib.Batch(256, 256, 256, 256, 256, ctypes.addressof(off), ctypes.addressof(roff),
+                   ctypes.addressof(order), 1, 2, 1, 0.5, 5)
+    assert lib.drt_batch_plan_create(ctypes.byref(b), None, ctypes.byref(plan)) == 1
+    assert b"dim" in lib.drt_last_error()
+    # 3D arrays need 4-byte alignment only (2D walls need 16)
+    b3 = _lib.Batch(260, 256, 260, 256, 256, ctypes.addressof(off), ctypes.addressof(roff),
+                    ctypes.addressof(order), 1, 2, 1, 0.5, 3)
+    assert lib.drt_batch_plan_create(ctypes.byref(b3), None, ctypes.byref(plan)) == 0
+    n = ctypes.c_size_t()
+    assert lib.drt_batch_workspace_size(plan, ctypes.byref(n)) == 0 and n.value > 0
+    assert lib.drt_batch_plan_destroy(plan) == 0
+    b2 = _lib.Batch(260, 256, 260, 256, 256, ctypes.addressof(off), ctypes.addressof(roff),
+                    ctypes.addressof(order), 1, 2, 1, 0.5, 2)
+    assert lib.drt_batch_plan_create(ctypes.byref(b2), None, ctypes.byref(plan)) == 1
