@@ -421,6 +421,12 @@ def measure_extras(drt, dev, sc, w, t, r):
     sv = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", gp), 2)
     sfs = timed(lambda: drt.forward(gw, gt, gr, 2, 100.0, "sigmoid"), 1)
     svs = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "sigmoid", gp), 1)
+    # the forward keeps every path's leg visibilities (N_K x 3 x R floats, 3.2 GB here)
+    # and the adjoint reads them instead of its first wall sweep
+    _, gsv = drt.forward_save(gw, gt, gr, 2, 100.0, "sigmoid")
+    sfss = timed(lambda: drt.forward_save(gw, gt, gr, 2, 100.0, "sigmoid"), 1)
+    svss = timed(lambda: drt.vjp(gw, gt, gr, 2, 100.0, "sigmoid", gp, saved=gsv), 1)
+    del gsv
     # coherent field and its adjoint (lambda 0.02, eps_r 5) on the same scene
     fE, _ = drt.field(gw, gt, gr, 2, 100.0, "hard_sigmoid", 0.02, 5.0)
     ffh = timed(lambda: drt.field(gw, gt, gr, 2, 100.0, "hard_sigmoid", 0.02, 5.0), 2)
@@ -484,7 +490,10 @@ def measure_extras(drt, dev, sc, w, t, r):
         "fwd_ms": sf * 1e3, "vjp_ms": sv * 1e3,
         "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sf + sv),
         "sigmoid": {"fwd_ms": sfs * 1e3, "vjp_ms": svs * 1e3,
-                    "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sfs + svs)},
+                    "fwd_plus_adjoint_evals_per_s": g.n_rx * gc / (sfs + svs),
+                    "saved_visibilities": {"fwd_save_ms": sfss * 1e3, "vjp_saved_ms": svss * 1e3,
+                                           "fwd_plus_adjoint_evals_per_s":
+                                               g.n_rx * gc / (sfss + svss)}},
         "coherent_field": {"wavelength": 0.02, "eps_r": 5.0, "hard_fwd_ms": ffh * 1e3,
                            "hard_vjp_ms": fvh * 1e3, "sigmoid_vjp_ms": fvs * 1e3}}
     return out

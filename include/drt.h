@@ -343,6 +343,29 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
                    float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
                    void* stream);
 
+/* The forward's leg visibilities kept for the adjoint (sigmoid).  The sigmoid's
+   adjoint spends about a quarter of its time rebuilding every leg's visibility
+   (its first wall sweep); drt_forward_save writes them while computing the power,
+   and drt_vjp_saved reads them instead.  Layout: saved[(c (K + 1) + j) n_rx + r]
+   = the visibility of leg j of candidate c (the candidate order of
+   drt_num_candidates) for receiver r, for j <= the candidate's order (the other
+   slots are not written).
+   drt_saved_vis_size: *floats = N_K (K + 1) n_rx (host out).
+   drt_forward_save: drt_forward (same arguments and workspace) that also fills
+   `saved` (device, 4-byte aligned, caller-owned, drt_saved_vis_size floats).
+   drt_vjp_saved: drt_vjp (same arguments and workspace) given the `saved` of a
+   drt_forward_save on the same scene; gradients equal drt_vjp's within FP32
+   rounding (the forward's visibilities and the adjoint's sweep differ in the
+   order of their products).
+   All three need smoothing DRT_SMOOTH_SIGMOID and n_walls <= DRT_MAX_WALLS
+   (DRT_ERR_UNSUPPORTED otherwise: the other smoothings' first sweep is cheap). */
+drt_status drt_saved_vis_size(const drt_scene* scene, int64_t* floats);
+drt_status drt_forward_save(const drt_scene* scene, const drt_tile* tile, float* power,
+                            float* saved, void* workspace, size_t workspace_bytes, void* stream);
+drt_status drt_vjp_saved(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
+                         const float* saved, float* grad_tx, float* grad_walls, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
 /* Gradient of the min-power loss (Eq. 8, Sec. III) w.r.t. the scene, in one call:
    with loss = -power[argmin[0]],
      grad_tx    = -(grad_loss ? grad_loss[0] : 1) * d power[argmin] / d tx,

@@ -21,11 +21,11 @@ The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
 from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, forward_fpt,
-                  forward_mpt, fpt_paths, loss, min_loss, min_loss_backward, min_loss_vjp,
+                  forward_mpt, forward_save, fpt_paths, loss, min_loss, min_loss_backward, min_loss_vjp,
                   mpt_paths, num_candidates, objective, objective_host, power, power3, vjp, vjp3,
                   vjp3_tx)
 
 __all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "forward3",
-           "forward_fpt", "forward_mpt", "fpt_paths", "loss", "min_loss", "min_loss_backward",
+           "forward_fpt", "forward_mpt", "forward_save", "fpt_paths", "loss", "min_loss", "min_loss_backward",
            "min_loss_vjp", "mpt_paths", "num_candidates", "objective", "objective_host", "power",
            "power3", "vjp", "vjp3", "vjp3_tx"]

@@ -100,6 +100,9 @@ SIGNATURES = {
     "drt_forward_mpt_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_forward_mpt": (ctypes.c_int, [_P, _P, _I32, ctypes.c_float, _P, _P, _SZ, _P]),
     "drt_mpt_paths": (ctypes.c_int, [_P, _I32, ctypes.c_float, _P, _P]),
+    "drt_saved_vis_size": (ctypes.c_int, [_P, _P]),
+    "drt_forward_save": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
+    "drt_vjp_saved": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "drt_forward_fpt_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_forward_fpt": (ctypes.c_int, [_P, _P, _I32, ctypes.c_float, _P, _P, _SZ, _P]),
     "drt_fpt_paths": (ctypes.c_int, [_P, _I32, ctypes.c_float, _P, _P]),

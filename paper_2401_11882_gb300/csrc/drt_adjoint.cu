@@ -28,7 +28,9 @@ namespace drt {
 
 namespace {
 
-template <int MODE, bool WG>
+// SAVED: the sigmoid's leg visibilities come from a.saved (the forward's) instead
+// of the first wall sweep.
+template <int MODE, bool WG, bool SAVED = false>
 __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
   extern __shared__ float4 smem[];
   const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
@@ -61,11 +63,13 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
     const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
     for (long long c = c0; c < c1; ++c) {
       const Cand cd = decode_candidate(c, a.W, a.K);
+      // the forward's saved visibilities, [n_cand][K + 1][R] (or none)
+      const float* sv = SAVED ? a.saved + c * (a.K + 1) * a.R + r : nullptr;
       switch (cd.k) {
-        case 0: path_vjp<MODE, 0, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb_x, txb_y); break;
-        case 1: path_vjp<MODE, 1, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y); break;
-        case 2: path_vjp<MODE, 2, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y); break;
-        default: path_vjp<MODE, 3, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y); break;
+        case 0: path_vjp<MODE, 0, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb_x, txb_y, nullptr, sv, a.R); break;
+        case 1: path_vjp<MODE, 1, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y, nullptr, sv, a.R); break;
+        case 2: path_vjp<MODE, 2, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y, nullptr, sv, a.R); break;
+        default: path_vjp<MODE, 3, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y, nullptr, sv, a.R); break;
       }
     }
   }
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
 #define DRT_VJP_PAIR_MAX_THREADS 256
 #endif
 
-template <bool WG>
+template <bool WG, bool SAVED = false>
 __global__ void __launch_bounds__(DRT_VJP_PAIR_MAX_THREADS, DRT_VJP_PAIR_MIN_CTAS)
     vjp_pair_kernel(const VjpArgs a) {
   extern __shared__ float4 smem[];
@@ -135,13 +139,17 @@ __global__ void __launch_bounds__(DRT_VJP_PAIR_MAX_THREADS, DRT_VJP_PAIR_MIN_CTA
     const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live1 ? r1 : a.R - 1));
     const long long c0 = chunk * a.chunk;
     const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+    // the forward's saved visibilities, [n_cand][K + 1][R] (or none)
+    const long long rr0 = live0 ? r0 : a.R - 1, rr1 = live1 ? r1 : a.R - 1;
     for (long long c = c0; c < c1; ++c) {
       const Cand cd = decode_candidate(c, a.W, a.K);
+      const float* sv0 = SAVED ? a.saved + c * (a.K + 1) * a.R + rr0 : nullptr;
+      const float* sv1 = SAVED ? a.saved + c * (a.K + 1) * a.R + rr1 : nullptr;
       switch (cd.k) {
-        case 0: path_vjp_pair<0, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], g0, g1, txb_x, txb_y); break;
-        case 1: path_vjp_pair<1, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], g0, g1, txb_x, txb_y); break;
-        case 2: path_vjp_pair<2, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], g0, g1, txb_x, txb_y); break;
-        default: path_vjp_pair<3, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], g0, g1, txb_x, txb_y); break;
+        case 0: path_vjp_pair<0, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
+        case 1: path_vjp_pair<1, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
+        case 2: path_vjp_pair<2, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
+        default: path_vjp_pair<3, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
       }
     }
   }
@@ -364,6 +372,8 @@ template <int MODE, bool WG>
 void launch_vjp_t(const VjpArgs& a, int ctas, int threads, size_t smem, cudaStream_t st) {
   if (a.rx_index)
     vjp_rx_kernel<MODE, WG><<<ctas, threads, smem, st>>>(a);
+  else if (MODE == MODE_SIGMOID && a.saved)
+    vjp_kernel<MODE, WG, true><<<ctas, threads, smem, st>>>(a);
   else
     vjp_kernel<MODE, WG><<<ctas, threads, smem, st>>>(a);
 }
@@ -383,7 +393,10 @@ cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaSt
   const bool wg = a.grad_walls != nullptr;
   const size_t smem = vjp_smem_bytes(a.W, wg, a.pairs && !a.rx_index && wg);
   if (a.pairs && !a.rx_index && mode == MODE_SIGMOID && wg) {
-    vjp_pair_kernel<true><<<ctas, threads, smem, st>>>(a);
+    if (a.saved)
+      vjp_pair_kernel<true, true><<<ctas, threads, smem, st>>>(a);
+    else
+      vjp_pair_kernel<true><<<ctas, threads, smem, st>>>(a);
   } else
   switch (mode * 2 + (wg ? 1 : 0)) {
     case MODE_SIGMOID * 2: launch_vjp_t<MODE_SIGMOID, false>(a, ctas, threads, smem, st); break;
@@ -464,6 +477,16 @@ cudaError_t vjp_set_smem_limit(int W) {
   cudaError_t e = cudaSuccess;
   e = cudaFuncSetAttribute(vjp_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)vjp_smem_bytes(W, true, true));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(vjp_pair_kernel<true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)vjp_smem_bytes(W, true, true));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(vjp_kernel<MODE_SIGMOID, true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(vjp_kernel<MODE_SIGMOID, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, s0);
   if (e != cudaSuccess) return e;
 #define DRT_SET(M, B, S)                                                                    \
   e = cudaFuncSetAttribute(vjp_kernel<M, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, S); \

@@ -242,8 +242,9 @@ drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* ti
   return DRT_OK;
 }
 
-drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
-                       void* workspace, size_t workspace_bytes, void* stream) {
+namespace {
+drt_status forward_impl(const drt_scene* scene, const drt_tile* tile, float* power, float* saved,
+                        void* workspace, size_t workspace_bytes, void* stream) {
   drt_status st = check_scene(scene, DRT_MAX_WALLS_STREAMED);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
@@ -256,7 +257,7 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
   if (!workspace || workspace_bytes < need || (streamed && !aligned(workspace, 16)))
     return fail(DRT_ERR_WORKSPACE, "forward needs %zu workspace bytes, got %zu", need,
                 workspace_bytes);
-  FwdArgs a;
+  FwdArgs a{};
   a.walls = reinterpret_cast<const float4*>(scene->walls);
   a.W = scene->n_walls;
   a.rx = scene->rx;
@@ -277,10 +278,51 @@ drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* powe
   a.staged = streamed ? reinterpret_cast<float4*>(static_cast<char*>(workspace) +
                                                   forward_partials_bytes(scene, d))
                       : nullptr;
+  a.saved = saved;
   cudaError_t e = launch_forward(a, scene->smoothing, d.ctas, d.threads,
                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   return DRT_OK;
+}
+
+// The saved visibilities' size, and the cases that can save them: the sigmoid
+// (whose adjoint's first sweep they replace), walls in shared memory.
+drt_status check_saved(const drt_scene* scene, const float* saved, long long* floats) {
+  if (scene->smoothing != DRT_SMOOTH_SIGMOID)
+    return fail(DRT_ERR_UNSUPPORTED, "saved visibilities are kept for the sigmoid only");
+  if (scene->n_walls > DRT_MAX_WALLS)
+    return fail(DRT_ERR_UNSUPPORTED, "saved visibilities need n_walls <= %d", DRT_MAX_WALLS);
+  const long long n = num_candidates(scene->n_walls, scene->max_order) *
+                      (scene->max_order + 1) * (long long)scene->n_rx;
+  if (floats) *floats = n;
+  if (n > 0 && (!saved || !aligned(saved, 4)))
+    return fail(DRT_ERR_INVALID_ARG, "saved must be a 4-byte aligned device pointer");
+  return DRT_OK;
+}
+}  // namespace
+
+drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  return forward_impl(scene, tile, power, nullptr, workspace, workspace_bytes, stream);
+}
+
+drt_status drt_saved_vis_size(const drt_scene* scene, int64_t* floats) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if (!floats) return fail(DRT_ERR_INVALID_ARG, "floats is NULL");
+  long long n = 0;
+  static const float dummy = 0.f;
+  if ((st = check_saved(scene, &dummy, &n)) != DRT_OK) return st;
+  *floats = n;
+  return DRT_OK;
+}
+
+drt_status drt_forward_save(const drt_scene* scene, const drt_tile* tile, float* power,
+                            float* saved, void* workspace, size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_saved(scene, saved, nullptr)) != DRT_OK) return st;
+  return forward_impl(scene, tile, power, saved, workspace, workspace_bytes, stream);
 }
 
 namespace {
@@ -731,9 +773,10 @@ drt_status drt_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile, 
   return DRT_OK;
 }
 
-drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
-                   float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
-                   void* stream) {
+namespace {
+drt_status vjp_impl(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
+                    const float* saved, float* grad_tx, float* grad_walls, void* workspace,
+                    size_t workspace_bytes, void* stream) {
   drt_status st = check_scene(scene);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
@@ -770,10 +813,29 @@ drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* gr
   a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
   a.grad_tx = grad_tx;
   a.grad_walls = grad_walls;
+  a.saved = saved;
   cudaError_t e = launch_vjp(a, scene->smoothing, d.ctas, d.threads,
                              static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "vjp launch");
   return DRT_OK;
+}
+}  // namespace
+
+drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
+                   float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
+                   void* stream) {
+  return vjp_impl(scene, tile, grad_power, nullptr, grad_tx, grad_walls, workspace,
+                  workspace_bytes, stream);
+}
+
+drt_status drt_vjp_saved(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
+                         const float* saved, float* grad_tx, float* grad_walls, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_saved(scene, saved, nullptr)) != DRT_OK) return st;
+  return vjp_impl(scene, tile, grad_power, saved, grad_tx, grad_walls, workspace,
+                  workspace_bytes, stream);
 }
 
 drt_status drt_field_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile,

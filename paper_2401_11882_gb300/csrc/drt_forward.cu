@@ -26,8 +26,9 @@ namespace {
 
 // GLOBAL: the wall records were written to a.staged by stage_global_kernel (scenes
 // with more walls than shared memory holds) and are read through the L1 / L2
-// caches instead of shared memory.
-template <int MODE, bool GLOBAL = false>
+// caches instead of shared memory.  SAVE: every path's leg visibilities are also
+// written to a.saved (for the sigmoid's adjoint).
+template <int MODE, bool GLOBAL = false, bool SAVE = false>
 __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_kernel(const FwdArgs a) {
   extern __shared__ float4 smem[];
   float4* base = GLOBAL ? a.staged : smem;
@@ -52,26 +53,36 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
     const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
     float acc = 0.f;
     const bool masked = a.alpha > FAST_SKIP_MAX_ALPHA;
+    float vbuf[KMAX + 1];   // the path's leg visibilities when they are saved
+    float* vo = SAVE ? vbuf : nullptr;
     Cand cd = decode_candidate(c0, a.W, a.K);
     for (int i = 0; i < nc; ++i) {
       if (i > 0) next_candidate(cd, a.W);
       float p;
+      if (vo) {
+#pragma unroll
+        for (int j = 0; j <= KMAX; ++j) vbuf[j] = 0.f;
+      }
       if (!masked) {
         switch (cd.k) {
-          case 0: p = path_power<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull); break;
-          case 1: p = path_power<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull); break;
-          case 2: p = path_power<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull); break;
-          default: p = path_power<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull); break;
+          case 0: p = path_power<MODE, 0>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull, vo); break;
+          case 1: p = path_power<MODE, 1>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull, vo); break;
+          case 2: p = path_power<MODE, 2>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull, vo); break;
+          default: p = path_power<MODE, 3>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull, vo); break;
         }
       } else {
         switch (cd.k) {
-          case 0: p = path_power<MODE, 0, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull); break;
-          case 1: p = path_power<MODE, 1, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull); break;
-          case 2: p = path_power<MODE, 2, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull); break;
-          default: p = path_power<MODE, 3, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull); break;
+          case 0: p = path_power<MODE, 0, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], a.cull, vo); break;
+          case 1: p = path_power<MODE, 1, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], a.cull, vo); break;
+          case 2: p = path_power<MODE, 2, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], a.cull, vo); break;
+          default: p = path_power<MODE, 3, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], a.cull, vo); break;
         }
       }
       acc += p;
+      if (vo && live) {   // [n_cand][K + 1][R]: consecutive lanes write consecutive floats
+        float* dst = a.saved + (long long)(c0 + i) * (a.K + 1) * a.R + r;
+        for (int j = 0; j <= cd.k; ++j) dst[j * a.R] = vbuf[j];
+      }
     }
     if (live) a.partial[chunk * a.R + r] = acc;
   }
@@ -80,7 +91,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
 // Hard sigmoid and sigmoid, two receivers per lane (tiles of 64 receivers:
 // lane l holds receivers l and l + 32 of its tile); the walls' paired records
 // follow the four single-receiver arrays in shared memory.
-template <int MODE, bool GLOBAL = false>
+template <int MODE, bool GLOBAL = false, bool SAVE = false>
 __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
   extern __shared__ float4 smem[];
   float4* base = GLOBAL ? a.staged : smem;
@@ -108,18 +119,31 @@ __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
     const int c0 = (int)(chunk * a.chunk);
     const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
     float acc0 = 0.f, acc1 = 0.f;
+    float2 vbuf[KMAX + 1];   // the path's leg visibilities when they are saved
+    float2* vo = SAVE ? vbuf : nullptr;
     Cand cd = decode_candidate(c0, a.W, a.K);
     for (int i = 0; i < nc; ++i) {
       if (i > 0) next_candidate(cd, a.W);
       float2 p;
+      if (vo) {
+#pragma unroll
+        for (int j = 0; j <= KMAX; ++j) vbuf[j] = make_float2(0.f, 0.f);
+      }
       switch (cd.k) {
-        case 0: p = path_power_pair<MODE, 0>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], a.cull); break;
-        case 1: p = path_power_pair<MODE, 1>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], a.cull); break;
-        case 2: p = path_power_pair<MODE, 2>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], a.cull); break;
-        default: p = path_power_pair<MODE, 3>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], a.cull); break;
+        case 0: p = path_power_pair<MODE, 0>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], a.cull, vo); break;
+        case 1: p = path_power_pair<MODE, 1>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], a.cull, vo); break;
+        case 2: p = path_power_pair<MODE, 2>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], a.cull, vo); break;
+        default: p = path_power_pair<MODE, 3>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], a.cull, vo); break;
       }
       acc0 += p.x;
       acc1 += p.y;
+      if (vo) {   // [n_cand][K + 1][R]: consecutive lanes write consecutive floats
+        float* dst = a.saved + (long long)(c0 + i) * (a.K + 1) * a.R;
+        for (int j = 0; j <= cd.k; ++j) {
+          if (live0) dst[j * a.R + r0] = vbuf[j].x;
+          if (live1) dst[j * a.R + r1] = vbuf[j].y;
+        }
+      }
     }
     if (live0) a.partial[chunk * a.R + r0] = acc0;
     if (live1) a.partial[chunk * a.R + r1] = acc1;
@@ -253,7 +277,14 @@ cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cu
     return launch_reduce_chunks(a.partial, a.n_chunks, a.R, a.power, st);
   }
   const size_t smem = forward_smem_bytes(a.W, a.pairs);
-  if (a.n_units > 0 && a.pairs) {
+  if (a.n_units > 0 && a.saved && mode == MODE_SIGMOID) {
+    if (a.pairs)
+      forward_pair_kernel<MODE_SIGMOID, false, true><<<ctas, threads, smem, st>>>(a);
+    else
+      forward_kernel<MODE_SIGMOID, false, true><<<ctas, threads, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if (a.n_units > 0 && a.pairs) {
     if (mode == MODE_SIGMOID)
       forward_pair_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);
     else
@@ -333,7 +364,13 @@ cudaError_t forward_set_smem_limit(int W) {
   e = cudaFuncSetAttribute(forward_pair_kernel<MODE_SIGMOID>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(forward_pair_kernel<MODE_SIGMOID, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(forward_kernel<MODE_SIGMOID>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(forward_kernel<MODE_SIGMOID, false, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(forward_kernel<MODE_HARD>,

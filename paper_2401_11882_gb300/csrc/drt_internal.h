@@ -39,6 +39,7 @@ struct FwdArgs {
   float* partial;   // [n_chunks][R]
   float* power;     // [R]
   float4* staged;   // [8 or 4][W] wall records in global memory (W > DRT_MAX_WALLS), or null
+  float* saved;     // sigmoid: every path's leg visibilities [n_cand][K + 1][R], or null
 };
 
 // Coherent field (drt_field.cu): the forward's decomposition (one or two
@@ -122,6 +123,9 @@ struct VjpArgs {
   float* warp_tx;            // [ctas * warps_per_cta][2]
   float* grad_tx;            // [2]
   float* grad_walls;         // [W][4] or null
+  // sigmoid: the forward's leg visibilities [n_cand][K + 1][R] (drt_forward_save), read
+  // instead of the first wall sweep; or null
+  const float* saved;
   // coherent-field adjoint only (drt_field_vjp): the field E [R] from drt_field and
   // the field's constants; grad_power then weighs |E_r|^2
   const float2* field;

@@ -382,7 +382,8 @@ __device__ __forceinline__ float path_power_of(const PathGeom<MODE, K>& g, const
 // Power of one path candidate of order K for this lane's receiver (Eq. 7 term).
 template <int MODE, int K, bool MASKED = false>
 __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx, float2 rx,
-                                            const Cand& cd, float alpha, float gk, int cull) {
+                                            const Cand& cd, float alpha, float gk, int cull,
+                                            float* vis_out = nullptr) {
   float Ix[K + 1], Iy[K + 1];
   tx_images<K>(s, tx, cd, Ix, Iy);
   PathGeom<MODE, K> g;
@@ -400,6 +401,10 @@ __device__ __forceinline__ float path_power(const SmemWalls& s, int W, float2 tx
     const bool bad = !g.degenerate && !(min_div >= 0.25f);
     if (__any_sync(0xffffffffu, bad))
       leg_visibility<MODE, K, true>(s, W, cd, g.Qx, g.Qy, g.mx, g.my, g.mc, vis);
+  }
+  if (vis_out) {
+#pragma unroll
+    for (int j = 0; j <= K; ++j) vis_out[j] = vis[j];
   }
   return path_power_of<MODE, K>(g, vis, gk);
 }

@@ -163,7 +163,8 @@ __device__ __forceinline__ void sigmoid_visibility_pair(const SmemWalls& s, cons
 template <int MODE, int K>
 __device__ __forceinline__ float2 path_power_pair(const SmemWalls& s, const SmemPairs& p, int W,
                                                   float2 tx, float2 rx0, float2 rx1, const Cand& cd,
-                                                  float alpha, float gk, int cull) {
+                                                  float alpha, float gk, int cull,
+                                                  float2* vis_out = nullptr) {
   float Ix[K + 1], Iy[K + 1];
   tx_images<K>(s, tx, cd, Ix, Iy);
   PathGeom<MODE, K> g0, g1;
@@ -208,6 +209,10 @@ __device__ __forceinline__ float2 path_power_pair(const SmemWalls& s, const Smem
     leg_visibility<MODE, K, true>(s, W, cd, g0.Qx, g0.Qy, g0.mx, g0.my, g0.mc, vis0);
   if (__any_sync(0xffffffffu, !g1.degenerate && !(d1 >= 0.25f)))
     leg_visibility<MODE, K, true>(s, W, cd, g1.Qx, g1.Qy, g1.mx, g1.my, g1.mc, vis1);
+  if (vis_out) {
+#pragma unroll
+    for (int j = 0; j <= K; ++j) vis_out[j] = f2(vis0[j], vis1[j]);
+  }
   return f2(path_power_of<MODE, K>(g0, vis0, gk), path_power_of<MODE, K>(g1, vis1, gk));
 }
 

@@ -516,7 +516,9 @@ template <int MODE, int K, bool WG, bool UNI, bool FIELD = false>
 __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float2 rx,
                                          const Cand& cd, float alpha, float gk, float g,
                                          float& txb_x, float& txb_y,
-                                         const FieldW* fw = nullptr) {
+                                         const FieldW* fw = nullptr,
+                                         const float* saved = nullptr,
+                                         long long saved_stride = 0) {
   // ------------------------------------------------ forward recompute (guarded)
   VjpPath<K> P;
   vjp_recompute<MODE, K>(s, tx, rx, cd, alpha, P);
@@ -549,7 +551,12 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
     mck[j] = -mq[j] * kap;
   }
   if constexpr (MODE == MODE_SIGMOID) {
-    sigmoid_vis_sweep<K>(s, W, cd, Qx, Qy, mxk, myk, mck, nz, zc);
+    if (!FIELD && saved) {   // the forward's visibilities of this path (sweep 1 done there)
+#pragma unroll
+      for (int j = 0; j <= K; ++j) nz[j] = __ldg(saved + j * saved_stride);
+    } else {
+      sigmoid_vis_sweep<K>(s, W, cd, Qx, Qy, mxk, myk, mck, nz, zc);
+    }
   } else {
   for (int w = 0; w < W; ++w) {
     const float4 G = s.G[w];

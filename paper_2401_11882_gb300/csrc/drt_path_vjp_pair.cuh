@@ -214,7 +214,10 @@ template <int K, bool WG>
 __device__ __forceinline__ void path_vjp_pair(const VSmem& s, const SmemPairsVjp& p, int W,
                                               float2 tx, float2 rx0, float2 rx1, const Cand& cd,
                                               float alpha, float gk, float g0, float g1,
-                                              float& txb_x, float& txb_y) {
+                                              float& txb_x, float& txb_y,
+                                              const float* saved0 = nullptr,
+                                              const float* saved1 = nullptr,
+                                              long long saved_stride = 0) {
   float2 Qx[K + 2], Qy[K + 2], mxk[K + 1], myk[K + 1], mck[K + 1];
   float V0[K + 1], V1[K + 1];
   float L0, L1;
@@ -250,7 +253,13 @@ __device__ __forceinline__ void path_vjp_pair(const VSmem& s, const SmemPairsVjp
   }
   // ------------------------------------------------ sweep 1: visibilities
   float2 vis[K + 1];
-  sigmoid_vis_sweep_pair<K>(s, p, W, cd, Qx, Qy, mxk, myk, mck, vis);
+  if (saved0) {   // the forward's visibilities of this path (sweep 1 done there)
+#pragma unroll
+    for (int j = 0; j <= K; ++j)
+      vis[j] = f2(__ldg(saved0 + j * saved_stride), __ldg(saved1 + j * saved_stride));
+  } else {
+    sigmoid_vis_sweep_pair<K>(s, p, W, cd, Qx, Qy, mxk, myk, mck, vis);
+  }
 #pragma unroll
   for (int j = 0; j <= K; ++j) {
     dead0 |= (vis[j].x == 0.f);

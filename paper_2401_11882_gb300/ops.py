@@ -102,6 +102,37 @@ def forward(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "hard_
     return power
 
 
+def saved_vis_floats(walls, tx, rx, max_order: int, alpha: float,
+                     smoothing: str = "sigmoid") -> int:
+    """Floats of the leg visibilities forward_save keeps (N_K (K + 1) R); raises when
+    they are not kept for this scene (not the sigmoid, or more than 1024 walls)."""
+    sc, _ = make_scene(walls, tx, rx, max_order, alpha, smoothing)
+    n = ctypes.c_int64()
+    _lib.call("drt_saved_vis_size", ctypes.byref(sc), ctypes.byref(n))
+    return int(n.value)
+
+
+def forward_save(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "sigmoid",
+                 refl_coef: float = 0.5, tile: TileConfig | None = None):
+    """(power [R], saved): the forward that also keeps every path's leg visibilities
+    (float32 [N_K (K + 1) R]) for ``vjp(..., saved=saved)``, which then skips the
+    adjoint's first wall sweep (drt_forward_save; sigmoid)."""
+    sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
+    dev = keep[0].device
+    n = ctypes.c_int64()
+    _lib.call("drt_saved_vis_size", ctypes.byref(sc), ctypes.byref(n))
+    saved = torch.empty(max(int(n.value), 1), dtype=torch.float32, device=dev)
+    tl = tile.as_c() if tile else None
+    tlp = ctypes.byref(tl) if tl is not None else None
+    nbytes = ctypes.c_size_t()
+    _lib.call("drt_forward_workspace_size", ctypes.byref(sc), tlp, ctypes.byref(nbytes))
+    ws = _workspace(dev, nbytes.value)
+    power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
+    _lib.call("drt_forward_save", ctypes.byref(sc), tlp, _ptr(power), _ptr(saved), _ptr(ws),
+              ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+    return power, saved
+
+
 def _finder_forward(name: str, walls, tx, rx, max_order, alpha, smoothing, n_iter, check_eps,
                     refl_coef, tile) -> torch.Tensor:
     sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
@@ -361,8 +392,11 @@ def min_loss_backward(argmin: torch.Tensor, grad_loss: torch.Tensor | None, n_rx
 
 
 def vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, grad_power: torch.Tensor,
-        refl_coef: float = 0.5, wall_grad: bool = True, tile: TileConfig | None = None):
-    """(grad_tx [2], grad_walls [W, 4] or None) = grad_power^T d power / d (tx, walls)."""
+        refl_coef: float = 0.5, wall_grad: bool = True, tile: TileConfig | None = None,
+        saved: torch.Tensor | None = None):
+    """(grad_tx [2], grad_walls [W, 4] or None) = grad_power^T d power / d (tx, walls).
+    ``saved``: the leg visibilities of a ``forward_save`` on the same scene (sigmoid),
+    read instead of the adjoint's first wall sweep (drt_vjp_saved)."""
     sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
     dev = keep[0].device
     gp = _as_f32(grad_power.reshape(-1, 1), 1, "grad_power", 4)
@@ -375,9 +409,16 @@ def vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, grad_power:
     ws = _workspace(dev, nbytes.value)
     gtx = torch.empty(2, dtype=torch.float32, device=dev)
     gw = torch.empty(sc.n_walls, 4, dtype=torch.float32, device=dev) if wall_grad else None
-    _lib.call("drt_vjp", ctypes.byref(sc), tlp, _ptr(gp), _ptr(gtx),
-              None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
-              _stream_ptr(dev))
+    if saved is not None:
+        if not (saved.is_cuda and saved.dtype == torch.float32 and saved.is_contiguous()):
+            raise TypeError("saved must be the float32 CUDA tensor forward_save returned")
+        _lib.call("drt_vjp_saved", ctypes.byref(sc), tlp, _ptr(gp), _ptr(saved), _ptr(gtx),
+                  None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                  _stream_ptr(dev))
+    else:
+        _lib.call("drt_vjp", ctypes.byref(sc), tlp, _ptr(gp), _ptr(gtx),
+                  None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                  _stream_ptr(dev))
     return gtx, gw
 
 
@@ -429,26 +470,51 @@ class ObjectiveFunction(torch.autograd.Function):
                 None, None, None, None, None, None)
 
 
+# Largest leg-visibility buffer (bytes) PowerFunction keeps for its backward
+# (sigmoid; override with DRT_SAVED_VIS_MAX_BYTES, 0 to always recompute).
+SAVED_VIS_MAX_BYTES = 4 << 30
+
+
+def _saved_vis_limit() -> int:
+    import os
+    v = os.environ.get("DRT_SAVED_VIS_MAX_BYTES")
+    return int(v) if v is not None else SAVED_VIS_MAX_BYTES
+
+
 class PowerFunction(torch.autograd.Function):
     """power = P(walls, tx) with the hand-written adjoint as backward.
 
-    The backward recomputes the path geometry (nothing but the inputs is saved)."""
+    The backward recomputes the path geometry; for the sigmoid the forward also keeps
+    every path's leg visibilities (up to ``SAVED_VIS_MAX_BYTES``), so that the backward
+    skips its first wall sweep."""
 
     @staticmethod
     def forward(ctx, walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile):
-        ctx.save_for_backward(walls, tx, rx)
         ctx.args = (max_order, alpha, smoothing, refl_coef, tile)
-        return forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
+        saved = None
+        if (smoothing == "sigmoid" and walls.shape[0] <= 1024 and rx.shape[0] > 0 and
+                (ctx.needs_input_grad[0] or ctx.needs_input_grad[1])):
+            n = saved_vis_floats(walls, tx, rx, max_order, alpha, smoothing)
+            if 4 * n <= _saved_vis_limit():
+                power, saved = forward_save(walls, tx, rx, max_order, alpha, smoothing,
+                                            refl_coef, tile)
+        if saved is None:
+            power = forward(walls, tx, rx, max_order, alpha, smoothing, refl_coef, tile)
+            ctx.save_for_backward(walls, tx, rx)
+        else:
+            ctx.save_for_backward(walls, tx, rx, saved)
+        return power
 
     @staticmethod
     def backward(ctx, grad_power):
-        walls, tx, rx = ctx.saved_tensors
+        walls, tx, rx, *rest = ctx.saved_tensors
+        saved = rest[0] if rest else None
         max_order, alpha, smoothing, refl_coef, tile = ctx.args
         need_w, need_tx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         if not (need_w or need_tx):
             return (None,) * 8
         gtx, gw = vjp(walls, tx, rx, max_order, alpha, smoothing, grad_power.contiguous(),
-                      refl_coef, wall_grad=need_w, tile=tile)
+                      refl_coef, wall_grad=need_w, tile=tile, saved=saved)
         return (gw if need_w else None, gtx.reshape(tx.shape) if need_tx else None,
                 None, None, None, None, None, None)
 

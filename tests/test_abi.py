@@ -225,3 +225,16 @@ def test_batch_plan_dimension_checks(lib):
     b2 = _lib.Batch(260, 256, 260, 256, 256, ctypes.addressof(off), ctypes.addressof(roff),
                     ctypes.addressof(order), 1, 2, 1, 0.5, 2)
     assert lib.drt_batch_plan_create(ctypes.byref(b2), None, ctypes.byref(plan)) == 1
+
+
+def test_saved_visibilities_size_host_only(lib):
+    out = ctypes.c_int64()
+    sc = _scene(n_walls=4, n_rx=3, max_order=1, smoothing=0)    # sigmoid
+    assert lib.drt_saved_vis_size(ctypes.byref(sc), ctypes.byref(out)) == 0
+    assert out.value == (1 + 4) * 2 * 3                        # N_K (K + 1) R
+    sc = _scene(n_walls=4, n_rx=3, max_order=1, smoothing=1)    # hard sigmoid: not kept
+    assert lib.drt_saved_vis_size(ctypes.byref(sc), ctypes.byref(out)) == 2
+    assert b"sigmoid" in lib.drt_last_error()
+    p = ctypes.c_void_p(256)
+    assert lib.drt_forward_save(ctypes.byref(sc), None, p, p, p, 1 << 20, None) == 2
+    assert lib.drt_vjp_saved(ctypes.byref(sc), None, p, p, p, None, p, 1 << 20, None) == 2

@@ -255,3 +255,81 @@ def test_sigmoid_pair_adjoint_on_gradient_scene(drt):
     assert np.linalg.norm(gtx - gtx1) <= 1e-5 * np.linalg.norm(gtx1)
     assert np.linalg.norm(gw - gw1) <= 1e-5 * np.linalg.norm(gw1)
     assert np.all(np.abs(gw - gw1) <= 1e-4 * np.abs(gw1) + 1e-6 * np.abs(gw1).max())
+
+
+SAVED_CASES = [   # sigmoid: (seed, W, R, K, alpha)
+    (60, 6, 45, 1, 20.0),
+    (61, 8, 70, 2, 50.0),
+    (62, 5, 33, 3, 15.0),
+    (63, 9, 64, 2, 100.0),
+]
+
+
+@pytest.mark.parametrize("seed,W,R,K,alpha", SAVED_CASES)
+@pytest.mark.parametrize("single_rx", [False, True])
+def test_saved_visibilities(drt, oracle_mod, seed, W, R, K, alpha, single_rx):
+    """drt_forward_save: the power of drt_forward bit for bit, and every path's leg
+    visibilities as the oracle computes them; drt_vjp_saved: drt_vjp's gradient (the
+    first wall sweep replaced by the saved values) and the oracle's."""
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, "sigmoid", boundary=(seed % 2 == 0))
+    w, t, r = _tensors(sc)
+    tile = drt.TileConfig(single_rx=True) if single_rx else None
+    P, saved = drt.forward_save(w, t, r, K, alpha, "sigmoid", sc.refl_coef, tile=tile)
+    P_plain = drt.forward(w, t, r, K, alpha, "sigmoid", sc.refl_coef, tile=tile)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(P.cpu().numpy(), P_plain.cpu().numpy())
+    sv = saved.cpu().numpy().astype(np.float64).reshape(-1, K + 1, sc.n_rx)
+    n_checked = 0
+    for ri in range(0, sc.n_rx, 7):
+        ref = oracle_mod.paths(sc.walls, sc.tx, sc.rx[ri], K, alpha, "sigmoid", sc.refl_coef)
+        ok = (ref["validity"] > 0) & ~ref["degenerate"].astype(bool)
+        for c in np.nonzero(ok)[0]:
+            k = int(ref["order"][c])
+            got, want = sv[c, :k + 1, ri], ref["vis"][c, :k + 1]
+            # a factor s(alpha z) moves by alpha (1 - s) dz relative for an FP32 error dz
+            # in a smoothed distance of the backtraced vertices (~1e-6 after two
+            # reflections): 2e-3 covers alpha <= 100
+            np.testing.assert_allclose(got, want, rtol=2e-3, atol=1e-6)
+            n_checked += k + 1
+    assert n_checked > 50
+    g = torch.tensor(rng.normal(size=sc.n_rx), dtype=torch.float32, device=w.device)
+    gtx_s, gw_s = drt.vjp(w, t, r, K, alpha, "sigmoid", g, sc.refl_coef, tile=tile, saved=saved)
+    gtx, gw = drt.vjp(w, t, r, K, alpha, "sigmoid", g, sc.refl_coef, tile=tile)
+    torch.cuda.synchronize()
+    assert_grad_close(gtx_s.cpu().numpy(), gtx.cpu().numpy(), "saved vs recomputed TX gradient")
+    assert_grad_close(gw_s.cpu().numpy().ravel(), gw.cpu().numpy().ravel(),
+                      "saved vs recomputed wall gradient")
+    ref = _oracle_grad(oracle_mod, sc, g.cpu().numpy().astype(np.float64))
+    assert_grad_close(np.concatenate([gtx_s.cpu().numpy(), gw_s.cpu().numpy().ravel()]), ref,
+                      "saved-visibility gradient vs oracle")
+    # the TX-only adjoint reads them too
+    gtx_only, _ = drt.vjp(w, t, r, K, alpha, "sigmoid", g, sc.refl_coef, wall_grad=False,
+                          tile=tile, saved=saved)
+    torch.cuda.synchronize()
+    assert_grad_close(gtx_only.cpu().numpy(), gtx.cpu().numpy(), "TX-only with saved values")
+
+
+def test_power_autograd_keeps_the_visibilities_for_the_sigmoid(drt, oracle_mod, monkeypatch):
+    from paper_2401_11882_gb300 import ops
+    rng = np.random.default_rng(64)
+    sc = scenes.random_small_scene(rng, 7, 50, 2, 40.0, "sigmoid", boundary=True)
+    dev = torch.device("cuda:0")
+    g = torch.tensor(rng.normal(size=sc.n_rx), dtype=torch.float32, device=dev)
+    grads = {}
+    calls = []
+    real = ops.forward_save
+    monkeypatch.setattr(ops, "forward_save", lambda *a, **k: calls.append(1) or real(*a, **k))
+    for limit in (None, "0"):
+        if limit is not None:
+            monkeypatch.setenv("DRT_SAVED_VIS_MAX_BYTES", limit)
+        w = torch.tensor(sc.walls, device=dev, requires_grad=True)
+        t = torch.tensor(sc.tx, device=dev, requires_grad=True)
+        r = torch.tensor(sc.rx, device=dev)
+        P = drt.power(w, t, r, 2, 40.0, "sigmoid")
+        (P * g).sum().backward()
+        grads[limit] = (t.grad.cpu().numpy(), w.grad.cpu().numpy())
+    assert len(calls) == 1                 # kept the first time, recomputed with limit 0
+    assert_grad_close(grads[None][0], grads["0"][0], "autograd TX gradient, saved vs not")
+    assert_grad_close(grads[None][1].ravel(), grads["0"][1].ravel(),
+                      "autograd wall gradient, saved vs not")
