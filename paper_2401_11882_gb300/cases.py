@@ -4,7 +4,8 @@ regex:vjp_kernel -s 2 -c 1 python -m paper_2401_11882_gb300.cases vjp --rx-grid 
 without ``--clock-control none`` ncu locks the GPU's clocks).
 
     forward   drt.forward on the scene
-    vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall)
+    vjp       drt.vjp with dense g = 1/R (gradient w.r.t. the TX and every wall;
+              --saved: the sigmoid adjoint reading drt.forward_save's visibilities)
     field     drt.field (coherent field, Fresnel TE, --eps-r, --wavelength)
     field_vjp drt.field_vjp with dense g = 1/R (after one drt.field)
     forward_mpt drt.forward_mpt (the iterative path finder, --n-iter steps, --check-eps)
@@ -47,6 +48,8 @@ def main() -> int:
     ap.add_argument("--eps-r", type=float, default=5.0)
     ap.add_argument("--single-rx", action="store_true", help="one receiver per lane")
     ap.add_argument("--tx-only", action="store_true", help="vjp3: transmitter gradient only")
+    ap.add_argument("--saved", action="store_true",
+                    help="vjp: read the forward's saved visibilities (sigmoid)")
     args = ap.parse_args()
     dev = torch.device("cuda:0")
     if args.op == "mlp":
@@ -101,6 +104,11 @@ def main() -> int:
     w, t, r = (torch.tensor(x, device=dev) for x in (sc.walls, sc.tx, rx))
     g = torch.full((r.shape[0],), 1.0 / r.shape[0], device=dev)
     E = None
+    saved = None
+    if args.op == "vjp" and args.saved:
+        tile0 = ops.TileConfig(single_rx=True) if args.single_rx else None
+        _, saved = ops.forward_save(w, t, r, sc.max_order, args.alpha, args.smoothing,
+                                    tile=tile0)
     if args.op == "field_vjp":
         E, _ = ops.field(w, t, r, sc.max_order, args.alpha, args.smoothing, args.wavelength,
                          args.eps_r)
@@ -119,7 +127,8 @@ def main() -> int:
         if args.op == "field_vjp":
             return ops.field_vjp(w, t, r, sc.max_order, args.alpha, args.smoothing,
                                  args.wavelength, args.eps_r, E, g)
-        return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g, tile=tile)
+        return ops.vjp(w, t, r, sc.max_order, args.alpha, args.smoothing, g, tile=tile,
+                       saved=saved)
 
     for _ in range(2):
         run()
@@ -131,7 +140,7 @@ def main() -> int:
     b.record()
     torch.cuda.synchronize(dev)
     res = {"op": args.op, "scene": args.scene, "smoothing": args.smoothing, "alpha": args.alpha,
-           "single_rx": args.single_rx,
+           "single_rx": args.single_rx, "saved": saved is not None,
            "n_rx": int(r.shape[0]), "ms": a.elapsed_time(b) / args.reps,
            "evals_per_s": int(r.shape[0]) * ops.num_candidates(sc.walls.shape[0], sc.max_order)
            / (a.elapsed_time(b) / args.reps / 1e3)}

@@ -552,8 +552,17 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
   }
   if constexpr (MODE == MODE_SIGMOID) {
     if (!FIELD && saved) {   // the forward's visibilities of this path (sweep 1 done there)
+      // A path the forward found degenerate (a zero-length leg) has no finite
+      // visibilities there and contributes nothing: such lanes, and lanes already
+      // at weight 0, take 1 so that their zero weight stays an exact zero.
 #pragma unroll
-      for (int j = 0; j <= K; ++j) nz[j] = __ldg(saved + j * saved_stride);
+      for (int j = 0; j <= K; ++j) {
+        const float v = __ldg(saved + j * saved_stride);
+        dead |= (v != v);
+        nz[j] = v;
+      }
+#pragma unroll
+      for (int j = 0; j <= K; ++j) nz[j] = dead ? 1.f : nz[j];
     } else {
       sigmoid_vis_sweep<K>(s, W, cd, Qx, Qy, mxk, myk, mck, nz, zc);
     }

@@ -254,9 +254,16 @@ __device__ __forceinline__ void path_vjp_pair(const VSmem& s, const SmemPairsVjp
   // ------------------------------------------------ sweep 1: visibilities
   float2 vis[K + 1];
   if (saved0) {   // the forward's visibilities of this path (sweep 1 done there)
+    // a path the forward found degenerate has no finite visibilities there: such
+    // lanes, and lanes already at weight 0, take 1 (their weight stays an exact 0)
 #pragma unroll
-    for (int j = 0; j <= K; ++j)
+    for (int j = 0; j <= K; ++j) {
       vis[j] = f2(__ldg(saved0 + j * saved_stride), __ldg(saved1 + j * saved_stride));
+      dead0 |= (vis[j].x != vis[j].x);
+      dead1 |= (vis[j].y != vis[j].y);
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) vis[j] = f2(dead0 ? 1.f : vis[j].x, dead1 ? 1.f : vis[j].y);
   } else {
     sigmoid_vis_sweep_pair<K>(s, p, W, cd, Qx, Qy, mxk, myk, mck, vis);
   }
