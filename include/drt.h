@@ -338,7 +338,11 @@ drt_status drt_vjp_workspace_size(const drt_scene* scene, const drt_tile* tile, 
    grad_power: [n_rx]; grad_tx: [2], overwritten; grad_walls: [n_walls][4],
    overwritten, or NULL to skip the wall gradient.  Receivers whose 32-wide
    tile has grad_power == 0 everywhere are skipped.  The hard sigmoid's
-   derivative is taken as 0 at its kinks (x = +-3/alpha). */
+   derivative is taken as 0 at its kinks (x = +-3/alpha).  Warps take their
+   (receiver tile, candidate chunk) units from a counter in the workspace, which
+   drt_vjp zeroes on `stream` first (a 16-byte memset), so one workspace serves
+   one call in flight at a time.  grad_tx is the same bit for bit from run to
+   run; grad_walls varies in the last bits (shared-memory atomics). */
 drt_status drt_vjp(const drt_scene* scene, const drt_tile* tile, const float* grad_power,
                    float* grad_tx, float* grad_walls, void* workspace, size_t workspace_bytes,
                    void* stream);

@@ -28,6 +28,29 @@ namespace drt {
 
 namespace {
 
+// Work stealing of the receiver-tile adjoints: a warp's first unit is its own
+// index, later ones come from a global counter (zeroed before the launch), so a
+// warp whose units end early (tiles at weight 0, paths skipped as exactly zero)
+// takes more.
+__device__ __forceinline__ long long next_unit(const VjpArgs& a, long long nwarps, int lane) {
+  unsigned long long v = 0;
+  if (lane == 0) v = atomicAdd(a.unit_counter, 1ULL);
+  return nwarps + (long long)__shfl_sync(FULL, v, 0);
+}
+
+// The TX adjoint of one unit, summed over the warp and stored per unit: the
+// finalize kernel adds the units in index order, so the TX gradient does not
+// depend on which warp took which unit.
+__device__ __forceinline__ void unit_tx_done(const VjpArgs& a, long long u, int lane, float ux,
+                                             float uy) {
+  ux = warp_sum(ux);
+  uy = warp_sum(uy);
+  if (lane == 0) {
+    a.unit_tx[2 * u] = ux;
+    a.unit_tx[2 * u + 1] = uy;
+  }
+}
+
 // SAVED: the sigmoid's leg visibilities come from a.saved (the forward's) instead
 // of the first wall sweep.
 template <int MODE, bool WG, bool SAVED = false>
@@ -49,35 +72,31 @@ __global__ void __launch_bounds__(256) vjp_kernel(const VjpArgs a) {
   const long long warps_per_cta = blockDim.x >> 5;
   const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
-  float txb_x = 0.f, txb_y = 0.f;
-  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+  for (long long u = gwarp; u < a.n_units; u = next_unit(a, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
     const bool live = r < a.R;
     if (!live) r = a.R - 1;
     const float g = live ? __ldg(a.grad_power + r) : 0.f;
-    if (__all_sync(FULL, g == 0.f)) continue;
-    const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
-    const long long c0 = chunk * a.chunk;
-    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
-    for (long long c = c0; c < c1; ++c) {
-      const Cand cd = decode_candidate(c, a.W, a.K);
-      // the forward's saved visibilities, [n_cand][K + 1][R] (or none)
-      const float* sv = SAVED ? a.saved + c * (a.K + 1) * a.R + r : nullptr;
-      switch (cd.k) {
-        case 0: path_vjp<MODE, 0, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb_x, txb_y, nullptr, sv, a.R); break;
-        case 1: path_vjp<MODE, 1, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb_x, txb_y, nullptr, sv, a.R); break;
-        case 2: path_vjp<MODE, 2, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb_x, txb_y, nullptr, sv, a.R); break;
-        default: path_vjp<MODE, 3, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb_x, txb_y, nullptr, sv, a.R); break;
+    float ux = 0.f, uy = 0.f;
+    if (!__all_sync(FULL, g == 0.f)) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
+      const long long c0 = chunk * a.chunk;
+      const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+      for (long long c = c0; c < c1; ++c) {
+        const Cand cd = decode_candidate(c, a.W, a.K);
+        // the forward's saved visibilities, [n_cand][K + 1][R] (or none)
+        const float* sv = SAVED ? a.saved + c * (a.K + 1) * a.R + r : nullptr;
+        switch (cd.k) {
+          case 0: path_vjp<MODE, 0, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, ux, uy, nullptr, sv, a.R); break;
+          case 1: path_vjp<MODE, 1, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, ux, uy, nullptr, sv, a.R); break;
+          case 2: path_vjp<MODE, 2, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, ux, uy, nullptr, sv, a.R); break;
+          default: path_vjp<MODE, 3, WG, true>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, ux, uy, nullptr, sv, a.R); break;
+        }
       }
     }
-  }
-  txb_x = warp_sum(txb_x);
-  txb_y = warp_sum(txb_y);
-  if (lane == 0) {
-    a.warp_tx[2 * gwarp] = txb_x;
-    a.warp_tx[2 * gwarp + 1] = txb_y;
+    unit_tx_done(a, u, lane, ux, uy);
   }
   if (WG) {
     __syncthreads();
@@ -126,38 +145,34 @@ __global__ void __launch_bounds__(DRT_VJP_PAIR_MAX_THREADS, DRT_VJP_PAIR_MIN_CTA
   const long long warps_per_cta = blockDim.x >> 5;
   const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
-  float txb_x = 0.f, txb_y = 0.f;
-  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+  for (long long u = gwarp; u < a.n_units; u = next_unit(a, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     const long long r0 = tile * 64 + lane, r1 = r0 + 32;
     const bool live0 = r0 < a.R, live1 = r1 < a.R;
     const float g0 = live0 ? __ldg(a.grad_power + r0) : 0.f;
     const float g1 = live1 ? __ldg(a.grad_power + r1) : 0.f;
-    if (__all_sync(FULL, g0 == 0.f && g1 == 0.f)) continue;
-    const float2 q0 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live0 ? r0 : a.R - 1));
-    const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live1 ? r1 : a.R - 1));
-    const long long c0 = chunk * a.chunk;
-    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
-    // the forward's saved visibilities, [n_cand][K + 1][R] (or none)
-    const long long rr0 = live0 ? r0 : a.R - 1, rr1 = live1 ? r1 : a.R - 1;
-    for (long long c = c0; c < c1; ++c) {
-      const Cand cd = decode_candidate(c, a.W, a.K);
-      const float* sv0 = SAVED ? a.saved + c * (a.K + 1) * a.R + rr0 : nullptr;
-      const float* sv1 = SAVED ? a.saved + c * (a.K + 1) * a.R + rr1 : nullptr;
-      switch (cd.k) {
-        case 0: path_vjp_pair<0, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
-        case 1: path_vjp_pair<1, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
-        case 2: path_vjp_pair<2, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
-        default: path_vjp_pair<3, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], g0, g1, txb_x, txb_y, sv0, sv1, a.R); break;
+    float ux = 0.f, uy = 0.f;
+    if (!__all_sync(FULL, g0 == 0.f && g1 == 0.f)) {
+      const float2 q0 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live0 ? r0 : a.R - 1));
+      const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.rx) + (live1 ? r1 : a.R - 1));
+      const long long c0 = chunk * a.chunk;
+      const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+      // the forward's saved visibilities, [n_cand][K + 1][R] (or none)
+      const long long rr0 = live0 ? r0 : a.R - 1, rr1 = live1 ? r1 : a.R - 1;
+      for (long long c = c0; c < c1; ++c) {
+        const Cand cd = decode_candidate(c, a.W, a.K);
+        const float* sv0 = SAVED ? a.saved + c * (a.K + 1) * a.R + rr0 : nullptr;
+        const float* sv1 = SAVED ? a.saved + c * (a.K + 1) * a.R + rr1 : nullptr;
+        switch (cd.k) {
+          case 0: path_vjp_pair<0, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], g0, g1, ux, uy, sv0, sv1, a.R); break;
+          case 1: path_vjp_pair<1, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], g0, g1, ux, uy, sv0, sv1, a.R); break;
+          case 2: path_vjp_pair<2, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], g0, g1, ux, uy, sv0, sv1, a.R); break;
+          default: path_vjp_pair<3, WG>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], g0, g1, ux, uy, sv0, sv1, a.R); break;
+        }
       }
     }
-  }
-  txb_x = warp_sum(txb_x);
-  txb_y = warp_sum(txb_y);
-  if (lane == 0) {
-    a.warp_tx[2 * gwarp] = txb_x;
-    a.warp_tx[2 * gwarp + 1] = txb_y;
+    unit_tx_done(a, u, lane, ux, uy);
   }
   if (WG) {
     __syncthreads();
@@ -347,9 +362,12 @@ __global__ void __launch_bounds__(256) vjp_finalize_kernel(const VjpArgs a, int 
   if (blockIdx.x == 0) {
     __shared__ float sx[256], sy[256];
     float x = 0.f, y = 0.f;
-    for (int i = threadIdx.x; i < n_warps; i += blockDim.x) {
-      x += a.warp_tx[2 * i];
-      y += a.warp_tx[2 * i + 1];
+    // per-unit TX adjoints (the receiver-tile kernels) or per-warp ones
+    const float* parts = a.unit_tx ? a.unit_tx : a.warp_tx;
+    const long long n_parts = a.unit_tx ? a.n_units : n_warps;
+    for (long long i = threadIdx.x; i < n_parts; i += blockDim.x) {
+      x += parts[2 * i];
+      y += parts[2 * i + 1];
     }
     sx[threadIdx.x] = x;
     sy[threadIdx.x] = y;
@@ -392,6 +410,10 @@ bool vjp_uses_pairs(int mode, int flags) {
 cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   const bool wg = a.grad_walls != nullptr;
   const size_t smem = vjp_smem_bytes(a.W, wg, a.pairs && !a.rx_index && wg);
+  if (!a.rx_index) {   // the receiver-tile kernels steal work: zero their counter
+    cudaError_t e = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
   if (a.pairs && !a.rx_index && mode == MODE_SIGMOID && wg) {
     if (a.saved)
       vjp_pair_kernel<true, true><<<ctas, threads, smem, st>>>(a);

@@ -122,6 +122,9 @@ drt_status check_tile(const drt_tile* t) {
 
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
+// Most (receiver tile, candidate chunk) units drt_vjp splits its work into (its
+// per-unit TX adjoints take 8 bytes each; more tiles than this make one unit per tile).
+constexpr long long MAX_VJP_UNITS = 1LL << 22;
 
 // VJP_RX: the min-loss adjoint's one-receiver kernel (lanes = candidates)
 // VJP_TX: drt_vjp without the wall gradient (one receiver per lane)
@@ -150,6 +153,12 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
               forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0)) ||
              (kern == VJP && vjp_uses_pairs(sc->smoothing, t ? t->flags : 0));
   d->n_tiles = d->pairs ? (R + 63) / 64 : (R + 31) / 32;
+  if ((kern == VJP || kern == VJP_TX) && d->n_tiles * d->n_chunks > MAX_VJP_UNITS) {
+    // larger chunks keep drt_vjp's per-unit TX table within MAX_VJP_UNITS entries
+    const long long max_chunks = std::max(1LL, MAX_VJP_UNITS / std::max(1LL, d->n_tiles));
+    d->chunk = (int)std::min((d->n_cand + max_chunks - 1) / max_chunks, 1LL << 30);
+    d->n_chunks = (d->n_cand + d->chunk - 1) / d->chunk;
+  }
   d->n_units = d->n_tiles * d->n_chunks;
   int per_sm = (t && t->ctas_per_sm) ? t->ctas_per_sm : 0;
   if (per_sm == 0) {
@@ -181,9 +190,14 @@ void gamma_powers(float gamma, float* gk) {
   for (int k = 1; k <= DRT_MAX_ORDER; ++k) gk[k] = gk[k - 1] * gamma;
 }
 
+// drt_vjp's workspace: [16 bytes: the work-stealing counter][ctas][W][VJP_SLOTS]
+// wall partials, [warps][2] TX partials, then [n_units][2] per-unit TX adjoints
+// (n_units <= max(MAX_VJP_UNITS, receiver tiles)).  The other adjoints use the
+// same size from offset 0.
 size_t vjp_workspace(const drt_scene* sc, const Decomp& d) {
   const size_t warps = (size_t)d.ctas * (d.threads / 32);
-  return (size_t)d.ctas * sc->n_walls * VJP_SLOTS * sizeof(float) + warps * 2 * sizeof(float);
+  return 16 + (size_t)d.ctas * sc->n_walls * VJP_SLOTS * sizeof(float) +
+         warps * 2 * sizeof(float) + (size_t)d.n_units * 2 * sizeof(float);
 }
 
 }  // namespace
@@ -809,8 +823,10 @@ drt_status vjp_impl(const drt_scene* scene, const drt_tile* tile, const float* g
   a.pairs = d.pairs;
   a.grad_power = grad_power;
   float* ws = static_cast<float*>(workspace);
-  a.cta_walls = ws;
-  a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.cta_walls = ws + 4;
+  a.warp_tx = a.cta_walls + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.unit_counter = static_cast<unsigned long long*>(workspace);
+  a.unit_tx = a.warp_tx + (size_t)d.ctas * (d.threads / 32) * 2;
   a.grad_tx = grad_tx;
   a.grad_walls = grad_walls;
   a.saved = saved;

@@ -121,6 +121,11 @@ struct VjpArgs {
   const float* grad_loss;    // [1] or null (one-receiver kernel)
   float* cta_walls;          // [ctas][W][9] per-CTA wall-gradient partials (wall gradient only)
   float* warp_tx;            // [ctas * warps_per_cta][2]
+  // receiver-tile kernels (drt_vjp): the work-stealing counter (zeroed by
+  // launch_vjp) and the per-unit TX adjoints [n_units][2]; null for the other
+  // adjoint kernels (per-warp TX adjoints in warp_tx)
+  unsigned long long* unit_counter;
+  float* unit_tx;
   float* grad_tx;            // [2]
   float* grad_walls;         // [W][4] or null
   // sigmoid: the forward's leg visibilities [n_cand][K + 1][R] (drt_forward_save), read

@@ -167,6 +167,24 @@ def test_vjp_deterministic_tx(drt):
     np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+def test_work_stealing_keeps_the_tx_gradient_bitwise(drt, smoothing):
+    """Warps take their units from a counter, so which warp handles which unit
+    changes from run to run; the TX gradient is added per unit in unit order and
+    must not change, with and without the wall gradient (the gradient scene: 128
+    walls, 128 x 128 receivers, 16,385 sequences, uneven units after the exact
+    zero-gradient skip)."""
+    sc = scenes.gradient_scene(alpha=100.0, smoothing=smoothing)
+    g = np.random.default_rng(3).normal(size=sc.n_rx)
+    for wall_grad in (True, False):
+        runs = [_vjp(drt, sc, g, wall_grad=wall_grad) for _ in range(3)]
+        for gtx, gw in runs[1:]:
+            np.testing.assert_array_equal(gtx, runs[0][0])
+            if wall_grad:
+                np.testing.assert_allclose(gw, runs[0][1], rtol=1e-4,
+                                           atol=1e-5 * np.abs(runs[0][1]).max())
+
+
 @pytest.mark.parametrize("seed,W,R,K,alpha,smoothing", CASES)
 def test_min_loss_vjp_matches_oracle(drt, oracle_mod, seed, W, R, K, alpha, smoothing):
     # loss = -P[argmin]: the one-receiver kernel (lanes = candidates) against the oracle
