@@ -121,7 +121,10 @@ drt_status drt_forward_workspace_size(const drt_scene* scene, const drt_tile* ti
    drt_forward_workspace_size bytes (contents undefined on return; 16-byte aligned
    when n_walls > DRT_MAX_WALLS: it then also holds the walls' records, which the
    kernels read through the caches instead of shared memory); tile: host pointer
-   or NULL for defaults. */
+   or NULL for defaults.  Warps take their (receiver tile, candidate chunk) units
+   from a counter that lives in power's first 8 bytes until the last kernel of the
+   call writes the powers (when n_rx >= 2 and power is 8-byte aligned; otherwise
+   the split is static); the powers do not depend on the split. */
 drt_status drt_forward(const drt_scene* scene, const drt_tile* tile, float* power,
                        void* workspace, size_t workspace_bytes, void* stream);
 

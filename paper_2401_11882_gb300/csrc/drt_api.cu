@@ -293,6 +293,10 @@ drt_status forward_impl(const drt_scene* scene, const drt_tile* tile, float* pow
                                                   forward_partials_bytes(scene, d))
                       : nullptr;
   a.saved = saved;
+  // the work-stealing counter borrows power's first 8 bytes: the forward kernel
+  // never touches power, and the chunk-sum kernel overwrites all of it afterwards
+  if (scene->n_rx >= 2 && aligned(power, 8))
+    a.unit_counter = reinterpret_cast<unsigned long long*>(power);
   cudaError_t e = launch_forward(a, scene->smoothing, d.ctas, d.threads,
                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");

@@ -40,6 +40,10 @@ struct FwdArgs {
   float* power;     // [R]
   float4* staged;   // [8 or 4][W] wall records in global memory (W > DRT_MAX_WALLS), or null
   float* saved;     // sigmoid: every path's leg visibilities [n_cand][K + 1][R], or null
+  // work-stealing counter (zeroed by launch_forward), or null for a static split;
+  // drt_forward points it at the first 8 bytes of `power`, which only the chunk-sum
+  // kernel writes, after the forward kernel has finished
+  unsigned long long* unit_counter;
 };
 
 // Coherent field (drt_field.cu): the forward's decomposition (one or two

@@ -363,3 +363,20 @@ def test_more_walls_than_shared_memory_holds(drt, oracle_mod, n_seg, K, alpha, s
     n = ctypes.c_size_t()
     _lib.call("drt_forward_workspace_size", ctypes.byref(desc), None, ctypes.byref(n))
     assert n.value >= 4 * 16 * sc.n_walls
+
+
+@pytest.mark.parametrize("smoothing", ["hard_sigmoid", "sigmoid"])
+def test_work_stealing_matches_the_static_split_bitwise(drt, smoothing):
+    """The forward's warps take units from a counter kept in the output's first 8
+    bytes; an output that is only 4-byte aligned runs the static split instead.
+    Every unit writes its own partial sums, so both give the same powers bit for
+    bit (benchmark scene: 64 walls, 256 x 256 receivers, 4097 sequences)."""
+    sc = scenes.large_scene(alpha=100.0, smoothing=smoothing)
+    dev = torch.device("cuda:0")
+    w, t, r = (torch.tensor(x, device=dev) for x in (sc.walls, sc.tx, sc.rx))
+    stolen = drt.forward(w, t, r, sc.max_order, 100.0, smoothing)
+    buf = torch.empty(sc.n_rx + 1, dtype=torch.float32, device=dev)
+    static = drt.forward(w, t, r, sc.max_order, 100.0, smoothing, out=buf[1:])
+    assert buf[1:].data_ptr() % 8 == 4
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(stolen.cpu().numpy(), static.cpu().numpy())
