@@ -209,8 +209,7 @@ __global__ void __launch_bounds__(256, WG ? 2 : 1) field_vjp_kernel(const VjpArg
   fw.k2pi = a.k2pi;
   fw.eps_r = a.eps_r;
   fw.refl_amp = a.refl_amp;
-  float txb_x = 0.f, txb_y = 0.f;
-  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+  for (long long u = gwarp; u < a.n_units; u = next_unit(a, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
@@ -221,25 +220,22 @@ __global__ void __launch_bounds__(256, WG ? 2 : 1) field_vjp_kernel(const VjpArg
     fw.wre = 2.f * gp * E.x;
     fw.wim = -2.f * gp * E.y;
     const float g = (fw.wre != 0.f || fw.wim != 0.f) ? 1.f : 0.f;
-    if (__all_sync(FULL, g == 0.f)) continue;
-    const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
-    const long long c0 = chunk * a.chunk;
-    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
-    for (long long c = c0; c < c1; ++c) {
-      const Cand cd = decode_candidate(c, a.W, a.K);
-      switch (cd.k) {
-        case 0: path_vjp<MODE, 0, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
-        case 1: path_vjp<MODE, 1, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
-        case 2: path_vjp<MODE, 2, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
-        default: path_vjp<MODE, 3, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, txb_x, txb_y, &fw); break;
+    float ux = 0.f, uy = 0.f;
+    if (!__all_sync(FULL, g == 0.f)) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(a.rx) + r);
+      const long long c0 = chunk * a.chunk;
+      const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+      for (long long c = c0; c < c1; ++c) {
+        const Cand cd = decode_candidate(c, a.W, a.K);
+        switch (cd.k) {
+          case 0: path_vjp<MODE, 0, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
+          case 1: path_vjp<MODE, 1, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
+          case 2: path_vjp<MODE, 2, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
+          default: path_vjp<MODE, 3, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
+        }
       }
     }
-  }
-  txb_x = warp_sum(txb_x);
-  txb_y = warp_sum(txb_y);
-  if (lane == 0) {
-    a.warp_tx[2 * gwarp] = txb_x;
-    a.warp_tx[2 * gwarp + 1] = txb_y;
+    unit_tx_done(a, u, lane, ux, uy);
   }
   if (WG) {
     __syncthreads();
@@ -439,6 +435,10 @@ cudaError_t launch_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaSt
 cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   const bool wg = a.grad_walls != nullptr;
   const size_t smem = vjp_smem_bytes(a.W, wg, false);
+  {   // the field adjoint steals work like the receiver-tile adjoints
+    cudaError_t e = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
   switch (mode * 2 + (wg ? 1 : 0)) {
     case MODE_SIGMOID * 2: field_vjp_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a); break;
     case MODE_SIGMOID * 2 + 1: field_vjp_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a); break;

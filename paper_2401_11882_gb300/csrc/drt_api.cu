@@ -122,8 +122,9 @@ drt_status check_tile(const drt_tile* t) {
 
 // Largest number of (chunk, receiver) partial sums the forward keeps.
 constexpr long long MAX_PARTIALS = 1LL << 26;
-// Most (receiver tile, candidate chunk) units drt_vjp splits its work into (its
-// per-unit TX adjoints take 8 bytes each; more tiles than this make one unit per tile).
+// Most (receiver tile, candidate chunk) units the dense adjoints (drt_vjp,
+// drt_field_vjp, drt3_vjp) split their work into: they keep one TX adjoint per unit
+// (8 or 12 bytes); more tiles than this make one unit per tile.
 constexpr long long MAX_VJP_UNITS = 1LL << 22;
 
 // VJP_RX: the min-loss adjoint's one-receiver kernel (lanes = candidates)
@@ -153,7 +154,8 @@ drt_status decompose(const drt_scene* sc, const drt_tile* t, Kernel kern, Decomp
               forward_uses_pairs(sc->smoothing, sc->alpha, t ? t->flags : 0)) ||
              (kern == VJP && vjp_uses_pairs(sc->smoothing, t ? t->flags : 0));
   d->n_tiles = d->pairs ? (R + 63) / 64 : (R + 31) / 32;
-  if ((kern == VJP || kern == VJP_TX) && d->n_tiles * d->n_chunks > MAX_VJP_UNITS) {
+  if ((kern == VJP || kern == VJP_TX || kern == FIELD_VJP || kern == VJP3 || kern == VJP3_TX) &&
+      d->n_tiles * d->n_chunks > MAX_VJP_UNITS) {
     // larger chunks keep drt_vjp's per-unit TX table within MAX_VJP_UNITS entries
     const long long max_chunks = std::max(1LL, MAX_VJP_UNITS / std::max(1LL, d->n_tiles));
     d->chunk = (int)std::min((d->n_cand + max_chunks - 1) / max_chunks, 1LL << 30);
@@ -412,6 +414,9 @@ drt_status finder_forward(int finder, const drt_scene* scene, const drt_tile* ti
   m.f.partial = static_cast<float*>(workspace);
   m.f.power = power;
   m.paths = nullptr;
+  // work stealing, the counter in power's first 8 bytes (as drt_forward)
+  if (scene->n_rx >= 2 && aligned(power, 8))
+    m.f.unit_counter = reinterpret_cast<unsigned long long*>(power);
   cudaError_t e = launch_forward_mpt(m, scene->smoothing, d.ctas, d.threads,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "path-finder forward launch");
@@ -511,7 +516,7 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
   if (!workspace || workspace_bytes < need || !aligned(workspace, 8))
     return fail(DRT_ERR_WORKSPACE, "field needs %zu 8-byte aligned workspace bytes, got %zu",
                 need, workspace_bytes);
-  FieldArgs a;
+  FieldArgs a{};
   a.walls = reinterpret_cast<const float4*>(scene->walls);
   a.W = scene->n_walls;
   a.rx = scene->rx;
@@ -535,6 +540,8 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
   a.partial = static_cast<float2*>(workspace);
   a.field = reinterpret_cast<float2*>(field);
   a.power = power;
+  // work stealing, the counter in field's first 8 bytes until the chunk sums land
+  if (aligned(field, 8)) a.unit_counter = reinterpret_cast<unsigned long long*>(field);
   cudaError_t e = launch_field(a, scene->smoothing, d.ctas, d.threads,
                                static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "field launch");
@@ -598,7 +605,7 @@ drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* po
   if (!workspace || workspace_bytes < need)
     return fail(DRT_ERR_WORKSPACE, "3D forward needs %zu workspace bytes, got %zu", need,
                 workspace_bytes);
-  Fwd3Args a;
+  Fwd3Args a{};
   a.tris = scene->tris;
   a.W = scene->n_tris;
   a.rx = scene->rx;
@@ -614,6 +621,10 @@ drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* po
   a.n_units = d.n_units;
   a.partial = static_cast<float*>(workspace);
   a.power = power;
+  // work stealing, the counter in power's first 8 bytes (as drt_forward)
+  a.unit_counter = (scene->n_rx >= 2 && aligned(power, 8))
+                       ? reinterpret_cast<unsigned long long*>(power)
+                       : nullptr;
   cudaError_t e = launch_forward3(a, scene->smoothing, d.ctas, d.threads,
                                   static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "3D forward launch");
@@ -630,9 +641,9 @@ drt_status drt3_vjp_workspace_size(const drt3_scene* scene, const drt_tile* tile
   Decomp d, dt;
   if ((st = decompose(&flat, tile, VJP3, &d)) != DRT_OK) return st;
   if ((st = decompose(&flat, tile, VJP3_TX, &dt)) != DRT_OK) return st;
-  *bytes = std::max(vjp3_workspace_floats(scene->n_tris, d.ctas, d.ctas * (d.threads / 32), true),
-                    vjp3_workspace_floats(scene->n_tris, dt.ctas, dt.ctas * (dt.threads / 32),
-                                          false)) * sizeof(float);
+  *bytes = std::max(vjp3_workspace_floats(scene->n_tris, d.ctas, d.n_units, true),
+                    vjp3_workspace_floats(scene->n_tris, dt.ctas, dt.n_units, false)) *
+           sizeof(float);
   return DRT_OK;
 }
 
@@ -649,9 +660,9 @@ drt_status drt3_vjp(const drt3_scene* scene, const drt_tile* tile, const float* 
     return fail(DRT_ERR_INVALID_ARG, "grad_tris must be 4-byte aligned");
   Decomp d;
   if ((st = decompose(&flat, tile, grad_tris ? VJP3 : VJP3_TX, &d)) != DRT_OK) return st;
-  const int warps = d.ctas * (d.threads / 32);
   const size_t need =
-      vjp3_workspace_floats(scene->n_tris, d.ctas, warps, grad_tris != nullptr) * sizeof(float);
+      vjp3_workspace_floats(scene->n_tris, d.ctas, d.n_units, grad_tris != nullptr) *
+      sizeof(float);
   if (!workspace || workspace_bytes < need || !aligned(workspace, 4))
     return fail(DRT_ERR_WORKSPACE, "3D vjp needs %zu workspace bytes, got %zu", need,
                 workspace_bytes);
@@ -671,8 +682,10 @@ drt_status drt3_vjp(const drt3_scene* scene, const drt_tile* tile, const float* 
   a.n_units = d.n_units;
   a.grad_power = grad_power;
   float* ws = static_cast<float*>(workspace);
-  a.warp_tx = ws;
-  a.cta_tris = grad_tris ? ws + (size_t)warps * 3 : nullptr;
+  // the counter on the first 8-byte boundary of the 4 leading floats
+  a.unit_counter = reinterpret_cast<unsigned long long*>(aligned(ws, 8) ? ws : ws + 1);
+  a.unit_tx = ws + 4;
+  a.cta_tris = grad_tris ? a.unit_tx + (size_t)d.n_units * 3 : nullptr;
   a.grad_tx = grad_tx;
   a.grad_tris = grad_tris;
   cudaError_t e = launch_vjp3(a, scene->smoothing, d.ctas, d.threads,
@@ -690,8 +703,7 @@ drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* t
   if (!bytes) return fail(DRT_ERR_INVALID_ARG, "bytes is NULL");
   Decomp d;
   if ((st = decompose(&flat, tile, VJP3_TX, &d)) != DRT_OK) return st;
-  *bytes = vjp3_workspace_floats(scene->n_tris, d.ctas, d.ctas * (d.threads / 32), false) *
-           sizeof(float);
+  *bytes = vjp3_workspace_floats(scene->n_tris, d.ctas, d.n_units, false) * sizeof(float);
   return DRT_OK;
 }
 
@@ -912,8 +924,10 @@ drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wav
   a.n_units = d.n_units;
   a.grad_power = grad_power;
   float* ws = static_cast<float*>(workspace);
-  a.cta_walls = ws;
-  a.warp_tx = ws + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.cta_walls = ws + 4;
+  a.warp_tx = a.cta_walls + (size_t)d.ctas * scene->n_walls * VJP_SLOTS;
+  a.unit_counter = static_cast<unsigned long long*>(workspace);
+  a.unit_tx = a.warp_tx + (size_t)d.ctas * (d.threads / 32) * 2;
   a.grad_tx = grad_tx;
   a.grad_walls = grad_walls;
   a.field = reinterpret_cast<const float2*>(field);

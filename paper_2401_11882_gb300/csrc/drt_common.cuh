@@ -44,6 +44,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // pipe and one compare.
 __device__ __forceinline__ bool same_side(float a, float b) { return a * b > 0.f; }
 
+// Work stealing of the persistent path kernels: a warp's first unit is its own
+// index; the next one is the static split's (counter == nullptr) or one taken from
+// a 64-bit counter that was zeroed before the launch, so no SM idles through a
+// ragged last wave.  Every unit writes its own partial sums: results do not depend
+// on which warp took which unit.  Warp-uniform; every lane must call it.
+__device__ __forceinline__ long long next_unit_of(unsigned long long* counter, long long u,
+                                                  long long nwarps, int lane) {
+  if (!counter) return u + nwarps;
+  unsigned long long v = 0;
+  if (lane == 0) v = atomicAdd(counter, 1ULL);
+  return nwarps + (long long)__shfl_sync(0xffffffffu, v, 0);
+}
+
 // ------------------------------------------------------------ smoothing
 // s(x; alpha) = s(alpha x) (Eq. 3) for the three functions of Sec. IV:
 // the value s(x), the complement s(-x) (by C4 equal to 1 - s(x), but

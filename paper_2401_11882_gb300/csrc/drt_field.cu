@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 2 : 3) field_kerne
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
   const bool masked = a.alpha > FAST_SKIP_MAX_ALPHA;
   for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
-       u += nwarps) {
+       u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, 2) field_pair_kernel(const FieldArgs a) {
   const long long warps_per_cta = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
   for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
-       u += nwarps) {
+       u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     const long long r0 = tile * 64 + lane, r1 = r0 + 32;
@@ -260,6 +260,10 @@ __global__ void reduce_field_kernel(const float2* __restrict__ partial, long lon
 
 cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   const size_t smem = forward_smem_bytes(a.W, a.pairs);
+  if (a.unit_counter && a.n_units > 0) {
+    cudaError_t e = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
   if (a.n_units > 0 && a.pairs) {
     if (mode == MODE_SIGMOID)
       field_pair_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);

@@ -24,18 +24,6 @@ namespace drt {
 
 namespace {
 
-// Work stealing: a warp's first unit is its own index, later ones come from
-// a.unit_counter (zeroed before the launch) when it is set, so no warp or SM idles
-// through a ragged last wave; otherwise the split is static.  Every unit writes
-// its own partial sums, so the result does not depend on which warp took it.
-__device__ __forceinline__ long long fwd_next_unit(const FwdArgs& a, long long u,
-                                                   long long nwarps, int lane) {
-  if (!a.unit_counter) return u + nwarps;
-  unsigned long long v = 0;
-  if (lane == 0) v = atomicAdd(a.unit_counter, 1ULL);
-  return nwarps + (long long)__shfl_sync(0xffffffffu, v, 0);
-}
-
 // GLOBAL: the wall records were written to a.staged by stage_global_kernel (scenes
 // with more walls than shared memory holds) and are read through the L1 / L2
 // caches instead of shared memory.  SAVE: every path's leg visibilities are also
@@ -53,7 +41,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
   const long long warps_per_cta = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
   for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
-       u = fwd_next_unit(a, u, nwarps, lane)) {
+       u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
@@ -121,7 +109,7 @@ __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
   const long long warps_per_cta = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
   for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
-       u = fwd_next_unit(a, u, nwarps, lane)) {
+       u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     const long long r0 = tile * 64 + lane, r1 = r0 + 32;

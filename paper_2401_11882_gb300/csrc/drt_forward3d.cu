@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256, 2) forward3_kernel(const Fwd3Args a) {
   const long long warps_per_cta = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
   for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
-       u += nwarps) {
+       u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
@@ -619,36 +619,40 @@ __global__ void __launch_bounds__(256, 1) vjp3_kernel(const Vjp3Args a) {
   const long long warps_per_cta = blockDim.x >> 5;
   const long long gwarp = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5);
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
-  float3 txb = make_float3(0.f, 0.f, 0.f);
-  for (long long u = gwarp; u < a.n_units; u += nwarps) {
+  // work stealing (next_unit_of): each unit's TX adjoint is summed over the warp and
+  // stored per unit; the finalize kernel adds the units in index order, so the TX
+  // gradient does not depend on which warp took which unit
+  for (long long u = gwarp; u < a.n_units; u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
     const bool live = r < a.R;
     if (!live) r = a.R - 1;
     const float g = live ? __ldg(a.grad_power + r) : 0.f;
-    if (__all_sync(0xffffffffu, g == 0.f)) continue;
-    const float3 q = make_float3(__ldg(a.rx + 3 * r), __ldg(a.rx + 3 * r + 1),
-                                 __ldg(a.rx + 3 * r + 2));
-    const long long c0 = chunk * a.chunk;
-    const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
-    for (long long c = c0; c < c1; ++c) {
-      const Cand cd = decode_candidate(c, a.W, a.K);
-      switch (cd.k) {
-        case 0: path_vjp3<MODE, 0, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb, acc); break;
-        case 1: path_vjp3<MODE, 1, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb, acc); break;
-        case 2: path_vjp3<MODE, 2, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb, acc); break;
-        default: path_vjp3<MODE, 3, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb, acc); break;
+    float3 txb = make_float3(0.f, 0.f, 0.f);
+    if (!__all_sync(0xffffffffu, g == 0.f)) {
+      const float3 q = make_float3(__ldg(a.rx + 3 * r), __ldg(a.rx + 3 * r + 1),
+                                   __ldg(a.rx + 3 * r + 2));
+      const long long c0 = chunk * a.chunk;
+      const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
+      for (long long c = c0; c < c1; ++c) {
+        const Cand cd = decode_candidate(c, a.W, a.K);
+        switch (cd.k) {
+          case 0: path_vjp3<MODE, 0, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[0], g, txb, acc); break;
+          case 1: path_vjp3<MODE, 1, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[1], g, txb, acc); break;
+          case 2: path_vjp3<MODE, 2, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[2], g, txb, acc); break;
+          default: path_vjp3<MODE, 3, WG>(s, a.W, tx, q, cd, a.alpha, a.gk[3], g, txb, acc); break;
+        }
       }
     }
-  }
-  txb.x = warp_sum3(txb.x);
-  txb.y = warp_sum3(txb.y);
-  txb.z = warp_sum3(txb.z);
-  if (lane == 0) {
-    a.warp_tx[3 * gwarp] = txb.x;
-    a.warp_tx[3 * gwarp + 1] = txb.y;
-    a.warp_tx[3 * gwarp + 2] = txb.z;
+    txb.x = warp_sum3(txb.x);
+    txb.y = warp_sum3(txb.y);
+    txb.z = warp_sum3(txb.z);
+    if (lane == 0) {
+      a.unit_tx[3 * u] = txb.x;
+      a.unit_tx[3 * u + 1] = txb.y;
+      a.unit_tx[3 * u + 2] = txb.z;
+    }
   }
   if (WG) {
     __syncthreads();
@@ -742,14 +746,28 @@ __global__ void __launch_bounds__(256) vjp3_tris_finalize_kernel(const Vjp3Args 
 }
 
 // grad_tx = sum of the per-warp partials, in warp order (one thread per component)
-__global__ void vjp3_finalize_kernel(const float* __restrict__ warp_tx, long long n_warps,
-                                     float* __restrict__ grad_tx) {
-  const int c = threadIdx.x;
-  if (c < 3) {
-    float acc = 0.f;
-    for (long long w = 0; w < n_warps; ++w) acc += warp_tx[3 * w + c];
-    grad_tx[c] = acc;
+// grad_tx = the sum of the per-unit TX adjoints, in a fixed order (one CTA of 256:
+// strided partial sums, then a tree)
+__global__ void __launch_bounds__(256) vjp3_finalize_kernel(const float* __restrict__ unit_tx,
+                                                            long long n_units,
+                                                            float* __restrict__ grad_tx) {
+  __shared__ float part[3][256];
+  float x = 0.f, y = 0.f, z = 0.f;
+  for (long long u = threadIdx.x; u < n_units; u += blockDim.x) {
+    x += unit_tx[3 * u];
+    y += unit_tx[3 * u + 1];
+    z += unit_tx[3 * u + 2];
   }
+  part[0][threadIdx.x] = x;
+  part[1][threadIdx.x] = y;
+  part[2][threadIdx.x] = z;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int c = 0; c < 3; ++c) part[c][threadIdx.x] += part[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) grad_tx[threadIdx.x] = part[threadIdx.x][0];
 }
 
 __global__ void reduce3_kernel(const float* __restrict__ partial, long long n_chunks, long long R,
@@ -1078,13 +1096,19 @@ size_t vjp3_smem_bytes(int W, bool tri_grad) {
   return forward3_smem_bytes(W) + (tri_grad ? (size_t)W * TRI_SLOTS * sizeof(float) : 0);
 }
 
-size_t vjp3_workspace_floats(int W, int ctas, int warps, bool tri_grad) {
-  return (size_t)warps * 3 + (tri_grad ? (size_t)ctas * W * TRI_SLOTS : 0);
+size_t vjp3_workspace_floats(int W, int ctas, long long n_units, bool tri_grad) {
+  // 4 floats for the 8-byte-aligned work-stealing counter, [n_units][3] TX adjoints,
+  // then the per-CTA triangle tables
+  return 4 + (size_t)n_units * 3 + (tri_grad ? (size_t)ctas * W * TRI_SLOTS : 0);
 }
 
 cudaError_t launch_forward3(const Fwd3Args& a, int mode, int ctas, int threads, cudaStream_t st) {
   const size_t smem = forward3_smem_bytes(a.W);
   if (a.n_units > 0) {
+    if (a.unit_counter) {
+      cudaError_t e = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return e;
+    }
     switch (mode) {
       case MODE_SIGMOID: forward3_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a); break;
       case MODE_HARD: forward3_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a); break;
@@ -1105,6 +1129,8 @@ cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cuda
   const bool wg = a.grad_tris != nullptr;
   const size_t smem = vjp3_smem_bytes(a.W, wg);
   if (a.n_units > 0) {
+    cudaError_t e0 = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
+    if (e0 != cudaSuccess) return e0;
     switch (mode * 2 + (wg ? 1 : 0)) {
       case MODE_SIGMOID * 2: vjp3_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a); break;
       case MODE_SIGMOID * 2 + 1: vjp3_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a); break;
@@ -1115,7 +1141,7 @@ cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cuda
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    vjp3_finalize_kernel<<<1, 32, 0, st>>>(a.warp_tx, (long long)ctas * (threads / 32), a.grad_tx);
+    vjp3_finalize_kernel<<<1, 256, 0, st>>>(a.unit_tx, a.n_units, a.grad_tx);
     if (wg) {
       vjp3_tris_finalize_kernel<<<(a.W + 255) / 256, 256, 0, st>>>(a, ctas);
     }

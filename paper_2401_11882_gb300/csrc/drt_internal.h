@@ -68,6 +68,9 @@ struct FieldArgs {
   float2* partial;   // [n_chunks][R]
   float2* field;     // [R]
   float* power;      // [R] or null
+  // work-stealing counter (zeroed by launch_field; drt_field points it at `field`,
+  // which only the chunk-sum kernel writes), or null for a static split
+  unsigned long long* unit_counter;
 };
 
 // 3D forward (drt_forward3d.cu): triangle walls, 3D receivers, one receiver per lane.
@@ -85,6 +88,9 @@ struct Fwd3Args {
   long long n_chunks, n_tiles, n_units;
   float* partial;      // [n_chunks][R]
   float* power;        // [R]
+  // work-stealing counter (zeroed by launch_forward3; drt3_forward points it at
+  // `power`, which only the chunk-sum kernel writes), or null for a static split
+  unsigned long long* unit_counter;
 };
 
 // 3D transmitter adjoint (drt_forward3d.cu): lanes are receivers; per-warp partials.
@@ -101,7 +107,8 @@ struct Vjp3Args {
   int chunk;
   long long n_chunks, n_tiles, n_units;
   const float* grad_power;   // [R]
-  float* warp_tx;            // [ctas * warps_per_cta][3]
+  unsigned long long* unit_counter;   // work stealing, zeroed by launch_vjp3
+  float* unit_tx;            // [n_units][3] per-unit TX adjoints
   float* grad_tx;            // [3]
   float* cta_tris;           // [ctas][W][16] per-CTA record adjoints (triangle gradient only)
   float* grad_tris;          // [W][9] or null
@@ -125,9 +132,9 @@ struct VjpArgs {
   const float* grad_loss;    // [1] or null (one-receiver kernel)
   float* cta_walls;          // [ctas][W][9] per-CTA wall-gradient partials (wall gradient only)
   float* warp_tx;            // [ctas * warps_per_cta][2]
-  // receiver-tile kernels (drt_vjp): the work-stealing counter (zeroed by
-  // launch_vjp) and the per-unit TX adjoints [n_units][2]; null for the other
-  // adjoint kernels (per-warp TX adjoints in warp_tx)
+  // receiver-tile kernels (drt_vjp, drt_field_vjp): the work-stealing counter
+  // (zeroed by launch_vjp / launch_field_vjp) and the per-unit TX adjoints
+  // [n_units][2]; null for the min-loss kernel (per-warp TX adjoints in warp_tx)
   unsigned long long* unit_counter;
   float* unit_tx;
   float* grad_tx;            // [2]
@@ -226,7 +233,7 @@ cudaError_t forward3_occupancy(int mode, int threads, int W, int* ctas_per_sm);
 cudaError_t forward3_set_smem_limit(int W);
 cudaError_t launch_vjp3(const Vjp3Args& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t vjp3_occupancy(int mode, bool tri_grad, int threads, int W, int* ctas_per_sm);
-size_t vjp3_workspace_floats(int W, int ctas, int warps, bool tri_grad);
+size_t vjp3_workspace_floats(int W, int ctas, long long n_units, bool tri_grad);
 
 cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cudaStream_t st);
 cudaError_t field_occupancy(int mode, bool pairs, int threads, int W, int* ctas_per_sm);

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(256, 2) forward_mpt_kernel(const MptArgs m) {
   const long long warps_per_cta = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * warps_per_cta;
   for (long long u = (long long)blockIdx.x * warps_per_cta + (threadIdx.x >> 5); u < a.n_units;
-       u += nwarps) {
+       u = next_unit_of(a.unit_counter, u, nwarps, lane)) {
     const long long tile = u % a.n_tiles;
     const long long chunk = u / a.n_tiles;
     long long r = tile * 32 + lane;
@@ -405,6 +405,10 @@ cudaError_t launch_mpt_t(F kern, const MptArgs& a, int ctas, int threads, cudaSt
 cudaError_t launch_forward_mpt(const MptArgs& a, int mode, int ctas, int threads, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (a.f.n_units > 0) {
+    if (a.f.unit_counter) {
+      e = cudaMemsetAsync(a.f.unit_counter, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return e;
+    }
     if (a.finder == FINDER_FPT) {
       switch (mode) {
         case MODE_SIGMOID: e = launch_mpt_t(forward_mpt_kernel<MODE_SIGMOID, FINDER_FPT>, a, ctas, threads, st); break;

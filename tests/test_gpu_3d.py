@@ -216,3 +216,15 @@ def test_power3_autograd_in_the_triangles(drt, oracle_mod):
                                           g.astype(np.float64), 0.5)
     assert_grad_close(tx.grad.cpu().numpy(), ref_tx, "autograd 3D grad_tx")
     assert_grad_close(tris.grad.cpu().numpy().ravel(), ref_tr.ravel(), "autograd 3D grad_tris")
+
+
+@pytest.mark.parametrize("tri_grad", [False, True])
+def test_work_stealing_keeps_the_tx_gradient_bitwise_on_the_room(drt, tri_grad):
+    """The 3D adjoint's warps take units from a counter; each unit's TX adjoint is
+    stored and added in unit order, so the TX gradient is the same bit for bit from
+    run to run (the room: 132 triangles, 64 x 64 receivers, uneven units)."""
+    sc = scenes.room3d(64, 100.0, "hard_sigmoid")
+    g = np.random.default_rng(4).normal(size=sc.n_rx).astype(np.float32)
+    runs = [_vjp3_full(drt, sc, g, tri_grad=tri_grad) for _ in range(3)]
+    for r in runs[1:]:
+        np.testing.assert_array_equal(r[0], runs[0][0])

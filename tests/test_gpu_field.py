@@ -256,3 +256,14 @@ def test_field_vjp_benchmark_scene_sampled(drt, oracle_mod):
                                     eps, g[idx], params, 0.5)
     got = np.concatenate([gtx, gw.ravel()])[params]
     _assert_field_grad_close(got, ref, "sampled gradient")
+
+
+def test_field_vjp_work_stealing_keeps_the_tx_gradient_bitwise(drt):
+    """The coherent-field adjoint takes its units from a counter; its TX gradient is
+    added per unit in unit order and does not change between runs."""
+    sc = scenes.gradient_scene(alpha=100.0, smoothing="hard_sigmoid")
+    g = np.random.default_rng(5).normal(size=sc.n_rx)
+    runs = [_field_vjp(drt, sc.walls, sc.tx, sc.rx, 2, 100.0, "hard_sigmoid", 0.02, 5.0, g)
+            for _ in range(3)]
+    for r in runs[1:]:
+        np.testing.assert_array_equal(r[0], runs[0][0])
