@@ -433,6 +433,12 @@ def measure_extras(drt, dev, sc, w, t, r):
     fvh = timed(lambda: drt.field_vjp(gw, gt, gr, 2, 100.0, "hard_sigmoid", 0.02, 5.0, fE, gp), 2)
     fEs, _ = drt.field(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0)
     fvs = timed(lambda: drt.field_vjp(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0, fEs, gp), 1)
+    # the same with the field forward's saved leg visibilities
+    fEs2, _, fsv = drt.field_save(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0)
+    ffss = timed(lambda: drt.field_save(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0), 1)
+    fvss = timed(lambda: drt.field_vjp(gw, gt, gr, 2, 100.0, "sigmoid", 0.02, 5.0, fEs2, gp,
+                                       saved=fsv), 1)
+    del fsv
     # batched descent on the first 64 scenes of the 4096-scene batch (4 starts each)
     from paper_2401_11882_gb300.batched import BatchedDescent
     full = scenes.scene_batch(64, 0)
@@ -495,7 +501,9 @@ def measure_extras(drt, dev, sc, w, t, r):
                                            "fwd_plus_adjoint_evals_per_s":
                                                g.n_rx * gc / (sfss + svss)}},
         "coherent_field": {"wavelength": 0.02, "eps_r": 5.0, "hard_fwd_ms": ffh * 1e3,
-                           "hard_vjp_ms": fvh * 1e3, "sigmoid_vjp_ms": fvs * 1e3}}
+                           "hard_vjp_ms": fvh * 1e3, "sigmoid_vjp_ms": fvs * 1e3,
+                           "sigmoid_saved_visibilities": {"fwd_save_ms": ffss * 1e3,
+                                                          "vjp_saved_ms": fvss * 1e3}}}
     return out
 
 

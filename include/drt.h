@@ -234,6 +234,23 @@ drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wav
                          float* grad_tx, float* grad_walls, void* workspace,
                          size_t workspace_bytes, void* stream);
 
+/* The coherent field with the leg visibilities kept for its adjoint (sigmoid):
+   drt_field_save is drt_field (same arguments and workspace) that also fills
+   `saved` in drt_forward_save's layout (drt_saved_vis_size floats, device, 4-byte
+   aligned, caller-owned); the values are drt_forward_save's, bit for bit (the
+   same obstruction loops).  drt_field_vjp_saved is drt_field_vjp given such a
+   `saved` for the same scene: its first wall sweep reads them instead; gradients
+   equal drt_field_vjp's within FP32 rounding.  Both need smoothing
+   DRT_SMOOTH_SIGMOID and n_walls <= DRT_MAX_WALLS (DRT_ERR_UNSUPPORTED otherwise);
+   a NULL or misaligned `saved` is DRT_ERR_INVALID_ARG. */
+drt_status drt_field_save(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                          float eps_r, float* field, float* power, float* saved,
+                          void* workspace, size_t workspace_bytes, void* stream);
+drt_status drt_field_vjp_saved(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                               float eps_r, const float* field, const float* grad_power,
+                               const float* saved, float* grad_tx, float* grad_walls,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------------
    3D scenes (Sec. VI: the method does not depend on the dimension).  Walls are
    triangles; planes replace lines, and a point lies on a triangle when its three

@@ -9,6 +9,8 @@ Public calls (PyTorch tensors on a CUDA device, float32):
 * ``field(...)``: the coherent reading of Eq. 7 (complex path fields, Fresnel
   reflection), field and power per receiver; ``field_power(...)`` is its power
   |E|^2, differentiable in ``walls`` and ``tx``; ``field_vjp`` the raw adjoint.
+* ``forward_save`` / ``field_save`` (sigmoid): the forward that also keeps every
+  path's leg visibilities, which ``vjp`` / ``field_vjp`` read with ``saved=``.
 * ``forward3(tris, tx, rx, ...)``: the 3D extension (triangle walls), power per receiver;
   ``power3`` differentiable in ``tris`` and ``tx``; ``vjp3`` its raw adjoint (``vjp3_tx``
   for the transmitter only).
@@ -20,12 +22,12 @@ Public calls (PyTorch tensors on a CUDA device, float32):
 The compiled CUDA library is loaded lazily, on the first call that needs it,
 so that the seeded scene generators (``scenes``) import without a GPU.
 """
-from .ops import (TileConfig, field, field_power, field_vjp, forward, forward3, forward_fpt,
-                  forward_mpt, forward_save, fpt_paths, loss, min_loss, min_loss_backward, min_loss_vjp,
-                  mpt_paths, num_candidates, objective, objective_host, power, power3, vjp, vjp3,
-                  vjp3_tx)
+from .ops import (TileConfig, field, field_power, field_save, field_vjp, forward, forward3,
+                  forward_fpt, forward_mpt, forward_save, fpt_paths, loss, min_loss,
+                  min_loss_backward, min_loss_vjp, mpt_paths, num_candidates, objective,
+                  objective_host, power, power3, vjp, vjp3, vjp3_tx)
 
-__all__ = ["TileConfig", "field", "field_power", "field_vjp", "forward", "forward3",
-           "forward_fpt", "forward_mpt", "forward_save", "fpt_paths", "loss", "min_loss", "min_loss_backward",
-           "min_loss_vjp", "mpt_paths", "num_candidates", "objective", "objective_host", "power",
-           "power3", "vjp", "vjp3", "vjp3_tx"]
+__all__ = ["TileConfig", "field", "field_power", "field_save", "field_vjp", "forward",
+           "forward3", "forward_fpt", "forward_mpt", "forward_save", "fpt_paths", "loss",
+           "min_loss", "min_loss_backward", "min_loss_vjp", "mpt_paths", "num_candidates",
+           "objective", "objective_host", "power", "power3", "vjp", "vjp3", "vjp3_tx"]

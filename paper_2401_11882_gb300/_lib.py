@@ -103,6 +103,10 @@ SIGNATURES = {
     "drt_saved_vis_size": (ctypes.c_int, [_P, _P]),
     "drt_forward_save": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
     "drt_vjp_saved": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "drt_field_save": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P,
+                                      _SZ, _P]),
+    "drt_field_vjp_saved": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P,
+                                           _P, _P, _P, _SZ, _P]),
     "drt_forward_fpt_workspace_size": (ctypes.c_int, [_P, _P, _P]),
     "drt_forward_fpt": (ctypes.c_int, [_P, _P, _I32, ctypes.c_float, _P, _P, _SZ, _P]),
     "drt_fpt_paths": (ctypes.c_int, [_P, _I32, ctypes.c_float, _P, _P]),

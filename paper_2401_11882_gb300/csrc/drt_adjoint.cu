@@ -183,8 +183,10 @@ __global__ void __launch_bounds__(DRT_VJP_PAIR_MAX_THREADS, DRT_VJP_PAIR_MIN_CTA
 
 // Adjoint of the coherent field's power |E_r|^2 with cotangent g_r: the same
 // mapping as vjp_kernel, each lane weighing its paths' fields by w = 2 g_r conj(E_r)
-// (E_r from drt_field, one load per unit).
-template <int MODE, bool WG>
+// (E_r from drt_field, one load per unit).  SAVED: the sigmoid's leg visibilities
+// come from a.saved (drt_field_save's or drt_forward_save's) instead of the first
+// wall sweep.
+template <int MODE, bool WG, bool SAVED = false>
 __global__ void __launch_bounds__(256, WG ? 2 : 1) field_vjp_kernel(const VjpArgs a) {
   extern __shared__ float4 smem[];
   const float2 tx = make_float2(__ldg(a.tx), __ldg(a.tx + 1));
@@ -227,11 +229,12 @@ __global__ void __launch_bounds__(256, WG ? 2 : 1) field_vjp_kernel(const VjpArg
       const long long c1 = min(c0 + (long long)a.chunk, a.n_cand);
       for (long long c = c0; c < c1; ++c) {
         const Cand cd = decode_candidate(c, a.W, a.K);
+        const float* sv = SAVED ? a.saved + c * (a.K + 1) * a.R + r : nullptr;
         switch (cd.k) {
-          case 0: path_vjp<MODE, 0, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
-          case 1: path_vjp<MODE, 1, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
-          case 2: path_vjp<MODE, 2, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
-          default: path_vjp<MODE, 3, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw); break;
+          case 0: path_vjp<MODE, 0, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw, sv, a.R); break;
+          case 1: path_vjp<MODE, 1, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw, sv, a.R); break;
+          case 2: path_vjp<MODE, 2, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw, sv, a.R); break;
+          default: path_vjp<MODE, 3, WG, true, true>(s, a.W, tx, q, cd, a.alpha, 1.f, g, ux, uy, &fw, sv, a.R); break;
         }
       }
     }
@@ -439,9 +442,20 @@ cudaError_t launch_field_vjp(const VjpArgs& a, int mode, int ctas, int threads, 
     cudaError_t e = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
+  const bool saved = a.saved && mode == MODE_SIGMOID;
   switch (mode * 2 + (wg ? 1 : 0)) {
-    case MODE_SIGMOID * 2: field_vjp_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a); break;
-    case MODE_SIGMOID * 2 + 1: field_vjp_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a); break;
+    case MODE_SIGMOID * 2:
+      if (saved)
+        field_vjp_kernel<MODE_SIGMOID, false, true><<<ctas, threads, smem, st>>>(a);
+      else
+        field_vjp_kernel<MODE_SIGMOID, false><<<ctas, threads, smem, st>>>(a);
+      break;
+    case MODE_SIGMOID * 2 + 1:
+      if (saved)
+        field_vjp_kernel<MODE_SIGMOID, true, true><<<ctas, threads, smem, st>>>(a);
+      else
+        field_vjp_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a);
+      break;
     case MODE_HARD * 2: field_vjp_kernel<MODE_HARD, false><<<ctas, threads, smem, st>>>(a); break;
     case MODE_HARD * 2 + 1: field_vjp_kernel<MODE_HARD, true><<<ctas, threads, smem, st>>>(a); break;
     case MODE_STEP * 2: field_vjp_kernel<MODE_STEP, false><<<ctas, threads, smem, st>>>(a); break;
@@ -508,6 +522,12 @@ cudaError_t vjp_set_smem_limit(int W) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(vjp_kernel<MODE_SIGMOID, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, s0);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(field_vjp_kernel<MODE_SIGMOID, true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(field_vjp_kernel<MODE_SIGMOID, false, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, s0);
   if (e != cudaSuccess) return e;
 #define DRT_SET(M, B, S)                                                                    \

@@ -495,9 +495,10 @@ drt_status drt_field_workspace_size(const drt_scene* scene, const drt_tile* tile
   return DRT_OK;
 }
 
-drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelength, float eps_r,
-                     float* field, float* power, void* workspace, size_t workspace_bytes,
-                     void* stream) {
+namespace {
+drt_status field_impl(const drt_scene* scene, const drt_tile* tile, float wavelength, float eps_r,
+                      float* field, float* power, float* saved, void* workspace,
+                      size_t workspace_bytes, void* stream) {
   drt_status st = check_scene(scene);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
@@ -542,10 +543,29 @@ drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelen
   a.power = power;
   // work stealing, the counter in field's first 8 bytes until the chunk sums land
   if (aligned(field, 8)) a.unit_counter = reinterpret_cast<unsigned long long*>(field);
+  a.saved = saved;
   cudaError_t e = launch_field(a, scene->smoothing, d.ctas, d.threads,
                                static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "field launch");
   return DRT_OK;
+}
+}  // namespace
+
+drt_status drt_field(const drt_scene* scene, const drt_tile* tile, float wavelength, float eps_r,
+                     float* field, float* power, void* workspace, size_t workspace_bytes,
+                     void* stream) {
+  return field_impl(scene, tile, wavelength, eps_r, field, power, nullptr, workspace,
+                    workspace_bytes, stream);
+}
+
+drt_status drt_field_save(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                          float eps_r, float* field, float* power, float* saved,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_saved(scene, saved, nullptr)) != DRT_OK) return st;
+  return field_impl(scene, tile, wavelength, eps_r, field, power, saved, workspace,
+                    workspace_bytes, stream);
 }
 
 // The 3D scene's counts and options in a drt_scene, for the shared decomposition.
@@ -882,10 +902,11 @@ drt_status drt_field_vjp_workspace_size(const drt_scene* scene, const drt_tile* 
   return DRT_OK;
 }
 
-drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wavelength,
-                         float eps_r, const float* field, const float* grad_power,
-                         float* grad_tx, float* grad_walls, void* workspace,
-                         size_t workspace_bytes, void* stream) {
+namespace {
+drt_status field_vjp_impl(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                          float eps_r, const float* field, const float* grad_power,
+                          const float* saved, float* grad_tx, float* grad_walls,
+                          void* workspace, size_t workspace_bytes, void* stream) {
   drt_status st = check_scene(scene);
   if (st != DRT_OK) return st;
   if ((st = check_tile(tile)) != DRT_OK) return st;
@@ -938,10 +959,31 @@ drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wav
   // as in drt_field: eps_r = 1 is the zero coefficient
   a.refl_amp = eps_r == 0.f ? -(float)std::sqrt((double)scene->refl_coef) : 0.f;
   a.eps_r = eps_r == 1.f ? 0.f : eps_r;
+  a.saved = saved;
   cudaError_t e = launch_field_vjp(a, scene->smoothing, d.ctas, d.threads,
                                    static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "field vjp launch");
   return DRT_OK;
+}
+}  // namespace
+
+drt_status drt_field_vjp(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                         float eps_r, const float* field, const float* grad_power,
+                         float* grad_tx, float* grad_walls, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  return field_vjp_impl(scene, tile, wavelength, eps_r, field, grad_power, nullptr, grad_tx,
+                        grad_walls, workspace, workspace_bytes, stream);
+}
+
+drt_status drt_field_vjp_saved(const drt_scene* scene, const drt_tile* tile, float wavelength,
+                               float eps_r, const float* field, const float* grad_power,
+                               const float* saved, float* grad_tx, float* grad_walls,
+                               void* workspace, size_t workspace_bytes, void* stream) {
+  drt_status st = check_scene(scene);
+  if (st != DRT_OK) return st;
+  if ((st = check_saved(scene, saved, nullptr)) != DRT_OK) return st;
+  return field_vjp_impl(scene, tile, wavelength, eps_r, field, grad_power, saved, grad_tx,
+                        grad_walls, workspace, workspace_bytes, stream);
 }
 
 drt_status drt_min_loss_vjp(const drt_scene* scene, const drt_tile* tile, const int32_t* argmin,

@@ -70,7 +70,8 @@ __device__ __forceinline__ float2 field_of_path(const SmemWalls& s, const FieldA
 // Field of one path candidate of order K for this lane's receiver.
 template <int MODE, int K, bool MASKED>
 __device__ __forceinline__ float2 path_field(const SmemWalls& s, const FieldArgs& a, float2 tx,
-                                             float2 rx, const Cand& cd) {
+                                             float2 rx, const Cand& cd,
+                                             float* vis_out = nullptr) {
   float Ix[K + 1], Iy[K + 1];
   tx_images<K>(s, tx, cd, Ix, Iy);
   PathGeom<MODE, K> g;
@@ -85,6 +86,10 @@ __device__ __forceinline__ float2 path_field(const SmemWalls& s, const FieldArgs
     if (__any_sync(0xffffffffu, bad))
       leg_visibility<MODE, K, true>(s, a.W, cd, g.Qx, g.Qy, g.mx, g.my, g.mc, vis);
   }
+  if (vis_out) {
+#pragma unroll
+    for (int j = 0; j <= K; ++j) vis_out[j] = vis[j];
+  }
   return field_of_path<MODE, K>(s, a, g, vis, cd);
 }
 
@@ -94,7 +99,7 @@ template <int MODE, int K>
 __device__ __forceinline__ void path_field_pair(const SmemWalls& s, const SmemPairs& p,
                                                 const FieldArgs& a, float2 tx, float2 rx0,
                                                 float2 rx1, const Cand& cd, float2& f0,
-                                                float2& f1) {
+                                                float2& f1, float2* vis_out = nullptr) {
   float Ix[K + 1], Iy[K + 1];
   tx_images<K>(s, tx, cd, Ix, Iy);
   PathGeom<MODE, K> g0, g1;
@@ -139,24 +144,30 @@ __device__ __forceinline__ void path_field_pair(const SmemWalls& s, const SmemPa
     leg_visibility<MODE, K, true>(s, a.W, cd, g0.Qx, g0.Qy, g0.mx, g0.my, g0.mc, vis0);
   if (__any_sync(0xffffffffu, !g1.degenerate && !(d1 >= 0.25f)))
     leg_visibility<MODE, K, true>(s, a.W, cd, g1.Qx, g1.Qy, g1.mx, g1.my, g1.mc, vis1);
+  if (vis_out) {
+#pragma unroll
+    for (int j = 0; j <= K; ++j) vis_out[j] = f2(vis0[j], vis1[j]);
+  }
   f0 = field_of_path<MODE, K>(s, a, g0, vis0, cd);
   f1 = field_of_path<MODE, K>(s, a, g1, vis1, cd);
 }
 
 template <int MODE, bool MASKED>
 __device__ __forceinline__ float2 field_of(const SmemWalls& s, const FieldArgs& a, float2 tx,
-                                           float2 q, const Cand& cd) {
+                                           float2 q, const Cand& cd, float* vis_out) {
   switch (cd.k) {
-    case 0: return path_field<MODE, 0, MASKED>(s, a, tx, q, cd);
-    case 1: return path_field<MODE, 1, MASKED>(s, a, tx, q, cd);
-    case 2: return path_field<MODE, 2, MASKED>(s, a, tx, q, cd);
-    default: return path_field<MODE, 3, MASKED>(s, a, tx, q, cd);
+    case 0: return path_field<MODE, 0, MASKED>(s, a, tx, q, cd, vis_out);
+    case 1: return path_field<MODE, 1, MASKED>(s, a, tx, q, cd, vis_out);
+    case 2: return path_field<MODE, 2, MASKED>(s, a, tx, q, cd, vis_out);
+    default: return path_field<MODE, 3, MASKED>(s, a, tx, q, cd, vis_out);
   }
 }
 
 // One receiver per lane; a unit is (32 receivers) x (a chunk of candidates), as in
-// the forward kernel, with one (re, im) partial sum per (chunk, receiver).
-template <int MODE>
+// the forward kernel, with one (re, im) partial sum per (chunk, receiver).  SAVE
+// (sigmoid): every path's leg visibilities also go to a.saved, as drt_forward_save
+// writes them (the same values: the same obstruction loops).
+template <int MODE, bool SAVE = false>
 __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 2 : 3) field_kernel(const FieldArgs a) {
   extern __shared__ float4 smem[];
   SmemWalls s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
@@ -179,13 +190,23 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 2 : 3) field_kerne
     const int c0 = (int)(chunk * a.chunk);
     const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
     float2 acc = make_float2(0.f, 0.f);
+    float vbuf[KMAX + 1];   // the path's leg visibilities when they are saved
+    float* vo = SAVE ? vbuf : nullptr;
     Cand cd = decode_candidate(c0, a.W, a.K);
     for (int i = 0; i < nc; ++i) {
       if (i > 0) next_candidate(cd, a.W);
-      const float2 f = masked ? field_of<MODE, true>(s, a, tx, q, cd)
-                              : field_of<MODE, false>(s, a, tx, q, cd);
+      if (vo) {
+#pragma unroll
+        for (int j = 0; j <= KMAX; ++j) vbuf[j] = 0.f;
+      }
+      const float2 f = masked ? field_of<MODE, true>(s, a, tx, q, cd, vo)
+                              : field_of<MODE, false>(s, a, tx, q, cd, vo);
       acc.x += f.x;
       acc.y += f.y;
+      if (vo && live) {   // [n_cand][K + 1][R]
+        float* dst = a.saved + (long long)(c0 + i) * (a.K + 1) * a.R + r;
+        for (int j = 0; j <= cd.k; ++j) dst[j * a.R] = vbuf[j];
+      }
     }
     if (live) a.partial[chunk * a.R + r] = acc;
   }
@@ -194,7 +215,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 2 : 3) field_kerne
 // Hard sigmoid and sigmoid, two receivers per lane: lane l holds receivers l and
 // l + 32 of its 64-receiver tile; the walls' paired records follow the four
 // single-receiver arrays in shared memory.
-template <int MODE>
+template <int MODE, bool SAVE = false>
 __global__ void __launch_bounds__(256, 2) field_pair_kernel(const FieldArgs a) {
   extern __shared__ float4 smem[];
   SmemWalls s{smem, smem + a.W, smem + 2 * a.W, smem + 3 * a.W};
@@ -219,20 +240,33 @@ __global__ void __launch_bounds__(256, 2) field_pair_kernel(const FieldArgs a) {
     const int c0 = (int)(chunk * a.chunk);
     const int nc = (int)(min(c0 + (long long)a.chunk, a.n_cand) - c0);
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    float2 vbuf[KMAX + 1];   // the path's leg visibilities when they are saved
+    float2* vo = SAVE ? vbuf : nullptr;
     Cand cd = decode_candidate(c0, a.W, a.K);
     for (int i = 0; i < nc; ++i) {
       if (i > 0) next_candidate(cd, a.W);
+      if (vo) {
+#pragma unroll
+        for (int j = 0; j <= KMAX; ++j) vbuf[j] = make_float2(0.f, 0.f);
+      }
       float2 f0, f1;
       switch (cd.k) {
-        case 0: path_field_pair<MODE, 0>(s, pr, a, tx, q0, q1, cd, f0, f1); break;
-        case 1: path_field_pair<MODE, 1>(s, pr, a, tx, q0, q1, cd, f0, f1); break;
-        case 2: path_field_pair<MODE, 2>(s, pr, a, tx, q0, q1, cd, f0, f1); break;
-        default: path_field_pair<MODE, 3>(s, pr, a, tx, q0, q1, cd, f0, f1); break;
+        case 0: path_field_pair<MODE, 0>(s, pr, a, tx, q0, q1, cd, f0, f1, vo); break;
+        case 1: path_field_pair<MODE, 1>(s, pr, a, tx, q0, q1, cd, f0, f1, vo); break;
+        case 2: path_field_pair<MODE, 2>(s, pr, a, tx, q0, q1, cd, f0, f1, vo); break;
+        default: path_field_pair<MODE, 3>(s, pr, a, tx, q0, q1, cd, f0, f1, vo); break;
       }
       acc0.x += f0.x;
       acc0.y += f0.y;
       acc1.x += f1.x;
       acc1.y += f1.y;
+      if (vo) {   // [n_cand][K + 1][R]
+        float* dst = a.saved + (long long)(c0 + i) * (a.K + 1) * a.R;
+        for (int j = 0; j <= cd.k; ++j) {
+          if (live0) dst[j * a.R + r0] = vbuf[j].x;
+          if (live1) dst[j * a.R + r1] = vbuf[j].y;
+        }
+      }
     }
     if (live0) a.partial[chunk * a.R + r0] = acc0;
     if (live1) a.partial[chunk * a.R + r1] = acc1;
@@ -264,8 +298,11 @@ cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cu
     cudaError_t e = cudaMemsetAsync(a.unit_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
   }
+  const bool save = a.saved && mode == MODE_SIGMOID;
   if (a.n_units > 0 && a.pairs) {
-    if (mode == MODE_SIGMOID)
+    if (mode == MODE_SIGMOID && save)
+      field_pair_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a);
+    else if (mode == MODE_SIGMOID)
       field_pair_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);
     else
       field_pair_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a);
@@ -273,7 +310,12 @@ cudaError_t launch_field(const FieldArgs& a, int mode, int ctas, int threads, cu
     if (e != cudaSuccess) return e;
   } else if (a.n_units > 0) {
     switch (mode) {
-      case MODE_SIGMOID: field_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a); break;
+      case MODE_SIGMOID:
+        if (save)
+          field_kernel<MODE_SIGMOID, true><<<ctas, threads, smem, st>>>(a);
+        else
+          field_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);
+        break;
       case MODE_HARD: field_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a); break;
       default: field_kernel<MODE_STEP><<<ctas, threads, smem, st>>>(a); break;
     }
@@ -318,7 +360,13 @@ cudaError_t field_set_smem_limit(int W) {
   e = cudaFuncSetAttribute(field_pair_kernel<MODE_SIGMOID>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(field_pair_kernel<MODE_SIGMOID, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(field_kernel<MODE_SIGMOID>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(field_kernel<MODE_SIGMOID, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(field_kernel<MODE_HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -68,6 +68,7 @@ struct FieldArgs {
   float2* partial;   // [n_chunks][R]
   float2* field;     // [R]
   float* power;      // [R] or null
+  float* saved;      // sigmoid: every path's leg visibilities [n_cand][K + 1][R], or null
   // work-stealing counter (zeroed by launch_field; drt_field points it at `field`,
   // which only the chunk-sum kernel writes), or null for a static split
   unsigned long long* unit_counter;

@@ -551,7 +551,7 @@ __device__ __forceinline__ void path_vjp(const VSmem& s, int W, float2 tx, float
     mck[j] = -mq[j] * kap;
   }
   if constexpr (MODE == MODE_SIGMOID) {
-    if (!FIELD && saved) {   // the forward's visibilities of this path (sweep 1 done there)
+    if (saved) {   // the forward's visibilities of this path (sweep 1 done there)
       // A path the forward found degenerate (a zero-length leg) has no finite
       // visibilities there and contributes nothing: such lanes, and lanes already
       // at weight 0, take 1 so that their zero weight stays an exact zero.

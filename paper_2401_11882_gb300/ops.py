@@ -195,14 +195,8 @@ def fpt_paths(walls, tx, rx, max_order: int, alpha: float, smoothing: str = "har
                          refl_coef)
 
 
-def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
-          eps_r: float, refl_coef: float = 0.5, tile: TileConfig | None = None):
-    """Coherent field and power per receiver on the current stream:
-    (field float32 [R, 2] = (re, im), power float32 [R] = |field|^2).
-
-    Eq. 7 as a sum of complex path fields prod_j C_j V vis exp(-2 pi i L / wavelength) / L,
-    C_j the Fresnel TE coefficient of relative permittivity ``eps_r`` (>= 1) at
-    each reflection, or -sqrt(refl_coef) when ``eps_r`` is 0 (drt_field)."""
+def _field(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef, tile,
+           save):
     sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
     dev = keep[0].device
     tl = tile.as_c() if tile else None
@@ -212,17 +206,48 @@ def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelengt
     ws = _workspace(dev, nbytes.value)
     E = torch.empty(sc.n_rx, 2, dtype=torch.float32, device=dev)
     power = torch.empty(sc.n_rx, dtype=torch.float32, device=dev)
-    _lib.call("drt_field", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
-              ctypes.c_float(eps_r), _ptr(E), _ptr(power), _ptr(ws),
+    if not save:
+        _lib.call("drt_field", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
+                  ctypes.c_float(eps_r), _ptr(E), _ptr(power), _ptr(ws),
+                  ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
+        return E, power
+    n = ctypes.c_int64()
+    _lib.call("drt_saved_vis_size", ctypes.byref(sc), ctypes.byref(n))
+    saved = torch.empty(max(int(n.value), 1), dtype=torch.float32, device=dev)
+    _lib.call("drt_field_save", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
+              ctypes.c_float(eps_r), _ptr(E), _ptr(power), _ptr(saved), _ptr(ws),
               ctypes.c_size_t(ws.numel()), _stream_ptr(dev))
-    return E, power
+    return E, power, saved
+
+
+def field(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
+          eps_r: float, refl_coef: float = 0.5, tile: TileConfig | None = None):
+    """Coherent field and power per receiver on the current stream:
+    (field float32 [R, 2] = (re, im), power float32 [R] = |field|^2).
+
+    Eq. 7 as a sum of complex path fields prod_j C_j V vis exp(-2 pi i L / wavelength) / L,
+    C_j the Fresnel TE coefficient of relative permittivity ``eps_r`` (>= 1) at
+    each reflection, or -sqrt(refl_coef) when ``eps_r`` is 0 (drt_field)."""
+    return _field(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef,
+                  tile, False)
+
+
+def field_save(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
+               eps_r: float, refl_coef: float = 0.5, tile: TileConfig | None = None):
+    """(field, power, saved): ``field`` that also keeps every path's leg visibilities
+    (the sigmoid; forward_save's layout and values) for ``field_vjp(..., saved=saved)``."""
+    return _field(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef,
+                  tile, True)
 
 
 def field_vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavelength: float,
               eps_r: float, field_values: torch.Tensor, grad_power: torch.Tensor,
-              refl_coef: float = 0.5, wall_grad: bool = True, tile: TileConfig | None = None):
+              refl_coef: float = 0.5, wall_grad: bool = True, tile: TileConfig | None = None,
+              saved: torch.Tensor | None = None):
     """(grad_tx [2], grad_walls [W, 4] or None) = grad_power^T d|E|^2 / d(tx, walls), with
-    ``field_values`` the [R, 2] field that ``field`` returned for the same arguments."""
+    ``field_values`` the [R, 2] field that ``field`` returned for the same arguments.
+    ``saved``: the visibilities of ``field_save`` or ``forward_save`` on the same scene
+    (drt_field_vjp_saved), or None."""
     sc, keep = make_scene(walls, tx, rx, max_order, alpha, smoothing, refl_coef)
     dev = keep[0].device
     gp = _as_f32(grad_power.reshape(-1, 1), 1, "grad_power", 4)
@@ -236,10 +261,17 @@ def field_vjp(walls, tx, rx, max_order: int, alpha: float, smoothing: str, wavel
     ws = _workspace(dev, nbytes.value)
     gtx = torch.empty(2, dtype=torch.float32, device=dev)
     gw = torch.empty(sc.n_walls, 4, dtype=torch.float32, device=dev) if wall_grad else None
-    _lib.call("drt_field_vjp", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
-              ctypes.c_float(eps_r), _ptr(E), _ptr(gp), _ptr(gtx),
-              None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
-              _stream_ptr(dev))
+    if saved is None:
+        _lib.call("drt_field_vjp", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
+                  ctypes.c_float(eps_r), _ptr(E), _ptr(gp), _ptr(gtx),
+                  None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                  _stream_ptr(dev))
+    else:
+        sv = _as_f32(saved.reshape(-1, 1), 1, "saved", 4)
+        _lib.call("drt_field_vjp_saved", ctypes.byref(sc), tlp, ctypes.c_float(wavelength),
+                  ctypes.c_float(eps_r), _ptr(E), _ptr(gp), _ptr(sv), _ptr(gtx),
+                  None if gw is None else _ptr(gw), _ptr(ws), ctypes.c_size_t(ws.numel()),
+                  _stream_ptr(dev))
     return gtx, gw
 
 
@@ -537,26 +569,39 @@ class MinLossFunction(torch.autograd.Function):
 
 class FieldPowerFunction(torch.autograd.Function):
     """|E|^2 of the coherent field, with drt_field_vjp as backward (the field E is
-    saved; the geometry is recomputed)."""
+    saved; the geometry is recomputed; for the sigmoid the leg visibilities are kept
+    as in PowerFunction)."""
 
     @staticmethod
     def forward(ctx, walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef,
                 tile):
-        E, P = field(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, refl_coef,
-                     tile)
-        ctx.save_for_backward(walls, tx, rx, E)
+        saved = None
+        if (smoothing == "sigmoid" and walls.shape[0] <= 1024 and rx.shape[0] > 0 and
+                (ctx.needs_input_grad[0] or ctx.needs_input_grad[1])):
+            n = saved_vis_floats(walls, tx, rx, max_order, alpha, smoothing)
+            if 4 * n <= _saved_vis_limit():
+                E, P, saved = field_save(walls, tx, rx, max_order, alpha, smoothing,
+                                         wavelength, eps_r, refl_coef, tile)
+        if saved is None:
+            E, P = field(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r,
+                         refl_coef, tile)
+            ctx.save_for_backward(walls, tx, rx, E)
+        else:
+            ctx.save_for_backward(walls, tx, rx, E, saved)
         ctx.args = (max_order, alpha, smoothing, wavelength, eps_r, refl_coef, tile)
         return P
 
     @staticmethod
     def backward(ctx, grad_power):
-        walls, tx, rx, E = ctx.saved_tensors
+        walls, tx, rx, E, *rest = ctx.saved_tensors
+        saved = rest[0] if rest else None
         max_order, alpha, smoothing, wavelength, eps_r, refl_coef, tile = ctx.args
         need_w, need_tx = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         if not (need_w or need_tx):
             return (None,) * 10
         gtx, gw = field_vjp(walls, tx, rx, max_order, alpha, smoothing, wavelength, eps_r, E,
-                            grad_power.contiguous(), refl_coef, wall_grad=need_w, tile=tile)
+                            grad_power.contiguous(), refl_coef, wall_grad=need_w, tile=tile,
+                            saved=saved)
         return (gw if need_w else None, gtx.reshape(tx.shape) if need_tx else None,
                 None, None, None, None, None, None, None, None)
 

@@ -238,3 +238,15 @@ def test_saved_visibilities_size_host_only(lib):
     p = ctypes.c_void_p(256)
     assert lib.drt_forward_save(ctypes.byref(sc), None, p, p, p, 1 << 20, None) == 2
     assert lib.drt_vjp_saved(ctypes.byref(sc), None, p, p, p, None, p, 1 << 20, None) == 2
+    # the coherent field's pair: also refused for the hard sigmoid, and for a NULL
+    # buffer with the sigmoid, before anything is enqueued
+    f = ctypes.c_float
+    assert lib.drt_field_save(ctypes.byref(sc), None, f(0.02), f(5.0), p, p, p, p, 1 << 20,
+                              None) == 2
+    assert lib.drt_field_vjp_saved(ctypes.byref(sc), None, f(0.02), f(5.0), p, p, p, p, None,
+                                   p, 1 << 20, None) == 2
+    sg = _scene(n_walls=4, n_rx=3, max_order=1, smoothing=0)
+    assert lib.drt_field_save(ctypes.byref(sg), None, f(0.02), f(5.0), p, p, None, p, 1 << 20,
+                              None) == 1
+    assert lib.drt_field_vjp_saved(ctypes.byref(sg), None, f(0.02), f(5.0), p, p, None, p,
+                                   None, p, 1 << 20, None) == 1

@@ -267,3 +267,81 @@ def test_field_vjp_work_stealing_keeps_the_tx_gradient_bitwise(drt):
             for _ in range(3)]
     for r in runs[1:]:
         np.testing.assert_array_equal(r[0], runs[0][0])
+
+
+@pytest.mark.parametrize("single_rx", [False, True])
+@pytest.mark.parametrize("seed,W,R,K,alpha,lam,eps", [(40, 6, 45, 1, 20.0, 0.05, 4.0),
+                                                      (41, 8, 70, 2, 50.0, 0.03, 0.0),
+                                                      (42, 5, 33, 3, 15.0, 0.1, 2.0)])
+def test_field_saved_visibilities(drt, oracle_mod, single_rx, seed, W, R, K, alpha, lam, eps):
+    """drt_field_save: drt_field's field and power bit for bit, and drt_forward_save's
+    visibilities bit for bit (the same obstruction loops); drt_field_vjp_saved:
+    drt_field_vjp's gradient within FP32 rounding, and the oracle's."""
+    rng = np.random.default_rng(seed)
+    sc = scenes.random_small_scene(rng, W, R, K, alpha, "sigmoid", boundary=(seed % 2 == 0))
+    dev = torch.device("cuda:0")
+    w, t, r = (torch.tensor(x, device=dev) for x in (sc.walls, sc.tx, sc.rx))
+    tile = drt.TileConfig(single_rx=True) if single_rx else None
+    E, P, sv = drt.field_save(w, t, r, K, alpha, "sigmoid", lam, eps, tile=tile)
+    E0, P0 = drt.field(w, t, r, K, alpha, "sigmoid", lam, eps, tile=tile)
+    _, sv_power = drt.forward_save(w, t, r, K, alpha, "sigmoid", tile=tile)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(E.cpu().numpy(), E0.cpu().numpy())
+    np.testing.assert_array_equal(P.cpu().numpy(), P0.cpu().numpy())
+    # compare the written slots only (a path's legs beyond its order are not written)
+    order = np.array([0] + [k for k in range(1, K + 1)
+                            for _ in range(W * (W - 1) ** (k - 1))])
+    written = (np.arange(K + 1)[None, :] <= order[:, None])
+    a = sv.cpu().numpy().reshape(-1, K + 1, sc.n_rx)[written]
+    b = sv_power.cpu().numpy().reshape(-1, K + 1, sc.n_rx)[written]
+    np.testing.assert_array_equal(a, b)
+    g = rng.normal(size=sc.n_rx)
+    gp = torch.tensor(g.astype(np.float32), device=dev)
+    gtx_s, gw_s = drt.field_vjp(w, t, r, K, alpha, "sigmoid", lam, eps, E, gp, saved=sv)
+    gtx, gw = drt.field_vjp(w, t, r, K, alpha, "sigmoid", lam, eps, E, gp)
+    torch.cuda.synchronize()
+    both = lambda x, y: np.concatenate([x.cpu().numpy(), y.cpu().numpy().ravel()])
+    got, plain = both(gtx_s, gw_s), both(gtx, gw)
+    np.testing.assert_allclose(got, plain, rtol=1e-4, atol=1e-5 * np.abs(plain).max())
+    ref = oracle_mod.field_gradient(sc.walls, sc.tx, sc.rx, K, alpha, "sigmoid", lam, eps,
+                                    g.astype(np.float32).astype(np.float64), "all", 0.5)
+    _assert_field_grad_close(got, ref, "saved-visibility field gradient vs oracle")
+
+
+def test_field_power_autograd_keeps_the_visibilities(drt, oracle_mod, monkeypatch):
+    from paper_2401_11882_gb300 import ops
+    rng = np.random.default_rng(43)
+    sc = scenes.random_small_scene(rng, 7, 50, 2, 30.0, "sigmoid", boundary=True)
+    dev = torch.device("cuda:0")
+    calls = []
+    real = ops.field_save
+    monkeypatch.setattr(ops, "field_save", lambda *a, **k: calls.append(1) or real(*a, **k))
+    w = torch.tensor(sc.walls, device=dev, requires_grad=True)
+    t = torch.tensor(sc.tx, device=dev, requires_grad=True)
+    r = torch.tensor(sc.rx, device=dev)
+    P = drt.field_power(w, t, r, 2, 30.0, "sigmoid", 0.05, 4.0)
+    g = torch.tensor(rng.normal(size=sc.n_rx).astype(np.float32), device=dev)
+    (P * g).sum().backward()
+    assert len(calls) == 1
+    ref = oracle_mod.field_gradient(sc.walls, sc.tx, sc.rx, 2, 30.0, "sigmoid", 0.05, 4.0,
+                                    g.cpu().numpy().astype(np.float64), "all", 0.5)
+    _assert_field_grad_close(t.grad.cpu().numpy(), ref[:2], "grad_tx")
+    _assert_field_grad_close(w.grad.cpu().numpy().ravel(), ref[2:], "grad_walls")
+
+
+def test_field_saved_visibilities_full_gradient_scene(drt):
+    """128 walls, 128 x 128 receivers, K <= 2 (3.2 GB of visibilities, degenerate legs
+    among them): the adjoint reading them equals the recomputing one within 1e-5 of
+    the largest component."""
+    g = scenes.gradient_scene(alpha=100.0, smoothing="sigmoid")
+    dev = torch.device("cuda:0")
+    w, t, r = (torch.tensor(x, device=dev) for x in (g.walls, g.tx, g.rx))
+    gp = torch.full((g.n_rx,), 1.0 / g.n_rx, device=dev)
+    E, _, sv = drt.field_save(w, t, r, 2, 100.0, "sigmoid", 0.02, 5.0)
+    a = drt.field_vjp(w, t, r, 2, 100.0, "sigmoid", 0.02, 5.0, E, gp, saved=sv)
+    del sv
+    b = drt.field_vjp(w, t, r, 2, 100.0, "sigmoid", 0.02, 5.0, E, gp)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.isfinite(x).all()
+        assert float((x - y).abs().max()) <= 1e-5 * float(y.abs().max())
