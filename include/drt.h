@@ -296,8 +296,9 @@ drt_status drt3_forward(const drt3_scene* scene, const drt_tile* tile, float* po
 /* Transmitter gradient of drt3_forward: grad_tx = sum_r grad_power[r] dP_r / dTX
    (reverse mode with the path recomputed, as drt_vjp; the gradient the antenna
    placement of Sec. VII needs).  grad_power: [n_rx] device; grad_tx: [3] device,
-   overwritten; workspace: at least drt3_vjp_tx_workspace_size bytes (per-warp
-   partials, added in a fixed order: deterministic). */
+   overwritten; workspace: at least drt3_vjp_tx_workspace_size bytes (warps take
+   their units from a counter there; per-unit partials, added in unit order:
+   deterministic). */
 drt_status drt3_vjp_tx_workspace_size(const drt3_scene* scene, const drt_tile* tile,
                                       size_t* bytes);
 drt_status drt3_vjp_tx(const drt3_scene* scene, const drt_tile* tile, const float* grad_power,
