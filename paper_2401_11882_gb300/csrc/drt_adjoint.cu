@@ -2,21 +2,23 @@
 // product  sum_r g_r dP_r / d(tx, walls)  (Sec. III: gradient of the loss with
 // respect to the scene parameters).
 //
-// Nothing of the forward pass is stored: each (receiver, candidate) recomputes
-// its image chain, reflection points, legs and validity, then runs two sweeps
-// over the walls.  Sweep 1 rebuilds each leg's visibility as a product of
-// non-zero factors plus a count of exact zeros, so that the derivative of the
-// product w.r.t. one factor never divides by zero.  Sweep 2 recomputes each
+// Each (receiver, candidate) recomputes its image chain, reflection points, legs
+// and validity, then runs two sweeps over the walls.  Sweep 1 rebuilds each
+// leg's visibility as a product of non-zero factors plus a count of exact zeros,
+// so that the derivative of the product w.r.t. one factor never divides by zero
+// (for the sigmoid the forward can keep these visibilities instead, and the
+// SAVED variants read them in place of sweep 1).  Sweep 2 recomputes each
 // factor and pushes its adjoint into the vertices, the leg normals and the
 // wall.  The vertex and leg adjoints then flow back through the leg lengths,
 // the validity, the backtrace and the image chain to the transmitter.
 //
 // The mapping is the forward's: 32 receivers per warp, one warp-uniform
-// candidate at a time.  Per-wall adjoints are summed over the warp with
-// shuffles (only when a lane has a non-zero one), added into a per-CTA
+// candidate at a time; warps take their units from a counter (work stealing)
+// and store each unit's TX adjoint.  Per-wall adjoints are summed over the warp
+// with shuffles (only when a lane has a non-zero one), added into a per-CTA
 // shared-memory table, and written per CTA; a last kernel adds the CTA tables
-// in a fixed order and chains the per-wall quantities (n, c, t0, len) back to
-// the end points.
+// in a fixed order, adds the units' TX adjoints in unit order, and chains the
+// per-wall quantities (n, c, t0, len) back to the end points.
 #include <cuda_runtime.h>
 
 #include "drt_common.cuh"

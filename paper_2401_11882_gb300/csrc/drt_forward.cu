@@ -5,9 +5,10 @@
 // one path candidate at a time, so the candidate's wall sequence, its TX image
 // chain and every branch are warp-uniform, and the walls are read from shared
 // memory as broadcasts.  A work unit is (32 receivers) x (a chunk of
-// candidates); a persistent grid strides over the units in a fixed order and
-// writes one partial sum per (chunk, receiver), which a second kernel adds up in
-// chunk order.  The result is therefore deterministic.
+// candidates); the warps of a persistent grid take units from a counter (work
+// stealing, next_unit_of) and write one partial sum per (chunk, receiver), which
+// a second kernel adds up in chunk order.  The result is therefore deterministic
+// whichever warp took which unit.
 //
 // Hot loop (obstruction, Sec. V-A with the comparison rule x0 > x1 -> s(x0 - x1)):
 // for every wall, the smoothed side of each path vertex is computed once and
