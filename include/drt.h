@@ -80,7 +80,8 @@ typedef struct {
 /* Work decomposition of the path kernels.  Zero fields take the defaults. */
 typedef struct {
   int32_t warps_per_cta;   /* 1..8 (default 8) */
-  int32_t cands_per_unit;  /* path candidates one warp evaluates per work unit (default 64) */
+  int32_t cands_per_unit;  /* path candidates one warp evaluates per work unit (default 32
+                              for drt_forward and drt_field, 64 for the other kernels) */
   int32_t ctas_per_sm;     /* resident CTAs per SM for the persistent grid (default: occupancy) */
   int32_t flags;           /* DRT_TILE_* bits */
 } drt_tile;
