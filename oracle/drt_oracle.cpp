@@ -28,6 +28,10 @@
 //      ("x and y on opposite sides"),
 //        blocked = X(d_w(Q_j), d_w(Q_{j+1})) * X(m . (A_w - Q_j), m . (B_w - Q_j)),
 //      m the unit normal of the leg; the leg's visibility is prod_w (1 - blocked).
+//      For the sigmoid, where blocked can lie within rounding of 1 (a wall that
+//      blocks a leg at large alpha), 1 - blocked is evaluated as the equal sum
+//      (1 - X1) + X1 (1 - X2) with 1 - X(x, y) = s(x) s(y) + s(-x) s(-y)
+//      (s(z) + s(-z) = 1): non-negative terms, no cancellation.
 //   5. path power (reading of Eq. 7 as incoherent scalar power):
 //        p = Gamma^k * prod_j V_j * prod_j vis_j / L^2,  L = sum of leg lengths;
 //      received power P_r = sum of p over the candidates (Eq. 7's sum over S).
@@ -227,7 +231,17 @@ T obstruction(const std::vector<Wall<T>>& walls, const std::vector<Vec<T>>& Q,
       T y2 = dot(leg_normal[j], sub(w.b, Q[j]));
       T cross2 = smooth(x2, a, kind) * smooth(T(-y2), a, kind) +
                  smooth(T(-x2), a, kind) * smooth(y2, a, kind);
-      vis = vis * (1.0 - cross1 * cross2);
+      if (kind == SIGMOID) {
+        // 1 - cross1 cross2 = (1 - cross1) + cross1 (1 - cross2), each complement
+        // "both on one side" written out
+        T same1 = smooth(x1, a, kind) * smooth(y1, a, kind) +
+                  smooth(T(-x1), a, kind) * smooth(T(-y1), a, kind);
+        T same2 = smooth(x2, a, kind) * smooth(y2, a, kind) +
+                  smooth(T(-x2), a, kind) * smooth(T(-y2), a, kind);
+        vis = vis * (same1 + cross1 * same2);
+      } else {
+        vis = vis * (1.0 - cross1 * cross2);
+      }
     }
     if (rec && j < 7) rec->vis[j] = re(vis);
     visibility = visibility * vis;
@@ -721,6 +735,7 @@ void set_threads(int nthreads) {
 //   triangle its end points lie on: the leg meets that plane only at the end
 //   point): X(x, y) * prod_k s(delta_k(P)), x = d_w(Q_j), y = d_w(Q_{j+1}), P the
 //   intersection of the leg's line with w's plane (no intersection: not blocked);
+//   for the sigmoid 1 - blocked is evaluated without cancellation as in 2D;
 //   path power Gamma^k V vis / L^2 as in 2D;
 //   two consecutive reflections on triangles of one plane (normals parallel and
 //   offsets equal to within 1e-5): a degenerate path (zero-length leg), power 0.
@@ -776,6 +791,17 @@ T inside(const Tri<T>& t, const V3<T>& p, double alpha, int kind) {
   T r = T(1.0);
   for (int k = 0; k < 3; ++k) r *= smooth(edge_dist(t, k, p), alpha, kind);
   return r;
+}
+
+// 1 - inside(t, p) for the sigmoid as the equal sum of non-negative terms
+// s(-d_0) + s(d_0) (s(-d_1) + s(d_1) s(-d_2)), d_k the in-plane edge distances
+// (1 - abc = (1 - a) + a (1 - b) + ab (1 - c), with 1 - s(d) = s(-d)).
+template <class T>
+T outside(const Tri<T>& t, const V3<T>& p, double alpha, int kind) {
+  const T d0 = edge_dist(t, 0, p), d1 = edge_dist(t, 1, p), d2 = edge_dist(t, 2, p);
+  return smooth(T(-d0), alpha, kind) +
+         smooth(d0, alpha, kind) * (smooth(T(-d1), alpha, kind) +
+                                    smooth(d1, alpha, kind) * smooth(T(-d2), alpha, kind));
 }
 
 // Triangles a and b lie in one plane (normals parallel, offsets equal, to 1e-5).
@@ -839,7 +865,15 @@ T path_power3(const std::vector<Tri<T>>& tris, const V3<T>& tx, const V3<T>& rx,
                             smooth(-x, al, kind) * smooth(y, al, kind);
       if (re(x) - re(y) == 0.0) continue;   // the leg's line never meets the plane
       const V3<T> hit = Q[j] + (x / (x - y)) * (Q[j + 1] - Q[j]);
-      visibility *= 1.0 - cross_plane * inside(t, hit, al, kind);
+      if (kind == SIGMOID) {
+        // 1 - cross_plane inside = (1 - cross_plane) + cross_plane (1 - inside),
+        // as in 2D: no cancellation where the triangle all but blocks the leg
+        const T same_plane = smooth(x, al, kind) * smooth(y, al, kind) +
+                             smooth(-x, al, kind) * smooth(-y, al, kind);
+        visibility *= same_plane + cross_plane * outside(t, hit, al, kind);
+      } else {
+        visibility *= 1.0 - cross_plane * inside(t, hit, al, kind);
+      }
     }
   }
   double gk = 1.0;

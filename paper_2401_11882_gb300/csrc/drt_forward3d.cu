@@ -73,6 +73,77 @@ __device__ void stage_tris(const float* __restrict__ tris, int W, SmemTris s) {
   }
 }
 
+// Sigmoid obstruction of every leg by every triangle (the forward's loop; the
+// adjoint keeps its own).  With e = 2^-|z| for the smoothed distances of a leg's
+// end points to the triangle's plane, the straddle term is X = x1 / D1 with
+// Ns = e_j + e_{j+1}, No = 1 + e_j e_{j+1}, D1 = Ns + No and x1 = Ns when both
+// lie on one side, No otherwise (xb1 the other one), as in 2D.  The on-triangle
+// factor at the crossing point is in = 1 / Pin with Pin = prod_k (1 + u_k),
+// u_k = 2^-a_k for the three scaled in-plane edge distances a_k (u_k capped at
+// 2^24, where s < 6e-8 already rounds the product); Pin - 1 is expanded as a sum
+// of products of the u_k.  Then
+//   1 - X in = (xb1 + x1 (1 - in)) / D1,   1 - in = (Pin - 1) / Pin,
+// a sum of non-negative terms: a leg nearly blocked by a triangle keeps its
+// relative accuracy, and one reciprocal gives the three edge factors (four MUFU
+// operations per test and one per vertex, against seven and two for three
+// separate sigmoids).  Numerators and D1 are multiplied up separately and folded
+// into vis every 8 triangles (D1 <= 4).
+template <int K>
+__device__ __forceinline__ void sigmoid_visibility3(const SmemTris& s, int W, const float3* Q,
+                                                    const float4* Pr, float alpha, float* vis) {
+  const float kap = alpha * LOG2E;
+  float vn[K + 1], vd[K + 1];
+#pragma unroll
+  for (int j = 0; j <= K; ++j) vn[j] = vd[j] = 1.f;
+  for (int w0 = 0; w0 < W; w0 += 8) {
+    const int w1 = min(w0 + 8, W);
+    for (int w = w0; w < w1; ++w) {
+      const float4 P = s.P[w], M0 = s.M0[w], M1 = s.M1[w], M2 = s.M2[w];
+      bool cop[K + 2];   // w in the plane of reflection j's triangle (warp-uniform)
+      cop[0] = cop[K + 1] = false;
+#pragma unroll
+      for (int j = 1; j <= K; ++j) {
+        const float nn = fmaf(P.x, Pr[j].x, fmaf(P.y, Pr[j].y, P.z * Pr[j].z));
+        cop[j] = fabsf(nn) >= 1.f - 1e-5f &&
+                 fabsf(fmaf(-nn, Pr[j].w, P.w)) <= 1e-5f * (1.f + fabsf(P.w));
+      }
+      float d[K + 2], ee[K + 2], e0[K + 2], e1[K + 2], e2[K + 2];
+#pragma unroll
+      for (int i = 0; i <= K + 1; ++i) {
+        d[i] = dot3(P, Q[i]) - P.w;
+        ee[i] = ex2_approx(-fabsf(d[i] * kap));
+        e0[i] = (dot3(M0, Q[i]) - M0.w) * kap;
+        e1[i] = (dot3(M1, Q[i]) - M1.w) * kap;
+        e2[i] = (dot3(M2, Q[i]) - M2.w) * kap;
+      }
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        if (cop[j] || cop[j + 1]) continue;
+        const float t = __fdividef(d[j], d[j] - d[j + 1]);
+        // the leg's line misses the plane (or meets it absurdly far): not blocked
+        if (!(fabsf(t) <= 1e8f)) continue;
+        const float ns = ee[j] + ee[j + 1];
+        const float no = fmaf(ee[j], ee[j + 1], 1.f);
+        const bool same = same_side(d[j], d[j + 1]);
+        const float x1 = same ? ns : no, xb1 = same ? no : ns;
+        const float u0 = ex2_approx(fminf(-fmaf(t, e0[j + 1] - e0[j], e0[j]), 24.f));
+        const float u1 = ex2_approx(fminf(-fmaf(t, e1[j + 1] - e1[j], e1[j]), 24.f));
+        const float u2 = ex2_approx(fminf(-fmaf(t, e2[j + 1] - e2[j], e2[j]), 24.f));
+        const float a01 = fmaf(u0, u1, u0 + u1);
+        const float pm1 = fmaf(u2, 1.f + a01, a01);
+        const float omi = pm1 * rcp_approx(1.f + pm1);
+        vn[j] *= fmaf(x1, omi, xb1);
+        vd[j] *= ns + no;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      vis[j] *= __fdividef(vn[j], vd[j]);
+      vn[j] = vd[j] = 1.f;
+    }
+  }
+}
+
 // Power of one candidate of order K for this lane's receiver.
 template <int MODE, int K>
 __device__ __forceinline__ float path_power3(const SmemTris& s, int W, float3 tx, float3 rx,
@@ -146,6 +217,9 @@ __device__ __forceinline__ float path_power3(const SmemTris& s, int W, float3 tx
   float4 Pr[K + 1];
 #pragma unroll
   for (int j = 1; j <= K; ++j) Pr[j] = s.P[cd.w[j - 1]];
+  if constexpr (MODE == MODE_SIGMOID) {
+    sigmoid_visibility3<K>(s, W, Q, Pr, alpha, vis);
+  } else {
   for (int w = 0; w < W; ++w) {
     const float4 P = s.P[w], M0 = s.M0[w], M1 = s.M1[w], M2 = s.M2[w];
     bool cop[K + 2];   // w in the plane of reflection j's triangle (warp-uniform)
@@ -179,6 +253,7 @@ __device__ __forceinline__ float path_power3(const SmemTris& s, int W, float3 tx
                        smooth3<MODE>(fmaf(t, e2[j + 1] - e2[j], e2[j]), alpha).s;
       vis[j] = fmaf(-X, in * vis[j], vis[j]);
     }
+  }
   }
   float p = V * gk;
 #pragma unroll
@@ -255,7 +330,17 @@ __device__ __forceinline__ bool leg_tri(const float4& P, const float4* M, float3
     r.sd[k] = smooth3<MODE>(fmaf(r.t, r.e1[k] - r.e0[k], r.e0[k]), alpha);
     r.ins *= r.sd[k].s;
   }
-  r.f = fmaf(-r.X, r.ins, 1.f);
+  if (MODE == MODE_SIGMOID) {
+    // f = 1 - X ins as sums of non-negative terms (s + sb = 1 for each smoothed
+    // value): 1 - X = s_x s_y + sb_x sb_y and 1 - ins = sb_0 + s_0 (sb_1 + s_1 sb_2),
+    // so f = (1 - X) + X (1 - ins) keeps its relative accuracy where a triangle
+    // nearly blocks the leg (1 - X ins there cancels to a few ulps of 1)
+    const float omx = fmaf(r.sx.s, r.sy.s, r.sx.sb * r.sy.sb);
+    const float omi = fmaf(r.sd[0].s, fmaf(r.sd[1].s, r.sd[2].sb, r.sd[1].sb), r.sd[0].sb);
+    r.f = fmaf(r.X, omi, omx);
+  } else {
+    r.f = fmaf(-r.X, r.ins, 1.f);
+  }
   return true;
 }
 

@@ -228,3 +228,37 @@ def test_work_stealing_keeps_the_tx_gradient_bitwise_on_the_room(drt, tri_grad):
     runs = [_vjp3_full(drt, sc, g, tri_grad=tri_grad) for _ in range(3)]
     for r in runs[1:]:
         np.testing.assert_array_equal(r[0], runs[0][0])
+
+
+def test_room_deep_shadow_sigmoid_at_alpha_1000(drt, oracle_mod):
+    """The receivers the loss cares about: the 12 lowest positive powers of the room
+    (132 triangles, 128 x 128 receivers, K <= 2) with the sigmoid at alpha = 1000,
+    where a triangle that nearly blocks a leg leaves a factor 1 - X in of 1e-8 or
+    less.  Each is held to 1e-4 relative (or 2x its FP32 input sensitivity) with no
+    max-power floor; forming the factor as 1 - X in in FP32 cancelled to nothing
+    there and gave powers off by many orders of magnitude."""
+    sc = scenes.room3d(128, 1000.0, "sigmoid")
+    P = _gpu3(drt, sc)
+    pos = np.nonzero(P > 0)[0]
+    idx = pos[np.argsort(P[pos])[:12]]
+    ref = _ref3(oracle_mod, sc, sc.rx[idx])
+    sens = fp32_sensitivity(lambda w, t, r: oracle_mod.power3(w, t, r, 2, 1000.0, "sigmoid"),
+                            sc.tris, sc.tx, sc.rx[idx])
+    tol = np.maximum(1e-4 * np.abs(ref), 2.0 * sens)
+    err = np.abs(P[idx].astype(np.float64) - ref)
+    assert np.all(err <= tol), (idx[err > tol], P[idx][err > tol], ref[err > tol])
+
+
+def test_room_deep_shadow_sigmoid_tx_gradient(drt, oracle_mod):
+    """The transmitter gradient of those deep-shadow receivers (alpha = 1000, the
+    adjoint's factors formed as sums of non-negative terms) against the oracle's."""
+    sc = scenes.room3d(128, 1000.0, "sigmoid")
+    P = _gpu3(drt, sc)
+    pos = np.nonzero(P > 0)[0]
+    idx = pos[np.argsort(P[pos])[:4]]
+    g = np.zeros(sc.n_rx, np.float32)
+    g[idx] = (1.0 / P[idx]).astype(np.float32)      # weigh each to the same scale
+    got = _vjp3(drt, sc, g)
+    ref = oracle_mod.gradient3_tx(sc.tris, sc.tx, sc.rx[idx], 2, 1000.0, "sigmoid",
+                                  g[idx].astype(np.float64), sc.refl_coef)
+    assert_grad_close(got, ref, "deep-shadow 3D grad_tx")

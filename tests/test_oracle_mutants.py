@@ -19,7 +19,7 @@ PIN_FILES = ["tests/test_oracle_smoothing.py", "tests/test_oracle_candidates.py"
              "tests/test_oracle_geometry.py", "tests/test_oracle_bruteforce.py",
              "tests/test_oracle_gradients.py", "tests/test_oracle_field.py",
              "tests/test_oracle_3d.py", "tests/test_oracle_mpt_finder.py",
-             "tests/test_oracle_fpt_finder.py"]
+             "tests/test_oracle_fpt_finder.py", "tests/test_oracle_deep_shadow.py"]
 
 MUTANTS = {
     "mirror sign": ("return Vec<T>{p.x - 2.0 * d * w.n.x", "return Vec<T>{p.x + 2.0 * d * w.n.x"),
@@ -105,6 +105,15 @@ MUTANTS = {
     "fpt line search takes increases": ("if (length(ft) <= L0 + 1e-4 * t * slope + tol)",
                                         "if (length(ft) >= L0 + 1e-4 * t * slope + tol)"),
     "mpt keeps paths with a vanishing leg": ("if (l < MPT_MIN_LEG) return false;", ""),
+    "sigmoid obstruction formed with cancellation": ("vis = vis * (same1 + cross1 * same2);",
+                                                     "vis = vis * (1.0 - cross1 * cross2);"),
+    "sigmoid same-side complement sign": ("T same2 = smooth(x2, a, kind) * smooth(y2, a, kind) +",
+                                          "T same2 = smooth(x2, a, kind) * smooth(T(-y2), a, kind) +"),
+    "3d sigmoid obstruction formed with cancellation": (
+        "visibility *= same_plane + cross_plane * outside(t, hit, al, kind);",
+        "visibility *= 1.0 - cross_plane * inside(t, hit, al, kind);"),
+    "3d outside drops a term": ("smooth(d1, alpha, kind) * smooth(T(-d2), alpha, kind));",
+                                "T(0.0));"),
     "along from B": ("T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.a)); }",
                      "T along(const Wall<T>& w, const Vec<T>& p) { return dot(w.u, sub(p, w.b)); }"),
 }
