@@ -239,7 +239,7 @@ def test_room_deep_shadow_sigmoid_at_alpha_1000(drt, oracle_mod):
     there and gave powers off by many orders of magnitude."""
     sc = scenes.room3d(128, 1000.0, "sigmoid")
     P = _gpu3(drt, sc)
-    pos = np.nonzero(P > 0)[0]
+    pos = np.nonzero(P > 1e-30)[0]   # FP32 keeps relative accuracy above its normal range
     idx = pos[np.argsort(P[pos])[:12]]
     ref = _ref3(oracle_mod, sc, sc.rx[idx])
     sens = fp32_sensitivity(lambda w, t, r: oracle_mod.power3(w, t, r, 2, 1000.0, "sigmoid"),
@@ -254,7 +254,7 @@ def test_room_deep_shadow_sigmoid_tx_gradient(drt, oracle_mod):
     adjoint's factors formed as sums of non-negative terms) against the oracle's."""
     sc = scenes.room3d(128, 1000.0, "sigmoid")
     P = _gpu3(drt, sc)
-    pos = np.nonzero(P > 0)[0]
+    pos = np.nonzero(P > 1e-30)[0]   # FP32 keeps relative accuracy above its normal range
     idx = pos[np.argsort(P[pos])[:4]]
     g = np.zeros(sc.n_rx, np.float32)
     g[idx] = (1.0 / P[idx]).astype(np.float32)      # weigh each to the same scale

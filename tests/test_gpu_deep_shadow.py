@@ -74,3 +74,25 @@ def test_3d_blocked_line_of_sight_gradient(drt, oracle_mod, alpha):
     assert_grad_close(gtx.cpu().numpy(), ref_tx, "3D blocked line-of-sight grad_tx")
     assert_grad_close(gtr.cpu().numpy().ravel(), ref_tr.ravel(),
                       "3D blocked line-of-sight grad_tris")
+
+
+def test_2d_gradient_scene_deep_shadow_sigmoid_at_alpha_1000(drt, oracle_mod):
+    """128 random segments, 128 x 128 receivers, K <= 2, sigmoid at alpha = 1000: the 12
+    lowest powers above 1e-30 (the receivers the loss cares about; below FP32's normal
+    range, from 1.2e-38, a power has no relative accuracy left and many receivers
+    here sit at 1e-45) against the oracle to 1e-4 relative (or twice their FP32
+    input sensitivity), no max-power floor."""
+    from parity import fp32_sensitivity
+    from paper_2401_11882_gb300 import scenes
+    sc = scenes.gradient_scene(alpha=1000.0, smoothing="sigmoid")
+    P = drt.forward(_t(sc.walls), _t(sc.tx), _t(sc.rx), 2, 1000.0, "sigmoid")
+    torch.cuda.synchronize()
+    P = P.cpu().numpy()
+    pos = np.nonzero(P > 1e-30)[0]
+    idx = pos[np.argsort(P[pos])[:12]]
+    ref = oracle_mod.power(sc.walls, sc.tx, sc.rx[idx], 2, 1000.0, "sigmoid")
+    sens = fp32_sensitivity(lambda w, t, r: oracle_mod.power(w, t, r, 2, 1000.0, "sigmoid"),
+                            sc.walls, sc.tx, sc.rx[idx])
+    tol = np.maximum(1e-4 * np.abs(ref), 2.0 * sens)
+    err = np.abs(P[idx].astype(np.float64) - ref)
+    assert np.all(err <= tol), (idx[err > tol], P[idx][err > tol], ref[err > tol])
