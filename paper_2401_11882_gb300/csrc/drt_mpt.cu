@@ -260,6 +260,7 @@ __device__ __forceinline__ void finder_points(const SmemWalls& s, const Cand& cd
     const float C0 = finder_objective<FINDER, K>(s, cd, f);
     const float tol = MPT_ROUNDING * C0;
     float t = 1.f;
+    bool moved = false;
     for (int m = 0; m < MPT_HALVINGS; ++m, t *= 0.5f) {
       float trial[K > 0 ? K : 1];
 #pragma unroll
@@ -269,11 +270,18 @@ __device__ __forceinline__ void finder_points(const SmemWalls& s, const Cand& cd
       if (ft.degenerate) continue;
       if (finder_objective<FINDER, K>(s, cd, ft) <= fmaf(1e-4f * t, slope, C0) + tol) {
 #pragma unroll
-        for (int q = 0; q < K; ++q) tau[q] = trial[q];
+        for (int q = 0; q < K; ++q) {
+          moved |= !(trial[q] == tau[q]);
+          tau[q] = trial[q];
+        }
         f = ft;
         break;
       }
     }
+    // a step that leaves every tau as it was (no step taken, or one below the
+    // rounding of tau) leaves the whole state as it was: the remaining steps would
+    // repeat it exactly, so the points are final (the result is the same bit for bit)
+    if (!moved) break;
   }
   res.degenerate = dead || f.degenerate;
 #pragma unroll
