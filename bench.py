@@ -364,6 +364,16 @@ def measure_extras(drt, dev, sc, w, t, r):
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
                                   tile=drt.TileConfig(cull_invalid=True)))
     out["hard_forward_culled_evals_per_s"] = ev / s
+    # the exact exit of fully blocked warps (DRT_TILE_EXIT_BLOCKED), alone, with the
+    # cull, and at the other alphas: every (leg, wall) pair is no longer tested, so
+    # these are reported beside the headline, not as it
+    for a_ in (10.0, sc.alpha, 1000.0):
+        s = timed(lambda: drt.forward(w, t, r, sc.max_order, a_, "hard_sigmoid",
+                                      tile=drt.TileConfig(exit_blocked=True)))
+        out[f"hard_forward_exit_blocked_alpha_{a_:g}_evals_per_s"] = ev / s
+    s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
+                                  tile=drt.TileConfig(cull_invalid=True, exit_blocked=True)))
+    out["hard_forward_culled_exit_blocked_evals_per_s"] = ev / s
     s = timed(lambda: drt.forward(w, t, r, sc.max_order, sc.alpha, "hard_sigmoid",
                                   tile=drt.TileConfig(single_rx=True)))
     out["hard_forward_one_rx_per_lane_evals_per_s"] = ev / s

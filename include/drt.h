@@ -98,6 +98,13 @@ typedef struct {
    receiver per lane. */
 #define DRT_TILE_SINGLE_RX 2
 
+/* Hard sigmoid forward of drt_forward with two receivers per lane (the default):
+   every 8 walls the warp leaves its obstruction loop once some leg of each of its
+   64 paths has a visibility of exactly 0, since no later wall can change a power
+   of 0 (exact: the powers are the same, bit for bit).  Ignored by the other kernels
+   and smoothings.  Off by default. */
+#define DRT_TILE_EXIT_BLOCKED 4
+
 /* Human-readable name of a status code (static string). */
 const char* drt_status_string(drt_status status);
 

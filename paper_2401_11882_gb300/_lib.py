@@ -21,6 +21,7 @@ MAX_ORDER = 3
 MAX_WALLS = 1024
 TILE_CULL_INVALID = 1
 TILE_SINGLE_RX = 2
+TILE_EXIT_BLOCKED = 4
 
 
 class Scene(ctypes.Structure):

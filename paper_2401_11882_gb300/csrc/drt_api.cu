@@ -292,6 +292,7 @@ drt_status forward_impl(const drt_scene* scene, const drt_tile* tile, float* pow
   a.n_tiles = d.n_tiles;
   a.n_units = d.n_units;
   a.cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  a.exit_blocked = (tile && (tile->flags & DRT_TILE_EXIT_BLOCKED)) ? 1 : 0;
   a.pairs = d.pairs;
   a.partial = static_cast<float*>(workspace);
   a.power = power;

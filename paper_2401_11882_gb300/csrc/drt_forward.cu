@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(256, MODE == MODE_SIGMOID ? 3 : 4) forward_ker
 // Hard sigmoid and sigmoid, two receivers per lane (tiles of 64 receivers:
 // lane l holds receivers l and l + 32 of its tile); the walls' paired records
 // follow the four single-receiver arrays in shared memory.
-template <int MODE, bool GLOBAL = false, bool SAVE = false>
+// EXIT (hard sigmoid): the obstruction loop's exit for warps whose 64 paths are
+// all blocked (DRT_TILE_EXIT_BLOCKED).
+template <int MODE, bool GLOBAL = false, bool SAVE = false, bool EXIT = false>
 __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
   extern __shared__ float4 smem[];
   float4* base = GLOBAL ? a.staged : smem;
@@ -131,10 +133,10 @@ __global__ void __launch_bounds__(256, 2) forward_pair_kernel(const FwdArgs a) {
         for (int j = 0; j <= KMAX; ++j) vbuf[j] = make_float2(0.f, 0.f);
       }
       switch (cd.k) {
-        case 0: p = path_power_pair<MODE, 0>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], a.cull, vo); break;
-        case 1: p = path_power_pair<MODE, 1>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], a.cull, vo); break;
-        case 2: p = path_power_pair<MODE, 2>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], a.cull, vo); break;
-        default: p = path_power_pair<MODE, 3>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], a.cull, vo); break;
+        case 0: p = path_power_pair<MODE, 0, EXIT>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[0], a.cull, vo); break;
+        case 1: p = path_power_pair<MODE, 1, EXIT>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[1], a.cull, vo); break;
+        case 2: p = path_power_pair<MODE, 2, EXIT>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[2], a.cull, vo); break;
+        default: p = path_power_pair<MODE, 3, EXIT>(s, pr, a.W, tx, q0, q1, cd, a.alpha, a.gk[3], a.cull, vo); break;
       }
       acc0 += p.x;
       acc1 += p.y;
@@ -267,6 +269,8 @@ cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cu
       if (a.pairs) {
         if (mode == MODE_SIGMOID)
           forward_pair_kernel<MODE_SIGMOID, true><<<ctas, threads, 0, st>>>(a);
+        else if (a.exit_blocked)
+          forward_pair_kernel<MODE_HARD, true, false, true><<<ctas, threads, 0, st>>>(a);
         else
           forward_pair_kernel<MODE_HARD, true><<<ctas, threads, 0, st>>>(a);
       } else {
@@ -292,6 +296,8 @@ cudaError_t launch_forward(const FwdArgs& a, int mode, int ctas, int threads, cu
   } else if (a.n_units > 0 && a.pairs) {
     if (mode == MODE_SIGMOID)
       forward_pair_kernel<MODE_SIGMOID><<<ctas, threads, smem, st>>>(a);
+    else if (a.exit_blocked)
+      forward_pair_kernel<MODE_HARD, false, false, true><<<ctas, threads, smem, st>>>(a);
     else
       forward_pair_kernel<MODE_HARD><<<ctas, threads, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -364,6 +370,9 @@ cudaError_t forward_set_smem_limit(int W) {
   cudaError_t e;
   const int psmem = (int)forward_smem_bytes(W, true);
   e = cudaFuncSetAttribute(forward_pair_kernel<MODE_HARD>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(forward_pair_kernel<MODE_HARD, false, false, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(forward_pair_kernel<MODE_SIGMOID>,

@@ -35,6 +35,7 @@ struct FwdArgs {
   int chunk;
   long long n_chunks, n_tiles, n_units;
   int cull;
+  int exit_blocked;   // hard sigmoid, pairs: leave the wall loop of fully blocked warps
   bool pairs;       // two receivers per lane (n_tiles counts 64-receiver tiles)
   float* partial;   // [n_chunks][R]
   float* power;     // [R]

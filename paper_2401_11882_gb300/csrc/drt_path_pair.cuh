@@ -56,7 +56,11 @@ __device__ __forceinline__ void same_side2(float2 a, float2 b, bool& sx, bool& s
 
 // Hard sigmoid: visibility of each leg of both receivers' paths, every wall
 // tested (the skipped pairs are divided out by the caller).
-template <int K>
+// EXIT: once some leg of each of the warp's 64 paths has a visibility of exactly 0
+// (a wall the hard sigmoid saturates to a full block), every power is 0 whatever
+// the remaining walls do (0 stays 0 under each factor), so the warp leaves the
+// wall loop; checked every 8 walls.
+template <int K, bool EXIT = false>
 __device__ __forceinline__ void hard_visibility_pair(const SmemWalls& s, const SmemPairs& p, int W,
                                                      const float2* Qx, const float2* Qy,
                                                      const float2* mx, const float2* my,
@@ -66,6 +70,15 @@ __device__ __forceinline__ void hard_visibility_pair(const SmemWalls& s, const S
   for (int j = 0; j <= K; ++j) vis[j] = one;
 #pragma unroll 2
   for (int w = 0; w < W; ++w) {
+    if (EXIT && (w & 7) == 0 && w > 0) {
+      bool z0 = false, z1 = false;
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        z0 |= vis[j].x == 0.f;
+        z1 |= vis[j].y == 0.f;
+      }
+      if (__all_sync(0xffffffffu, z0 && z1)) break;
+    }
     const float4 A = p.A[w], B = p.B[w], C = p.C[w];
     const float hx = s.H[w].x;
     const float2 hy = f2(A.x, A.y), hz = f2(A.z, A.w);
@@ -160,7 +173,7 @@ __device__ __forceinline__ void sigmoid_visibility_pair(const SmemWalls& s, cons
 }
 
 // Powers of one path candidate of order K for the receivers rx0 and rx1.
-template <int MODE, int K>
+template <int MODE, int K, bool EXIT = false>
 __device__ __forceinline__ float2 path_power_pair(const SmemWalls& s, const SmemPairs& p, int W,
                                                   float2 tx, float2 rx0, float2 rx1, const Cand& cd,
                                                   float alpha, float gk, int cull,
@@ -186,7 +199,7 @@ __device__ __forceinline__ float2 path_power_pair(const SmemWalls& s, const Smem
     mc[j] = f2(g0.mc[j], g1.mc[j]);
   }
   if (MODE == MODE_HARD)
-    hard_visibility_pair<K>(s, p, W, Qx, Qy, mx, my, mc, vis2);
+    hard_visibility_pair<K, EXIT>(s, p, W, Qx, Qy, mx, my, mc, vis2);
   else
     sigmoid_visibility_pair<K>(s, p, W, Qx, Qy, mx, my, mc, vis2);
   float vis0[K + 1], vis1[K + 1];

@@ -24,10 +24,12 @@ class TileConfig:
     ctas_per_sm: int = 0
     cull_invalid: bool = False
     single_rx: bool = False   # (hard) sigmoid forward: one receiver per lane instead of two
+    exit_blocked: bool = False   # hard sigmoid forward: leave the wall loop of blocked warps
 
     def as_c(self) -> _lib.Tile:
         flags = ((_lib.TILE_CULL_INVALID if self.cull_invalid else 0)
-                 | (_lib.TILE_SINGLE_RX if self.single_rx else 0))
+                 | (_lib.TILE_SINGLE_RX if self.single_rx else 0)
+                 | (_lib.TILE_EXIT_BLOCKED if self.exit_blocked else 0))
         return _lib.Tile(self.warps_per_cta, self.cands_per_unit, self.ctas_per_sm, flags)
 
 

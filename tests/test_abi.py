@@ -42,6 +42,19 @@ def test_binding_covers_every_declared_symbol():
     assert _declared() <= set(_lib.SIGNATURES), sorted(_declared() - set(_lib.SIGNATURES))
 
 
+def test_binding_constants_match_the_header():
+    """The binding's copies of the header's #define values (tile flags, limits)."""
+    from paper_2401_11882_gb300 import _lib
+    text = "".join(open(h).read() for h in HEADERS)
+    defs = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"^#define\s+DRT_(\w+)\s+(\d+)\b", text, re.M)}
+    for name in ("TILE_CULL_INVALID", "TILE_SINGLE_RX", "TILE_EXIT_BLOCKED", "MAX_ORDER",
+                 "MAX_WALLS"):
+        assert defs[name] == getattr(_lib, name), name
+    flags = [v for k, v in defs.items() if k.startswith("TILE_")]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
+
+
 def test_num_candidates_host_only(lib):
     out = ctypes.c_int64()
     assert lib.drt_num_candidates(64, 2, ctypes.byref(out)) == 0 and out.value == 4097

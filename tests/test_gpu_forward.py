@@ -380,3 +380,66 @@ def test_work_stealing_matches_the_static_split_bitwise(drt, smoothing):
     assert buf[1:].data_ptr() % 8 == 4
     torch.cuda.synchronize()
     np.testing.assert_array_equal(stolen.cpu().numpy(), static.cpu().numpy())
+
+
+EXIT_CASES = [
+    # (seed, n_seg, grid, K, alpha): clutter scenes (square + n_seg segments) with
+    # enough walls to block most paths; grids whose receiver counts leave ragged
+    # 64-receiver tiles
+    (40, 12, 9, 2, 1000.0),
+    (41, 30, 13, 2, 100.0),
+    (42, 60, 23, 2, 1e4),
+    (43, 120, 11, 1, 300.0),
+    (44, 28, 7, 3, 100.0),
+    (45, 60, 17, 2, 10.0),
+    (46, 60, 16, 2, 0.0),
+]
+
+
+@pytest.mark.parametrize("seed,n_seg,grid,K,alpha", EXIT_CASES)
+def test_exit_blocked_option_is_exact(drt, seed, n_seg, grid, K, alpha):
+    """DRT_TILE_EXIT_BLOCKED leaves the hard-sigmoid wall loop of a warp once every
+    path of it has a leg of visibility 0: the powers are the same bit for bit, with
+    and without the invalid-path cull and under another chunking."""
+    sc = scenes.clutter_scene(n_seg, grid, seed=seed, alpha=alpha, smoothing="hard_sigmoid",
+                              max_order=K, boundary=True)
+    a = _run(drt, sc)
+    b = _run(drt, sc, drt.TileConfig(exit_blocked=True))
+    np.testing.assert_array_equal(a, b)
+    c = _run(drt, sc, drt.TileConfig(warps_per_cta=3, cands_per_unit=5, cull_invalid=True))
+    d = _run(drt, sc, drt.TileConfig(warps_per_cta=3, cands_per_unit=5, cull_invalid=True,
+                                     exit_blocked=True))
+    np.testing.assert_array_equal(c, d)
+
+
+@pytest.mark.parametrize("alpha", [10.0, 100.0, 1000.0])
+def test_exit_blocked_option_is_exact_on_benchmark_scene(drt, alpha):
+    # full benchmark launch (64 walls, 65536 receivers, 4097 sequences)
+    sc = scenes.large_scene(alpha=alpha, smoothing="hard_sigmoid")
+    a = _run(drt, sc)
+    np.testing.assert_array_equal(a, _run(drt, sc, drt.TileConfig(exit_blocked=True)))
+    np.testing.assert_array_equal(_run(drt, sc, drt.TileConfig(cull_invalid=True)),
+                                  _run(drt, sc, drt.TileConfig(cull_invalid=True,
+                                                               exit_blocked=True)))
+
+
+def test_exit_blocked_option_with_streamed_walls(drt):
+    # 4096 walls (records staged in the workspace): most legs are blocked early
+    rng = np.random.default_rng(47)
+    rx = rng.uniform(0.05, 0.95, (300, 2)).astype(np.float32)
+    sc = scenes.clutter_scene(4092, 1, seed=47, alpha=100.0, smoothing="hard_sigmoid",
+                              max_order=1, boundary=True, rx=rx)
+    a = _run(drt, sc)
+    np.testing.assert_array_equal(a, _run(drt, sc, drt.TileConfig(exit_blocked=True)))
+
+
+@pytest.mark.parametrize("smoothing,alpha,single_rx", [("sigmoid", 100.0, False),
+                                                       ("step", 1.0, False),
+                                                       ("hard_sigmoid", 100.0, True),
+                                                       ("hard_sigmoid", 2e4, False)])
+def test_exit_blocked_option_is_ignored_elsewhere(drt, smoothing, alpha, single_rx):
+    # the flag only changes the paired hard-sigmoid kernel
+    sc = scenes.clutter_scene(40, 12, seed=48, alpha=alpha, smoothing=smoothing, max_order=2)
+    a = _run(drt, sc, drt.TileConfig(single_rx=single_rx))
+    b = _run(drt, sc, drt.TileConfig(single_rx=single_rx, exit_blocked=True))
+    np.testing.assert_array_equal(a, b)
