@@ -459,11 +459,19 @@ def measure_extras(drt, dev, sc, w, t, r):
     bflops = sum(full.tx0.shape[1] * workload.forward_work(
         int(full.wall_off[i + 1] - full.wall_off[i]), int(full.max_order[i]),
         int(full.rx_off[i + 1] - full.rx_off[i]))["flops"] for i in range(full.n_scenes))
+    # the same steps with the exact invalid-path skip and blocked-warp exit (the
+    # skipped work is not done: reported beside the literal step)
+    bdx = BatchedDescent(full, history=0,
+                         tile=drt.TileConfig(cull_invalid=True, exit_blocked=True))
+    bdx.run(1)
+    torch.cuda.synchronize(dev)
+    bsx = timed(lambda: bdx.run(1), 2)
     out["batched_descent_64_scenes"] = {
         "workload": "first 64 scenes of the 4096-scene batch (W 8-256, R 64-4096, K 0-2), 4 starts "
                     "each, alpha=100, hard sigmoid; one step = forward + argmin + adjoint + Adam",
         "ms_per_step": bs * 1e3, "steps_per_s": 1.0 / bs,
-        "forward_tflops_by_convention": bflops / bs / 1e12}
+        "forward_tflops_by_convention": bflops / bs / 1e12,
+        "exact_skip_and_blocked_exit_ms_per_step": bsx * 1e3}
     # batched descent on 3D rooms (Sec. VI): 64 rooms of 16-72 triangles, R 16-512,
     # K 0-2, 4 starts each, alpha 100, hard sigmoid
     full3 = scenes.scene_batch3(64, 0)
@@ -481,6 +489,7 @@ def measure_extras(drt, dev, sc, w, t, r):
         "ms_per_step": bs3 * 1e3, "steps_per_s": 1.0 / bs3, "evals_per_s": ev3 / bs3}
     bd3.close()
     bd.close()
+    bdx.close()
     # surrogate MLP (tcgen05 path), batch 8192
     from paper_2401_11882_gb300.surrogate import SurrogateMLP
     m = SurrogateMLP(dev, batch=8192)

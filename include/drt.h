@@ -98,7 +98,8 @@ typedef struct {
    receiver per lane. */
 #define DRT_TILE_SINGLE_RX 2
 
-/* Hard sigmoid forward of drt_forward with two receivers per lane (the default):
+/* Hard sigmoid forward of drt_forward and of the 2D batched descent, with two
+   receivers per lane (the default):
    every 8 walls the warp leaves its obstruction loop once some leg of each of its
    64 paths has a visibility of exactly 0, since no later wall can change a power
    of 0 (exact: the powers are the same, bit for bit).  Ignored by the other kernels
@@ -490,8 +491,9 @@ typedef struct drt_batch_plan drt_batch_plan;
 
 /* Plans the work of a batch (host memory only): validates the host copies of
    the offsets, orders the forward work longest first, sizes the workspace.
-   tile: warps_per_cta (1..8), ctas_per_sm and the DRT_TILE_CULL_INVALID flag
-   are used; NULL for defaults.
+   tile: warps_per_cta (1..8), ctas_per_sm and the DRT_TILE_CULL_INVALID,
+   DRT_TILE_SINGLE_RX and DRT_TILE_EXIT_BLOCKED flags (the last two for 2D
+   batches) are used; NULL for defaults.
    *plan receives a handle owned by the caller (drt_batch_plan_destroy). */
 drt_status drt_batch_plan_create(const drt_batch* batch, const drt_tile* tile,
                                  drt_batch_plan** plan);

@@ -106,7 +106,7 @@ __device__ __forceinline__ float batch_path_power(const SmemWalls& sw, int W, fl
                 : path_power<MODE, K>(sw, W, txy, q, cd, alpha, gk, cull);
 }
 
-template <int MODE, int K>
+template <int MODE, int K, bool EXIT>
 __device__ __forceinline__ float2 batch_path_power2(const SmemWalls& sw, const SmemPairs& pr, int W,
                                                     float2 txy, float2 q0, float2 q1,
                                                     const Cand& cd, float alpha, float gk,
@@ -114,11 +114,13 @@ __device__ __forceinline__ float2 batch_path_power2(const SmemWalls& sw, const S
   if (masked)   // alpha above the packed loop's range: one receiver at a time, masked
     return make_float2(path_power<MODE, K, true>(sw, W, txy, q0, cd, alpha, gk, cull),
                        path_power<MODE, K, true>(sw, W, txy, q1, cd, alpha, gk, cull));
-  return path_power_pair<MODE, K>(sw, pr, W, txy, q0, q1, cd, alpha, gk, cull);
+  return path_power_pair<MODE, K, EXIT>(sw, pr, W, txy, q0, q1, cd, alpha, gk, cull);
 }
 
 // PAIRS: lane l holds receivers l and l + 32 of a 64-receiver tile.
-template <int MODE, bool PAIRS>
+// EXIT (hard sigmoid, PAIRS): the exact exit of warps whose paths are all blocked
+// (DRT_TILE_EXIT_BLOCKED).
+template <int MODE, bool PAIRS, bool EXIT = false>
 __global__ void __launch_bounds__(256, PAIRS ? 2 : 1) batch_forward_kernel(const BatchArgs a) {
   extern __shared__ float4 smem[];
   __shared__ long long s_unit;
@@ -171,10 +173,10 @@ __global__ void __launch_bounds__(256, PAIRS ? 2 : 1) batch_forward_kernel(const
       if (PAIRS) {
         float2 pp;
         switch (cd.k) {
-          case 0: pp = batch_path_power2<MODE, 0>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[0], a.cull, masked); break;
-          case 1: pp = batch_path_power2<MODE, 1>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[1], a.cull, masked); break;
-          case 2: pp = batch_path_power2<MODE, 2>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[2], a.cull, masked); break;
-          default: pp = batch_path_power2<MODE, 3>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[3], a.cull, masked); break;
+          case 0: pp = batch_path_power2<MODE, 0, EXIT>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[0], a.cull, masked); break;
+          case 1: pp = batch_path_power2<MODE, 1, EXIT>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[1], a.cull, masked); break;
+          case 2: pp = batch_path_power2<MODE, 2, EXIT>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[2], a.cull, masked); break;
+          default: pp = batch_path_power2<MODE, 3, EXIT>(sw, pr, W, txy, q0, q1, cd, alpha, a.gk[3], a.cull, masked); break;
         }
         acc0 += pp.x;
         acc1 += pp.y;
@@ -370,7 +372,7 @@ struct BatchPlan {
   std::vector<int32_t> fwd_prob, fwd_unit;
   std::vector<long long> fwd_prefix, adj_prefix, pw_off;
   long long n_fwd_units = 0, n_adj_units = 0, n_power = 0;
-  int ctas_fwd = 1, ctas_adj = 1, per_sm_req = 0, cull = 0;
+  int ctas_fwd = 1, ctas_adj = 1, per_sm_req = 0, cull = 0, exit_blocked = 0;
   bool pairs = false;   // forward with two receivers per lane (64-receiver tiles)
   size_t off_funit = 0;
   size_t off_counter = 0, off_prob = 0, off_fprefix = 0, off_aprefix = 0, off_pwoff = 0,
@@ -416,6 +418,7 @@ cudaError_t set_smem_limits(int Wmax) {
   if (e != cudaSuccess) return e;
   DRT_B((batch_forward_kernel<MODE_SIGMOID, true>), s1)
   DRT_B((batch_forward_kernel<MODE_HARD, true>), s1)
+  DRT_B((batch_forward_kernel<MODE_HARD, true, true>), s1)
   DRT_B((batch_forward_kernel<MODE_SIGMOID, false>), s1)
   DRT_B((batch_forward_kernel<MODE_HARD, false>), s1)
   DRT_B((batch_forward_kernel<MODE_STEP, false>), s1)
@@ -430,6 +433,8 @@ void launch_batch_forward(BatchPlan* pl, size_t sf, cudaStream_t st) {
   const BatchArgs& a = pl->args;
   if (pl->pairs && pl->mode == MODE_SIGMOID)
     batch_forward_kernel<MODE_SIGMOID, true><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
+  else if (pl->pairs && pl->exit_blocked)
+    batch_forward_kernel<MODE_HARD, true, true><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
   else if (pl->pairs)
     batch_forward_kernel<MODE_HARD, true><<<pl->ctas_fwd, pl->threads, sf, st>>>(a);
   else if (pl->mode == MODE_SIGMOID)
@@ -505,6 +510,7 @@ drt_status batch_plan_create(const drt_batch* b, const drt_tile* tile, BatchPlan
   pl->threads = pl->warps * 32;
   pl->per_sm_req = tile ? tile->ctas_per_sm : 0;
   pl->cull = (tile && (tile->flags & DRT_TILE_CULL_INVALID)) ? 1 : 0;
+  pl->exit_blocked = (tile && (tile->flags & DRT_TILE_EXIT_BLOCKED)) ? 1 : 0;
   pl->pairs = pl->dim == 2 && (pl->mode == MODE_HARD || pl->mode == MODE_SIGMOID) &&
               !(tile && (tile->flags & DRT_TILE_SINGLE_RX));
   std::vector<double> cost(pl->P);

@@ -243,10 +243,13 @@ def batch_tile_study(n_scenes=4096, tune_scenes=64, timed_steps=1, seed=0, devic
     """The batch autotuner on the 4096-scene batch: autotune.tune_batch times every
     candidate tile (warps per CTA x CTAs per SM) on the first tune_scenes scenes; the
     full batch is then timed with the library's default tile, with the tuned tile,
-    and with the tuned tile plus the exact invalid-path skip (DRT_TILE_CULL_INVALID:
+    with the tuned tile plus the exact invalid-path skip (DRT_TILE_CULL_INVALID:
     warps whose paths all have hard-sigmoid validity exactly 0 skip the obstruction
     loop; the losses are unchanged bit for bit, but the step no longer does the
-    literal work the FLOP convention counts, so its rate is reported apart)."""
+    literal work the FLOP convention counts, so its rate is reported apart), and
+    with the exact blocked-warp exit (DRT_TILE_EXIT_BLOCKED: a warp whose paths all
+    have a leg of visibility exactly 0 leaves the wall loop), alone and with the
+    skip, reported apart for the same reason."""
     from dataclasses import asdict, replace
     from . import autotune, workload
     full = scenes.scene_batch(n_scenes, seed, smoothing=smoothing)
@@ -270,6 +273,12 @@ def batch_tile_study(n_scenes=4096, tune_scenes=64, timed_steps=1, seed=0, devic
                             tile=replace(best, cull_invalid=True))
     skip.pop("tflops_by_convention")   # the skipped paths are not computed
     out["tuned_tile_exact_skip"] = skip
+    for key, t in (("tuned_tile_blocked_exit", replace(best, exit_blocked=True)),
+                   ("tuned_tile_exact_skip_blocked_exit",
+                    replace(best, cull_invalid=True, exit_blocked=True))):
+        r = _time_full_batch(full, timed_steps, fl, evals, dev, tile=t)
+        r.pop("tflops_by_convention")
+        out[key] = r
     return out
 
 

@@ -231,3 +231,25 @@ def test_exact_skip_gives_the_same_descent(drt):
     np.testing.assert_array_equal(a.tx.cpu().numpy(), b.tx.cpu().numpy())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("alpha", [100.0, 1000.0])
+def test_blocked_warp_exit_gives_the_same_descent(drt, alpha):
+    # DRT_TILE_EXIT_BLOCKED: a warp whose 64 paths all have a leg of hard-sigmoid
+    # visibility exactly 0 leaves the wall loop; those powers are 0 either way.
+    # W up to 60, so that the exit's check (every 8 walls) runs
+    from paper_2401_11882_gb300.batched import BatchedDescent
+    batch = scenes.scene_batch(8, 7, walls_range=(9, 60), rx_range=(33, 150), orders=(0, 1, 2),
+                               n_tx=3, alpha=alpha, smoothing="hard_sigmoid")
+    runs = []
+    for tile in (None, drt.TileConfig(exit_blocked=True),
+                 drt.TileConfig(cull_invalid=True), drt.TileConfig(cull_invalid=True,
+                                                                   exit_blocked=True)):
+        d = BatchedDescent(batch, history=3, tile=tile, alpha=alpha)
+        d.run(3)
+        torch.cuda.synchronize()
+        runs.append((d.history.cpu().numpy(), d.tx.cpu().numpy()))
+        d.close()
+    for h, tx in runs[1:]:
+        np.testing.assert_array_equal(runs[0][0], h)
+        np.testing.assert_array_equal(runs[0][1], tx)
