@@ -393,6 +393,9 @@ EXIT_CASES = [
     (44, 28, 7, 3, 100.0),
     (45, 60, 17, 2, 10.0),
     (46, 60, 16, 2, 0.0),
+    (49, 4, 1, 2, 1000.0),    # 8 walls (the loop ends before its first check), 1 receiver
+    (50, 5, 3, 3, 1000.0),    # 9 walls: one check, at the last wall
+    (51, 12, 8, 2, 1000.0),   # exactly one 64-receiver tile
 ]
 
 
@@ -410,6 +413,10 @@ def test_exit_blocked_option_is_exact(drt, seed, n_seg, grid, K, alpha):
     d = _run(drt, sc, drt.TileConfig(warps_per_cta=3, cands_per_unit=5, cull_invalid=True,
                                      exit_blocked=True))
     np.testing.assert_array_equal(c, d)
+    # one candidate per unit, one warp per CTA
+    e = _run(drt, sc, drt.TileConfig(warps_per_cta=1, cands_per_unit=1))
+    f = _run(drt, sc, drt.TileConfig(warps_per_cta=1, cands_per_unit=1, exit_blocked=True))
+    np.testing.assert_array_equal(e, f)
 
 
 @pytest.mark.parametrize("alpha", [10.0, 100.0, 1000.0])
