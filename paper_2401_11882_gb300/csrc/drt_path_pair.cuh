@@ -59,7 +59,8 @@ __device__ __forceinline__ void same_side2(float2 a, float2 b, bool& sx, bool& s
 // EXIT: once some leg of each of the warp's 64 paths has a visibility of exactly 0
 // (a wall the hard sigmoid saturates to a full block), every power is 0 whatever
 // the remaining walls do (0 stays 0 under each factor), so the warp leaves the
-// wall loop; checked every 8 walls.
+// wall loop; checked between blocks of 8 walls (a block has no exit inside, so it
+// keeps the plain loop's schedule).
 template <int K, bool EXIT = false>
 __device__ __forceinline__ void hard_visibility_pair(const SmemWalls& s, const SmemPairs& p, int W,
                                                      const float2* Qx, const float2* Qy,
@@ -68,17 +69,7 @@ __device__ __forceinline__ void hard_visibility_pair(const SmemWalls& s, const S
   const float2 one = f2(1.f, 1.f), m2 = f2(-2.f, -2.f);
 #pragma unroll
   for (int j = 0; j <= K; ++j) vis[j] = one;
-#pragma unroll 2
-  for (int w = 0; w < W; ++w) {
-    if (EXIT && (w & 7) == 0 && w > 0) {
-      bool z0 = false, z1 = false;
-#pragma unroll
-      for (int j = 0; j <= K; ++j) {
-        z0 |= vis[j].x == 0.f;
-        z1 |= vis[j].y == 0.f;
-      }
-      if (__all_sync(0xffffffffu, z0 && z1)) break;
-    }
+  auto wall = [&](int w) {
     const float4 A = p.A[w], B = p.B[w], C = p.C[w];
     const float hx = s.H[w].x;
     const float2 hy = f2(A.x, A.y), hz = f2(A.z, A.w);
@@ -103,6 +94,25 @@ __device__ __forceinline__ void hard_visibility_pair(const SmemWalls& s, const S
       const float2 x1 = (j == 0) ? fma2(sv[0], uv[1], sv[1]) : fma2(sv[j + 1], uv[j], sv[j]);
       vis[j] = fma2(f2(-vis[j].x, -vis[j].y), mul2(x1, x2), vis[j]);
     }
+  };
+  if (!EXIT) {
+#pragma unroll 2
+    for (int w = 0; w < W; ++w) wall(w);
+    return;
+  }
+  for (int w0 = 0; w0 < W; w0 += 8) {
+    if (w0 > 0) {
+      bool z0 = false, z1 = false;
+#pragma unroll
+      for (int j = 0; j <= K; ++j) {
+        z0 |= vis[j].x == 0.f;
+        z1 |= vis[j].y == 0.f;
+      }
+      if (__all_sync(0xffffffffu, z0 && z1)) break;
+    }
+    const int we = min(w0 + 8, W);
+#pragma unroll 2
+    for (int w = w0; w < we; ++w) wall(w);
   }
 }
 
